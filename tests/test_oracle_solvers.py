@@ -1,0 +1,202 @@
+"""Pins of the oracle's perturbation bases (Eq. 4-5), local updates (Eq. 3, 7,
+9-12) and solvers against brute force, closed forms and the paper's claims."""
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import fem, material, solvers, subspace, topology
+
+
+def _setup(n=3, kind="snh", nu=0.3, factor=1.05, jit=0.05, seed=1):
+    sc = meshgen.stretch_box(n, n, n, E=1e5, nu=nu, factor=factor, jitter_amount=jit, seed=seed)
+    pb = fem.problem_from_scene(sc, kind)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    return sc, pb, topo
+
+
+def _state(sc, amp=0.01, seed=3):
+    d = meshgen.normal(seed, np.arange(3 * sc.n)).reshape(-1, 3) * amp
+    return sc.x0 + d * (sc.pinned == 0)[:, None]
+
+
+def test_global_basis_two_constructions_agree():
+    sc, pb, topo = _setup()
+    H = pb.hessian(sc.X)
+    for i in np.flatnonzero(pb.free)[:4]:
+        S1, U1 = subspace.global_basis(pb, H, int(i))
+        S2, U2 = subspace.global_basis_inverse(pb, H, int(i))
+        np.testing.assert_array_equal(S1, S2)
+        np.testing.assert_allclose(U1, U2, rtol=0, atol=1e-10 * np.abs(U1).max())
+
+
+def test_basis_solves_block_system_with_zero_complementary_force():
+    """Eq. 4: [H_ii H_iC; H_Ci H_CC][I; U] = [df; 0], and df = (W_ii)^{-1}."""
+    sc, pb, topo = _setup()
+    H = pb.hessian(sc.X).toarray()
+    F = np.flatnonzero(pb.free)
+    Fd = subspace.dofs(F)
+    W = np.linalg.inv(H[np.ix_(Fd, Fd)])
+    for p, i in enumerate(F[:3]):
+        S, U = subspace.global_basis(pb, pb.hessian(sc.X), int(i))
+        I, C = subspace.dofs([i]), subspace.dofs(S)
+        Uf = U.reshape(-1, 3)
+        lower = H[np.ix_(C, I)] + H[np.ix_(C, C)] @ Uf
+        assert np.abs(lower).max() <= 1e-9 * np.abs(H).max()
+        df = H[np.ix_(I, I)] + H[np.ix_(I, C)] @ Uf
+        np.testing.assert_allclose(df, np.linalg.inv(W[3 * p:3 * p + 3, 3 * p:3 * p + 3]), rtol=1e-8)
+
+
+def test_local_basis_residual_and_full_ring_equals_global():
+    sc, pb, topo = _setup(n=2)
+    H = pb.hessian(sc.X)
+    sup, bases = subspace.build_local_bases(pb, topo, k=6)   # k >= diameter: whole mesh
+    for i in np.flatnonzero(pb.free):
+        S, U = subspace.global_basis(pb, H, int(i))
+        np.testing.assert_array_equal(sup[i], S)
+        np.testing.assert_allclose(bases[i], U, rtol=0, atol=1e-10 * max(1.0, np.abs(U).max()))
+    sup2, bases2 = subspace.build_local_bases(pb, topo, k=1)
+    for i in np.flatnonzero(pb.free):
+        P = subspace.dofs(sup2[i])
+        if len(P):
+            r = H[P][:, P].toarray() @ bases2[i].reshape(-1, 3) + H[P][:, subspace.dofs([i])].toarray()
+            assert np.abs(r).max() <= 1e-9 * abs(H).max()
+
+
+def test_cc_update_is_first_block_of_the_reduced_block_system():
+    """Eq. 9-12 against a direct solve of Eq. 10 with an explicit dense B_i."""
+    sc, pb, topo = _setup(n=3, factor=1.2)
+    x = _state(sc, 0.02)
+    sup, bases = subspace.build_local_bases(pb, topo, 1)
+    H = pb.hessian(x).toarray()
+    g = pb.gradient(x)
+    Hs = pb.hessian(x)
+    for i in np.flatnonzero(pb.free)[::3]:
+        B = np.zeros((3 * pb.n, 6))
+        B[3 * i:3 * i + 3, :3] = np.eye(3)
+        for s, j in enumerate(sup[i]):
+            B[3 * j:3 * j + 3, 3:] = bases[i][s]
+        q = np.linalg.solve(B.T @ H @ B, -B.T @ g.ravel())
+        dx = solvers.local_update("cc", Hs, g, int(i), sup[i], bases[i])
+        np.testing.assert_allclose(dx, q[:3], rtol=1e-9, atol=1e-14)
+
+
+def test_jgs2_and_cd_updates_match_their_formulas():
+    sc, pb, topo = _setup(n=3, factor=1.2)
+    x = _state(sc, 0.02)
+    sup, bases = subspace.build_local_bases(pb, topo, 1)
+    H = pb.hessian(x).toarray()
+    g = pb.gradient(x)
+    for i in np.flatnonzero(pb.free)[::4]:
+        I, P = subspace.dofs([i]), subspace.dofs(sup[i])
+        Uf = bases[i].reshape(-1, 3)
+        M = H[np.ix_(I, I)] + Uf.T @ H[np.ix_(P, P)] @ Uf
+        rhs = g[i] + Uf.T @ g.ravel()[P]
+        np.testing.assert_allclose(solvers.local_update("jgs2", pb.hessian(x), g, int(i), sup[i], bases[i]),
+                                   -np.linalg.solve(M, rhs), rtol=1e-9)
+        np.testing.assert_allclose(solvers.local_update("cd", pb.hessian(x), g, int(i), sup[i], bases[i]),
+                                   -np.linalg.solve(H[np.ix_(I, I)], g[i]), rtol=1e-12)
+
+
+def test_exact_current_basis_cc_jacobi_step_equals_newton_step():
+    """With untruncated bases built at the current x, S is the exact Schur
+    complement and the Jacobi CC direction is the Newton direction."""
+    sc, pb, topo = _setup(n=3, factor=1.05)
+    x = _state(sc, 0.01)
+    assert np.linalg.eigvalsh(pb.free_hessian(pb.hessian(x)).toarray()).min() > 0
+    sup, bases = subspace.all_global_bases(pb, x)
+    st = solvers.Stats()
+    d_cc = solvers.jacobi_direction(pb, sup, bases, x, None, "cc", st)
+    d_nt = solvers.newton_direction(pb, x)
+    assert st.fallback_empty + st.fallback_reduced + st.fallback_schur == 0
+    assert np.abs(d_cc - d_nt).max() <= 1e-10 * np.abs(d_nt).max()
+    # JGS2 "strictly adds stiffness" (Sec. 3.1): H_ii + Ht - H_ii is PSD; CC deflates it
+    H = pb.hessian(x)
+    g = pb.gradient(x)
+    for i in np.flatnonzero(pb.free)[:5]:
+        H_ii, g_i, A, Ht, b = solvers.local_terms(H, g, int(i), sup[i], bases[i])
+        assert np.linalg.eigvalsh(Ht).min() > 0
+        S = A @ np.linalg.solve(Ht, A.T)
+        assert np.linalg.eigvalsh(S).min() > -1e-9 * np.abs(S).max()
+
+
+@pytest.mark.parametrize("schedule", ["jacobi", "colored"])
+def test_quadratic_problem_converges_in_one_iteration_with_exact_rest_basis(schedule):
+    """Sec. 4.3: for a quadratic energy and the rest-shape basis the Schur
+    complement is the exact global response: a single iteration solves it."""
+    sc, pb, topo = _setup(n=3, kind="linear", nu=0.45, factor=1.5)
+    sup, bases = subspace.all_global_bases(pb)
+    x, hist = solvers.solve(pb, topo, sup, bases, sc.x0, kind="cc", schedule=schedule, max_iters=1)
+    assert hist.iterations == 1
+    assert hist.rel[-1] <= 1e-10
+    xn, hn = solvers.newton(pb, sc.x0, tol=1e-13)
+    np.testing.assert_allclose(x, xn, rtol=0, atol=1e-10)
+
+
+def test_one_free_vertex_cc_equals_cd_equals_newton():
+    sc = meshgen.stretch_box(2, 2, 2, E=1e5, nu=0.45, factor=1.3)
+    pinned = np.ones(sc.n, dtype=np.uint8)
+    centre = 1 + 3 * (1 + 3 * 1)
+    pinned[centre] = 0
+    pb = fem.Problem(sc.X, sc.tets, pinned, material.Model("snh", 1e5, 0.45))
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    x = sc.x0.copy()
+    x[centre] += [0.05, -0.02, 0.03]
+    sup, bases = subspace.build_local_bases(pb, topo, 2)
+    assert len(sup[centre]) == 0
+    st = solvers.Stats()
+    d_cc = solvers.jacobi_direction(pb, sup, bases, x, None, "cc", st)
+    d_cd = solvers.jacobi_direction(pb, sup, bases, x, None, "cd")
+    d_nt = solvers.newton_direction(pb, x)
+    assert st.fallback_empty == 1
+    np.testing.assert_allclose(d_cc, d_cd, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(d_cc, d_nt, rtol=1e-10, atol=1e-15)
+
+
+def test_newton_converges_quadratically_on_stretch():
+    sc = meshgen.stretch_box(4, 4, 4, E=1e5, nu=0.45, factor=1.5)
+    pb = fem.problem_from_scene(sc)
+    x, hist = solvers.newton(pb, sc.x0, tol=1e-12, max_iters=30)
+    assert hist.converged
+    g = hist.grad_norm
+    tail = [k for k in range(1, len(g)) if g[k - 1] < 1e-2 * g[0]]
+    assert len(tail) >= 2
+    # ||g_{k+1}|| <= K ||g_k||^2 in the last iterations (quadratic convergence)
+    K = max(g[k] / g[k - 1] ** 2 for k in tail if g[k] > 1e-14 * g[0])
+    assert K * g[tail[0] - 1] < 0.5
+
+
+def test_coloured_cc_beats_coloured_cd_on_compressible_stretch():
+    """The paper's central claim (Sec. 4.2-4.3), checked qualitatively on a
+    3D stretch with the truncated 2-ring basis at nu = 0.3."""
+    sc, pb, topo = _setup(n=4, nu=0.3, factor=1.2, jit=0.0)
+    sup, bases = subspace.build_local_bases(pb, topo, 2)
+    _, h_cc = solvers.solve(pb, topo, sup, bases, sc.x0, kind="cc", schedule="colored", max_iters=12, tol=0)
+    _, h_cd = solvers.solve(pb, topo, sup, bases, sc.x0, kind="cd", schedule="colored", max_iters=12, tol=0)
+    assert h_cc.rel[-1] < 0.1 * h_cd.rel[-1]
+
+
+def test_spd_guard_agrees_with_eigenvalues():
+    for s in range(40):
+        A = meshgen.normal(100 + s, np.arange(9)).reshape(3, 3)
+        M = A @ A.T - (s % 3) * 0.7 * np.eye(3)
+        ev = np.linalg.eigvalsh(M)
+        if ev.min() > 1e-6 * ev.max():
+            assert solvers.spd_ok(M)
+        if ev.min() < -1e-6 * abs(ev).max():
+            assert not solvers.spd_ok(M)
+
+
+def test_backtracking_line_search_decreases_energy():
+    sc, pb, topo = _setup(n=3, nu=0.45, factor=1.5, jit=0.0)
+    sup, bases = subspace.build_local_bases(pb, topo, 2)
+    d = solvers.jacobi_direction(pb, sup, bases, sc.x0, None, "cc")
+    a = solvers.backtracking(pb, sc.x0, d)
+    assert 0 < a <= 1
+    assert pb.energy(sc.x0 + a * d) < pb.energy(sc.x0)
+
+
+def test_normalized_residual_definition():
+    sc, pb, topo = _setup(n=2)
+    g = np.linalg.norm(pb.gradient(sc.x0)[pb.free])
+    r = solvers.normalized_residual(pb, g)
+    assert r == pytest.approx(g / (pb.total_volume() * pb.n * 1e5))
