@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the Coordinate Condensation hot path on one or more GB300s.
+
+Workload (one "step"): quasistatic stretch of the jittered 32x32x32-cell
+Kuhn cube (35 937 vertices, 196 608 tets; x = 0 face clamped, x = 1 face
+pulled to 1.5), stable Neo-Hookean, 2-ring perturbation bases, coloured
+Coordinate Condensation sweeps in mixed precision until the free gradient
+norm drops by 1e-6 (max 400 sweeps), once for each E in {1e4, 1e5, 1e6, 1e7}.
+Inputs are resident in HBM when a step starts; L2 is flushed between steps.
+
+The metric is vertex-updates/s (free vertices x sweeps / solve time) and
+time to tolerance; the same solves in plain float64 are timed beside them.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+Multi-GPU (torchrun): each rank solves its own copy of the workload (weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ms to 1e-6 rel grad-norm & vertex-updates/s on 1 GB300, mixed/learned vs plain CC"
+E_SWEEP = [1e4, 1e5, 1e6, 1e7]
+DIMS = (32, 32, 32)
+K_RING = 2
+MAX_ITERS = 400
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--nu", type=float, default=0.3)
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solves")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def scenes(nu):
+    import meshgen
+    return [meshgen.stretch_box(*DIMS, E=E, nu=nu, factor=1.5, jitter_amount=0.05, seed=0,
+                                name=f"cube32_E{E:g}") for E in E_SWEEP]
+
+
+def workload_config(nu, n, T, n_free):
+    return {"workload": f"cube32_stretch: {DIMS[0]}x{DIMS[1]}x{DIMS[2]} cells x 6 tets ({n} vertices, {T} tets), "
+                        f"jitter 5% seed 0, x=0 clamped, x=1 pulled to 1.5, SNH nu={nu}, E in {E_SWEEP}, "
+                        f"{K_RING}-ring bases, coloured CC, tol 1e-6 rel grad-norm",
+            "n_free": n_free, "k_ring": K_RING, "schedule": "colored", "update": "cc",
+            "l2": "flushed between steps (256 MiB write)", "inputs": "resident in HBM"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[3 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def oracle_rate(scene, n_updates, seed=5):
+    """Vertex-updates/s of the FP64 oracle's coloured CC sweep, from one timed
+    gradient+Hessian assembly and ``n_updates`` timed local updates, scaled to
+    a full sweep (C assemblies + n_free updates)."""
+    from oracle import fem, solvers, subspace, topology
+    import meshgen
+    pb = fem.problem_from_scene(scene)
+    nb_ptr, nb_idx = topology.vertex_neighbors(pb.n, pb.tets)
+    color = topology.greedy_coloring(pb.n, nb_ptr, nb_idx)
+    C = int(color.max()) + 1
+    free = np.flatnonzero(pb.free)
+    pick = free[(meshgen.uniform01(seed, np.arange(n_updates)) * len(free)).astype(int)]
+    H0 = pb.hessian(pb.X)
+    sup = {}
+    bases = {}
+    for i in pick:
+        S = np.array([j for j in topology.k_ring(int(i), K_RING, nb_ptr, nb_idx) if j != i and pb.free[j]])
+        sup[int(i)] = S
+        bases[int(i)] = subspace.local_basis(H0, int(i), S)
+    t0 = time.perf_counter()
+    g = pb.gradient(scene.x0)
+    H = pb.hessian(scene.x0)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for i in pick:
+        solvers.local_update("cc", H, g, int(i), sup[int(i)], bases[int(i)])
+    t_upd = (time.perf_counter() - t0) / len(pick)
+    sweep_s = C * t_asm + len(free) * t_upd
+    return len(free) / sweep_s, {"t_assembly_s": t_asm, "t_update_s": t_upd, "colors": C,
+                                 "sweep_s": sweep_s}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    sc = scenes(args.nu)[1]
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, info = oracle_rate(sc, 60, seed=11 + k)
+        if k >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    n_free = int((sc.pinned == 0).sum())
+    sample = (f"per step: one float64 gradient+Hessian assembly of the full cube and 60 local CC updates, "
+              f"scaled to one {info['colors']}-colour sweep ({n_free} updates)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "vertex-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_free / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.nu, sc.n, sc.T, n_free),
+        "cpu_baseline": {"value": value, "unit": "vertex-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "vertex-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU
+def local_solve_flops(mesh):
+    """Algorithmic float32 FLOPs of the coupling products per free vertex:
+    2 x 27 per (j, l) block pair in S x S with H_jl != 0 (Y_j = sum H_jl U_l),
+    2 x (27 + 9) per j in S (U_j^T Y_j and U_j^T g_j), 2 x 27 per l in S in
+    row i (A).  Returns an array over vertices (0 for pinned)."""
+    nb_ptr, nb_idx = mesh.export("nbr_ptr"), mesh.export("nbr_idx")
+    sp, si = mesh.export("sup_ptr"), mesh.export("sup_idx")
+    n = len(sp) - 1
+    out = np.zeros(n)
+    insup = np.zeros(n, dtype=bool)
+    for i in range(n):
+        S = si[sp[i]:sp[i + 1]]
+        if len(S) == 0:
+            continue
+        insup[S] = True
+        pairs = 0
+        for j in S:
+            row = nb_idx[nb_ptr[j]:nb_ptr[j + 1]]
+            pairs += int(insup[row].sum()) + 1
+        rowi = nb_idx[nb_ptr[i]:nb_ptr[i + 1]]
+        out[i] = 2 * (27 * pairs + 36 * len(S) + 27 * int(insup[rowi].sum()))
+        insup[S] = False
+    return out
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2510_12053_gb300 as cc
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    scs = scenes(args.nu)
+    t_setup = time.perf_counter()
+    meshes = []
+    for sc in scs:
+        m = cc.Mesh.from_scene(sc, stream=stream)
+        m.color()
+        m.build_subspace(K_RING)
+        meshes.append(m)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t_setup) / len(scs)
+    n, T = scs[0].n, scs[0].T
+    n_free = int((scs[0].pinned == 0).sum())
+    x0 = cc.to_soa(scs[0].x0, device=dev)
+    x = torch.empty_like(x0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def dist_barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def one_step(precision):
+        sweeps, conv = 0, True
+        for m in meshes:
+            x.copy_(x0)
+            r = m.solve_step(x, precision=precision, tol=1e-6, max_iters=MAX_ITERS, check_every=4)
+            sweeps += r.iterations
+            conv &= r.converged
+        return sweeps, conv
+
+    for _ in range(args.warmup):
+        one_step("mixed")
+    torch.cuda.synchronize()
+    for m in meshes:
+        m.profile_enable(True)
+    clocks = Clocks(dev.index)
+    dist_barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, sweeps_total, all_conv = [], 0, True
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s, c = one_step("mixed")
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        sweeps_total += s
+        all_conv &= c
+    torch.cuda.synchronize()
+    dist_barrier()
+    wall_ms = 1e3 * (time.perf_counter() - t_wall)
+    clk = clocks.stop()
+    prof = [m.profile_read() for m in meshes]
+    for m in meshes:
+        m.profile_enable(False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = n_free * sweeps_total
+    value = world * updates / (total_ms / 1e3)
+    sweeps_per_solve = sweeps_total / (args.steps * len(meshes))
+
+    # per-class device time over the timed region
+    cls = {k: {"ms": sum(p[k]["ms"] for p in prof), "launches": sum(p[k]["launches"] for p in prof)}
+           for k in cc.PROFILE_CLASSES}
+    launches = sum(p["total_launches"] for p in prof)
+    dominant = max(cc.PROFILE_CLASSES, key=lambda k: cls[k]["ms"])
+    fl = local_solve_flops(meshes[0])
+    flops_per_sweep = float(fl.sum())
+    ls = cls["local_solve"]
+    achieved = flops_per_sweep * sweeps_total / (ls["ms"] / 1e3) / 1e12 if ls["ms"] > 0 else None
+    roofline = {"kernel": "k_local_solve (coupling SpMM + Schur solve)", "bound": "alu",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "avg_launch_ms": ls["ms"] / max(ls["launches"], 1),
+                "flops_per_sweep": flops_per_sweep}
+
+    # plain float64 CC on the same solves
+    fp64 = None
+    if not args.no_fp64:
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s64, c64 = one_step("fp64")
+        ev1.record(stream)
+        ev1.synchronize()
+        ms64 = ev0.elapsed_time(ev1)
+        fp64 = {"ms_to_tol_per_solve": ms64 / len(meshes), "sweeps_per_solve": s64 / len(meshes),
+                "vertex_updates_per_s": n_free * s64 / (ms64 / 1e3), "converged": bool(c64)}
+
+    # end to end through the public API with host buffers
+    x_host = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+    x_host.copy_(torch.as_tensor(np.ascontiguousarray(scs[0].x0.T)))
+    out_host = torch.empty_like(x_host, pin_memory=True)
+    e2e_ms, e2e_sweeps = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for m in meshes:
+            x.copy_(x_host, non_blocking=True)
+            r = m.solve_step(x, precision="mixed", tol=1e-6, max_iters=MAX_ITERS, check_every=4)
+            e2e_sweeps += r.iterations
+            out_host.copy_(x, non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        e2e_ms.append(ev0.elapsed_time(ev1))
+    e2e_value = world * n_free * e2e_sweeps / (sum(e2e_ms) / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, info = oracle_rate(scs[1], 300)
+        cpu = {"value": v, "unit": "vertex-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"one float64 gradient+Hessian assembly of the full cube ({info['t_assembly_s']:.2f} s) "
+                         f"and 300 local CC updates ({1e3 * info['t_update_s']:.2f} ms each), scaled to one "
+                         f"{info['colors']}-colour sweep"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "vertex-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed (f32 + f32x2 + f64)",
+            "data": "synthetic",
+            "config": dict(workload_config(args.nu, n, T, n_free), parallelism=f"replicas x{world}"),
+            "ms_to_tol_per_solve": total_ms / (args.steps * len(meshes)),
+            "sweeps_per_solve": sweeps_per_solve, "converged": bool(all_conv), "setup_ms_per_mesh": setup_ms,
+            "plain_fp64": fp64,
+            "speedup_vs_fp64": (fp64["ms_to_tol_per_solve"] / (total_ms / (args.steps * len(meshes))))
+            if fp64 else None,
+            "wall_ms_timed": wall_ms,
+            "roofline": roofline,
+            "kernel_ms": {k: round(v["ms"], 3) for k, v in cls.items()},
+            "dominant_kernel_class": dominant,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "vertex-updates/s", "h2d_bytes_per_step": 24 * n * len(meshes),
+                    "d2h_bytes_per_step": 24 * n * len(meshes)},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    for m in meshes:
+        m.close()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * cc.h — C ABI of the GB300 (sm_103a) Coordinate Condensation library.
+ *
+ * The library advances implicit elastodynamics or quasistatics on linear
+ * tetrahedral meshes by solving, per time step,
+ *
+ *     x^{t+1} = argmin_x E(x),                                   (Eq. 1)
+ *     E(x)    = 1/2 (x - xt)^T M (x - xt) + h^2 Psi(x)            (Eq. 2)
+ *
+ * (quasistatic: E = Psi), with the graph-coloured per-vertex Coordinate
+ * Condensation sweep of Section 3 (Algorithm 1 is its one-colour Jacobi
+ * form).  Psi is stable Neo-Hookean in its rest-stable, log-free form
+ *     Psi(F) = mu/2 (|F|^2 - 3) - mu (J - 1) + lam_hat/2 (J - 1)^2,
+ *     lam_hat = lam + mu, J = det F,
+ * whose rest linearisation is Hooke's law for (E, nu).  M is the lumped
+ * mass (rho V_t / 4 per tet corner).
+ *
+ * Conventions for every entry point
+ *   - Device positions are caller-owned float64 buffers in SoA layout
+ *     [3][n]: x[a * n + j] is coordinate a of vertex j.  Pinned (Dirichlet)
+ *     vertices keep whatever the caller stored there; the library never
+ *     writes them.
+ *   - Host arrays passed to cc_build_mesh are copied; the caller keeps them.
+ *   - All device work is ordered on the stream given to cc_build_mesh
+ *     (a cudaStream_t, or NULL for the legacy default stream).  Entry points
+ *     that return host scalars synchronise that stream.
+ *   - Every call returns a cc_status; CC_OK is 0.  No exception or abort
+ *     crosses the ABI.  cc_last_error() returns a thread-local, human
+ *     readable message for the last failing call on this thread.
+ *   - A cc_mesh is not thread-safe: serialise calls on one mesh.
+ */
+#ifndef CC_GB300_H
+#define CC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CC_OK = 0,
+  CC_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum or mesh */
+  CC_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has it) */
+  CC_ERR_OOM = 3,           /* device allocation failed */
+  CC_ERR_NUMERIC = 4,       /* a NaN or Inf appeared in an update or residual */
+  CC_ERR_TIMEOUT = 5,       /* a bounded device wait expired */
+  CC_ERR_NOT_CONVERGED = 6, /* max_iters reached; stats are valid */
+  CC_ERR_STATE = 7          /* call made in the wrong order (e.g. no subspace) */
+} cc_status;
+
+typedef struct cc_mesh cc_mesh; /* opaque; owns device and host rest data */
+
+typedef struct {
+  double E;   /* Young's modulus [Pa], > 0 */
+  double nu;  /* Poisson ratio, in (-1, 0.5) */
+  double rho; /* density [kg/m^3], >= 0 (used by the mass matrix only) */
+} cc_material;
+
+/* Arithmetic of a sweep.
+ *   CC_PREC_FP64  : everything in float64 ("plain").
+ *   CC_PREC_MIXED : per-tet Hessians, the Hessian blocks and the subspace
+ *                   coupling products (H U, U^T H U, U^T g) in float32; the
+ *                   per-tet gradient in float-float (pairs of float32, about
+ *                   48 significant bits); the Schur condensation, the 3x3
+ *                   solves, the position update and the residual reduction
+ *                   in float64. */
+typedef enum { CC_PREC_FP64 = 0, CC_PREC_MIXED = 1 } cc_precision;
+
+/* CC_SCHED_COLORED: for each colour in turn, g and H are re-evaluated at the
+ *   current x and every free vertex of that colour is updated (Gauss-Seidel
+ *   across colours, Jacobi within one).  CC_SCHED_JACOBI: one evaluation,
+ *   every free vertex updated from it (Algorithm 1). */
+typedef enum { CC_SCHED_COLORED = 0, CC_SCHED_JACOBI = 1 } cc_schedule;
+
+/* Local update of a free vertex i (g, H at the current x; U = U_i):
+ *   CC_UPDATE_CC   dx_i = -(H_ii - S)^{-1} gt,  S = A Ht^{-1} A^T,
+ *                  gt = g_i - A Ht^{-1} b,  A = H_iC U, Ht = U^T H_CC U,
+ *                  b = U^T g_C                         (Eq. 9-12)
+ *   CC_UPDATE_CD   dx_i = -H_ii^{-1} g_i               (Eq. 3, one Newton step)
+ *   CC_UPDATE_JGS2 dx_i = -(H_ii + Ht)^{-1} (g_i + b)  (Eq. 7)
+ * Guard: a 3x3 system counts as SPD when all Cholesky pivots exceed 1e-12
+ * times its largest diagonal entry.  CC falls back to the CD step when U_i is
+ * empty, Ht fails the test, or H_ii - S fails it; JGS2 when H_ii + Ht fails.
+ * Fallbacks are counted in the stats, they are not errors. */
+typedef enum { CC_UPDATE_CC = 0, CC_UPDATE_CD = 1, CC_UPDATE_JGS2 = 2 } cc_update;
+
+typedef struct {
+  cc_update update;
+  cc_schedule schedule;
+  cc_precision precision;
+  int32_t color_begin; /* first colour to run (0 for a whole sweep) */
+  int32_t color_end;   /* one past the last colour; -1 = all.  Ignored for Jacobi. */
+} cc_sweep_opts;
+
+typedef struct {
+  int64_t updates;          /* local solves performed */
+  int64_t fallback_empty;   /* CC/JGS2 with an empty basis -> CD step */
+  int64_t fallback_reduced; /* Ht (CC) / H_ii + Ht (JGS2) not SPD -> CD step */
+  int64_t fallback_schur;   /* H_ii - S not SPD -> CD step */
+} cc_sweep_stats;
+
+typedef struct {
+  cc_update update;
+  cc_schedule schedule;
+  cc_precision precision;
+  double tol;          /* stop when ||g_free(x)|| <= tol * ||g_free(x_start)|| */
+  int32_t max_iters;   /* sweeps at most */
+  int32_t min_iters;   /* sweeps at least (0 normally) */
+  int32_t check_every; /* read the residual on the host every this many sweeps (>= 1) */
+  int32_t use_graph;   /* 1: replay the check_every sweeps as one captured CUDA graph */
+  double* residual_history; /* host, max_iters + 1 entries (or NULL): ||g_free|| after
+                               each checked sweep, entry 0 = start; unchecked entries = -1 */
+} cc_step_opts;
+
+typedef struct {
+  int32_t iterations;  /* sweeps performed */
+  int32_t converged;   /* 1 if the tolerance was met */
+  double g0;           /* ||g_free|| at the start */
+  double g_final;      /* ||g_free|| at the end */
+  double energy_final; /* E at the end (float64) */
+  cc_sweep_stats sweeps; /* summed over the sweeps */
+} cc_step_stats;
+
+typedef struct {
+  int64_t n, T, n_free, nnz_blocks;
+  int32_t num_colors;  /* 0 until cc_color */
+  int32_t k_ring;      /* 0 until cc_build_subspace */
+  int64_t support_total; /* sum of |S_i| (0 until cc_build_subspace) */
+  int32_t support_max;
+  int32_t max_valence; /* tets per vertex, maximum */
+} cc_mesh_info;
+
+/* Arrays cc_export can copy to the host (element type in brackets). */
+typedef enum {
+  CC_ARR_VT_PTR = 0,    /* [n+1] int64: vertex -> tet CSR offsets */
+  CC_ARR_VT_TET = 1,    /* [4T] int32: incident tets, ascending per vertex */
+  CC_ARR_VT_CORNER = 2, /* [4T] int32: corner of the vertex in that tet */
+  CC_ARR_NBR_PTR = 3,   /* [n+1] int64: 1-ring CSR offsets (self excluded) */
+  CC_ARR_NBR_IDX = 4,   /* [sum] int32: 1-ring neighbours, ascending */
+  CC_ARR_COLOR = 5,     /* [n] int32: greedy colour of every vertex */
+  CC_ARR_SUP_PTR = 6,   /* [n+1] int64: support CSR offsets (empty for pinned) */
+  CC_ARR_SUP_IDX = 7,   /* [support_total] int32: S_i, ascending */
+  CC_ARR_U = 8,         /* [support_total][3][3] float64: U_i blocks, row-major
+                           (row = DOF of the support vertex, col = direction) */
+  CC_ARR_MASS = 9       /* [n] float64: lumped masses */
+} cc_array;
+
+/* Builds the rest data of a mesh (shape matrices, volumes, lumped masses,
+ * vertex-tet and 1-ring adjacency, the 3x3-block Hessian pattern).
+ *   X       host [n][3] float64 rest positions (row-major, AoS)
+ *   tets    host [T][4] int32 vertex ids; every tet must have positive
+ *           volume after orientation (corners 1 and 2 are swapped when the
+ *           signed volume is negative; a zero-volume tet is an error)
+ *   pinned  host [n] uint8, 1 = Dirichlet vertex (may be NULL: none)
+ *   h       time step (> 0: dynamic energy of Eq. 2; 0: quasistatic E = Psi)
+ *   gravity host [3] acceleration folded into the inertial target by
+ *           cc_solve_step (may be NULL: zero); ignored when h == 0
+ *   stream  cudaStream_t for all work on this mesh (NULL: default stream)
+ * Errors: CC_ERR_INVALID_ARG (n < 4, T < 1, ids out of range, bad material,
+ * degenerate tet), CC_ERR_OOM, CC_ERR_CUDA. */
+cc_status cc_build_mesh(const double* X, int64_t n, const int32_t* tets, int64_t T,
+                        const uint8_t* pinned, const cc_material* mat, double h,
+                        const double* gravity, void* stream, cc_mesh** out);
+
+/* Frees all device and host memory of the mesh (NULL is a no-op). */
+void cc_destroy_mesh(cc_mesh* mesh);
+
+/* Greedy colouring of the 1-ring graph (vertices share a tet) on the GPU:
+ * every vertex, pinned ones included, takes the smallest colour unused by its
+ * lower-id neighbours (Jones-Plassmann rounds with index priority, identical
+ * to sequential greedy in ascending id).  Same-coloured vertices share no
+ * tet.  colors_out: host [n] int32 or NULL; num_colors: host or NULL. */
+cc_status cc_color(cc_mesh* mesh, int32_t* colors_out, int32_t* num_colors);
+
+/* Perturbation bases U_i = -H_PP^{-1} H_Pi at the rest configuration
+ * (Eq. 5, Sec. 3.1), one per free vertex i, on the patch P = S_i: the free
+ * vertices within k_ring 1-ring hops of i, i excluded, every DOF outside P
+ * held fixed.  H is the rest Hessian of E (dynamic meshes: M + h^2 K).
+ * Dense float64 Cholesky per patch on the GPU.  k_ring in [1, 4].
+ * Requires cc_color first (CC_ERR_STATE otherwise). */
+cc_status cc_build_subspace(cc_mesh* mesh, int32_t k_ring);
+
+/* Replaces the bases with caller-supplied ones (e.g. noisy or learned):
+ * sup_ptr host [n+1] int64, sup_idx host [sup_ptr[n]] int32 (ascending,
+ * free vertices other than i), U host [sup_ptr[n]][3][3] float64.
+ * Pinned vertices must have empty supports. */
+cc_status cc_set_subspace(cc_mesh* mesh, const int64_t* sup_ptr, const int32_t* sup_idx,
+                          const double* U);
+
+/* E(x) and the gradient at x.
+ *   x_dev       device [3][n] float64
+ *   xtilde_dev  device [3][n] inertial target (required iff h > 0)
+ *   energy      host out (may be NULL)
+ *   grad_dev    device [3][n] float64 out (may be NULL); pinned rows are 0
+ *   grad_norm   host out: ||g_free||_2 (may be NULL)
+ * precision selects the gradient arithmetic (float64 or float-float). */
+cc_status cc_energy_grad(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev,
+                         cc_precision precision, double* energy, double* grad_dev,
+                         double* grad_norm);
+
+/* One sweep (or the colour range in opts) updating the free rows of x_dev
+ * in place.  Requires cc_color; CC and JGS2 also require a subspace.
+ * stats: host out or NULL.  CC_ERR_NUMERIC when an update is not finite
+ * (x is then left partially updated). */
+cc_status cc_sweep(cc_mesh* mesh, double* x_dev, const double* xtilde_dev,
+                   const cc_sweep_opts* opts, cc_sweep_stats* stats);
+
+/* One quasistatic solve (v_dev == NULL) or one backward Euler step:
+ * xt = x + h v + h^2 gravity; sweeps from x until the tolerance or
+ * max_iters; then v = (x_new - x_old) / h.  x_dev, v_dev device [3][n].
+ * Returns CC_ERR_NOT_CONVERGED (stats valid, x updated) when max_iters is
+ * reached first. */
+cc_status cc_solve_step(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_step_opts* opts,
+                        cc_step_stats* stats);
+
+cc_status cc_get_info(const cc_mesh* mesh, cc_mesh_info* info);
+
+/* Copies one of the cc_array arrays to host memory dst of capacity elements.
+ * count (host, may be NULL) receives the array's length.  CC_ERR_INVALID_ARG
+ * if capacity is too small; CC_ERR_STATE if the array does not exist yet. */
+cc_status cc_export(const cc_mesh* mesh, cc_array which, void* dst, int64_t capacity,
+                    int64_t* count);
+
+/* Per-kernel-class device timing for profiling a caller's timed region.
+ * When enabled, every kernel launch of the mesh is bracketed by a pair of
+ * CUDA events recorded on the mesh's stream; cc_profile_read synchronises
+ * the stream, returns the summed milliseconds and launch counts per class
+ * and resets the accumulators.  Classes: 0 per-tet derivatives, 1 gather
+ * (gradient + Hessian blocks), 2 local solve (coupling products + Schur
+ * solve), 3 reductions, 4 other (mirrors, targets, velocities). */
+#define CC_PROFILE_CLASSES 5
+typedef struct {
+  double ms[CC_PROFILE_CLASSES];
+  int64_t launches[CC_PROFILE_CLASSES];
+  int64_t total_launches; /* kernel launches since the last read (counted
+                             whether or not event timing is enabled) */
+} cc_profile;
+
+cc_status cc_profile_enable(cc_mesh* mesh, int32_t on);
+cc_status cc_profile_read(cc_mesh* mesh, cc_profile* out);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* cc_last_error(void);
+
+/* Library version string. */
+const char* cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_GB300_H */

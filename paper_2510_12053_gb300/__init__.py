@@ -1,0 +1,285 @@
+"""GB300-native Coordinate Condensation (arxiv 2510.12053): Python binding.
+
+A thin ``ctypes`` layer over the C ABI in ``include/cc.h``.  It only
+marshals arguments: every step of the sweep runs in the CUDA kernels of
+``_lib/libcc_gb300.so``.  If that library is missing, importing works but
+every call raises :class:`CCError` (there is no CPU fallback).
+
+Device arrays are ``torch`` float64 CUDA tensors in SoA layout ``[3, n]``;
+PyTorch supplies memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcc_gb300.so")
+
+# cc_status
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_STATE = range(8)
+STATUS_NAMES = ["CC_OK", "CC_ERR_INVALID_ARG", "CC_ERR_CUDA", "CC_ERR_OOM", "CC_ERR_NUMERIC",
+                "CC_ERR_TIMEOUT", "CC_ERR_NOT_CONVERGED", "CC_ERR_STATE"]
+PREC = {"fp64": 0, "mixed": 1}
+SCHED = {"colored": 0, "jacobi": 1}
+UPDATE = {"cc": 0, "cd": 1, "jgs2": 2}
+ARRAYS = {"vt_ptr": (0, np.int64), "vt_tet": (1, np.int32), "vt_corner": (2, np.int32),
+          "nbr_ptr": (3, np.int64), "nbr_idx": (4, np.int32), "color": (5, np.int32),
+          "sup_ptr": (6, np.int64), "sup_idx": (7, np.int32), "U": (8, np.float64),
+          "mass": (9, np.float64)}
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class SweepOpts(ctypes.Structure):
+    _fields_ = [("update", ctypes.c_int), ("schedule", ctypes.c_int), ("precision", ctypes.c_int),
+                ("color_begin", ctypes.c_int32), ("color_end", ctypes.c_int32)]
+
+
+class SweepStats(ctypes.Structure):
+    _fields_ = [("updates", ctypes.c_int64), ("fallback_empty", ctypes.c_int64),
+                ("fallback_reduced", ctypes.c_int64), ("fallback_schur", ctypes.c_int64)]
+
+
+class StepOpts(ctypes.Structure):
+    _fields_ = [("update", ctypes.c_int), ("schedule", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("min_iters", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("residual_history", ctypes.POINTER(ctypes.c_double))]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("g0", ctypes.c_double),
+                ("g_final", ctypes.c_double), ("energy_final", ctypes.c_double), ("sweeps", SweepStats)]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("T", ctypes.c_int64), ("n_free", ctypes.c_int64),
+                ("nnz_blocks", ctypes.c_int64), ("num_colors", ctypes.c_int32), ("k_ring", ctypes.c_int32),
+                ("support_total", ctypes.c_int64), ("support_max", ctypes.c_int32),
+                ("max_valence", ctypes.c_int32)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5), ("total_launches", ctypes.c_int64)]
+
+
+PROFILE_CLASSES = ["tet_eval", "gather", "local_solve", "reduce", "other"]
+
+_lib_handle = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "cc_build_mesh": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.POINTER(Material),
+                                     ctypes.c_double, _P, _P, ctypes.POINTER(_P)]),
+    "cc_destroy_mesh": (None, [_P]),
+    "cc_color": (ctypes.c_int, [_P, _P, _P]),
+    "cc_build_subspace": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cc_set_subspace": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cc_energy_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
+    "cc_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepStats)]),
+    "cc_solve_step": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(StepStats)]),
+    "cc_get_info": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
+    "cc_export": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "cc_last_error": (ctypes.c_char_p, []),
+    "cc_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded C library (raises CCError if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise CCError(ERR_STATE, f"CUDA library not built ({LIB_PATH}); run "
+                                     "`python -m paper_2510_12053_gb300.build`")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib_handle = h
+    return _lib_handle
+
+
+def _check(status: int):
+    if status != OK:
+        raise CCError(status, lib().cc_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev3n(t, n, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and tuple(t.shape) == (3, n)):
+        raise CCError(ERR_INVALID_ARG, f"{name} must be a contiguous float64 CUDA tensor of shape (3, {n})")
+    return t.data_ptr()
+
+
+@dataclasses.dataclass
+class SolveResult:
+    iterations: int
+    converged: bool
+    g0: float
+    g_final: float
+    energy: float
+    updates: int
+    fallback_empty: int
+    fallback_reduced: int
+    fallback_schur: int
+    residuals: Optional[np.ndarray] = None
+
+
+class Mesh:
+    """A tet mesh on the GPU (owns the library's ``cc_mesh``)."""
+
+    def __init__(self, X, tets, pinned=None, *, E: float, nu: float, rho: float = 1000.0, h: float = 0.0,
+                 gravity=None, stream=None):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.n, self.T = int(X.shape[0]), int(tets.shape[0])
+        pin = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)
+        grav = None if gravity is None else np.ascontiguousarray(gravity, dtype=np.float64)
+        mat = Material(E, nu, rho)
+        out = _P()
+        self._h = None
+        _check(lib().cc_build_mesh(X.ctypes.data, self.n, tets.ctypes.data, self.T,
+                                   None if pin is None else pin.ctypes.data, ctypes.byref(mat), float(h),
+                                   None if grav is None else grav.ctypes.data, _stream_ptr(stream),
+                                   ctypes.byref(out)))
+        self._h = out
+        self.dynamic = h > 0.0
+
+    @classmethod
+    def from_scene(cls, scene, stream=None) -> "Mesh":
+        m = scene.material
+        return cls(scene.X, scene.tets, scene.pinned, E=m.E, nu=m.nu, rho=m.rho, h=scene.h,
+                   gravity=scene.gravity, stream=stream)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().cc_destroy_mesh(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def color(self) -> np.ndarray:
+        cols = np.empty(self.n, dtype=np.int32)
+        nc = ctypes.c_int32()
+        _check(lib().cc_color(self._h, cols.ctypes.data, ctypes.byref(nc)))
+        return cols
+
+    def build_subspace(self, k: int):
+        _check(lib().cc_build_subspace(self._h, int(k)))
+
+    def set_subspace(self, sup_ptr, sup_idx, U):
+        sp = np.ascontiguousarray(sup_ptr, dtype=np.int64)
+        si = np.ascontiguousarray(sup_idx, dtype=np.int32)
+        Ub = np.ascontiguousarray(U, dtype=np.float64)
+        _check(lib().cc_set_subspace(self._h, sp.ctypes.data, si.ctypes.data if si.size else None,
+                                     Ub.ctypes.data))
+
+    def info(self) -> MeshInfo:
+        inf = MeshInfo()
+        _check(lib().cc_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def export(self, name: str) -> np.ndarray:
+        which, dt = ARRAYS[name]
+        cnt = ctypes.c_int64()
+        _check(lib().cc_export(self._h, which, None, 0, ctypes.byref(cnt)))
+        out = np.empty(max(cnt.value, 1), dtype=dt)
+        _check(lib().cc_export(self._h, which, out.ctypes.data, out.size, ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def profile_enable(self, on: bool = True):
+        _check(lib().cc_profile_enable(self._h, int(on)))
+
+    def profile_read(self) -> dict:
+        """Per-class device milliseconds and launch counts since the last read."""
+        p = Profile()
+        _check(lib().cc_profile_read(self._h, ctypes.byref(p)))
+        out = {k: {"ms": p.ms[i], "launches": p.launches[i]} for i, k in enumerate(PROFILE_CLASSES)}
+        out["total_launches"] = p.total_launches
+        return out
+
+    def energy_grad(self, x, xtilde=None, precision: str = "fp64", want_grad: bool = True):
+        import torch
+        gx = _dev3n(x, self.n, "x")
+        gt = _dev3n(xtilde, self.n, "xtilde")
+        grad = torch.empty_like(x) if want_grad else None
+        e, gn = ctypes.c_double(), ctypes.c_double()
+        _check(lib().cc_energy_grad(self._h, gx, gt, PREC[precision], ctypes.byref(e), _ptr(grad),
+                                    ctypes.byref(gn)))
+        return e.value, grad, gn.value
+
+    def sweep(self, x, xtilde=None, update: str = "cc", schedule: str = "colored", precision: str = "fp64",
+              color_begin: int = 0, color_end: int = -1) -> SweepStats:
+        o = SweepOpts(UPDATE[update], SCHED[schedule], PREC[precision], color_begin, color_end)
+        st = SweepStats()
+        _check(lib().cc_sweep(self._h, _dev3n(x, self.n, "x"), _dev3n(xtilde, self.n, "xtilde"),
+                              ctypes.byref(o), ctypes.byref(st)))
+        return st
+
+    def solve_step(self, x, v=None, *, update: str = "cc", schedule: str = "colored", precision: str = "mixed",
+                   tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0, check_every: int = 1,
+                   use_graph: bool = False, history: bool = False) -> SolveResult:
+        hist = np.full(max_iters + 1, -1.0) if history else None
+        o = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters, check_every,
+                     int(use_graph),
+                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None)
+        st = StepStats()
+        rc = lib().cc_solve_step(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
+                                 ctypes.byref(st))
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            _check(rc)
+        return SolveResult(st.iterations, bool(st.converged), st.g0, st.g_final, st.energy_final,
+                           st.sweeps.updates, st.sweeps.fallback_empty, st.sweeps.fallback_reduced,
+                           st.sweeps.fallback_schur, hist)
+
+
+def version() -> str:
+    return lib().cc_version().decode()
+
+
+def to_soa(x_n3, device="cuda"):
+    """[n, 3] array -> contiguous (3, n) float64 tensor on ``device``."""
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(np.asarray(x_n3, dtype=np.float64).T), device=device).contiguous()
+
+
+def from_soa(t) -> np.ndarray:
+    """(3, n) tensor -> [n, 3] numpy array."""
+    return t.detach().cpu().numpy().T.copy()

@@ -1,0 +1,561 @@
+// C ABI entry points (include/cc.h): argument checks, state management and
+// the order of kernel launches for sweeps and solves.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "cc_internal.cuh"
+
+namespace ccg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+enum { P_TET = 0, P_GATHER = 1, P_SOLVE = 2, P_RED = 3, P_OTHER = 4 };
+
+int prof_event(Mesh& m) {
+  if (!m.prof.on) return -1;
+  if (m.prof.used == m.prof.pool.size()) {
+    cudaEvent_t e;
+    CCG_CUDA(cudaEventCreate(&e));
+    m.prof.pool.push_back(e);
+  }
+  const int k = (int)m.prof.used++;
+  CCG_CUDA(cudaEventRecord(m.prof.pool[k], m.stream));
+  return k;
+}
+
+// Counts `launches` kernels of class `cls`; with timing on, records the
+// closing event of an interval opened by prof_event.
+void prof_close(Mesh& m, int cls, int begin, int launches) {
+  m.prof.total_launches += launches;
+  if (!m.prof.on || begin < 0) return;
+  const int end = prof_event(m);
+  m.prof.mark_cls.push_back(cls);
+  m.prof.mark_begin.push_back(begin);
+  m.prof.mark_end.push_back(end);
+  m.prof.mark_launches.push_back(launches);
+}
+
+double elastic_weight(const Mesh& m) { return m.h > 0.0 ? m.h * m.h : 1.0; }
+
+void ensure_state(Mesh& m, cc_precision p) {
+  cudaStream_t s = m.stream;
+  const size_t ne = 4 * (size_t)m.T;
+  if (p == CC_PREC_FP64) {
+    if (!m.f64.gcon.p) {
+      m.f64.gcon.alloc(3 * ne);
+      m.f64.hcon.alloc(36 * ne);
+      m.f64.g.alloc(3 * m.n);
+      m.f64.bsr.alloc(9 * m.nnzb);
+      CCG_CUDA(cudaMemsetAsync(m.f64.g.p, 0, 3 * m.n * sizeof(double), s));
+    }
+  } else {
+    if (!m.mx.gcon.p) {
+      m.mx.gcon.alloc(3 * ne);
+      m.mx.hcon.alloc(36 * ne);
+      m.mx.g_hi.alloc(3 * m.n);
+      m.mx.g_lo.alloc(3 * m.n);
+      m.mx.bsr.alloc(9 * m.nnzb);
+      m.mx.x_hi.alloc(m.n);
+      m.mx.x_lo.alloc(m.n);
+      m.mx.xt_hi.alloc(m.n);
+      m.mx.xt_lo.alloc(m.n);
+      CCG_CUDA(cudaMemsetAsync(m.mx.g_hi.p, 0, 3 * m.n * sizeof(float), s));
+      CCG_CUDA(cudaMemsetAsync(m.mx.g_lo.p, 0, 3 * m.n * sizeof(float), s));
+      CCG_CUDA(cudaMemsetAsync(m.mx.xt_hi.p, 0, m.n * sizeof(float4), s));
+      CCG_CUDA(cudaMemsetAsync(m.mx.xt_lo.p, 0, m.n * sizeof(float4), s));
+    }
+  }
+}
+
+// Re-evaluates the per-tet derivatives for a tet list and re-gathers g, H.
+void refresh(Mesh& m, cc_precision p, const double* x, const double* xt, const int32_t* list, int64_t count) {
+  cudaStream_t s = m.stream;
+  int e0 = prof_event(m);
+  if (p == CC_PREC_FP64)
+    launch_tet_eval_f64(m, x, list, count, elastic_weight(m), s);
+  else
+    launch_tet_eval_mixed(m, list, count, elastic_weight(m), s);
+  prof_close(m, P_TET, e0, count > 0 ? 1 : 0);
+  e0 = prof_event(m);
+  if (p == CC_PREC_FP64)
+    launch_gather_f64(m, x, xt, s);
+  else
+    launch_gather_mixed(m, m.h > 0.0, s);
+  prof_close(m, P_GATHER, e0, 2);
+}
+
+void refresh_all(Mesh& m, cc_precision p, const double* x, const double* xt) {
+  refresh(m, p, x, xt, m.d_all_tets.p, m.n_active_tets);
+}
+
+SweepCounters counters(Mesh& m) { return SweepCounters{m.d_counters.p, m.d_counters.p + 4}; }
+
+void solve_list(Mesh& m, const cc_sweep_opts& o, const int32_t* verts, int64_t count, double* x) {
+  if (count <= 0) return;
+  const int e0 = prof_event(m);
+  if (o.precision == CC_PREC_FP64)
+    launch_local_solve_f64(m, o.update, verts, count, x, counters(m), m.stream);
+  else
+    launch_local_solve_mixed(m, o.update, verts, count, x, counters(m), m.stream);
+  prof_close(m, P_SOLVE, e0, 1);
+}
+
+// One sweep over colours [cb, ce).  `fresh` means g and H already hold the
+// derivatives at x (no refresh needed before the first colour).
+void sweep_body(Mesh& m, double* x, const double* xt, const cc_sweep_opts& o, int cb, int ce, bool fresh) {
+  if (o.schedule == CC_SCHED_JACOBI) {
+    if (!fresh) refresh_all(m, o.precision, x, xt);
+    solve_list(m, o, m.d_free_rows.p, m.n_free, x);
+    return;
+  }
+  for (int c = cb; c < ce; ++c) {
+    if (c == cb) {
+      if (!fresh) refresh_all(m, o.precision, x, xt);
+    } else {
+      refresh(m, o.precision, x, xt, m.d_tl.p + m.tl_ptr[c - 1], m.tl_ptr[c] - m.tl_ptr[c - 1]);
+    }
+    solve_list(m, o, m.d_cv_idx.p + m.cv_ptr[c], m.cv_ptr[c + 1] - m.cv_ptr[c], x);
+  }
+}
+
+// Brings g and H up to date after a sweep over [cb, ce).
+void post_refresh(Mesh& m, double* x, const double* xt, const cc_sweep_opts& o, int ce) {
+  if (o.schedule == CC_SCHED_JACOBI)
+    refresh_all(m, o.precision, x, xt);
+  else
+    refresh(m, o.precision, x, xt, m.d_tl.p + m.tl_ptr[ce - 1], m.tl_ptr[ce] - m.tl_ptr[ce - 1]);
+}
+
+void gnorm(Mesh& m, cc_precision p, double* grad_out, double* out) {
+  const int e0 = prof_event(m);
+  if (p == CC_PREC_FP64)
+    launch_gnorm_f64(m, grad_out, out, m.stream);
+  else
+    launch_gnorm_mixed(m, grad_out, out, m.stream);
+  prof_close(m, P_RED, e0, 2);
+}
+
+void split(Mesh& m, const double* x, float4* hi, float4* lo) {
+  const int e0 = prof_event(m);
+  launch_split_df(x, m.n, hi, lo, m.stream);
+  prof_close(m, P_OTHER, e0, 1);
+}
+
+double read_scalar(Mesh& m, const double* dev) {
+  CCG_CUDA(cudaMemcpyAsync(m.h_pinned_scalars, dev, sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+  CCG_CUDA(cudaStreamSynchronize(m.stream));
+  return m.h_pinned_scalars[0];
+}
+
+void read_counters(Mesh& m, cc_sweep_stats* st, int64_t updates) {
+  unsigned long long h[8];
+  CCG_CUDA(cudaMemcpyAsync(h, m.d_counters.p, sizeof(h), cudaMemcpyDeviceToHost, m.stream));
+  CCG_CUDA(cudaStreamSynchronize(m.stream));
+  if (st) {
+    st->updates = updates;
+    st->fallback_empty = (int64_t)h[0];
+    st->fallback_reduced = (int64_t)h[1];
+    st->fallback_schur = (int64_t)h[2];
+  }
+  CCG_CHECK(h[4] == 0, CC_ERR_NUMERIC, "non-finite local update");
+}
+
+void check_sweep_opts(const Mesh& m, const cc_sweep_opts& o, int* cb, int* ce) {
+  CCG_CHECK(o.update >= CC_UPDATE_CC && o.update <= CC_UPDATE_JGS2, CC_ERR_INVALID_ARG, "bad update kind");
+  CCG_CHECK(o.schedule == CC_SCHED_COLORED || o.schedule == CC_SCHED_JACOBI, CC_ERR_INVALID_ARG, "bad schedule");
+  CCG_CHECK(o.precision == CC_PREC_FP64 || o.precision == CC_PREC_MIXED, CC_ERR_INVALID_ARG, "bad precision");
+  CCG_CHECK(m.num_colors > 0, CC_ERR_STATE, "cc_color must run before sweeps");
+  CCG_CHECK(o.update == CC_UPDATE_CD || m.k_ring > 0, CC_ERR_STATE, "CC and JGS2 need a subspace");
+  *cb = 0;
+  *ce = m.num_colors;
+  if (o.schedule == CC_SCHED_COLORED) {
+    *cb = o.color_begin;
+    *ce = o.color_end < 0 ? m.num_colors : o.color_end;
+    CCG_CHECK(*cb >= 0 && *cb < *ce && *ce <= m.num_colors, CC_ERR_INVALID_ARG, "bad colour range");
+  }
+}
+
+}  // namespace
+}  // namespace ccg
+
+using namespace ccg;
+
+struct cc_mesh : public ccg::Mesh {};
+
+#define CC_API_BODY(name, ...)                                   \
+  try {                                                           \
+    ccg::g_last_error.clear();                                    \
+    __VA_ARGS__;                                                  \
+    return CC_OK;                                                 \
+  } catch (const ccg::Fail& f) {                                  \
+    if (ccg::g_last_error.empty()) ccg::g_last_error = name;      \
+    return f.st;                                                  \
+  } catch (const std::bad_alloc&) {                               \
+    ccg::g_last_error = std::string(name) + ": host out of memory"; \
+    return CC_ERR_OOM;                                            \
+  } catch (...) {                                                 \
+    ccg::g_last_error = std::string(name) + ": unexpected error"; \
+    return CC_ERR_STATE;                                          \
+  }
+
+extern "C" {
+
+const char* cc_last_error(void) { return ccg::g_last_error.c_str(); }
+
+const char* cc_version(void) { return "cc-gb300 0.1 (sm_103a)"; }
+
+cc_status cc_build_mesh(const double* X, int64_t n, const int32_t* tets, int64_t T, const uint8_t* pinned,
+                        const cc_material* mat, double h, const double* gravity, void* stream, cc_mesh** out) {
+  cc_mesh* m = nullptr;
+  try {
+    ccg::g_last_error.clear();
+    CCG_CHECK(out != nullptr, CC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    CCG_CHECK(X && tets && mat, CC_ERR_INVALID_ARG, "NULL input array");
+    CCG_CHECK(n >= 4 && T >= 1 && n < (int64_t(1) << 31) && T < (int64_t(1) << 29), CC_ERR_INVALID_ARG,
+              "n or T out of range");
+    CCG_CHECK(mat->E > 0 && mat->nu > -1.0 && mat->nu < 0.5 && mat->rho >= 0 && std::isfinite(mat->E),
+              CC_ERR_INVALID_ARG, "bad material");
+    CCG_CHECK(h >= 0 && std::isfinite(h), CC_ERR_INVALID_ARG, "bad time step");
+    m = new cc_mesh();
+    m->n = n;
+    m->T = T;
+    m->E = mat->E;
+    m->nu = mat->nu;
+    m->rho = mat->rho;
+    m->mu = mat->E / (2.0 * (1.0 + mat->nu));
+    const double lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
+    m->lam_hat = lam + m->mu;
+    m->h = h;
+    if (gravity && h > 0)
+      for (int a = 0; a < 3; ++a) m->grav[a] = gravity[a];
+    m->stream = (cudaStream_t)stream;
+    m->X.assign(X, X + 3 * n);
+    for (int64_t k = 0; k < 3 * n; ++k) CCG_CHECK(std::isfinite(X[k]), CC_ERR_INVALID_ARG, "non-finite rest position");
+    m->tets.assign(tets, tets + 4 * T);
+    m->pinned.assign(n, 0);
+    if (pinned)
+      for (int64_t v = 0; v < n; ++v) m->pinned[v] = pinned[v] ? 1 : 0;
+    ccg::build_topology(*m);
+    CCG_CHECK(m->n_free > 0, CC_ERR_INVALID_ARG, "every vertex is pinned");
+    m->d_red.alloc(4096);
+    m->d_scalars.alloc(8);
+    m->d_counters.alloc(8);
+    CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), m->stream));
+    CCG_CUDA(cudaMallocHost((void**)&m->h_pinned_scalars, 8 * sizeof(double)));
+    *out = m;
+    return CC_OK;
+  } catch (const ccg::Fail& f) {
+    cc_destroy_mesh(m);
+    return f.st;
+  } catch (...) {
+    cc_destroy_mesh(m);
+    ccg::g_last_error = "cc_build_mesh: unexpected error";
+    return CC_ERR_STATE;
+  }
+}
+
+void cc_destroy_mesh(cc_mesh* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  else cudaDeviceSynchronize();
+  if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+  for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
+  auto rel = [](auto& b) { b.release(); };
+  rel(m->d_tets); rel(m->d_tslot); rel(m->d_Bm); rel(m->d_Bm_df); rel(m->d_Bm32); rel(m->d_vol); rel(m->d_mass);
+  rel(m->d_pinned); rel(m->d_vt_ptr); rel(m->d_nbr_ptr); rel(m->d_nbr_idx); rel(m->d_bsr_ptr); rel(m->d_bsr_col);
+  rel(m->d_bsr_row); rel(m->d_blk_ptr); rel(m->d_blk_src); rel(m->d_free_rows); rel(m->d_free_blocks);
+  rel(m->d_color); rel(m->d_cv_idx); rel(m->d_tl); rel(m->d_all_tets); rel(m->d_sup_ptr); rel(m->d_sup_idx);
+  rel(m->f64.gcon); rel(m->f64.hcon); rel(m->f64.g); rel(m->f64.bsr); rel(m->f64.U);
+  rel(m->mx.gcon); rel(m->mx.hcon); rel(m->mx.g_hi); rel(m->mx.g_lo); rel(m->mx.bsr); rel(m->mx.U);
+  rel(m->mx.x_hi); rel(m->mx.x_lo); rel(m->mx.xt_hi); rel(m->mx.xt_lo);
+  rel(m->d_red); rel(m->d_scalars); rel(m->d_counters); rel(m->d_xtilde); rel(m->d_xold);
+  if (m->h_pinned_scalars) cudaFreeHost(m->h_pinned_scalars);
+  delete m;
+}
+
+cc_status cc_color(cc_mesh* m, int32_t* colors_out, int32_t* num_colors) {
+  CC_API_BODY("cc_color", {
+    CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    ccg::run_coloring(*m);
+    if (colors_out) std::memcpy(colors_out, m->color.data(), m->n * sizeof(int32_t));
+    if (num_colors) *num_colors = m->num_colors;
+  })
+}
+
+cc_status cc_build_subspace(cc_mesh* m, int32_t k) {
+  CC_API_BODY("cc_build_subspace", {
+    CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    CCG_CHECK(k >= 1 && k <= 4, CC_ERR_INVALID_ARG, "k_ring must be in [1, 4]");
+    CCG_CHECK(m->num_colors > 0, CC_ERR_STATE, "cc_color must run before cc_build_subspace");
+    ensure_state(*m, CC_PREC_FP64);
+    ccg::run_subspace_build(*m, k);
+  })
+}
+
+cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup_idx, const double* U) {
+  CC_API_BODY("cc_set_subspace", {
+    CCG_CHECK(m && sup_ptr && U, CC_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n = m->n;
+    CCG_CHECK(sup_ptr[0] == 0, CC_ERR_INVALID_ARG, "sup_ptr[0] must be 0");
+    int32_t supmax = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      CCG_CHECK(sup_ptr[v + 1] >= sup_ptr[v], CC_ERR_INVALID_ARG, "sup_ptr not monotone");
+      const int64_t len = sup_ptr[v + 1] - sup_ptr[v];
+      CCG_CHECK(!m->pinned[v] || len == 0, CC_ERR_INVALID_ARG, "pinned vertex with a non-empty support");
+      for (int64_t p = sup_ptr[v]; p < sup_ptr[v + 1]; ++p) {
+        const int32_t j = sup_idx[p];
+        CCG_CHECK(j >= 0 && j < n && j != v && !m->pinned[j], CC_ERR_INVALID_ARG, "bad support vertex");
+        CCG_CHECK(p == sup_ptr[v] || sup_idx[p - 1] < j, CC_ERR_INVALID_ARG, "support not ascending");
+      }
+      supmax = std::max<int32_t>(supmax, (int32_t)len);
+    }
+    const int64_t total = sup_ptr[n];
+    CCG_CHECK(total < (int64_t(1) << 31) && supmax < 32768, CC_ERR_INVALID_ARG, "support too large");
+    m->sup_ptr.assign(sup_ptr, sup_ptr + n + 1);
+    m->sup_idx.assign(sup_idx, sup_idx + total);
+    m->U.assign(U, U + 9 * total);
+    m->sup_max = supmax;
+    int hs = 32;
+    while (hs < 2 * std::max(supmax, 1)) hs <<= 1;
+    m->hash_size = hs;
+    if (m->k_ring == 0) m->k_ring = -1;  // custom
+    std::vector<int32_t> sp32(n + 1);
+    for (int64_t v = 0; v <= n; ++v) sp32[v] = (int32_t)sup_ptr[v];
+    m->d_sup_ptr.upload(sp32, m->stream);
+    m->d_sup_idx.upload(m->sup_idx, m->stream);
+    m->f64.U.upload(m->U, m->stream);
+    std::vector<float> u32(9 * std::max<int64_t>(total, 1), 0.f);
+    for (int64_t q = 0; q < 9 * total; ++q) u32[q] = (float)m->U[q];
+    m->mx.U.upload(u32, m->stream);
+    CCG_CUDA(cudaStreamSynchronize(m->stream));
+  })
+}
+
+cc_status cc_energy_grad(cc_mesh* m, const double* x, const double* xt, cc_precision p, double* energy,
+                         double* grad, double* grad_norm) {
+  CC_API_BODY("cc_energy_grad", {
+    CCG_CHECK(m && x, CC_ERR_INVALID_ARG, "NULL argument");
+    CCG_CHECK(p == CC_PREC_FP64 || p == CC_PREC_MIXED, CC_ERR_INVALID_ARG, "bad precision");
+    CCG_CHECK(m->h == 0.0 || xt, CC_ERR_INVALID_ARG, "dynamic mesh needs xtilde");
+    ensure_state(*m, p);
+    cudaStream_t s = m->stream;
+    if (p == CC_PREC_MIXED) {
+      split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
+      if (m->h > 0.0) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
+    }
+    refresh_all(*m, p, x, xt);
+    if (grad) CCG_CUDA(cudaMemsetAsync(grad, 0, 3 * m->n * sizeof(double), s));
+    gnorm(*m, p, grad, m->d_scalars.p);
+    launch_energy(*m, x, m->h > 0.0 ? xt : nullptr, m->d_scalars.p + 1, s);
+    CCG_CUDA(cudaGetLastError());
+    CCG_CUDA(cudaMemcpyAsync(m->h_pinned_scalars, m->d_scalars.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    if (grad_norm) *grad_norm = std::sqrt(m->h_pinned_scalars[0]);
+    if (energy) *energy = m->h_pinned_scalars[1];
+  })
+}
+
+cc_status cc_sweep(cc_mesh* m, double* x, const double* xt, const cc_sweep_opts* opts, cc_sweep_stats* stats) {
+  CC_API_BODY("cc_sweep", {
+    CCG_CHECK(m && x && opts, CC_ERR_INVALID_ARG, "NULL argument");
+    CCG_CHECK(m->h == 0.0 || xt, CC_ERR_INVALID_ARG, "dynamic mesh needs xtilde");
+    int cb, ce;
+    check_sweep_opts(*m, *opts, &cb, &ce);
+    ensure_state(*m, opts->precision);
+    cudaStream_t s = m->stream;
+    CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
+    if (opts->precision == CC_PREC_MIXED) {
+      split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
+      if (m->h > 0.0) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
+    }
+    sweep_body(*m, x, xt, *opts, cb, ce, false);
+    CCG_CUDA(cudaGetLastError());
+    int64_t upd = opts->schedule == CC_SCHED_JACOBI ? m->n_free : (int64_t)(m->cv_ptr[ce] - m->cv_ptr[cb]);
+    read_counters(*m, stats, upd);
+  })
+}
+
+cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o, cc_step_stats* st) {
+  cc_status rc = CC_OK;
+  try {
+    ccg::g_last_error.clear();
+    CCG_CHECK(m && x && o, CC_ERR_INVALID_ARG, "NULL argument");
+    CCG_CHECK(o->max_iters >= 0 && o->min_iters >= 0 && o->tol >= 0, CC_ERR_INVALID_ARG, "bad iteration limits");
+    CCG_CHECK((m->h > 0.0) == (v != nullptr), CC_ERR_INVALID_ARG,
+              "v must be given exactly for dynamic meshes (h > 0)");
+    cc_sweep_opts so{o->update, o->schedule, o->precision, 0, -1};
+    int cb, ce;
+    check_sweep_opts(*m, so, &cb, &ce);
+    ensure_state(*m, o->precision);
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n;
+    const bool dyn = m->h > 0.0;
+    const double* xt = nullptr;
+    if (dyn) {
+      if (!m->d_xtilde.p) {
+        m->d_xtilde.alloc(3 * n);
+        m->d_xold.alloc(3 * n);
+      }
+      CCG_CUDA(cudaMemcpyAsync(m->d_xold.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      const int e0 = prof_event(*m);
+      launch_inertial_target(x, v, n, m->h, m->grav, m->d_xtilde.p, s);
+      prof_close(*m, P_OTHER, e0, 1);
+      xt = m->d_xtilde.p;
+    }
+    CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
+    if (o->precision == CC_PREC_MIXED) {
+      split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
+      if (dyn) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
+    }
+    refresh_all(*m, o->precision, x, xt);
+    gnorm(*m, o->precision, nullptr, m->d_scalars.p);
+    const double g0 = std::sqrt(read_scalar(*m, m->d_scalars.p));
+    CCG_CHECK(std::isfinite(g0), CC_ERR_NUMERIC, "non-finite initial residual");
+    if (o->residual_history) {
+      o->residual_history[0] = g0;
+      for (int k = 1; k <= o->max_iters; ++k) o->residual_history[k] = -1.0;
+    }
+    const int every = std::max(1, o->check_every);
+    double gcur = g0;
+    int it = 0;
+    bool conv = (g0 == 0.0);
+    while (!conv && it < o->max_iters) {
+      const int chunk = std::min(every, o->max_iters - it);
+      for (int k = 0; k < chunk; ++k) {
+        sweep_body(*m, x, xt, so, cb, ce, true);
+        post_refresh(*m, x, xt, so, ce);
+      }
+      CCG_CUDA(cudaGetLastError());
+      it += chunk;
+      gnorm(*m, o->precision, nullptr, m->d_scalars.p);
+      gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
+      if (o->residual_history) o->residual_history[it] = gcur;
+      CCG_CHECK(std::isfinite(gcur), CC_ERR_NUMERIC, "non-finite residual");
+      if (it >= o->min_iters && gcur <= o->tol * g0) conv = true;
+    }
+    int e1 = prof_event(*m);
+    launch_energy(*m, x, xt, m->d_scalars.p + 1, s);
+    prof_close(*m, P_RED, e1, dyn ? 3 : 2);
+    const double energy = read_scalar(*m, m->d_scalars.p + 1);
+    if (dyn) {
+      e1 = prof_event(*m);
+      launch_velocity(x, m->d_xold.p, n, m->h, v, s);
+      prof_close(*m, P_OTHER, e1, 1);
+    }
+    cc_step_stats tmp{};
+    read_counters(*m, &tmp.sweeps, (int64_t)it * m->n_free);
+    tmp.iterations = it;
+    tmp.converged = conv ? 1 : 0;
+    tmp.g0 = g0;
+    tmp.g_final = gcur;
+    tmp.energy_final = energy;
+    CCG_CUDA(cudaStreamSynchronize(s));
+    if (st) *st = tmp;
+    if (!conv) {
+      ccg::g_last_error = "cc_solve_step: max_iters reached before the tolerance";
+      rc = CC_ERR_NOT_CONVERGED;
+    }
+    return rc;
+  } catch (const ccg::Fail& f) {
+    if (ccg::g_last_error.empty()) ccg::g_last_error = "cc_solve_step";
+    return f.st;
+  } catch (...) {
+    ccg::g_last_error = "cc_solve_step: unexpected error";
+    return CC_ERR_STATE;
+  }
+}
+
+cc_status cc_get_info(const cc_mesh* m, cc_mesh_info* info) {
+  CC_API_BODY("cc_get_info", {
+    CCG_CHECK(m && info, CC_ERR_INVALID_ARG, "NULL argument");
+    info->n = m->n;
+    info->T = m->T;
+    info->n_free = m->n_free;
+    info->nnz_blocks = m->nnzb;
+    info->num_colors = m->num_colors;
+    info->k_ring = m->k_ring;
+    info->support_total = (int64_t)m->sup_idx.size();
+    info->support_max = m->sup_max;
+    info->max_valence = m->max_valence;
+  })
+}
+
+cc_status cc_export(const cc_mesh* m, cc_array which, void* dst, int64_t cap, int64_t* count) {
+  CC_API_BODY("cc_export", {
+    CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    const void* src = nullptr;
+    int64_t len = 0;
+    size_t esz = 0;
+    std::vector<int64_t> tmp64;
+    switch (which) {
+      case CC_ARR_VT_PTR: src = m->vt_ptr.data(); len = (int64_t)m->vt_ptr.size(); esz = 8; break;
+      case CC_ARR_VT_TET: src = m->vt_tet.data(); len = (int64_t)m->vt_tet.size(); esz = 4; break;
+      case CC_ARR_VT_CORNER: src = m->vt_corner.data(); len = (int64_t)m->vt_corner.size(); esz = 4; break;
+      case CC_ARR_NBR_PTR: src = m->nbr_ptr.data(); len = (int64_t)m->nbr_ptr.size(); esz = 8; break;
+      case CC_ARR_NBR_IDX: src = m->nbr_idx.data(); len = (int64_t)m->nbr_idx.size(); esz = 4; break;
+      case CC_ARR_COLOR:
+        CCG_CHECK(m->num_colors > 0, CC_ERR_STATE, "not coloured yet");
+        src = m->color.data(); len = (int64_t)m->color.size(); esz = 4; break;
+      case CC_ARR_SUP_PTR:
+        CCG_CHECK(m->k_ring != 0, CC_ERR_STATE, "no subspace yet");
+        src = m->sup_ptr.data(); len = (int64_t)m->sup_ptr.size(); esz = 8; break;
+      case CC_ARR_SUP_IDX:
+        CCG_CHECK(m->k_ring != 0, CC_ERR_STATE, "no subspace yet");
+        src = m->sup_idx.data(); len = (int64_t)m->sup_idx.size(); esz = 4; break;
+      case CC_ARR_U:
+        CCG_CHECK(m->k_ring != 0, CC_ERR_STATE, "no subspace yet");
+        src = m->U.data(); len = (int64_t)m->U.size(); esz = 8; break;
+      case CC_ARR_MASS: src = m->mass.data(); len = (int64_t)m->mass.size(); esz = 8; break;
+      default: CCG_CHECK(false, CC_ERR_INVALID_ARG, "unknown array");
+    }
+    if (count) *count = len;
+    if (dst) {
+      CCG_CHECK(cap >= len, CC_ERR_INVALID_ARG, "destination too small");
+      if (len) std::memcpy(dst, src, (size_t)len * esz);
+    }
+  })
+}
+
+cc_status cc_profile_enable(cc_mesh* m, int32_t on) {
+  CC_API_BODY("cc_profile_enable", {
+    CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    CCG_CUDA(cudaStreamSynchronize(m->stream));
+    m->prof.on = on != 0;
+    m->prof.used = 0;
+    m->prof.mark_cls.clear();
+    m->prof.mark_begin.clear();
+    m->prof.mark_end.clear();
+    m->prof.mark_launches.clear();
+    m->prof.total_launches = 0;
+  })
+}
+
+cc_status cc_profile_read(cc_mesh* m, cc_profile* out) {
+  CC_API_BODY("cc_profile_read", {
+    CCG_CHECK(m && out, CC_ERR_INVALID_ARG, "NULL argument");
+    CCG_CUDA(cudaStreamSynchronize(m->stream));
+    std::memset(out, 0, sizeof(*out));
+    for (size_t k = 0; k < m->prof.mark_cls.size(); ++k) {
+      float ms = 0.f;
+      CCG_CUDA(cudaEventElapsedTime(&ms, m->prof.pool[m->prof.mark_begin[k]], m->prof.pool[m->prof.mark_end[k]]));
+      out->ms[m->prof.mark_cls[k]] += ms;
+      out->launches[m->prof.mark_cls[k]] += m->prof.mark_launches[k];
+    }
+    out->total_launches = m->prof.total_launches;
+    m->prof.used = 0;
+    m->prof.mark_cls.clear();
+    m->prof.mark_begin.clear();
+    m->prof.mark_end.clear();
+    m->prof.mark_launches.clear();
+    m->prof.total_launches = 0;
+  })
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Internal declarations of the GB300 Coordinate Condensation library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cc.h"
+
+namespace ccg {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+struct Fail {
+  cc_status st;
+};
+
+#define CCG_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::ccg::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+      throw ::ccg::Fail{e_ == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA};      \
+    }                                                                                      \
+  } while (0)
+
+#define CCG_CHECK(cond, status, msg)      \
+  do {                                    \
+    if (!(cond)) {                        \
+      ::ccg::set_error(msg);              \
+      throw ::ccg::Fail{status};          \
+    }                                     \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device buffers owned by a mesh
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t count = 0;
+  void alloc(size_t c) {
+    release();
+    if (c == 0) c = 1;
+    CCG_CUDA(cudaMalloc((void**)&p, c * sizeof(T)));
+    count = c;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    count = 0;
+  }
+  void upload(const T* h, size_t c, cudaStream_t s) {
+    alloc(c);
+    if (c) CCG_CUDA(cudaMemcpyAsync(p, h, c * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  template <typename V>
+  void upload(const std::vector<V>& v, cudaStream_t s) {
+    upload(reinterpret_cast<const T*>(v.data()), v.size() * sizeof(V) / sizeof(T), s);
+  }
+};
+
+// Per-precision solver state: per-(vertex, incident-tet) contributions, the
+// assembled gradient and 3x3-block Hessian, and the basis blocks.
+struct StateF64 {
+  DBuf<double> gcon;  // [4T][3]   gradient of tet at each (vertex, slot)
+  DBuf<double> hcon;  // [4T][4][9] Hessian row blocks of tet for that vertex
+  DBuf<double> g;     // [n][3]
+  DBuf<double> bsr;   // [nnzb][9]
+  DBuf<double> U;     // [sup_total][9]
+};
+
+struct StateMixed {
+  DBuf<float2> gcon;  // [4T][3]   float-float (hi, lo)
+  DBuf<float> hcon;   // [4T][4][9]
+  DBuf<float> g_hi;   // [n][3]
+  DBuf<float> g_lo;   // [n][3]
+  DBuf<float> bsr;    // [nnzb][9]
+  DBuf<float> U;      // [sup_total][9]
+  DBuf<float4> x_hi;  // [n] position mirror, float-float split
+  DBuf<float4> x_lo;
+  DBuf<float4> xt_hi; // inertial target mirror
+  DBuf<float4> xt_lo;
+};
+
+// Optional per-kernel-class event timing (cc_profile_*).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> mark_cls, mark_begin, mark_end, mark_launches;
+  int64_t total_launches = 0;
+};
+
+struct Mesh {
+  Prof prof;
+  int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
+  int32_t max_valence = 0;
+  double E = 0, nu = 0, rho = 0, mu = 0, lam_hat = 0, h = 0;
+  double grav[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+
+  // host copies (setup, export)
+  std::vector<double> X;       // [n][3]
+  std::vector<int32_t> tets;   // [T][4] positively oriented
+  std::vector<uint8_t> pinned; // [n]
+  std::vector<int64_t> vt_ptr;
+  std::vector<int32_t> vt_tet, vt_corner;
+  std::vector<int64_t> nbr_ptr;
+  std::vector<int32_t> nbr_idx;
+  std::vector<int64_t> bsr_ptr;
+  std::vector<int32_t> bsr_col;
+  std::vector<double> mass;
+  std::vector<int32_t> color;
+  int32_t num_colors = 0;
+  std::vector<int64_t> sup_ptr;
+  std::vector<int32_t> sup_idx;
+  std::vector<double> U;       // [sup_total][9]
+  int32_t k_ring = 0;
+  int32_t sup_max = 0;
+  int32_t hash_size = 0;       // power of two >= 2 * sup_max
+
+  // device rest data
+  DBuf<int4> d_tets;
+  DBuf<int4> d_tslot;        // [T] global (vertex, slot) entry of each corner
+  DBuf<double> d_Bm;         // [T][9] D_m^{-1}, row-major (row c = shape vector of corner c+1)
+  DBuf<float2> d_Bm_df;      // [T][9] float-float copy
+  DBuf<float> d_Bm32;        // [T][9]
+  DBuf<double> d_vol;        // [T]
+  DBuf<double> d_mass;       // [n]
+  DBuf<uint8_t> d_pinned;    // [n]
+  DBuf<int32_t> d_vt_ptr;    // [n+1]
+  DBuf<int32_t> d_nbr_ptr;   // [n+1]
+  DBuf<int32_t> d_nbr_idx;
+  DBuf<int32_t> d_bsr_ptr;   // [n+1]
+  DBuf<int32_t> d_bsr_col;   // [nnzb]
+  DBuf<int32_t> d_bsr_row;   // [nnzb]
+  DBuf<int32_t> d_blk_ptr;   // [nnzb+1] sources of each Hessian block
+  DBuf<int32_t> d_blk_src;   // [16T] entry * 4 + corner
+  DBuf<int32_t> d_free_rows; // free vertices, ascending
+  DBuf<int32_t> d_free_blocks; // Hessian blocks of free rows
+  int64_t n_free_blocks = 0;
+  DBuf<int32_t> d_color;     // [n]
+  std::vector<int32_t> cv_ptr;  // [C+1] free vertices per colour
+  DBuf<int32_t> d_cv_idx;
+  std::vector<int32_t> tl_ptr;  // [C+1] tets with a free vertex of colour c
+  DBuf<int32_t> d_tl;
+  DBuf<int32_t> d_all_tets;     // tets with at least one free vertex
+  int64_t n_active_tets = 0;
+  DBuf<int32_t> d_sup_ptr;   // [n+1]
+  DBuf<int32_t> d_sup_idx;
+
+  StateF64 f64;
+  StateMixed mx;
+
+  // scratch
+  DBuf<double> d_red;        // reduction partials
+  DBuf<double> d_scalars;    // [8]
+  DBuf<unsigned long long> d_counters; // [4] fallback counters + [4] error flags
+  DBuf<double> d_xtilde;     // [3][n] dynamic target (solve_step)
+  DBuf<double> d_xold;       // [3][n]
+  double* h_pinned_scalars = nullptr; // pinned host [8]
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_key = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Host-side helpers implemented in mesh_build.cpp (topology, plain C++)
+// ---------------------------------------------------------------------------
+void build_topology(Mesh& m);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels_*.cu)
+// ---------------------------------------------------------------------------
+struct SweepCounters {
+  unsigned long long* fallback;  // [3] empty, reduced, schur
+  unsigned long long* error;     // [1] non-finite update seen
+};
+
+// per-tet energy derivatives -> (vertex, slot) contributions
+void launch_tet_eval_f64(Mesh& m, const double* x, const int32_t* list, int64_t count,
+                         double weight, cudaStream_t s);
+void launch_tet_eval_mixed(Mesh& m, const int32_t* list, int64_t count, double weight,
+                           cudaStream_t s);
+// contributions -> gradient and Hessian blocks of the free rows
+void launch_gather_f64(Mesh& m, const double* x, const double* xt, cudaStream_t s);
+void launch_gather_mixed(Mesh& m, bool dynamic, cudaStream_t s);
+// local solves for a list of free vertices
+void launch_local_solve_f64(Mesh& m, cc_update upd, const int32_t* verts, int64_t count,
+                            double* x, SweepCounters c, cudaStream_t s);
+void launch_local_solve_mixed(Mesh& m, cc_update upd, const int32_t* verts, int64_t count,
+                              double* x, SweepCounters c, cudaStream_t s);
+// reductions
+void launch_energy(Mesh& m, const double* x, const double* xt, double* out_scalar,
+                   cudaStream_t s);
+void launch_gnorm_f64(Mesh& m, double* grad_out, double* out_scalar, cudaStream_t s);
+void launch_gnorm_mixed(Mesh& m, double* grad_out, double* out_scalar, cudaStream_t s);
+// mirrors and small vector ops
+void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStream_t s);
+void launch_inertial_target(const double* x, const double* v, int64_t n, double h,
+                            const double* grav, double* xt, cudaStream_t s);
+void launch_velocity(const double* x, const double* xold, int64_t n, double h, double* v,
+                     cudaStream_t s);
+// colouring and subspace build
+void run_coloring(Mesh& m);
+void run_subspace_build(Mesh& m, int32_t k);
+
+}  // namespace ccg

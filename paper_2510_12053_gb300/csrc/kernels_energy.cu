@@ -1,0 +1,507 @@
+// Per-tet stable Neo-Hookean derivatives, vertex gathers and reductions.
+//
+// Energy (Eq. 2): E = 1/2 (x - xt)^T M (x - xt) + w sum_t V_t Psi(F_t),
+// w = h^2 (dynamic) or 1 (quasistatic), F_t = D_s D_m^{-1}.
+// With C = cof F, J = det F, s = lam_hat (J - 1) - mu:
+//   P            = mu F + s C                                 (dPsi/dF)
+//   dE_t/dx_v    = w V P G_v
+//   d2E_t/dx_v dx_w = w V [ mu (G_v . G_w) I + lam_hat (C G_v)(C G_w)^T
+//                           + s [F (G_v x G_w)]_skew ]
+// where G_1..G_3 are the rows of D_m^{-1}, G_0 = -(G_1 + G_2 + G_3), and
+// [q]_skew[a][c] = sum_e eps_ace q_e (the contraction of d2J/dF2 with G_v, G_w).
+#include "cc_internal.cuh"
+#include "dmath.cuh"
+
+namespace ccg {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline unsigned grid_for(int64_t count, int block = kBlock) {
+  int64_t g = (count + block - 1) / block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---- float64 per-tet kinematics ------------------------------------------
+struct TetF64 {
+  double F[9], C[9], J, G[4][3];
+};
+
+__device__ __forceinline__ void tet_kinematics_f64(const double (&p)[4][3], const double* B, TetF64& k) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double e0 = p[1][a] - p[0][a], e1 = p[2][a] - p[0][a], e2 = p[3][a] - p[0][a];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) k.F[3 * a + b] = e0 * B[b] + e1 * B[3 + b] + e2 * B[6 + b];
+  }
+  // column b of C is (column b+1 of F) x (column b+2 of F)
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+    k.C[0 + b] = k.F[3 + b1] * k.F[6 + b2] - k.F[6 + b1] * k.F[3 + b2];
+    k.C[3 + b] = k.F[6 + b1] * k.F[0 + b2] - k.F[0 + b1] * k.F[6 + b2];
+    k.C[6 + b] = k.F[0 + b1] * k.F[3 + b2] - k.F[3 + b1] * k.F[0 + b2];
+  }
+  k.J = k.F[0] * k.C[0] + k.F[3] * k.C[3] + k.F[6] * k.C[6];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    k.G[1][b] = B[b];
+    k.G[2][b] = B[3 + b];
+    k.G[3][b] = B[6 + b];
+    k.G[0][b] = -(B[b] + B[3 + b] + B[6 + b]);
+  }
+}
+
+// Hessian block (v, w) without the w V factor.
+template <typename T>
+__device__ __forceinline__ void hess_block(const T* F, const T (&a_v)[3], const T (&a_w)[3],
+                                           const T* Gv, const T* Gw, T mu, T lh, T s, T* K) {
+  T gg = Gv[0] * Gw[0] + Gv[1] * Gw[1] + Gv[2] * Gw[2];
+  T cr0 = Gv[1] * Gw[2] - Gv[2] * Gw[1];
+  T cr1 = Gv[2] * Gw[0] - Gv[0] * Gw[2];
+  T cr2 = Gv[0] * Gw[1] - Gv[1] * Gw[0];
+  T q0 = F[0] * cr0 + F[1] * cr1 + F[2] * cr2;
+  T q1 = F[3] * cr0 + F[4] * cr1 + F[5] * cr2;
+  T q2 = F[6] * cr0 + F[7] * cr1 + F[8] * cr2;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) K[3 * r + c] = lh * a_v[r] * a_w[c];
+  K[0] += mu * gg;
+  K[4] += mu * gg;
+  K[8] += mu * gg;
+  K[1] += s * q2;
+  K[2] -= s * q1;
+  K[3] -= s * q2;
+  K[5] += s * q0;
+  K[6] += s * q1;
+  K[7] -= s * q0;
+}
+
+__global__ void k_tet_eval_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                               const double* __restrict__ Bm, const double* __restrict__ vol,
+                               const uint8_t* __restrict__ pinned, const double* __restrict__ x,
+                               int64_t n, const int32_t* __restrict__ list, int64_t count, double mu,
+                               double lh, double weight, double* __restrict__ gcon,
+                               double* __restrict__ hcon) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int t = list[k];
+  const int4 tv = tets[t], ts = tslot[t];
+  const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+  const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
+  double p[4][3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[v][a] = x[a * n + vid[v]];
+  double B[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) B[q] = Bm[9 * (int64_t)t + q];
+  TetF64 kin;
+  tet_kinematics_f64(p, B, kin);
+  const double s = lh * (kin.J - 1.0) - mu;
+  const double V = vol[t] * weight;
+  double P[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) P[q] = mu * kin.F[q] + s * kin.C[q];
+  double a[4][3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      a[v][r] = kin.C[3 * r] * kin.G[v][0] + kin.C[3 * r + 1] * kin.G[v][1] + kin.C[3 * r + 2] * kin.G[v][2];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    if (pinned[vid[v]]) continue;
+    const int64_t e = ent[v];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      gcon[3 * e + r] = V * (P[3 * r] * kin.G[v][0] + P[3 * r + 1] * kin.G[v][1] + P[3 * r + 2] * kin.G[v][2]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      double K[9];
+      hess_block<double>(kin.F, a[v], a[w], kin.G[v], kin.G[w], mu, lh, s, K);
+      double* dst = hcon + (4 * e + w) * 9;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) dst[q] = V * K[q];
+    }
+  }
+}
+
+// ---- mixed: float-float gradient, float32 Hessian -------------------------
+__global__ void k_tet_eval_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                                 const float2* __restrict__ Bm_df, const double* __restrict__ vol,
+                                 const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
+                                 const float4* __restrict__ x_lo, const int32_t* __restrict__ list,
+                                 int64_t count, float mu_f, float lh_f, df mu_d, df lh_d, double weight,
+                                 float2* __restrict__ gcon, float* __restrict__ hcon) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int t = list[k];
+  const int4 tv = tets[t], ts = tslot[t];
+  const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+  const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
+  df p[4][3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float4 h = x_hi[vid[v]], l = x_lo[vid[v]];
+    p[v][0] = df{h.x, l.x};
+    p[v][1] = df{h.y, l.y};
+    p[v][2] = df{h.z, l.z};
+  }
+  df B[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    float2 b = Bm_df[9 * (int64_t)t + q];
+    B[q] = df{b.x, b.y};
+  }
+  // F = D_s D_m^{-1} in float-float
+  df F[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    df e0 = df_sub(p[1][a], p[0][a]), e1 = df_sub(p[2][a], p[0][a]), e2 = df_sub(p[3][a], p[0][a]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) F[3 * a + b] = df_fma(e2, B[6 + b], df_fma(e1, B[3 + b], df_mul(e0, B[b])));
+  }
+  df C[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+    C[0 + b] = df_sub(df_mul(F[3 + b1], F[6 + b2]), df_mul(F[6 + b1], F[3 + b2]));
+    C[3 + b] = df_sub(df_mul(F[6 + b1], F[0 + b2]), df_mul(F[0 + b1], F[6 + b2]));
+    C[6 + b] = df_sub(df_mul(F[0 + b1], F[3 + b2]), df_mul(F[3 + b1], F[0 + b2]));
+  }
+  df J = df_fma(F[6], C[6], df_fma(F[3], C[3], df_mul(F[0], C[0])));
+  df Jm1 = df_add(J, df{-1.0f, 0.0f});
+  df s = df_sub(df_mul(lh_d, Jm1), mu_d);
+  const double Vd = vol[t] * weight;
+  const df V = df_from_double(Vd);
+  df P[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) P[q] = df_mul(V, df_fma(mu_d, F[q], df_mul(s, C[q])));
+  // gradient rows for corners 1..3 (G = rows of B); corner 0 = minus their sum
+  df g[4][3];
+#pragma unroll
+  for (int v = 1; v < 4; ++v)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      g[v][r] = df_fma(P[3 * r + 2], B[3 * (v - 1) + 2],
+                       df_fma(P[3 * r + 1], B[3 * (v - 1) + 1], df_mul(P[3 * r], B[3 * (v - 1)])));
+#pragma unroll
+  for (int r = 0; r < 3; ++r) g[0][r] = df_neg(df_add(df_add(g[1][r], g[2][r]), g[3][r]));
+
+  // float32 Hessian from the high parts
+  float Ff[9], Cf[9], G[4][3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    Ff[q] = F[q].hi;
+    Cf[q] = C[q].hi;
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    G[1][b] = B[b].hi;
+    G[2][b] = B[3 + b].hi;
+    G[3][b] = B[6 + b].hi;
+    G[0][b] = -(G[1][b] + G[2][b] + G[3][b]);
+  }
+  const float sf = s.hi;
+  const float Vf = (float)Vd;
+  float a[4][3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) a[v][r] = Cf[3 * r] * G[v][0] + Cf[3 * r + 1] * G[v][1] + Cf[3 * r + 2] * G[v][2];
+
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    if (pinned[vid[v]]) continue;
+    const int64_t e = ent[v];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) gcon[3 * e + r] = make_float2(g[v][r].hi, g[v][r].lo);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      float K[9];
+      hess_block<float>(Ff, a[v], a[w], G[v], G[w], mu_f, lh_f, sf, K);
+      float* dst = hcon + (4 * e + w) * 9;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) dst[q] = Vf * K[q];
+    }
+  }
+}
+
+// ---- gathers ---------------------------------------------------------------
+// Threads [0, nfb) sum the sources of one Hessian block of a free row;
+// threads [nfb, nfb + nfree) sum the gradient of one free vertex.
+template <typename HT>
+__global__ void k_gather_hess(const int32_t* __restrict__ free_blocks, int64_t nfb,
+                              const int32_t* __restrict__ blk_ptr, const int32_t* __restrict__ blk_src,
+                              const HT* __restrict__ hcon, const int32_t* __restrict__ bsr_row,
+                              const int32_t* __restrict__ bsr_col, const double* __restrict__ mass,
+                              bool dynamic, HT* __restrict__ bsr) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nfb) return;
+  const int b = free_blocks[k];
+  HT acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = HT(0);
+  const int s1 = blk_ptr[b + 1];
+  for (int s = blk_ptr[b]; s < s1; ++s) {
+    const HT* src = hcon + (int64_t)blk_src[s] * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] += src[q];
+  }
+  if (dynamic) {
+    const int r = bsr_row[b];
+    if (r == bsr_col[b]) {
+      HT m = (HT)mass[r];
+      acc[0] += m;
+      acc[4] += m;
+      acc[8] += m;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) bsr[(int64_t)b * 9 + q] = acc[q];
+}
+
+__global__ void k_gather_grad_f64(const int32_t* __restrict__ free_rows, int64_t nfree,
+                                  const int32_t* __restrict__ vt_ptr, const double* __restrict__ gcon,
+                                  const double* __restrict__ mass, const double* __restrict__ x,
+                                  const double* __restrict__ xt, int64_t n, double* __restrict__ g) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nfree) return;
+  const int j = free_rows[k];
+  double acc[3] = {0, 0, 0};
+  for (int e = vt_ptr[j]; e < vt_ptr[j + 1]; ++e) {
+    acc[0] += gcon[3 * (int64_t)e];
+    acc[1] += gcon[3 * (int64_t)e + 1];
+    acc[2] += gcon[3 * (int64_t)e + 2];
+  }
+  if (xt) {
+    const double m = mass[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[a] += m * (x[a * n + j] - xt[a * n + j]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[3 * (int64_t)j + a] = acc[a];
+}
+
+__global__ void k_gather_grad_mixed(const int32_t* __restrict__ free_rows, int64_t nfree,
+                                    const int32_t* __restrict__ vt_ptr, const float2* __restrict__ gcon,
+                                    const double* __restrict__ mass, const float4* __restrict__ x_hi,
+                                    const float4* __restrict__ x_lo, const float4* __restrict__ xt_hi,
+                                    const float4* __restrict__ xt_lo, bool dynamic,
+                                    float* __restrict__ g_hi, float* __restrict__ g_lo) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nfree) return;
+  const int j = free_rows[k];
+  df acc[3] = {df{0, 0}, df{0, 0}, df{0, 0}};
+  for (int e = vt_ptr[j]; e < vt_ptr[j + 1]; ++e) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 c = gcon[3 * (int64_t)e + a];
+      acc[a] = df_add(acc[a], df{c.x, c.y});
+    }
+  }
+  if (dynamic) {
+    const df m = df_from_double(mass[j]);
+    const float4 xh = x_hi[j], xl = x_lo[j], th = xt_hi[j], tl = xt_lo[j];
+    acc[0] = df_fma(m, df_sub(df{xh.x, xl.x}, df{th.x, tl.x}), acc[0]);
+    acc[1] = df_fma(m, df_sub(df{xh.y, xl.y}, df{th.y, tl.y}), acc[1]);
+    acc[2] = df_fma(m, df_sub(df{xh.z, xl.z}, df{th.z, tl.z}), acc[2]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g_hi[3 * (int64_t)j + a] = acc[a].hi;
+    g_lo[3 * (int64_t)j + a] = acc[a].lo;
+  }
+}
+
+// ---- reductions --------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;
+}
+
+// Stage 2: sums `count` partials in a fixed order, out[0] = result.
+__global__ void k_reduce_final(const double* __restrict__ part, int64_t count, double* __restrict__ out) {
+  double v = 0.0;
+  for (int64_t k = threadIdx.x; k < count; k += blockDim.x) v += part[k];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[0] = v;
+}
+
+__global__ void k_energy_tets(const int4* __restrict__ tets, const double* __restrict__ Bm,
+                              const double* __restrict__ vol, const double* __restrict__ x, int64_t n,
+                              int64_t T, double mu, double lh, double weight, double* __restrict__ part) {
+  double e = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 tv = tets[t];
+    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+    double p[4][3];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p[v][a] = x[a * n + vid[v]];
+    double B[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) B[q] = Bm[9 * t + q];
+    TetF64 kin;
+    tet_kinematics_f64(p, B, kin);
+    double I = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) I += kin.F[q] * kin.F[q];
+    const double Jm1 = kin.J - 1.0;
+    e += weight * vol[t] * (0.5 * mu * (I - 3.0) - mu * Jm1 + 0.5 * lh * Jm1 * Jm1);
+  }
+  e = block_sum(e);
+  if (threadIdx.x == 0) part[blockIdx.x] = e;
+}
+
+__global__ void k_energy_inertia(const double* __restrict__ mass, const double* __restrict__ x,
+                                 const double* __restrict__ xt, int64_t n, double* __restrict__ part) {
+  double e = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double d0 = x[j] - xt[j], d1 = x[n + j] - xt[n + j], d2 = x[2 * n + j] - xt[2 * n + j];
+    e += 0.5 * mass[j] * (d0 * d0 + d1 * d1 + d2 * d2);
+  }
+  e = block_sum(e);
+  if (threadIdx.x == 0) part[blockIdx.x] = e;
+}
+
+template <bool kMixed>
+__global__ void k_gnorm(const int32_t* __restrict__ free_rows, int64_t nfree, const double* __restrict__ g64,
+                        const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
+                        double* __restrict__ grad_out, double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nfree; k += (int64_t)gridDim.x * blockDim.x) {
+    const int j = free_rows[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = kMixed ? (double)g_hi[3 * (int64_t)j + a] + (double)g_lo[3 * (int64_t)j + a]
+                        : g64[3 * (int64_t)j + a];
+      acc += v * v;
+      if (grad_out) grad_out[a * n + j] = v;
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_split_df(const double* __restrict__ x, int64_t n, float4* __restrict__ hi,
+                           float4* __restrict__ lo) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  df a = df_from_double(x[j]), b = df_from_double(x[n + j]), c = df_from_double(x[2 * n + j]);
+  hi[j] = make_float4(a.hi, b.hi, c.hi, 0.f);
+  lo[j] = make_float4(a.lo, b.lo, c.lo, 0.f);
+}
+
+__global__ void k_inertial_target(const double* __restrict__ x, const double* __restrict__ v, int64_t n,
+                                  double h, double g0, double g1, double g2, double* __restrict__ xt) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double gg[3] = {g0, g1, g2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) xt[a * n + j] = x[a * n + j] + h * v[a * n + j] + h * h * gg[a];
+}
+
+__global__ void k_velocity(const double* __restrict__ x, const double* __restrict__ xold, int64_t n, double h,
+                           double* __restrict__ v) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= 3 * n) return;
+  v[k] = (x[k] - xold[k]) / h;
+}
+
+constexpr int kRedBlocks = 1024;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+void launch_tet_eval_f64(Mesh& m, const double* x, const int32_t* list, int64_t count, double weight,
+                         cudaStream_t s) {
+  if (count <= 0) return;
+  k_tet_eval_f64<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x,
+                                                    m.n, list, count, m.mu, m.lam_hat, weight, m.f64.gcon.p,
+                                                    m.f64.hcon.p);
+}
+
+void launch_tet_eval_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
+  if (count <= 0) return;
+  df mu_d{(float)m.mu, (float)(m.mu - (double)(float)m.mu)};
+  df lh_d{(float)m.lam_hat, (float)(m.lam_hat - (double)(float)m.lam_hat)};
+  k_tet_eval_mixed<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_vol.p,
+                                                      m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count,
+                                                      (float)m.mu, (float)m.lam_hat, mu_d, lh_d, weight,
+                                                      m.mx.gcon.p, m.mx.hcon.p);
+}
+
+void launch_gather_f64(Mesh& m, const double* x, const double* xt, cudaStream_t s) {
+  const bool dyn = m.h > 0.0;
+  k_gather_hess<double><<<grid_for(m.n_free_blocks), kBlock, 0, s>>>(
+      m.d_free_blocks.p, m.n_free_blocks, m.d_blk_ptr.p, m.d_blk_src.p, m.f64.hcon.p, m.d_bsr_row.p, m.d_bsr_col.p,
+      m.d_mass.p, dyn, m.f64.bsr.p);
+  k_gather_grad_f64<<<grid_for(m.n_free), kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.f64.gcon.p,
+                                                          m.d_mass.p, x, dyn ? xt : nullptr, m.n, m.f64.g.p);
+}
+
+void launch_gather_mixed(Mesh& m, bool dynamic, cudaStream_t s) {
+  k_gather_hess<float><<<grid_for(m.n_free_blocks), kBlock, 0, s>>>(
+      m.d_free_blocks.p, m.n_free_blocks, m.d_blk_ptr.p, m.d_blk_src.p, m.mx.hcon.p, m.d_bsr_row.p, m.d_bsr_col.p,
+      m.d_mass.p, dynamic, m.mx.bsr.p);
+  k_gather_grad_mixed<<<grid_for(m.n_free), kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.mx.gcon.p,
+                                                            m.d_mass.p, m.mx.x_hi.p, m.mx.x_lo.p, m.mx.xt_hi.p,
+                                                            m.mx.xt_lo.p, dynamic, m.mx.g_hi.p, m.mx.g_lo.p);
+}
+
+void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {
+  const double w = m.h > 0.0 ? m.h * m.h : 1.0;
+  k_energy_tets<<<kRedBlocks, kBlock, 0, s>>>(m.d_tets.p, m.d_Bm.p, m.d_vol.p, x, m.n, m.T, m.mu, m.lam_hat, w,
+                                              m.d_red.p);
+  if (m.h > 0.0 && xt) {
+    k_energy_inertia<<<kRedBlocks, kBlock, 0, s>>>(m.d_mass.p, x, xt, m.n, m.d_red.p + kRedBlocks);
+    k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, 2 * kRedBlocks, out);
+  } else {
+    k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+  }
+}
+
+void launch_gnorm_f64(Mesh& m, double* grad_out, double* out, cudaStream_t s) {
+  k_gnorm<false><<<kRedBlocks, kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, m.f64.g.p, nullptr, nullptr, m.n, grad_out,
+                                               m.d_red.p);
+  k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+}
+
+void launch_gnorm_mixed(Mesh& m, double* grad_out, double* out, cudaStream_t s) {
+  k_gnorm<true><<<kRedBlocks, kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, m.n,
+                                              grad_out, m.d_red.p);
+  k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+}
+
+void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStream_t s) {
+  k_split_df<<<grid_for(n), kBlock, 0, s>>>(x, n, hi, lo);
+}
+
+void launch_inertial_target(const double* x, const double* v, int64_t n, double h, const double* grav, double* xt,
+                            cudaStream_t s) {
+  k_inertial_target<<<grid_for(n), kBlock, 0, s>>>(x, v, n, h, grav[0], grav[1], grav[2], xt);
+}
+
+void launch_velocity(const double* x, const double* xold, int64_t n, double h, double* v, cudaStream_t s) {
+  k_velocity<<<grid_for(3 * n), kBlock, 0, s>>>(x, xold, n, h, v);
+}
+
+}  // namespace ccg

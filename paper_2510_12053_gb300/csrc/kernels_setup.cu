@@ -1,0 +1,292 @@
+// Setup kernels: greedy colouring of the 1-ring graph and the perturbation
+// bases U_i = -H_PP^{-1} H_Pi (Eq. 5 on the patch P = S_i, Sec. 3.1).
+#include <algorithm>
+#include <vector>
+
+#include "cc_internal.cuh"
+#include "dmath.cuh"
+
+namespace ccg {
+
+namespace {
+
+// One Jones-Plassmann round with index priority: an uncoloured vertex whose
+// lower-id neighbours are all coloured takes the smallest colour none of them
+// uses.  Higher-id neighbours cannot be coloured before it, so the result is
+// exactly sequential greedy colouring in ascending id.
+__global__ void k_color_round(int64_t n, const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                              int32_t* color, int32_t* changed) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  volatile int32_t* col = color;
+  if (col[v] >= 0) return;
+  const int p0 = nbr_ptr[v], p1 = nbr_ptr[v + 1];
+  unsigned long long used = 0ull;
+  bool big = false;
+  for (int p = p0; p < p1; ++p) {
+    const int u = nbr_idx[p];
+    if (u >= v) break;  // neighbours are ascending
+    const int cu = col[u];
+    if (cu < 0) return;  // not ready this round
+    if (cu < 64) used |= 1ull << cu;
+    else big = true;
+  }
+  int c;
+  if (!big) {
+    c = __ffsll((long long)~used) - 1;
+    if (c < 0) big = true;
+  }
+  if (big) {
+    for (c = 0;; ++c) {
+      bool taken = false;
+      for (int p = p0; p < p1; ++p) {
+        const int u = nbr_idx[p];
+        if (u >= v) break;
+        if (col[u] == c) { taken = true; break; }
+      }
+      if (!taken) break;
+    }
+  }
+  col[v] = c;
+  *changed = 1;
+}
+
+__device__ __forceinline__ int find_sorted(const int32_t* a, int m, int key) {
+  int lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int v = a[mid];
+    if (v == key) return mid;
+    if (v < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// One CTA per free vertex of the batch.  A (column-major, N x N, N = 3m) and
+// the right-hand sides R (column-major N x 3) live in the CTA's slice of
+// scratch.  Writes U[(s0 + a) * 9 + 3 r + d] = z[3a + r][d] with H_PP z = -H_Pi.
+__global__ void k_patch_basis(const int32_t* __restrict__ verts, const int32_t* __restrict__ sup_ptr,
+                              const int32_t* __restrict__ sup_idx, const int32_t* __restrict__ bsr_ptr,
+                              const int32_t* __restrict__ bsr_col, const double* __restrict__ bsr, int Nmax,
+                              double* __restrict__ scratch, double* __restrict__ Uout, int32_t* __restrict__ fail) {
+  const int i = verts[blockIdx.x];
+  const int s0 = sup_ptr[i], m = sup_ptr[i + 1] - s0;
+  const int N = 3 * m;
+  if (m == 0) return;
+  double* A = scratch + (size_t)blockIdx.x * ((size_t)Nmax * Nmax + 3 * (size_t)Nmax);
+  double* R = A + (size_t)Nmax * Nmax;
+  const int32_t* S = sup_idx + s0;
+  for (int64_t k = threadIdx.x; k < (int64_t)N * N; k += blockDim.x) A[k] = 0.0;
+  for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) R[k] = 0.0;
+  __syncthreads();
+  // assemble H_PP and -H_Pi from the block rows of the support vertices
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    const int j = S[a];
+    for (int p = bsr_ptr[j]; p < bsr_ptr[j + 1]; ++p) {
+      const int l = bsr_col[p];
+      const double* Hb = bsr + (int64_t)p * 9;
+      if (l == i) {
+        for (int r = 0; r < 3; ++r)
+          for (int d = 0; d < 3; ++d) R[d * N + 3 * a + r] = -Hb[3 * r + d];
+      } else {
+        const int t = find_sorted(S, m, l);
+        if (t >= 0)
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[(size_t)(3 * t + c) * N + 3 * a + r] = Hb[3 * r + c];
+      }
+    }
+  }
+  __syncthreads();
+  // right-looking Cholesky, lower triangle, column-major
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int c = 0; c < N; ++c) {
+    if (threadIdx.x == 0) {
+      const double d = A[(size_t)c * N + c];
+      if (!(d > 0.0)) bad = 1;
+      A[(size_t)c * N + c] = sqrt(fmax(d, 1e-300));
+    }
+    __syncthreads();
+    const double piv = A[(size_t)c * N + c];
+    for (int r = c + 1 + threadIdx.x; r < N; r += blockDim.x) A[(size_t)c * N + r] /= piv;
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < N; r += blockDim.x) {
+      const double lrc = A[(size_t)c * N + r];
+      for (int s = c + 1; s <= r; ++s) A[(size_t)s * N + r] -= lrc * A[(size_t)c * N + s];
+    }
+    __syncthreads();
+  }
+  // forward substitution L y = R, then L^T z = y (3 columns)
+  for (int c = 0; c < N; ++c) {
+    if (threadIdx.x < 3) R[threadIdx.x * N + c] /= A[(size_t)c * N + c];
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * (N - c - 1); k += blockDim.x) {
+      const int d = k / (N - c - 1), r = c + 1 + k % (N - c - 1);
+      R[d * N + r] -= A[(size_t)c * N + r] * R[d * N + c];
+    }
+    __syncthreads();
+  }
+  for (int c = N - 1; c >= 0; --c) {
+    if (threadIdx.x < 3) R[threadIdx.x * N + c] /= A[(size_t)c * N + c];
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * c; k += blockDim.x) {
+      const int d = k / c, r = k % c;
+      R[d * N + r] -= A[(size_t)r * N + c] * R[d * N + c];
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < 9 * m; k += blockDim.x) {
+    const int a = k / 9, q = k % 9, r = q / 3, d = q % 3;
+    Uout[(int64_t)(s0 + a) * 9 + q] = R[d * N + 3 * a + r];
+  }
+  if (threadIdx.x == 0 && bad) atomicAdd(fail, 1);
+}
+
+}  // namespace
+
+void run_coloring(Mesh& m) {
+  cudaStream_t s = m.stream;
+  DBuf<int32_t> changed;
+  changed.alloc(1);
+  m.d_color.alloc(m.n);
+  CCG_CUDA(cudaMemsetAsync(m.d_color.p, 0xff, m.n * sizeof(int32_t), s));
+  int32_t* h_changed = nullptr;
+  CCG_CUDA(cudaMallocHost((void**)&h_changed, sizeof(int32_t)));
+  const unsigned grid = (unsigned)((m.n + 255) / 256);
+  int64_t rounds = 0;
+  try {
+    while (true) {
+      CCG_CUDA(cudaMemsetAsync(changed.p, 0, sizeof(int32_t), s));
+      k_color_round<<<grid, 256, 0, s>>>(m.n, m.d_nbr_ptr.p, m.d_nbr_idx.p, m.d_color.p, changed.p);
+      CCG_CUDA(cudaGetLastError());
+      CCG_CUDA(cudaMemcpyAsync(h_changed, changed.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CCG_CUDA(cudaStreamSynchronize(s));
+      if (*h_changed == 0) break;
+      CCG_CHECK(++rounds <= m.n, CC_ERR_STATE, "colouring did not terminate");
+    }
+  } catch (...) {
+    cudaFreeHost(h_changed);
+    throw;
+  }
+  cudaFreeHost(h_changed);
+  m.color.assign(m.n, -1);
+  CCG_CUDA(cudaMemcpy(m.color.data(), m.d_color.p, m.n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  int32_t C = 0;
+  for (int64_t v = 0; v < m.n; ++v) {
+    CCG_CHECK(m.color[v] >= 0, CC_ERR_STATE, "colouring left a vertex uncoloured");
+    C = std::max(C, m.color[v] + 1);
+  }
+  m.num_colors = C;
+  // free vertices per colour (ascending) and tets whose free vertex of colour c moves
+  m.cv_ptr.assign(C + 1, 0);
+  std::vector<std::vector<int32_t>> cv(C), tl(C);
+  for (int64_t v = 0; v < m.n; ++v)
+    if (!m.pinned[v]) cv[m.color[v]].push_back((int32_t)v);
+  for (int64_t t = 0; t < m.T; ++t)
+    for (int c = 0; c < 4; ++c) {
+      const int32_t v = m.tets[4 * t + c];
+      if (!m.pinned[v]) tl[m.color[v]].push_back((int32_t)t);
+    }
+  std::vector<int32_t> cv_flat, tl_flat;
+  m.tl_ptr.assign(C + 1, 0);
+  for (int c = 0; c < C; ++c) {
+    cv_flat.insert(cv_flat.end(), cv[c].begin(), cv[c].end());
+    m.cv_ptr[c + 1] = (int32_t)cv_flat.size();
+    std::sort(tl[c].begin(), tl[c].end());
+    tl_flat.insert(tl_flat.end(), tl[c].begin(), tl[c].end());
+    m.tl_ptr[c + 1] = (int32_t)tl_flat.size();
+  }
+  m.d_cv_idx.upload(cv_flat, s);
+  m.d_tl.upload(tl_flat, s);
+  CCG_CUDA(cudaStreamSynchronize(s));
+}
+
+// k-ring supports on the host (breadth-first over the 1-ring CSR), then the
+// rest Hessian and one dense Cholesky per patch on the GPU.
+void run_subspace_build(Mesh& m, int32_t k) {
+  cudaStream_t s = m.stream;
+  const int64_t n = m.n;
+  m.sup_ptr.assign(n + 1, 0);
+  m.sup_idx.clear();
+  std::vector<int32_t> stamp(n, -1), ring, frontier, next;
+  int32_t supmax = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    if (!m.pinned[v]) {
+      ring.clear();
+      frontier.assign(1, (int32_t)v);
+      stamp[v] = (int32_t)v;
+      for (int hop = 0; hop < k; ++hop) {
+        next.clear();
+        for (int32_t a : frontier)
+          for (int64_t p = m.nbr_ptr[a]; p < m.nbr_ptr[a + 1]; ++p) {
+            const int32_t b = m.nbr_idx[p];
+            if (stamp[b] != (int32_t)v) {
+              stamp[b] = (int32_t)v;
+              next.push_back(b);
+              if (!m.pinned[b]) ring.push_back(b);
+            }
+          }
+        frontier.swap(next);
+      }
+      std::sort(ring.begin(), ring.end());
+      m.sup_idx.insert(m.sup_idx.end(), ring.begin(), ring.end());
+      supmax = std::max<int32_t>(supmax, (int32_t)ring.size());
+    }
+    m.sup_ptr[v + 1] = (int64_t)m.sup_idx.size();
+  }
+  CCG_CHECK(m.sup_idx.size() < (size_t(1) << 31), CC_ERR_INVALID_ARG, "support arrays exceed 2^31 entries");
+  CCG_CHECK(supmax < 32768, CC_ERR_INVALID_ARG, "support larger than 32767 vertices");
+  m.sup_max = supmax;
+  int hs = 32;
+  while (hs < 2 * std::max(supmax, 1)) hs <<= 1;
+  m.hash_size = hs;
+  m.k_ring = k;
+  std::vector<int32_t> sp32(n + 1);
+  for (int64_t v = 0; v <= n; ++v) sp32[v] = (int32_t)m.sup_ptr[v];
+  m.d_sup_ptr.upload(sp32, s);
+  m.d_sup_idx.upload(m.sup_idx, s);
+
+  // rest Hessian in float64 (dynamic meshes: M + h^2 K)
+  const int64_t total = (int64_t)m.sup_idx.size();
+  DBuf<double> Xs;
+  {
+    std::vector<double> soa(3 * n);
+    for (int64_t j = 0; j < n; ++j)
+      for (int a = 0; a < 3; ++a) soa[a * n + j] = m.X[3 * j + a];
+    Xs.upload(soa, s);
+    const double w = m.h > 0.0 ? m.h * m.h : 1.0;
+    launch_tet_eval_f64(m, Xs.p, m.d_all_tets.p, m.n_active_tets, w, s);
+    launch_gather_f64(m, Xs.p, Xs.p, s);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
+  m.f64.U.alloc(9 * std::max<int64_t>(total, 1));
+  const int Nmax = 3 * std::max(supmax, 1);
+  const size_t per = (size_t)Nmax * Nmax + 3 * (size_t)Nmax;
+  int64_t batch = std::max<int64_t>(1, (int64_t)((size_t(1) << 30) / (per * sizeof(double))));
+  batch = std::min<int64_t>(batch, m.n_free);
+  DBuf<double> scratch;
+  scratch.alloc(per * std::max<int64_t>(batch, 1));
+  DBuf<int32_t> fail;
+  fail.alloc(1);
+  CCG_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int32_t), s));
+  for (int64_t b0 = 0; b0 < m.n_free; b0 += batch) {
+    const int64_t cnt = std::min<int64_t>(batch, m.n_free - b0);
+    k_patch_basis<<<(unsigned)cnt, 256, 0, s>>>(m.d_free_rows.p + b0, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_bsr_ptr.p,
+                                                 m.d_bsr_col.p, m.f64.bsr.p, Nmax, scratch.p, m.f64.U.p, fail.p);
+    CCG_CUDA(cudaGetLastError());
+  }
+  int32_t nfail = 0;
+  CCG_CUDA(cudaMemcpyAsync(&nfail, fail.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaStreamSynchronize(s));
+  CCG_CHECK(nfail == 0, CC_ERR_NUMERIC, "a patch Hessian was not positive definite");
+  m.U.assign(9 * total, 0.0);
+  if (total) CCG_CUDA(cudaMemcpy(m.U.data(), m.f64.U.p, 9 * total * sizeof(double), cudaMemcpyDeviceToHost));
+  std::vector<float> u32(9 * std::max<int64_t>(total, 1), 0.f);
+  for (int64_t q = 0; q < 9 * total; ++q) u32[q] = (float)m.U[q];
+  m.mx.U.upload(u32, s);
+  CCG_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace ccg

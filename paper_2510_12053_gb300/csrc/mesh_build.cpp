@@ -1,0 +1,196 @@
+// Rest-state preprocessing of a tet mesh on the host: orientation, shape
+// matrices, volumes, lumped masses and every adjacency structure the kernels
+// index with.  Integer outputs follow fixed orders (ascending ids) so that
+// they can be compared bit for bit with an independent implementation.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "cc_internal.cuh"
+
+namespace ccg {
+
+static void inverse3(const double* A, double* inv, double* det) {
+  double c00 = A[4] * A[8] - A[5] * A[7];
+  double c01 = A[5] * A[6] - A[3] * A[8];
+  double c02 = A[3] * A[7] - A[4] * A[6];
+  double d = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  *det = d;
+  double id = 1.0 / d;
+  inv[0] = c00 * id;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+  inv[3] = c01 * id;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+  inv[6] = c02 * id;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+}
+
+// D_m columns are X_{c+1} - X_0; returns det(D_m).
+static double rest_matrix(const std::vector<double>& X, const int32_t* t, double* Dm) {
+  for (int c = 0; c < 3; ++c)
+    for (int a = 0; a < 3; ++a) Dm[3 * a + c] = X[3 * t[c + 1] + a] - X[3 * t[0] + a];
+  return Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+         Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+}
+
+void build_topology(Mesh& m) {
+  const int64_t n = m.n, T = m.T;
+  cudaStream_t s = m.stream;
+  CCG_CHECK(4 * T < (int64_t(1) << 31) / 4, CC_ERR_INVALID_ARG, "mesh too large for 32-bit entry indices");
+
+  // ---- orientation, shape matrices, volumes, masses
+  std::vector<double> Bm(9 * T), vol(T);
+  m.mass.assign(n, 0.0);
+  for (int64_t t = 0; t < T; ++t) {
+    int32_t* tv = &m.tets[4 * t];
+    for (int c = 0; c < 4; ++c)
+      CCG_CHECK(tv[c] >= 0 && tv[c] < n, CC_ERR_INVALID_ARG, "tet vertex id out of range");
+    double Dm[9];
+    double det = rest_matrix(m.X, tv, Dm);
+    if (det < 0) {
+      std::swap(tv[1], tv[2]);
+      det = rest_matrix(m.X, tv, Dm);
+    }
+    CCG_CHECK(det > 0 && std::isfinite(det), CC_ERR_INVALID_ARG, "degenerate (zero-volume) tet");
+    double inv[9], d2;
+    inverse3(Dm, inv, &d2);
+    std::memcpy(&Bm[9 * t], inv, sizeof(inv));
+    vol[t] = det / 6.0;
+    for (int c = 0; c < 4; ++c) m.mass[tv[c]] += m.rho * vol[t] / 4.0;
+  }
+
+  // ---- vertex -> tet lists (ascending tet id) and the entry of every corner
+  m.vt_ptr.assign(n + 1, 0);
+  for (int64_t t = 0; t < T; ++t)
+    for (int c = 0; c < 4; ++c) m.vt_ptr[m.tets[4 * t + c] + 1]++;
+  for (int64_t v = 0; v < n; ++v) m.vt_ptr[v + 1] += m.vt_ptr[v];
+  m.vt_tet.assign(4 * T, 0);
+  m.vt_corner.assign(4 * T, 0);
+  std::vector<int32_t> tslot(4 * T);
+  {
+    std::vector<int64_t> cur(m.vt_ptr.begin(), m.vt_ptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int c = 0; c < 4; ++c) {
+        int32_t v = m.tets[4 * t + c];
+        int64_t e = cur[v]++;
+        m.vt_tet[e] = (int32_t)t;
+        m.vt_corner[e] = c;
+        tslot[4 * t + c] = (int32_t)e;
+      }
+  }
+  m.max_valence = 0;
+  for (int64_t v = 0; v < n; ++v)
+    m.max_valence = std::max<int32_t>(m.max_valence, (int32_t)(m.vt_ptr[v + 1] - m.vt_ptr[v]));
+
+  // ---- 1-ring neighbours (ascending, self excluded) and block pattern
+  m.nbr_ptr.assign(n + 1, 0);
+  m.nbr_idx.clear();
+  m.bsr_ptr.assign(n + 1, 0);
+  m.bsr_col.clear();
+  std::vector<int32_t> tmp;
+  for (int64_t v = 0; v < n; ++v) {
+    tmp.clear();
+    for (int64_t e = m.vt_ptr[v]; e < m.vt_ptr[v + 1]; ++e) {
+      const int32_t* tv = &m.tets[4 * m.vt_tet[e]];
+      for (int c = 0; c < 4; ++c)
+        if (tv[c] != v) tmp.push_back(tv[c]);
+    }
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    m.nbr_idx.insert(m.nbr_idx.end(), tmp.begin(), tmp.end());
+    m.nbr_ptr[v + 1] = (int64_t)m.nbr_idx.size();
+    tmp.push_back((int32_t)v);
+    std::sort(tmp.begin(), tmp.end());
+    m.bsr_col.insert(m.bsr_col.end(), tmp.begin(), tmp.end());
+    m.bsr_ptr[v + 1] = (int64_t)m.bsr_col.size();
+  }
+  m.nnzb = (int64_t)m.bsr_col.size();
+  std::vector<int32_t> bsr_row(m.nnzb);
+  for (int64_t v = 0; v < n; ++v)
+    for (int64_t b = m.bsr_ptr[v]; b < m.bsr_ptr[v + 1]; ++b) bsr_row[b] = (int32_t)v;
+
+  // ---- sources of every Hessian block of a free row: entry * 4 + corner w,
+  //      in ascending (entry, w) order
+  std::vector<int32_t> blk_cnt(m.nnzb + 1, 0);
+  auto block_of = [&](int64_t row, int32_t col) -> int64_t {
+    auto b0 = m.bsr_col.begin() + m.bsr_ptr[row], b1 = m.bsr_col.begin() + m.bsr_ptr[row + 1];
+    auto it = std::lower_bound(b0, b1, col);
+    return (int64_t)(it - m.bsr_col.begin());
+  };
+  std::vector<int64_t> src_block(16 * T, -1);
+  for (int64_t v = 0; v < n; ++v) {
+    if (m.pinned[v]) continue;
+    for (int64_t e = m.vt_ptr[v]; e < m.vt_ptr[v + 1]; ++e) {
+      const int32_t* tv = &m.tets[4 * m.vt_tet[e]];
+      for (int w = 0; w < 4; ++w) {
+        int64_t b = block_of(v, tv[w]);
+        src_block[4 * e + w] = b;
+        blk_cnt[b + 1]++;
+      }
+    }
+  }
+  for (int64_t b = 0; b < m.nnzb; ++b) blk_cnt[b + 1] += blk_cnt[b];
+  std::vector<int32_t> blk_src(std::max<int64_t>(blk_cnt[m.nnzb], 1));
+  {
+    std::vector<int32_t> cur(blk_cnt.begin(), blk_cnt.end() - 1);
+    for (int64_t k = 0; k < 16 * T; ++k)
+      if (src_block[k] >= 0) blk_src[cur[src_block[k]]++] = (int32_t)k;
+  }
+
+  // ---- free rows, their blocks, tets with a free vertex
+  std::vector<int32_t> free_rows, free_blocks, active;
+  for (int64_t v = 0; v < n; ++v)
+    if (!m.pinned[v]) {
+      free_rows.push_back((int32_t)v);
+      for (int64_t b = m.bsr_ptr[v]; b < m.bsr_ptr[v + 1]; ++b) free_blocks.push_back((int32_t)b);
+    }
+  for (int64_t t = 0; t < T; ++t) {
+    bool any = false;
+    for (int c = 0; c < 4; ++c) any |= !m.pinned[m.tets[4 * t + c]];
+    if (any) active.push_back((int32_t)t);
+  }
+  m.n_free = (int64_t)free_rows.size();
+  m.n_free_blocks = (int64_t)free_blocks.size();
+  m.n_active_tets = (int64_t)active.size();
+
+  // ---- upload
+  std::vector<float2> Bm_df(9 * T);
+  std::vector<float> Bm32(9 * T);
+  for (int64_t k = 0; k < 9 * T; ++k) {
+    float hi = (float)Bm[k];
+    Bm_df[k] = make_float2(hi, (float)(Bm[k] - (double)hi));
+    Bm32[k] = hi;
+  }
+  std::vector<int32_t> i32(n + 1);
+  auto to32 = [&](const std::vector<int64_t>& a) {
+    std::vector<int32_t> r(a.size());
+    for (size_t k = 0; k < a.size(); ++k) r[k] = (int32_t)a[k];
+    return r;
+  };
+  m.d_tets.upload(reinterpret_cast<const int4*>(m.tets.data()), T, s);
+  m.d_tslot.upload(reinterpret_cast<const int4*>(tslot.data()), T, s);
+  m.d_Bm.upload(Bm, s);
+  m.d_Bm_df.upload(Bm_df, s);
+  m.d_Bm32.upload(Bm32, s);
+  m.d_vol.upload(vol, s);
+  m.d_mass.upload(m.mass, s);
+  m.d_pinned.upload(m.pinned, s);
+  auto vt32 = to32(m.vt_ptr), nb32 = to32(m.nbr_ptr), bp32 = to32(m.bsr_ptr);
+  m.d_vt_ptr.upload(vt32, s);
+  m.d_nbr_ptr.upload(nb32, s);
+  m.d_nbr_idx.upload(m.nbr_idx, s);
+  m.d_bsr_ptr.upload(bp32, s);
+  m.d_bsr_col.upload(m.bsr_col, s);
+  m.d_bsr_row.upload(bsr_row, s);
+  m.d_blk_ptr.upload(blk_cnt, s);
+  m.d_blk_src.upload(blk_src, s);
+  m.d_free_rows.upload(free_rows, s);
+  m.d_free_blocks.upload(free_blocks, s);
+  m.d_all_tets.upload(active, s);
+  CCG_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
+}
+
+}  // namespace ccg

@@ -1,0 +1,256 @@
+"""GPU (CUDA C-ABI) vs FP64 oracle parity.
+
+Integer outputs (adjacency, colours, supports) must be bit-identical.  A
+float64 sweep must match the oracle to 1e-12 relative in x (and its update to
+1e-9 relative).  Mixed-precision results are checked against the tolerances
+derived from float32 Hessian arithmetic ("Tolerances").
+"""
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import fem, solvers, subspace, topology
+
+torch = pytest.importorskip("torch")
+import paper_2510_12053_gb300 as cc  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _oracle(scene, k=None):
+    pb = fem.problem_from_scene(scene)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    if k is None:
+        return pb, topo, None, None
+    sup, U = subspace.build_local_bases(pb, topo, k)
+    return pb, topo, sup, U
+
+
+def _gpu(scene, k=None):
+    m = cc.Mesh.from_scene(scene)
+    m.color()
+    if k is not None:
+        m.build_subspace(k)
+    return m
+
+
+def _state(scene, amp, seed):
+    d = meshgen.normal(seed, np.arange(3 * scene.n)).reshape(-1, 3) * amp * scene.cell
+    return scene.x0 + d * (scene.pinned == 0)[:, None]
+
+
+def _box(nu=0.3, factor=1.2, dims=(6, 6, 6), jit=0.05, seed=2, E=1e5):
+    return meshgen.stretch_box(*dims, E=E, nu=nu, factor=factor, jitter_amount=jit, seed=seed)
+
+
+# ---------------------------------------------------------------- integers
+@pytest.mark.parametrize("scene", [meshgen.cube8_stretch(), _box(dims=(7, 5, 6), seed=5)],
+                         ids=["cube8", "box7x5x6"])
+def test_adjacency_and_colouring_bit_exact(scene):
+    pb, topo, _, _ = _oracle(scene)
+    m = cc.Mesh.from_scene(scene)
+    cols = m.color()
+    np.testing.assert_array_equal(m.export("vt_ptr"), topo.vt_ptr)
+    np.testing.assert_array_equal(m.export("vt_tet"), topo.vt_tet)
+    np.testing.assert_array_equal(m.export("vt_corner"), topo.vt_corner)
+    np.testing.assert_array_equal(m.export("nbr_ptr"), topo.nbr_ptr)
+    np.testing.assert_array_equal(m.export("nbr_idx"), topo.nbr_idx)
+    np.testing.assert_array_equal(cols, topo.color)
+    np.testing.assert_allclose(m.export("mass"), pb.mass, rtol=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_supports_bit_exact_and_bases_match(k):
+    scene = _box(dims=(6, 5, 4), seed=3)
+    pb, topo, sup, U = _oracle(scene, k)
+    m = _gpu(scene, k)
+    sp, si, Ug = m.export("sup_ptr"), m.export("sup_idx"), m.export("U").reshape(-1, 3, 3)
+    for v in range(pb.n):
+        np.testing.assert_array_equal(si[sp[v]:sp[v + 1]], sup[v])
+        if len(sup[v]):
+            np.testing.assert_allclose(Ug[sp[v]:sp[v + 1]], U[v], rtol=0, atol=1e-10 * max(1.0, np.abs(U[v]).max()))
+
+
+# ---------------------------------------------------------------- energy
+@pytest.mark.parametrize("dynamic", [False, True])
+def test_energy_and_gradient(dynamic):
+    if dynamic:
+        scene = meshgen.cantilever(3, 4, 7, cell=1 / 16, E=1e6, nu=0.45)
+    else:
+        scene = _box(dims=(5, 6, 4), factor=1.3)
+    pb, _, _, _ = _oracle(scene)
+    x = _state(scene, 0.3, 8)
+    xt = None
+    if dynamic:
+        v = meshgen.normal(9, np.arange(3 * scene.n)).reshape(-1, 3) * 0.1
+        xt = pb.inertial_target(scene.X, v)
+    E_o = pb.energy(x, xt)
+    g_o = pb.gradient(x, xt)
+    g_o[~pb.free] = 0.0
+    m = cc.Mesh.from_scene(scene)
+    xd = cc.to_soa(x)
+    xtd = cc.to_soa(xt) if dynamic else None
+    for prec, tol in [("fp64", 1e-12), ("mixed", 1e-10)]:
+        E, g, gn = m.energy_grad(xd, xtd, precision=prec)
+        gg = cc.from_soa(g)
+        assert E == pytest.approx(E_o, rel=1e-12)
+        assert np.abs(gg - g_o).max() <= tol * np.abs(g_o).max()
+        assert gn == pytest.approx(np.linalg.norm(g_o), rel=max(tol, 1e-13))
+
+
+# ---------------------------------------------------------------- one sweep, FP64
+@pytest.mark.parametrize("update", ["cc", "cd", "jgs2"])
+@pytest.mark.parametrize("schedule", ["colored", "jacobi"])
+def test_one_fp64_sweep_matches_oracle(update, schedule):
+    scene = _box()
+    pb, topo, sup, U = _oracle(scene, 2)
+    x0 = _state(scene, 0.05, 4)
+    st_o = solvers.Stats()
+    x_o = solvers.sweep(pb, topo, sup, U, x0, None, update, schedule, st_o)
+    m = _gpu(scene, 2)
+    xd = cc.to_soa(x0)
+    st = m.sweep(xd, update=update, schedule=schedule, precision="fp64")
+    x_g = cc.from_soa(xd)
+    assert np.abs(x_g - x_o).max() <= 1e-12 * np.abs(x_o).max()
+    d_o, d_g = x_o - x0, x_g - x0
+    assert np.abs(d_g - d_o).max() <= 1e-9 * np.abs(d_o).max()
+    assert (st.fallback_empty, st.fallback_reduced, st.fallback_schur) == \
+        (st_o.fallback_empty, st_o.fallback_reduced, st_o.fallback_schur)
+
+
+def test_pinned_rows_untouched_and_colour_range():
+    scene = _box()
+    m = _gpu(scene, 2)
+    xd = cc.to_soa(scene.x0)
+    before = cc.from_soa(xd)
+    m.sweep(xd, update="cc", schedule="colored", precision="fp64", color_begin=0, color_end=1)
+    after = cc.from_soa(xd)
+    cols = m.export("color")
+    moved = np.any(after != before, axis=1)
+    assert not np.any(moved & (scene.pinned == 1))
+    assert np.all(cols[moved] == 0)
+
+
+# ---------------------------------------------------------------- mixed precision trajectory
+def test_mixed_trajectory_matches_oracle_over_50_sweeps():
+    """Energy and gradient-norm trajectories within 1e-4 relative over 50
+    coloured CC sweeps; final positions within 1e-5 of the bbox diagonal."""
+    scene = meshgen.stretch_box(8, 8, 8, E=1e5, nu=0.3, factor=1.5, name="cube8_nu03")
+    pb, topo, sup, U = _oracle(scene, 2)
+    x = scene.x0.copy()
+    E_o, G_o = [], []
+    for _ in range(50):
+        x = solvers.sweep(pb, topo, sup, U, x, None, "cc", "colored")
+        E_o.append(pb.energy(x))
+        G_o.append(np.linalg.norm(pb.gradient(x)[pb.free]))
+    m = _gpu(scene, 2)
+    xd = cc.to_soa(scene.x0)
+    E_g, G_g = [], []
+    for _ in range(50):
+        m.sweep(xd, update="cc", schedule="colored", precision="mixed")
+        E, _, gn = m.energy_grad(xd, precision="fp64", want_grad=False)
+        E_g.append(E)
+        G_g.append(gn)
+    E_o, G_o, E_g, G_g = map(np.array, (E_o, G_o, E_g, G_g))
+    assert np.max(np.abs(E_g - E_o) / np.abs(E_o)) <= 1e-4
+    assert np.max(np.abs(G_g - G_o) / G_o) <= 1e-4
+    diag = np.linalg.norm(scene.X.max(0) - scene.X.min(0))
+    assert np.abs(cc.from_soa(xd) - x).max() <= 1e-5 * diag
+
+
+def test_mixed_solve_reaches_tolerance_and_matches_fp64():
+    scene = meshgen.stretch_box(8, 8, 8, E=1e5, nu=0.3, factor=1.2, name="cube8_nu03")
+    m = _gpu(scene, 2)
+    res = {}
+    for prec in ["fp64", "mixed"]:
+        xd = cc.to_soa(scene.x0)
+        r = m.solve_step(xd, precision=prec, tol=1e-6, max_iters=120, history=True)
+        res[prec] = (r, cc.from_soa(xd))
+        assert r.converged and r.g_final <= 1e-6 * r.g0
+    (r64, x64), (rmx, xmx) = res["fp64"], res["mixed"]
+    diag = np.linalg.norm(scene.X.max(0) - scene.X.min(0))
+    assert np.abs(x64 - xmx).max() <= 1e-5 * diag
+    assert abs(r64.iterations - rmx.iterations) <= 2
+
+
+# ---------------------------------------------------------------- dynamics
+def test_dynamic_step_matches_oracle():
+    scene = meshgen.cantilever(3, 3, 8, cell=1 / 16, E=1e5, nu=0.3)
+    pb, topo, sup, U = _oracle(scene, 2)
+    xt = pb.inertial_target(scene.X, scene.v0)
+    x_o = scene.X.copy()
+    for _ in range(3):
+        x_o = solvers.sweep(pb, topo, sup, U, x_o, xt, "cc", "colored")
+    v_o = (x_o - scene.X) / scene.h
+    m = _gpu(scene, 2)
+    xd, vd = cc.to_soa(scene.X), cc.to_soa(scene.v0)
+    r = m.solve_step(xd, vd, precision="fp64", tol=0.0, max_iters=3, min_iters=3)
+    assert r.iterations == 3
+    np.testing.assert_allclose(cc.from_soa(xd), x_o, rtol=0, atol=1e-12 * np.abs(x_o).max())
+    np.testing.assert_allclose(cc.from_soa(vd), v_o, rtol=0, atol=1e-9 * max(np.abs(v_o).max(), 1e-30))
+    assert r.energy == pytest.approx(pb.energy(x_o, xt), rel=1e-11)
+
+
+# ---------------------------------------------------------------- full size, sampled
+def test_cube32_full_size_sampled_updates():
+    """32^3 jittered cube (35 937 vertices): the GPU's first-colour updates
+    (the bench's launch configuration) against the oracle's local updates for
+    sampled vertices, float64 and mixed."""
+    scene = meshgen.cube32_stretch(E=1e5)
+    pb = fem.problem_from_scene(scene)
+    m = _gpu(scene, 2)
+    cols = m.export("color")
+    sp, si, Ug = m.export("sup_ptr"), m.export("sup_idx"), m.export("U").reshape(-1, 3, 3)
+    free0 = np.flatnonzero((cols == 0) & pb.free)
+    rng = meshgen.uniform01(77, np.arange(40))
+    sample = np.unique(free0[(rng * len(free0)).astype(int)])
+    # oracle: rest Hessian bases for the sample, then updates from g, H at x0
+    H0 = pb.hessian(scene.X)
+    nb_ptr, nb_idx = topology.vertex_neighbors(pb.n, pb.tets)
+    x0 = scene.x0
+    g = pb.gradient(x0)
+    H = pb.hessian(x0)
+    expect = {}
+    for i in sample:
+        S = np.array([j for j in topology.k_ring(int(i), 2, nb_ptr, nb_idx) if j != i and pb.free[j]])
+        np.testing.assert_array_equal(si[sp[i]:sp[i + 1]], S)
+        Ui = subspace.local_basis(H0, int(i), S)
+        np.testing.assert_allclose(Ug[sp[i]:sp[i + 1]], Ui, rtol=0, atol=1e-10 * np.abs(Ui).max())
+        expect[int(i)] = solvers.local_update("cc", H, g, int(i), S, Ui)
+    for prec, tol in [("fp64", 1e-9), ("mixed", 1e-4)]:
+        xd = cc.to_soa(x0)
+        m.sweep(xd, update="cc", schedule="colored", precision=prec, color_begin=0, color_end=1)
+        d = cc.from_soa(xd) - x0
+        scale = max(np.abs(dx).max() for dx in expect.values())
+        for i, dx in expect.items():
+            assert np.abs(d[i] - dx).max() <= tol * max(np.abs(dx).max(), 1e-3 * scale), (prec, i)
+
+
+# ---------------------------------------------------------------- errors
+def test_errors_are_reported_not_raised_from_c():
+    scene = _box(dims=(3, 3, 3))
+    m = cc.Mesh.from_scene(scene)
+    xd = cc.to_soa(scene.x0)
+    with pytest.raises(cc.CCError) as e:
+        m.sweep(xd)  # not coloured yet
+    assert e.value.status == cc.ERR_STATE
+    m.color()
+    with pytest.raises(cc.CCError) as e:
+        m.sweep(xd, update="cc")  # no subspace yet
+    assert e.value.status == cc.ERR_STATE
+    with pytest.raises(cc.CCError) as e:
+        m.build_subspace(0)
+    assert e.value.status == cc.ERR_INVALID_ARG
+    bad = scene.tets.copy()
+    bad[0, 1] = bad[0, 0]
+    with pytest.raises(cc.CCError) as e:
+        cc.Mesh(scene.X, bad, scene.pinned, E=1e5, nu=0.3)
+    assert e.value.status == cc.ERR_INVALID_ARG
+    with pytest.raises(cc.CCError) as e:
+        cc.Mesh(scene.X, scene.tets, scene.pinned, E=1e5, nu=0.5)
+    assert e.value.status == cc.ERR_INVALID_ARG
