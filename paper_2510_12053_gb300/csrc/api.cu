@@ -2,7 +2,10 @@
 // the order of kernel launches for sweeps and solves.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "cc_internal.cuh"
@@ -13,12 +16,32 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+void set_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  if (bytes <= 48 * 1024) return;
+  int dev = 0;
+  CCG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[{dev, kernel}];
+  if (have >= bytes) return;
+  CCG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+}
+
 namespace {
 
 enum { P_TET = 0, P_GATHER = 1, P_SOLVE = 2, P_RED = 3, P_OTHER = 4 };
 
 int prof_event(Mesh& m) {
   if (!m.prof.on) return -1;
+  if (m.prof.capturing) {
+    cudaEvent_t e;
+    CCG_CUDA(cudaEventCreate(&e));
+    m.prof.gpool.push_back(e);
+    CCG_CUDA(cudaEventRecord(e, m.stream));
+    return (int)m.prof.gpool.size() - 1;
+  }
   if (m.prof.used == m.prof.pool.size()) {
     cudaEvent_t e;
     CCG_CUDA(cudaEventCreate(&e));
@@ -32,6 +55,16 @@ int prof_event(Mesh& m) {
 // Counts `launches` kernels of class `cls`; with timing on, records the
 // closing event of an interval opened by prof_event.
 void prof_close(Mesh& m, int cls, int begin, int launches) {
+  if (m.prof.capturing) {
+    m.prof.graph_launches += launches;
+    if (!m.prof.on || begin < 0) return;
+    const int end = prof_event(m);
+    m.prof.gmark_cls.push_back(cls);
+    m.prof.gmark_begin.push_back(begin);
+    m.prof.gmark_end.push_back(end);
+    m.prof.gmark_launches.push_back(launches);
+    return;
+  }
   m.prof.total_launches += launches;
   if (!m.prof.on || begin < 0) return;
   const int end = prof_event(m);
@@ -39,6 +72,32 @@ void prof_close(Mesh& m, int cls, int begin, int launches) {
   m.prof.mark_begin.push_back(begin);
   m.prof.mark_end.push_back(end);
   m.prof.mark_launches.push_back(launches);
+}
+
+// After a completed graph replay: adds the replay's launches and, with timing
+// on, the intervals between its captured event nodes.
+void prof_after_replay(Mesh& m) {
+  m.prof.total_launches += m.prof.graph_launches;
+  if (!m.prof.on) return;
+  for (size_t k = 0; k < m.prof.gmark_cls.size(); ++k) {
+    float ms = 0.f;
+    CCG_CUDA(cudaEventElapsedTime(&ms, m.prof.gpool[m.prof.gmark_begin[k]], m.prof.gpool[m.prof.gmark_end[k]]));
+    m.prof.acc_ms[m.prof.gmark_cls[k]] += ms;
+    m.prof.acc_launches[m.prof.gmark_cls[k]] += m.prof.gmark_launches[k];
+  }
+}
+
+void drop_graph(Mesh& m) {
+  if (m.graph_exec) cudaGraphExecDestroy(m.graph_exec);
+  m.graph_exec = nullptr;
+  m.graph_key.clear();
+  for (cudaEvent_t e : m.prof.gpool) cudaEventDestroy(e);
+  m.prof.gpool.clear();
+  m.prof.gmark_cls.clear();
+  m.prof.gmark_begin.clear();
+  m.prof.gmark_end.clear();
+  m.prof.gmark_launches.clear();
+  m.prof.graph_launches = 0;
 }
 
 double elastic_weight(const Mesh& m) { return m.h > 0.0 ? m.h * m.h : 1.0; }
@@ -49,18 +108,18 @@ void ensure_state(Mesh& m, cc_precision p) {
   if (p == CC_PREC_FP64) {
     if (!m.f64.gcon.p) {
       m.f64.gcon.alloc(3 * ne);
-      m.f64.hcon.alloc(36 * ne);
       m.f64.g.alloc(3 * m.n);
-      m.f64.bsr.alloc(9 * m.nnzb);
+      m.f64.bsr.alloc(12 * m.nnz_up);
+      m.f64.cpl.alloc(32 * m.n_free);
       CCG_CUDA(cudaMemsetAsync(m.f64.g.p, 0, 3 * m.n * sizeof(double), s));
     }
   } else {
     if (!m.mx.gcon.p) {
       m.mx.gcon.alloc(3 * ne);
-      m.mx.hcon.alloc(36 * ne);
       m.mx.g_hi.alloc(3 * m.n);
       m.mx.g_lo.alloc(3 * m.n);
-      m.mx.bsr.alloc(9 * m.nnzb);
+      m.mx.bsr.alloc(12 * m.nnz_up);
+      m.mx.cpl.alloc(32 * m.n_free);
       m.mx.x_hi.alloc(m.n);
       m.mx.x_lo.alloc(m.n);
       m.mx.xt_hi.alloc(m.n);
@@ -78,16 +137,16 @@ void refresh(Mesh& m, cc_precision p, const double* x, const double* xt, const i
   cudaStream_t s = m.stream;
   int e0 = prof_event(m);
   if (p == CC_PREC_FP64)
-    launch_tet_eval_f64(m, x, list, count, elastic_weight(m), s);
+    launch_tet_grad_f64(m, x, list, count, elastic_weight(m), s);
   else
-    launch_tet_eval_mixed(m, list, count, elastic_weight(m), s);
+    launch_tet_grad_mixed(m, list, count, elastic_weight(m), s);
   prof_close(m, P_TET, e0, count > 0 ? 1 : 0);
   e0 = prof_event(m);
   if (p == CC_PREC_FP64)
-    launch_gather_f64(m, x, xt, s);
+    launch_rows_f64(m, x, xt, elastic_weight(m), s);
   else
-    launch_gather_mixed(m, m.h > 0.0, s);
-  prof_close(m, P_GATHER, e0, 2);
+    launch_rows_mixed(m, elastic_weight(m), s);
+  prof_close(m, P_GATHER, e0, 1);
 }
 
 void refresh_all(Mesh& m, cc_precision p, const double* x, const double* xt) {
@@ -103,7 +162,7 @@ void solve_list(Mesh& m, const cc_sweep_opts& o, const int32_t* verts, int64_t c
     launch_local_solve_f64(m, o.update, verts, count, x, counters(m), m.stream);
   else
     launch_local_solve_mixed(m, o.update, verts, count, x, counters(m), m.stream);
-  prof_close(m, P_SOLVE, e0, 1);
+  prof_close(m, P_SOLVE, e0, o.update == CC_UPDATE_CD ? 1 : 2);
 }
 
 // One sweep over colours [cb, ce).  `fresh` means g and H already hold the
@@ -265,15 +324,16 @@ void cc_destroy_mesh(cc_mesh* m) {
   if (!m) return;
   if (m->stream) cudaStreamSynchronize(m->stream);
   else cudaDeviceSynchronize();
-  if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+  drop_graph(*m);
   for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
   auto rel = [](auto& b) { b.release(); };
-  rel(m->d_tets); rel(m->d_tslot); rel(m->d_Bm); rel(m->d_Bm_df); rel(m->d_Bm32); rel(m->d_vol); rel(m->d_mass);
-  rel(m->d_pinned); rel(m->d_vt_ptr); rel(m->d_nbr_ptr); rel(m->d_nbr_idx); rel(m->d_bsr_ptr); rel(m->d_bsr_col);
-  rel(m->d_bsr_row); rel(m->d_blk_ptr); rel(m->d_blk_src); rel(m->d_free_rows); rel(m->d_free_blocks);
+  rel(m->d_tets); rel(m->d_tslot); rel(m->d_Bm); rel(m->d_Bm_df); rel(m->d_Bm32); rel(m->d_vol); rel(m->d_volw); rel(m->d_volw32); rel(m->d_volw_df); rel(m->d_mass);
+  rel(m->d_mass32); rel(m->d_mass_df);
+  rel(m->d_pinned); rel(m->d_vt_ptr); rel(m->d_nbr_ptr); rel(m->d_nbr_idx); rel(m->d_vt_tet); rel(m->d_vt_corner);
+  rel(m->d_up_ptr); rel(m->d_up_col); rel(m->d_rs_ptr); rel(m->d_rs_idx); rel(m->d_free_rows);
   rel(m->d_color); rel(m->d_cv_idx); rel(m->d_tl); rel(m->d_all_tets); rel(m->d_sup_ptr); rel(m->d_sup_idx);
-  rel(m->f64.gcon); rel(m->f64.hcon); rel(m->f64.g); rel(m->f64.bsr); rel(m->f64.U);
-  rel(m->mx.gcon); rel(m->mx.hcon); rel(m->mx.g_hi); rel(m->mx.g_lo); rel(m->mx.bsr); rel(m->mx.U);
+  rel(m->f64.gcon); rel(m->f64.g); rel(m->f64.cpl); rel(m->f64.bsr); rel(m->f64.U);
+  rel(m->mx.gcon); rel(m->mx.cpl); rel(m->mx.g_hi); rel(m->mx.g_lo); rel(m->mx.bsr); rel(m->mx.U);
   rel(m->mx.x_hi); rel(m->mx.x_lo); rel(m->mx.xt_hi); rel(m->mx.xt_lo);
   rel(m->d_red); rel(m->d_scalars); rel(m->d_counters); rel(m->d_xtilde); rel(m->d_xold);
   if (m->h_pinned_scalars) cudaFreeHost(m->h_pinned_scalars);
@@ -426,16 +486,60 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
     double gcur = g0;
     int it = 0;
     bool conv = (g0 == 0.0);
+    // Graph mode: the `every` sweeps and the residual reduction between two
+    // host checks are captured once and replayed.  The first chunk always runs
+    // launch by launch (it sets kernel attributes outside any capture), and
+    // the legacy default stream cannot be captured, so it never uses graphs.
+    const bool graph = o->use_graph && s != nullptr;
+    std::string key;
+    if (graph) {
+      char buf[256];
+      std::snprintf(buf, sizeof(buf), "%p %p %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
+                    (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0);
+      key = buf;
+    }
     while (!conv && it < o->max_iters) {
       const int chunk = std::min(every, o->max_iters - it);
-      for (int k = 0; k < chunk; ++k) {
-        sweep_body(*m, x, xt, so, cb, ce, true);
-        post_refresh(*m, x, xt, so, ce);
+      if (graph && chunk == every && it > 0) {
+        if (m->graph_key != key) {
+          drop_graph(*m);
+          cudaGraph_t g = nullptr;
+          CCG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          m->prof.capturing = true;
+          try {
+            for (int k = 0; k < chunk; ++k) {
+              sweep_body(*m, x, xt, so, cb, ce, true);
+              post_refresh(*m, x, xt, so, ce);
+            }
+            gnorm(*m, o->precision, nullptr, m->d_scalars.p);
+          } catch (...) {
+            m->prof.capturing = false;
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            drop_graph(*m);
+            throw;
+          }
+          m->prof.capturing = false;
+          CCG_CUDA(cudaStreamEndCapture(s, &g));
+          cudaError_t ie = cudaGraphInstantiate(&m->graph_exec, g, 0);
+          cudaGraphDestroy(g);
+          CCG_CUDA(ie);
+          m->graph_key = key;
+        }
+        CCG_CUDA(cudaGraphLaunch(m->graph_exec, s));
+        it += chunk;
+        gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
+        prof_after_replay(*m);
+      } else {
+        for (int k = 0; k < chunk; ++k) {
+          sweep_body(*m, x, xt, so, cb, ce, true);
+          post_refresh(*m, x, xt, so, ce);
+        }
+        CCG_CUDA(cudaGetLastError());
+        it += chunk;
+        gnorm(*m, o->precision, nullptr, m->d_scalars.p);
+        gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
       }
-      CCG_CUDA(cudaGetLastError());
-      it += chunk;
-      gnorm(*m, o->precision, nullptr, m->d_scalars.p);
-      gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
       if (o->residual_history) o->residual_history[it] = gcur;
       CCG_CHECK(std::isfinite(gcur), CC_ERR_NUMERIC, "non-finite residual");
       if (it >= o->min_iters && gcur <= o->tol * g0) conv = true;
@@ -527,8 +631,13 @@ cc_status cc_profile_enable(cc_mesh* m, int32_t on) {
   CC_API_BODY("cc_profile_enable", {
     CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
     CCG_CUDA(cudaStreamSynchronize(m->stream));
+    if ((on != 0) != m->prof.on) drop_graph(*m);
     m->prof.on = on != 0;
     m->prof.used = 0;
+    for (int c = 0; c < CC_PROFILE_CLASSES; ++c) {
+      m->prof.acc_ms[c] = 0;
+      m->prof.acc_launches[c] = 0;
+    }
     m->prof.mark_cls.clear();
     m->prof.mark_begin.clear();
     m->prof.mark_end.clear();
@@ -547,6 +656,12 @@ cc_status cc_profile_read(cc_mesh* m, cc_profile* out) {
       CCG_CUDA(cudaEventElapsedTime(&ms, m->prof.pool[m->prof.mark_begin[k]], m->prof.pool[m->prof.mark_end[k]]));
       out->ms[m->prof.mark_cls[k]] += ms;
       out->launches[m->prof.mark_cls[k]] += m->prof.mark_launches[k];
+    }
+    for (int c = 0; c < CC_PROFILE_CLASSES; ++c) {
+      out->ms[c] += m->prof.acc_ms[c];
+      out->launches[c] += m->prof.acc_launches[c];
+      m->prof.acc_ms[c] = 0;
+      m->prof.acc_launches[c] = 0;
     }
     out->total_launches = m->prof.total_launches;
     m->prof.used = 0;

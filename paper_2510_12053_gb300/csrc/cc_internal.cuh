@@ -69,33 +69,45 @@ struct DBuf {
 // assembled gradient and 3x3-block Hessian, and the basis blocks.
 struct StateF64 {
   DBuf<double> gcon;  // [4T][3]   gradient of tet at each (vertex, slot)
-  DBuf<double> hcon;  // [4T][4][9] Hessian row blocks of tet for that vertex
   DBuf<double> g;     // [n][3]
-  DBuf<double> bsr;   // [nnzb][9]
+  DBuf<double> bsr;   // [nnz_up][12] upper Hessian blocks, rows padded to 4
   DBuf<double> U;     // [sup_total][9]
+  DBuf<double> cpl;   // [n_free][32] coupling products of the vertices being solved
 };
 
 struct StateMixed {
   DBuf<float2> gcon;  // [4T][3]   float-float (hi, lo)
-  DBuf<float> hcon;   // [4T][4][9]
   DBuf<float> g_hi;   // [n][3]
   DBuf<float> g_lo;   // [n][3]
-  DBuf<float> bsr;    // [nnzb][9]
+  DBuf<float> bsr;    // [nnz_up][12]
   DBuf<float> U;      // [sup_total][9]
+  DBuf<float> cpl;    // [n_free][32]
   DBuf<float4> x_hi;  // [n] position mirror, float-float split
   DBuf<float4> x_lo;
   DBuf<float4> xt_hi; // inertial target mirror
   DBuf<float4> xt_lo;
 };
 
-// Optional per-kernel-class event timing (cc_profile_*).
+// Optional per-kernel-class event timing (cc_profile_*).  Intervals recorded
+// while a graph is being captured become event nodes of that graph; their
+// times are added up after every replay.
 struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<int> mark_cls, mark_begin, mark_end, mark_launches;
   int64_t total_launches = 0;
+  bool capturing = false;
+  std::vector<cudaEvent_t> gpool;
+  std::vector<int> gmark_cls, gmark_begin, gmark_end, gmark_launches;
+  int64_t graph_launches = 0;    // kernel launches per replay of the current graph
+  double acc_ms[CC_PROFILE_CLASSES] = {0, 0, 0, 0, 0};
+  int64_t acc_launches[CC_PROFILE_CLASSES] = {0, 0, 0, 0, 0};
 };
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device):
+// the attribute call costs host time and is not repeated on every launch.
+void set_smem_limit(const void* kernel, size_t bytes);
 
 struct Mesh {
   Prof prof;
@@ -113,8 +125,9 @@ struct Mesh {
   std::vector<int32_t> vt_tet, vt_corner;
   std::vector<int64_t> nbr_ptr;
   std::vector<int32_t> nbr_idx;
-  std::vector<int64_t> bsr_ptr;
-  std::vector<int32_t> bsr_col;
+  std::vector<int64_t> up_ptr;   // upper 3x3-block pattern (diagonal first)
+  std::vector<int32_t> up_col;
+  int64_t nnz_up = 0;
   std::vector<double> mass;
   std::vector<int32_t> color;
   int32_t num_colors = 0;
@@ -132,19 +145,23 @@ struct Mesh {
   DBuf<float2> d_Bm_df;      // [T][9] float-float copy
   DBuf<float> d_Bm32;        // [T][9]
   DBuf<double> d_vol;        // [T]
+  DBuf<double> d_volw;       // [T] vol * elastic weight (h^2 or 1), float64
+  DBuf<float> d_volw32;      // [T] same, float32
+  DBuf<float2> d_volw_df;    // [T] same, float-float
   DBuf<double> d_mass;       // [n]
+  DBuf<float> d_mass32;      // [n]
+  DBuf<float2> d_mass_df;    // [n]
   DBuf<uint8_t> d_pinned;    // [n]
   DBuf<int32_t> d_vt_ptr;    // [n+1]
   DBuf<int32_t> d_nbr_ptr;   // [n+1]
   DBuf<int32_t> d_nbr_idx;
-  DBuf<int32_t> d_bsr_ptr;   // [n+1]
-  DBuf<int32_t> d_bsr_col;   // [nnzb]
-  DBuf<int32_t> d_bsr_row;   // [nnzb]
-  DBuf<int32_t> d_blk_ptr;   // [nnzb+1] sources of each Hessian block
-  DBuf<int32_t> d_blk_src;   // [16T] entry * 4 + corner
+  DBuf<int32_t> d_vt_tet;    // [4T]
+  DBuf<uint8_t> d_vt_corner; // [4T]
+  DBuf<int32_t> d_up_ptr;    // [n+1] upper block rows
+  DBuf<int32_t> d_up_col;    // [nnz_up]
+  DBuf<int32_t> d_rs_ptr;    // [nnz_up+1] sources of each upper block (free rows)
+  DBuf<uint16_t> d_rs_idx;   // local source index 4 * slot + corner
   DBuf<int32_t> d_free_rows; // free vertices, ascending
-  DBuf<int32_t> d_free_blocks; // Hessian blocks of free rows
-  int64_t n_free_blocks = 0;
   DBuf<int32_t> d_color;     // [n]
   std::vector<int32_t> cv_ptr;  // [C+1] free vertices per colour
   DBuf<int32_t> d_cv_idx;
@@ -166,7 +183,7 @@ struct Mesh {
   DBuf<double> d_xold;       // [3][n]
   double* h_pinned_scalars = nullptr; // pinned host [8]
   cudaGraphExec_t graph_exec = nullptr;
-  int64_t graph_key = 0;
+  std::string graph_key;
 };
 
 // ---------------------------------------------------------------------------
@@ -182,14 +199,13 @@ struct SweepCounters {
   unsigned long long* error;     // [1] non-finite update seen
 };
 
-// per-tet energy derivatives -> (vertex, slot) contributions
-void launch_tet_eval_f64(Mesh& m, const double* x, const int32_t* list, int64_t count,
-                         double weight, cudaStream_t s);
-void launch_tet_eval_mixed(Mesh& m, const int32_t* list, int64_t count, double weight,
-                           cudaStream_t s);
-// contributions -> gradient and Hessian blocks of the free rows
-void launch_gather_f64(Mesh& m, const double* x, const double* xt, cudaStream_t s);
-void launch_gather_mixed(Mesh& m, bool dynamic, cudaStream_t s);
+// phase A: per-tet gradient contributions of a tet list -> (vertex, slot) entries
+void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t count, double weight,
+                         cudaStream_t s);
+void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s);
+// phase B: gradient and upper Hessian block rows of every free vertex
+void launch_rows_f64(Mesh& m, const double* x, const double* xt, double weight, cudaStream_t s);
+void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s);
 // local solves for a list of free vertices
 void launch_local_solve_f64(Mesh& m, cc_update upd, const int32_t* verts, int64_t count,
                             double* x, SweepCounters c, cudaStream_t s);

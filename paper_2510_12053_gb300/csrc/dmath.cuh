@@ -147,3 +147,83 @@ __device__ __forceinline__ void chol3_solve(const double* L, double* b) {
 }
 
 }  // namespace ccg
+
+namespace ccg {
+
+// float-float division a / b (one correction step on the float32 quotient)
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df r = df_sub(a, df_mul(b, df{q1, 0.0f}));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  return fast_two_sum(q1, q2);
+}
+
+// Scalar arithmetic used by the batched 3x3 condensation, for float64 and
+// for float-float.
+template <typename T>
+struct Arith;
+
+template <>
+struct Arith<double> {
+  using V = double;
+  static __device__ __forceinline__ V mk(double a) { return a; }
+  static __device__ __forceinline__ V mkf(float a) { return (double)a; }
+  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+  static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
+  static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ V div(V a, V b) { return a / b; }
+  static __device__ __forceinline__ V neg(V a) { return -a; }
+  static __device__ __forceinline__ bool gt(V a, V b) { return a > b; }
+  static __device__ __forceinline__ double to_double(V a) { return a; }
+};
+
+template <>
+struct Arith<df> {
+  using V = df;
+  static __device__ __forceinline__ V mk(double a) { return df_from_double(a); }
+  static __device__ __forceinline__ V mkf(float a) { return df{a, 0.0f}; }
+  static __device__ __forceinline__ V add(V a, V b) { return df_add(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return df_sub(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return df_mul(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return df_fma(a, b, c); }
+  static __device__ __forceinline__ V div(V a, V b) { return df_div(a, b); }
+  static __device__ __forceinline__ V neg(V a) { return df_neg(a); }
+  static __device__ __forceinline__ bool gt(V a, V b) {
+    const df d = df_sub(a, b);
+    return d.hi > 0.0f || (d.hi == 0.0f && d.lo > 0.0f);
+  }
+  static __device__ __forceinline__ double to_double(V a) { return df_to_double(a); }
+};
+
+// Symmetric 3x3 (lower triangle of M read): adjugate in s[6] = (00 01 02 11 12 22)
+// and determinant.  Returns false when M is not SPD by the pivot test: the
+// Cholesky pivots M00, det2 / M00, det3 / det2 must all exceed rel * max diag.
+template <typename T>
+__device__ __forceinline__ bool sym3_adj(const typename Arith<T>::V* M, typename Arith<T>::V rel,
+                                         typename Arith<T>::V* adj, typename Arith<T>::V* det) {
+  using A = Arith<T>;
+  using V = typename A::V;
+  const V m00 = M[0], m10 = M[3], m20 = M[6], m11 = M[4], m21 = M[7], m22 = M[8];
+  V dmax = m00;
+  if (A::gt(m11, dmax)) dmax = m11;
+  if (A::gt(m22, dmax)) dmax = m22;
+  if (!A::gt(dmax, A::mkf(0.0f))) return false;
+  const V thr = A::mul(rel, dmax);
+  const V c00 = A::sub(A::mul(m11, m22), A::mul(m21, m21));
+  const V c01 = A::sub(A::mul(m21, m20), A::mul(m10, m22));
+  const V c02 = A::sub(A::mul(m10, m21), A::mul(m11, m20));
+  const V c11 = A::sub(A::mul(m00, m22), A::mul(m20, m20));
+  const V c12 = A::sub(A::mul(m10, m20), A::mul(m00, m21));
+  const V c22 = A::sub(A::mul(m00, m11), A::mul(m10, m10));
+  const V d3 = A::fma(m00, c00, A::fma(m10, c01, A::mul(m20, c02)));
+  // pivots: p0 = m00, p1 = c22 / m00, p2 = d3 / c22
+  if (!A::gt(m00, thr)) return false;
+  if (!A::gt(c22, A::mul(thr, m00))) return false;
+  if (!A::gt(d3, A::mul(thr, c22))) return false;
+  adj[0] = c00; adj[1] = c01; adj[2] = c02; adj[3] = c11; adj[4] = c12; adj[5] = c22;
+  *det = d3;
+  return true;
+}
+
+}  // namespace ccg

@@ -79,12 +79,12 @@ __device__ __forceinline__ void hess_block(const T* F, const T (&a_v)[3], const 
   K[7] -= s * q0;
 }
 
-__global__ void k_tet_eval_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+// ---- phase A: per-tet gradients of the tets whose vertices moved ----------
+__global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                const double* __restrict__ Bm, const double* __restrict__ vol,
-                               const uint8_t* __restrict__ pinned, const double* __restrict__ x,
-                               int64_t n, const int32_t* __restrict__ list, int64_t count, double mu,
-                               double lh, double weight, double* __restrict__ gcon,
-                               double* __restrict__ hcon) {
+                               const uint8_t* __restrict__ pinned, const double* __restrict__ x, int64_t n,
+                               const int32_t* __restrict__ list, int64_t count, double mu, double lh,
+                               double weight, double* __restrict__ gcon) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= count) return;
   const int t = list[k];
@@ -106,12 +106,6 @@ __global__ void k_tet_eval_f64(const int4* __restrict__ tets, const int4* __rest
   double P[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) P[q] = mu * kin.F[q] + s * kin.C[q];
-  double a[4][3];
-#pragma unroll
-  for (int v = 0; v < 4; ++v)
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-      a[v][r] = kin.C[3 * r] * kin.G[v][0] + kin.C[3 * r + 1] * kin.G[v][1] + kin.C[3 * r + 2] * kin.G[v][2];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     if (pinned[vid[v]]) continue;
@@ -119,24 +113,14 @@ __global__ void k_tet_eval_f64(const int4* __restrict__ tets, const int4* __rest
 #pragma unroll
     for (int r = 0; r < 3; ++r)
       gcon[3 * e + r] = V * (P[3 * r] * kin.G[v][0] + P[3 * r + 1] * kin.G[v][1] + P[3 * r + 2] * kin.G[v][2]);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      double K[9];
-      hess_block<double>(kin.F, a[v], a[w], kin.G[v], kin.G[w], mu, lh, s, K);
-      double* dst = hcon + (4 * e + w) * 9;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) dst[q] = V * K[q];
-    }
   }
 }
 
-// ---- mixed: float-float gradient, float32 Hessian -------------------------
-__global__ void k_tet_eval_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
-                                 const float2* __restrict__ Bm_df, const double* __restrict__ vol,
+__global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                                 const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
                                  const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
-                                 const float4* __restrict__ x_lo, const int32_t* __restrict__ list,
-                                 int64_t count, float mu_f, float lh_f, df mu_d, df lh_d, double weight,
-                                 float2* __restrict__ gcon, float* __restrict__ hcon) {
+                                 const float4* __restrict__ x_lo, const int32_t* __restrict__ list, int64_t count,
+                                 df mu_d, df lh_d, float2* __restrict__ gcon) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= count) return;
   const int t = list[k];
@@ -157,7 +141,6 @@ __global__ void k_tet_eval_mixed(const int4* __restrict__ tets, const int4* __re
     float2 b = Bm_df[9 * (int64_t)t + q];
     B[q] = df{b.x, b.y};
   }
-  // F = D_s D_m^{-1} in float-float
   df F[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -176,12 +159,11 @@ __global__ void k_tet_eval_mixed(const int4* __restrict__ tets, const int4* __re
   df J = df_fma(F[6], C[6], df_fma(F[3], C[3], df_mul(F[0], C[0])));
   df Jm1 = df_add(J, df{-1.0f, 0.0f});
   df s = df_sub(df_mul(lh_d, Jm1), mu_d);
-  const double Vd = vol[t] * weight;
-  const df V = df_from_double(Vd);
+  const float2 vw = volw[t];
+  const df V{vw.x, vw.y};
   df P[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) P[q] = df_mul(V, df_fma(mu_d, F[q], df_mul(s, C[q])));
-  // gradient rows for corners 1..3 (G = rows of B); corner 0 = minus their sum
   df g[4][3];
 #pragma unroll
   for (int v = 1; v < 4; ++v)
@@ -191,130 +173,239 @@ __global__ void k_tet_eval_mixed(const int4* __restrict__ tets, const int4* __re
                        df_fma(P[3 * r + 1], B[3 * (v - 1) + 1], df_mul(P[3 * r], B[3 * (v - 1)])));
 #pragma unroll
   for (int r = 0; r < 3; ++r) g[0][r] = df_neg(df_add(df_add(g[1][r], g[2][r]), g[3][r]));
-
-  // float32 Hessian from the high parts
-  float Ff[9], Cf[9], G[4][3];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    Ff[q] = F[q].hi;
-    Cf[q] = C[q].hi;
-  }
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    G[1][b] = B[b].hi;
-    G[2][b] = B[3 + b].hi;
-    G[3][b] = B[6 + b].hi;
-    G[0][b] = -(G[1][b] + G[2][b] + G[3][b]);
-  }
-  const float sf = s.hi;
-  const float Vf = (float)Vd;
-  float a[4][3];
-#pragma unroll
-  for (int v = 0; v < 4; ++v)
-#pragma unroll
-    for (int r = 0; r < 3; ++r) a[v][r] = Cf[3 * r] * G[v][0] + Cf[3 * r + 1] * G[v][1] + Cf[3 * r + 2] * G[v][2];
-
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     if (pinned[vid[v]]) continue;
     const int64_t e = ent[v];
 #pragma unroll
     for (int r = 0; r < 3; ++r) gcon[3 * e + r] = make_float2(g[v][r].hi, g[v][r].lo);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      float K[9];
-      hess_block<float>(Ff, a[v], a[w], G[v], G[w], mu_f, lh_f, sf, K);
-      float* dst = hcon + (4 * e + w) * 9;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) dst[q] = Vf * K[q];
-    }
   }
 }
 
-// ---- gathers ---------------------------------------------------------------
-// Threads [0, nfb) sum the sources of one Hessian block of a free row;
-// threads [nfb, nfb + nfree) sum the gradient of one free vertex.
+// ---- phase B: one warp per free row j ---------------------------------------
+// Lanes take j's incident tets.  Each computes its tet's Hessian blocks
+// (corner of j, w) for the corners w whose vertex id is >= j, in the row's
+// arithmetic (float64, or float32 from float-float edge vectors), and stages
+// them in shared memory; then each upper block of the row sums its sources in
+// a fixed order (deterministic) and is written padded to 3 x 4.  The gradient
+// sum of the row's per-tet contributions uses a fixed butterfly.
 template <typename HT>
-__global__ void k_gather_hess(const int32_t* __restrict__ free_blocks, int64_t nfb,
-                              const int32_t* __restrict__ blk_ptr, const int32_t* __restrict__ blk_src,
-                              const HT* __restrict__ hcon, const int32_t* __restrict__ bsr_row,
-                              const int32_t* __restrict__ bsr_col, const double* __restrict__ mass,
-                              bool dynamic, HT* __restrict__ bsr) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nfb) return;
-  const int b = free_blocks[k];
-  HT acc[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) acc[q] = HT(0);
-  const int s1 = blk_ptr[b + 1];
-  for (int s = blk_ptr[b]; s < s1; ++s) {
-    const HT* src = hcon + (int64_t)blk_src[s] * 9;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] += src[q];
-  }
-  if (dynamic) {
-    const int r = bsr_row[b];
-    if (r == bsr_col[b]) {
-      HT m = (HT)mass[r];
-      acc[0] += m;
-      acc[4] += m;
-      acc[8] += m;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 9; ++q) bsr[(int64_t)b * 9 + q] = acc[q];
-}
+struct RowArith;
 
-__global__ void k_gather_grad_f64(const int32_t* __restrict__ free_rows, int64_t nfree,
-                                  const int32_t* __restrict__ vt_ptr, const double* __restrict__ gcon,
-                                  const double* __restrict__ mass, const double* __restrict__ x,
-                                  const double* __restrict__ xt, int64_t n, double* __restrict__ g) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nfree) return;
-  const int j = free_rows[k];
-  double acc[3] = {0, 0, 0};
-  for (int e = vt_ptr[j]; e < vt_ptr[j + 1]; ++e) {
-    acc[0] += gcon[3 * (int64_t)e];
-    acc[1] += gcon[3 * (int64_t)e + 1];
-    acc[2] += gcon[3 * (int64_t)e + 2];
-  }
-  if (xt) {
-    const double m = mass[j];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) acc[a] += m * (x[a * n + j] - xt[a * n + j]);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) g[3 * (int64_t)j + a] = acc[a];
-}
-
-__global__ void k_gather_grad_mixed(const int32_t* __restrict__ free_rows, int64_t nfree,
-                                    const int32_t* __restrict__ vt_ptr, const float2* __restrict__ gcon,
-                                    const double* __restrict__ mass, const float4* __restrict__ x_hi,
-                                    const float4* __restrict__ x_lo, const float4* __restrict__ xt_hi,
-                                    const float4* __restrict__ xt_lo, bool dynamic,
-                                    float* __restrict__ g_hi, float* __restrict__ g_lo) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nfree) return;
-  const int j = free_rows[k];
-  df acc[3] = {df{0, 0}, df{0, 0}, df{0, 0}};
-  for (int e = vt_ptr[j]; e < vt_ptr[j + 1]; ++e) {
+template <>
+struct RowArith<double> {
+  static __device__ __forceinline__ void edges(const double* x, const float4*, const float4*, int64_t n,
+                                               const int (&vid)[4], double (&e)[3][3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      float2 c = gcon[3 * (int64_t)e + a];
-      acc[a] = df_add(acc[a], df{c.x, c.y});
+      const double p0 = x[a * n + vid[0]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) e[c][a] = x[a * n + vid[c + 1]] - p0;
     }
   }
-  if (dynamic) {
-    const df m = df_from_double(mass[j]);
-    const float4 xh = x_hi[j], xl = x_lo[j], th = xt_hi[j], tl = xt_lo[j];
-    acc[0] = df_fma(m, df_sub(df{xh.x, xl.x}, df{th.x, tl.x}), acc[0]);
-    acc[1] = df_fma(m, df_sub(df{xh.y, xl.y}, df{th.y, tl.y}), acc[1]);
-    acc[2] = df_fma(m, df_sub(df{xh.z, xl.z}, df{th.z, tl.z}), acc[2]);
-  }
+};
+
+template <>
+struct RowArith<float> {
+  static __device__ __forceinline__ void edges(const double*, const float4* xh, const float4* xl, int64_t,
+                                               const int (&vid)[4], float (&e)[3][3]) {
+    const float4 h0 = xh[vid[0]], l0 = xl[vid[0]];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    g_hi[3 * (int64_t)j + a] = acc[a].hi;
-    g_lo[3 * (int64_t)j + a] = acc[a].lo;
+    for (int c = 0; c < 3; ++c) {
+      const float4 h = xh[vid[c + 1]], l = xl[vid[c + 1]];
+      e[c][0] = (h.x - h0.x) + (l.x - l0.x);
+      e[c][1] = (h.y - h0.y) + (l.y - l0.y);
+      e[c][2] = (h.z - h0.z) + (l.z - l0.z);
+    }
+  }
+};
+
+template <typename HT, bool kMixed>
+__global__ void k_row_assemble(const int32_t* __restrict__ rows, int64_t nrows, const int32_t* __restrict__ vt_ptr,
+                               const int32_t* __restrict__ vt_tet, const uint8_t* __restrict__ vt_corner,
+                               const int4* __restrict__ tets, const HT* __restrict__ Bm,
+                               const HT* __restrict__ volw, const double* __restrict__ x,
+                               const float4* __restrict__ x_hi, const float4* __restrict__ x_lo, int64_t n,
+                               const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ rs_ptr,
+                               const uint16_t* __restrict__ rs_idx, const double* __restrict__ gcon64,
+                               const float2* __restrict__ gcon_df, const HT* __restrict__ massh,
+                               const double* __restrict__ mass64, const float2* __restrict__ mass_df,
+                               const double* __restrict__ xt, const float4* __restrict__ xt_hi,
+                               const float4* __restrict__ xt_lo, bool dynamic, HT mu, HT lh,
+                               int stage_blocks, HT* __restrict__ bsr, double* __restrict__ g64,
+                               float* __restrict__ g_hi, float* __restrict__ g_lo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  HT* stage = reinterpret_cast<HT*>(smem_raw) + (size_t)warp * stage_blocks * 9;
+  const int64_t wid = (int64_t)blockIdx.x * wpb + warp;
+  if (wid >= nrows) return;
+  const int j = rows[wid];
+  const int e0 = vt_ptr[j], val = vt_ptr[j + 1] - e0;
+  double gs[3] = {0.0, 0.0, 0.0};
+  df gd[3] = {df{0, 0}, df{0, 0}, df{0, 0}};
+  HT diag[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) diag[c] = HT(0);
+  for (int k = lane; k < val; k += 32) {
+    const int e = e0 + k;
+    const int t = vt_tet[e];
+    const int cj = vt_corner[e];
+    const int4 tv = tets[t];
+    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+    HT ed[3][3];
+    RowArith<HT>::edges(x, x_hi, x_lo, n, vid, ed);
+    HT B[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) B[q] = Bm[9 * (int64_t)t + q];
+    HT F[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) F[3 * a + b] = ed[0][a] * B[b] + ed[1][a] * B[3 + b] + ed[2][a] * B[6 + b];
+    HT C[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+      C[0 + b] = F[3 + b1] * F[6 + b2] - F[6 + b1] * F[3 + b2];
+      C[3 + b] = F[6 + b1] * F[0 + b2] - F[0 + b1] * F[6 + b2];
+      C[6 + b] = F[0 + b1] * F[3 + b2] - F[3 + b1] * F[0 + b2];
+    }
+    const HT J = F[0] * C[0] + F[3] * C[3] + F[6] * C[6];
+    const HT s = lh * (J - HT(1)) - mu;
+    const HT V = volw[t];
+    HT G[4][3], a[4][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      G[1][b] = B[b];
+      G[2][b] = B[3 + b];
+      G[3][b] = B[6 + b];
+      G[0][b] = -(B[b] + B[3 + b] + B[6 + b]);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) a[v][r] = C[3 * r] * G[v][0] + C[3 * r + 1] * G[v][1] + C[3 * r + 2] * G[v][2];
+    HT Gc[3], ac[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      Gc[r] = G[0][r];
+      ac[r] = a[0][r];
+    }
+#pragma unroll
+    for (int v = 1; v < 4; ++v)
+      if (v == cj) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          Gc[r] = G[v][r];
+          ac[r] = a[v][r];
+        }
+      }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (vid[w] < j) continue;
+      HT K[9];
+      hess_block<HT>(F, ac, a[w], Gc, G[w], mu, lh, s, K);
+      if (w == cj) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) diag[q] += V * K[q];
+      } else {
+        HT* dst = stage + (size_t)(4 * k + w) * 9;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dst[q] = V * K[q];
+      }
+    }
+    if (kMixed) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float2 c = gcon_df[3 * (int64_t)e + r];
+        gd[r] = df_add(gd[r], df{c.x, c.y});
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gs[r] += gcon64[3 * (int64_t)e + r];
+    }
+  }
+  __syncwarp();
+  // diagonal block: fixed butterfly over the lanes
+  const int p0 = up_ptr[j], nup = up_ptr[j + 1] - p0;
+#pragma unroll
+  for (int c = 0; c < 9; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diag[c] += __shfl_xor_sync(0xffffffffu, diag[c], o);
+  if (lane == 0) {
+    if (dynamic) {
+      const HT mj = massh[j];
+      diag[0] += mj;
+      diag[4] += mj;
+      diag[8] += mj;
+    }
+    HT* dst = bsr + (int64_t)p0 * 12;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dst[4 * r + 0] = diag[3 * r + 0];
+      dst[4 * r + 1] = diag[3 * r + 1];
+      dst[4 * r + 2] = diag[3 * r + 2];
+      dst[4 * r + 3] = HT(0);
+    }
+  }
+  // off-diagonal upper blocks: each sums its staged sources in a fixed order
+  for (int q = 1 + lane; q < nup; q += 32) {
+    const int p = p0 + q;
+    HT acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = HT(0);
+    const int s1 = rs_ptr[p + 1];
+    for (int sidx = rs_ptr[p]; sidx < s1; ++sidx) {
+      const HT* src = stage + (size_t)rs_idx[sidx] * 9;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc[c] += src[c];
+    }
+    HT* dst = bsr + (int64_t)p * 12;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dst[4 * r + 0] = acc[3 * r + 0];
+      dst[4 * r + 1] = acc[3 * r + 1];
+      dst[4 * r + 2] = acc[3 * r + 2];
+      dst[4 * r + 3] = HT(0);
+    }
+  }
+  // gradient of the row: fixed butterfly over the lanes
+  if (kMixed) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        df other{__shfl_xor_sync(0xffffffffu, gd[r].hi, o), __shfl_xor_sync(0xffffffffu, gd[r].lo, o)};
+        gd[r] = df_add(gd[r], other);
+      }
+    if (lane == 0) {
+      if (dynamic) {
+        const df mj{mass_df[j].x, mass_df[j].y};
+        const float4 xh = x_hi[j], xl = x_lo[j], th = xt_hi[j], tl = xt_lo[j];
+        gd[0] = df_fma(mj, df_sub(df{xh.x, xl.x}, df{th.x, tl.x}), gd[0]);
+        gd[1] = df_fma(mj, df_sub(df{xh.y, xl.y}, df{th.y, tl.y}), gd[1]);
+        gd[2] = df_fma(mj, df_sub(df{xh.z, xl.z}, df{th.z, tl.z}), gd[2]);
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        g_hi[3 * (int64_t)j + r] = gd[r].hi;
+        g_lo[3 * (int64_t)j + r] = gd[r].lo;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) gs[r] += __shfl_xor_sync(0xffffffffu, gs[r], o);
+    if (lane == 0) {
+      if (dynamic) {
+        const double mj = mass64[j];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gs[r] += mj * (x[r * n + j] - xt[r * n + j]);
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) g64[3 * (int64_t)j + r] = gs[r];
+    }
   }
 }
 
@@ -431,40 +522,56 @@ constexpr int kRedBlocks = 1024;
 }  // namespace
 
 // ---------------------------------------------------------------------------
-void launch_tet_eval_f64(Mesh& m, const double* x, const int32_t* list, int64_t count, double weight,
+void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t count, double weight,
                          cudaStream_t s) {
   if (count <= 0) return;
-  k_tet_eval_f64<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x,
-                                                    m.n, list, count, m.mu, m.lam_hat, weight, m.f64.gcon.p,
-                                                    m.f64.hcon.p);
+  k_tet_grad_f64<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x, m.n,
+                                                    list, count, m.mu, m.lam_hat, weight, m.f64.gcon.p);
 }
 
-void launch_tet_eval_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
+void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
   if (count <= 0) return;
   df mu_d{(float)m.mu, (float)(m.mu - (double)(float)m.mu)};
   df lh_d{(float)m.lam_hat, (float)(m.lam_hat - (double)(float)m.lam_hat)};
-  k_tet_eval_mixed<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_vol.p,
-                                                      m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count,
-                                                      (float)m.mu, (float)m.lam_hat, mu_d, lh_d, weight,
-                                                      m.mx.gcon.p, m.mx.hcon.p);
+  (void)weight;
+  k_tet_grad_mixed<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_volw_df.p,
+                                                      m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, mu_d, lh_d,
+                                                      m.mx.gcon.p);
 }
 
-void launch_gather_f64(Mesh& m, const double* x, const double* xt, cudaStream_t s) {
+template <typename HT, bool kMixed>
+static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, const HT* Bm, const HT* volw,
+                        const HT* massh, cudaStream_t s) {
+  const int stage_blocks = 4 * m.max_valence;
+  int wpb = 4;
+  size_t smem = (size_t)wpb * stage_blocks * 9 * sizeof(HT);
+  while (wpb > 1 && smem > 200 * 1024) {
+    wpb >>= 1;
+    smem = (size_t)wpb * stage_blocks * 9 * sizeof(HT);
+  }
+  CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "vertex valence too high for the row assembly");
+  auto kern = k_row_assemble<HT, kMixed>;
+  set_smem_limit(reinterpret_cast<const void*>(kern), smem);
   const bool dyn = m.h > 0.0;
-  k_gather_hess<double><<<grid_for(m.n_free_blocks), kBlock, 0, s>>>(
-      m.d_free_blocks.p, m.n_free_blocks, m.d_blk_ptr.p, m.d_blk_src.p, m.f64.hcon.p, m.d_bsr_row.p, m.d_bsr_col.p,
-      m.d_mass.p, dyn, m.f64.bsr.p);
-  k_gather_grad_f64<<<grid_for(m.n_free), kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.f64.gcon.p,
-                                                          m.d_mass.p, x, dyn ? xt : nullptr, m.n, m.f64.g.p);
+  const int64_t blocks = (m.n_free + wpb - 1) / wpb;
+  kern<<<(unsigned)blocks, 32 * wpb, smem, s>>>(
+      m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.d_vt_tet.p, m.d_vt_corner.p, m.d_tets.p, Bm, volw, x,
+      kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr, m.n, m.d_up_ptr.p, m.d_rs_ptr.p, m.d_rs_idx.p,
+      kMixed ? nullptr : m.f64.gcon.p, kMixed ? m.mx.gcon.p : nullptr, massh, m.d_mass.p, m.d_mass_df.p,
+      dyn ? xt : nullptr, kMixed ? m.mx.xt_hi.p : nullptr, kMixed ? m.mx.xt_lo.p : nullptr, dyn, (HT)m.mu,
+      (HT)m.lam_hat,
+      stage_blocks, bsr, kMixed ? nullptr : m.f64.g.p, kMixed ? m.mx.g_hi.p : nullptr,
+      kMixed ? m.mx.g_lo.p : nullptr);
 }
 
-void launch_gather_mixed(Mesh& m, bool dynamic, cudaStream_t s) {
-  k_gather_hess<float><<<grid_for(m.n_free_blocks), kBlock, 0, s>>>(
-      m.d_free_blocks.p, m.n_free_blocks, m.d_blk_ptr.p, m.d_blk_src.p, m.mx.hcon.p, m.d_bsr_row.p, m.d_bsr_col.p,
-      m.d_mass.p, dynamic, m.mx.bsr.p);
-  k_gather_grad_mixed<<<grid_for(m.n_free), kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.mx.gcon.p,
-                                                            m.d_mass.p, m.mx.x_hi.p, m.mx.x_lo.p, m.mx.xt_hi.p,
-                                                            m.mx.xt_lo.p, dynamic, m.mx.g_hi.p, m.mx.g_lo.p);
+void launch_rows_f64(Mesh& m, const double* x, const double* xt, double weight, cudaStream_t s) {
+  (void)weight;
+  launch_rows<double, false>(m, x, xt, m.f64.bsr.p, m.d_Bm.p, m.d_volw.p, m.d_mass.p, s);
+}
+
+void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s) {
+  (void)weight;
+  launch_rows<float, true>(m, nullptr, nullptr, m.mx.bsr.p, m.d_Bm32.p, m.d_volw32.p, m.d_mass32.p, s);
 }
 
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {

@@ -65,10 +65,13 @@ __device__ __forceinline__ int find_sorted(const int32_t* a, int m, int key) {
 
 // One CTA per free vertex of the batch.  A (column-major, N x N, N = 3m) and
 // the right-hand sides R (column-major N x 3) live in the CTA's slice of
-// scratch.  Writes U[(s0 + a) * 9 + 3 r + d] = z[3a + r][d] with H_PP z = -H_Pi.
+// scratch.  H is read from its upper 3x3 blocks (padded to 3 x 4): a block
+// (j, l) of a support row j fills both (a, t) and (t, a); block (j, i) and
+// blocks (i, l) of row i fill -H_Pi.  Writes
+// U[(s0 + a) * 9 + 3 r + d] = z[3a + r][d] with H_PP z = -H_Pi.
 __global__ void k_patch_basis(const int32_t* __restrict__ verts, const int32_t* __restrict__ sup_ptr,
-                              const int32_t* __restrict__ sup_idx, const int32_t* __restrict__ bsr_ptr,
-                              const int32_t* __restrict__ bsr_col, const double* __restrict__ bsr, int Nmax,
+                              const int32_t* __restrict__ sup_idx, const int32_t* __restrict__ up_ptr,
+                              const int32_t* __restrict__ up_col, const double* __restrict__ bsr, int Nmax,
                               double* __restrict__ scratch, double* __restrict__ Uout, int32_t* __restrict__ fail) {
   const int i = verts[blockIdx.x];
   const int s0 = sup_ptr[i], m = sup_ptr[i + 1] - s0;
@@ -80,20 +83,33 @@ __global__ void k_patch_basis(const int32_t* __restrict__ verts, const int32_t* 
   for (int64_t k = threadIdx.x; k < (int64_t)N * N; k += blockDim.x) A[k] = 0.0;
   for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) R[k] = 0.0;
   __syncthreads();
-  // assemble H_PP and -H_Pi from the block rows of the support vertices
-  for (int a = threadIdx.x; a < m; a += blockDim.x) {
-    const int j = S[a];
-    for (int p = bsr_ptr[j]; p < bsr_ptr[j + 1]; ++p) {
-      const int l = bsr_col[p];
-      const double* Hb = bsr + (int64_t)p * 9;
-      if (l == i) {
-        for (int r = 0; r < 3; ++r)
-          for (int d = 0; d < 3; ++d) R[d * N + 3 * a + r] = -Hb[3 * r + d];
-      } else {
+  for (int a = threadIdx.x; a <= m; a += blockDim.x) {
+    const int j = a < m ? S[a] : i;
+    for (int p = up_ptr[j]; p < up_ptr[j + 1]; ++p) {
+      const int l = up_col[p];
+      const double* Hb = bsr + (int64_t)p * 12;  // H_jl, row r at Hb[4 r]
+      if (a < m) {
+        if (l == j) {
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[(size_t)(3 * a + c) * N + 3 * a + r] = Hb[4 * r + c];
+        } else if (l == i) {
+          for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) R[d * N + 3 * a + r] = -Hb[4 * r + d];
+        } else {
+          const int t = find_sorted(S, m, l);
+          if (t >= 0)
+            for (int r = 0; r < 3; ++r)
+              for (int c = 0; c < 3; ++c) {
+                A[(size_t)(3 * t + c) * N + 3 * a + r] = Hb[4 * r + c];
+                A[(size_t)(3 * a + r) * N + 3 * t + c] = Hb[4 * r + c];
+              }
+        }
+      } else if (l != i) {
+        // row i: H_il with l > i; the patch needs H_li = H_il^T
         const int t = find_sorted(S, m, l);
         if (t >= 0)
           for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) A[(size_t)(3 * t + c) * N + 3 * a + r] = Hb[3 * r + c];
+            for (int d = 0; d < 3; ++d) R[d * N + 3 * t + r] = -Hb[4 * d + r];
       }
     }
   }
@@ -257,8 +273,8 @@ void run_subspace_build(Mesh& m, int32_t k) {
       for (int a = 0; a < 3; ++a) soa[a * n + j] = m.X[3 * j + a];
     Xs.upload(soa, s);
     const double w = m.h > 0.0 ? m.h * m.h : 1.0;
-    launch_tet_eval_f64(m, Xs.p, m.d_all_tets.p, m.n_active_tets, w, s);
-    launch_gather_f64(m, Xs.p, Xs.p, s);
+    launch_tet_grad_f64(m, Xs.p, m.d_all_tets.p, m.n_active_tets, w, s);
+    launch_rows_f64(m, Xs.p, Xs.p, w, s);
     CCG_CUDA(cudaStreamSynchronize(s));
   }
   m.f64.U.alloc(9 * std::max<int64_t>(total, 1));
@@ -273,8 +289,8 @@ void run_subspace_build(Mesh& m, int32_t k) {
   CCG_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int32_t), s));
   for (int64_t b0 = 0; b0 < m.n_free; b0 += batch) {
     const int64_t cnt = std::min<int64_t>(batch, m.n_free - b0);
-    k_patch_basis<<<(unsigned)cnt, 256, 0, s>>>(m.d_free_rows.p + b0, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_bsr_ptr.p,
-                                                 m.d_bsr_col.p, m.f64.bsr.p, Nmax, scratch.p, m.f64.U.p, fail.p);
+    k_patch_basis<<<(unsigned)cnt, 256, 0, s>>>(m.d_free_rows.p + b0, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_up_ptr.p,
+                                                 m.d_up_col.p, m.f64.bsr.p, Nmax, scratch.p, m.f64.U.p, fail.p);
     CCG_CUDA(cudaGetLastError());
   }
   int32_t nfail = 0;

@@ -1,16 +1,17 @@
 // Fused subspace-coupling products and Schur-condensed local solve
-// (Eq. 9-12), one warp per free vertex i of the current colour.
+// (Eq. 9-12), one CTA per free vertex i of the current colour.
 //
 // For vertex i with support S (|S| = m) and basis blocks U[s] (3x3):
-//   A  = sum_{l in row i, l in S} H_il U[l]                 (= H_iC U_i)
-//   Y_j = sum_{l in row j, l in S} H_jl U[l],   j in S
-//   Ht = sum_{j in S} U[j]^T Y_j                             (= U^T H_CC U)
+//   A  = sum_{l in S} H_il U[l]                              (= H_iC U_i)
+//   Ht = sum_{j, l in S} U[j]^T H_jl U[l]                    (= U^T H_CC U)
 //   b  = sum_{j in S} U[j]^T g_j                             (= U^T g_C)
-// then, in float64 on lane 0:
+// then, in float64 on one thread:
 //   S = A Ht^{-1} A^T,  gt = g_i - A Ht^{-1} b,  dx_i = -(H_ii - S)^{-1} gt
 // and x_i += dx_i (the subspace part U dalpha is discarded, Sec. 3.1).
-// The warp stages U_i in shared memory and indexes it through an open
-// addressing hash (vertex id -> support slot), so any mesh works.
+// H is stored as its upper 3x3 blocks (l >= j, diagonal first, each block
+// padded to 3 x 4 for 128-bit loads), so each unordered pair of the support
+// is read once.  The CTA stages U_i in shared memory and indexes it through an
+// open-addressing hash (vertex id -> support slot), so any mesh works.
 // Same-coloured vertices share no tet, and this kernel reads only g, H and U,
 // so writing x in place is race-free for both schedules.
 #include "cc_internal.cuh"
@@ -23,11 +24,6 @@ namespace {
 constexpr double kPivotRel = 1e-12;
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-template <typename HT>
-__host__ __device__ inline size_t warp_smem_bytes(int sup_max, int hash_size) {
-  return align16((size_t)sup_max * 9 * sizeof(HT)) + (size_t)hash_size * 4 + align16((size_t)hash_size * 2);
-}
 
 __device__ __forceinline__ unsigned hash_slot(int id, int bits) {
   return ((unsigned)id * 2654435761u) >> (32 - bits);
@@ -51,92 +47,143 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <typename HT, bool kMixed, int kUpd>
-__global__ void k_local_solve(const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
-                              const int32_t* __restrict__ sup_idx, const HT* __restrict__ U,
-                              const int32_t* __restrict__ bsr_ptr, const int32_t* __restrict__ bsr_col,
-                              const HT* __restrict__ bsr, const double* __restrict__ g64,
-                              const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
-                              int hash_bits, int sup_max, double* __restrict__ x, float4* __restrict__ x_hi,
-                              float4* __restrict__ x_lo, unsigned long long* __restrict__ fallback,
-                              unsigned long long* __restrict__ err) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int hs = 1 << hash_bits;
-  unsigned char* base = smem + (size_t)warp * warp_smem_bytes<HT>(sup_max, hs);
-  HT* Us = reinterpret_cast<HT*>(base);
-  int* keys = reinterpret_cast<int*>(base + align16((size_t)sup_max * 9 * sizeof(HT)));
-  short* vals = reinterpret_cast<short*>(keys + hs);
+// Loads the 3x3 block p of the padded upper rows.
+template <typename HT>
+__device__ __forceinline__ void load_block(const HT* __restrict__ bsr, int64_t p, HT* H);
 
-  const int64_t wid = (int64_t)blockIdx.x * wpb + warp;
-  if (wid >= count) return;  // uniform per warp
-  const int i = verts[wid];
+template <>
+__device__ __forceinline__ void load_block<float>(const float* __restrict__ bsr, int64_t p, float* H) {
+  const float4* b = reinterpret_cast<const float4*>(bsr + p * 12);
+  const float4 r0 = __ldg(b), r1 = __ldg(b + 1), r2 = __ldg(b + 2);
+  H[0] = r0.x; H[1] = r0.y; H[2] = r0.z;
+  H[3] = r1.x; H[4] = r1.y; H[5] = r1.z;
+  H[6] = r2.x; H[7] = r2.y; H[8] = r2.z;
+}
+
+template <>
+__device__ __forceinline__ void load_block<double>(const double* __restrict__ bsr, int64_t p, double* H) {
+  const double2* b = reinterpret_cast<const double2*>(bsr + p * 12);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double2 u = __ldg(b + 2 * r), v = __ldg(b + 2 * r + 1);
+    H[3 * r] = u.x; H[3 * r + 1] = u.y; H[3 * r + 2] = v.x;
+  }
+}
+
+constexpr int kSolveThreads = 128;
+
+template <typename HT>
+__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int hash_size) {
+  return align16((size_t)sup_max * 9 * sizeof(HT)) + (size_t)hash_size * 4 + align16((size_t)hash_size * 2) +
+         3 * align16((size_t)(sup_max + 1) * 4) + 4 * 32 * sizeof(HT);
+}
+
+// Coupling products, one CTA per free vertex i of the list.  Quarter-warps take
+// the block rows of the support S and of i itself; their lanes take the row's
+// upper blocks (H_jl, l >= j).  For j, l in S every unordered pair is visited
+// once and contributes M + M^T with M = U_j^T H_jl U_l (H is symmetric); a
+// block (j, i) of a support row gives A's term H_ij U_j = H_ji^T U_j; row i
+// gives H_ii and the terms H_il U_l with l > i.  The CTA writes 27 values per
+// vertex: Ht (6, symmetric), A (9), b (3), H_ii (9).
+template <typename HT, bool kMixed, int kUpd>
+__global__ void __launch_bounds__(kSolveThreads) k_couple(
+    const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
+    const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
+    const int32_t* __restrict__ up_col, const HT* __restrict__ bsr, const double* __restrict__ g64,
+    const float* __restrict__ g_hi, int hash_bits, int sup_max, HT* __restrict__ cpl) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int hs = 1 << hash_bits;
+  unsigned char* ptr = smem;
+  HT* Us = reinterpret_cast<HT*>(ptr);
+  ptr += align16((size_t)sup_max * 9 * sizeof(HT));
+  int* keys = reinterpret_cast<int*>(ptr);
+  short* vals = reinterpret_cast<short*>(keys + hs);
+  ptr += (size_t)hs * 4 + align16((size_t)hs * 2);
+  int* rstart = reinterpret_cast<int*>(ptr);
+  ptr += align16((size_t)(sup_max + 1) * 4);
+  int* rlen = reinterpret_cast<int*>(ptr);
+  ptr += align16((size_t)(sup_max + 1) * 4);
+  int* rid = reinterpret_cast<int*>(ptr);
+  ptr += align16((size_t)(sup_max + 1) * 4);
+  HT* red = reinterpret_cast<HT*>(ptr);  // [4 warps][32]
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = verts[blockIdx.x];
   const int s0 = sup_ptr[i];
   const int m = sup_ptr[i + 1] - s0;
 
-  if (kUpd != CC_UPDATE_CD) {
-    for (int k = lane; k < hs; k += 32) keys[k] = -1;
-    for (int k = lane; k < 9 * m; k += 32) Us[k] = U[(int64_t)s0 * 9 + k];
-    __syncwarp();
-    for (int s = lane; s < m; s += 32) {
-      const int id = sup_idx[s0 + s];
-      unsigned h = hash_slot(id, hash_bits);
-      while (true) {
-        const int prev = atomicCAS(&keys[h], -1, id);
-        if (prev == -1) {
-          vals[h] = (short)s;
-          break;
-        }
-        h = (h + 1) & (unsigned)(hs - 1);
-      }
-    }
-    __syncwarp();
+  for (int k = tid; k < hs; k += kSolveThreads) keys[k] = -1;
+  for (int k = tid; k < 9 * m; k += kSolveThreads) Us[k] = U[(int64_t)s0 * 9 + k];
+  for (int s = tid; s <= m; s += kSolveThreads) {
+    const int j = s < m ? sup_idx[s0 + s] : i;
+    const int a = up_ptr[j];
+    rstart[s] = a;
+    rlen[s] = up_ptr[j + 1] - a;
+    rid[s] = j;
   }
+  __syncthreads();
+  for (int s = tid; s < m; s += kSolveThreads) {
+    const int id = rid[s];
+    unsigned h = hash_slot(id, hash_bits);
+    while (true) {
+      const int prev = atomicCAS(&keys[h], -1, id);
+      if (prev == -1) {
+        vals[h] = (short)s;
+        break;
+      }
+      h = (h + 1) & (unsigned)(hs - 1);
+    }
+  }
+  __syncthreads();
 
-  HT Hii[9], A[9], Ht[9], b[3];
-  mat3_zero(Hii);
+  // symmetric Ht (6), A (9), b (3), H_ii (9)
+  HT h00 = 0, h01 = 0, h02 = 0, h11 = 0, h12 = 0, h22 = 0;
+  HT A[9], Hii[9], b[3] = {0, 0, 0};
   mat3_zero(A);
-  mat3_zero(Ht);
-  b[0] = b[1] = b[2] = HT(0);
-
-  // row i: diagonal block and A = H_iC U
-  const int r0 = bsr_ptr[i], r1 = bsr_ptr[i + 1];
-  for (int p = r0 + lane; p < r1; p += 32) {
-    const int l = bsr_col[p];
-    const HT* Hb = bsr + (int64_t)p * 9;
-    if (l == i) {
+  mat3_zero(Hii);
+  const int qw = tid >> 3, l8 = tid & 7;
+  for (int r = qw; r <= m; r += kSolveThreads / 8) {
+    const int P = rstart[r], L = rlen[r];
+    const HT* Uj = Us + 9 * r;
+    for (int q = l8; q < L; q += 8) {
+      const int64_t p = P + q;
+      const int l = up_col[p];
+      HT H[9];
+      load_block(bsr, p, H);
+      if (r < m) {
+        if (q == 0) {
+          HT T[9], M[9];
+          mat3_zero(T);
+          mat3_mul_acc(H, Uj, T);
+          mat3_zero(M);
+          mat3_tmul_acc(Uj, T, M);
+          h00 += M[0]; h01 += M[1]; h02 += M[2]; h11 += M[4]; h12 += M[5]; h22 += M[8];
+        } else if (l == i) {
+          if (kUpd == CC_UPDATE_CC) mat3_tmul_acc(H, Uj, A);
+        } else {
+          const int t = hash_find(keys, vals, l, hash_bits);
+          if (t >= 0) {
+            HT T[9], M[9];
+            mat3_zero(T);
+            mat3_mul_acc(H, Us + 9 * t, T);
+            mat3_zero(M);
+            mat3_tmul_acc(Uj, T, M);
+            h00 += 2 * M[0]; h11 += 2 * M[4]; h22 += 2 * M[8];
+            h01 += M[1] + M[3]; h02 += M[2] + M[6]; h12 += M[5] + M[7];
+          }
+        }
+      } else {
+        if (q == 0) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Hii[q] = Hb[q];
-    } else if (kUpd == CC_UPDATE_CC) {
-      const int t = hash_find(keys, vals, l, hash_bits);
-      if (t >= 0) {
-        HT Hl[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) Hl[q] = Hb[q];
-        mat3_mul_acc(Hl, Us + 9 * t, A);
-      }
-    }
-  }
-
-  // Ht = U^T H_CC U and b = U^T g_C over the support rows
-  if (kUpd != CC_UPDATE_CD) {
-    for (int s = lane; s < m; s += 32) {
-      const int j = sup_idx[s0 + s];
-      HT Y[9];
-      mat3_zero(Y);
-      const int p1 = bsr_ptr[j + 1];
-      for (int p = bsr_ptr[j]; p < p1; ++p) {
-        const int t = hash_find(keys, vals, bsr_col[p], hash_bits);
-        if (t >= 0) {
-          HT Hl[9];
-          const HT* Hb = bsr + (int64_t)p * 9;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) Hl[q] = Hb[q];
-          mat3_mul_acc(Hl, Us + 9 * t, Y);
+          for (int c = 0; c < 9; ++c) Hii[c] = H[c];
+        } else if (kUpd == CC_UPDATE_CC) {
+          const int t = hash_find(keys, vals, l, hash_bits);
+          if (t >= 0) mat3_mul_acc(H, Us + 9 * t, A);
         }
       }
-      const HT* Uj = Us + 9 * s;
-      mat3_tmul_acc(Uj, Y, Ht);
+    }
+    if (l8 == 0 && r < m) {
+      const int j = rid[r];
       HT gj[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) gj[a] = kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
@@ -145,103 +192,150 @@ __global__ void k_local_solve(const int32_t* __restrict__ verts, int64_t count, 
     }
   }
 
+  // CTA reduction of 27 values in a fixed order
+  HT vals27[27] = {h00, h01, h02, h11, h12, h22, A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], A[8],
+                   b[0], b[1], b[2], Hii[0], Hii[1], Hii[2], Hii[3], Hii[4], Hii[5], Hii[6], Hii[7], Hii[8]};
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    Hii[q] = warp_sum(Hii[q]);
-    A[q] = warp_sum(A[q]);
-    Ht[q] = warp_sum(Ht[q]);
+  for (int v = 0; v < 27; ++v) vals27[v] = warp_sum(vals27[v]);
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < 27; ++v) red[warp * 32 + v] = vals27[v];
+  __syncthreads();
+  if (tid >= 27) return;
+  // fixed-order sum of the four warps' partials
+  cpl[(int64_t)blockIdx.x * 32 + tid] = ((red[tid] + red[32 + tid]) + red[64 + tid]) + red[96 + tid];
+}
+
+// Batched condensation (Eq. 9-12), one free vertex per thread: a warp
+// condenses 32 vertices at once, so the float64 or float-float 3x3 algebra
+// runs at full SIMD width instead of on one lane per vertex.  3x3 inverses
+// use the adjugate; the SPD guard is the Cholesky pivot test written with
+// leading minors.  `AR` is the arithmetic: double (float64 path) or df
+// (float-float, mixed path).
+template <typename AR, typename HT, bool kMixed, int kUpd>
+__global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, const HT* __restrict__ cpl,
+                           const int32_t* __restrict__ sup_ptr, const int32_t* __restrict__ up_ptr,
+                           const HT* __restrict__ bsr, const double* __restrict__ g64,
+                           const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
+                           double* __restrict__ x, float4* __restrict__ x_hi, float4* __restrict__ x_lo,
+                           AR rel, unsigned long long* __restrict__ fallback,
+                           unsigned long long* __restrict__ err) {
+  using Ar = Arith<AR>;
+  using V = typename Ar::V;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int i = verts[k];
+  auto ld = [](HT v) -> V {
+    if constexpr (sizeof(HT) == 4) return Ar::mkf((float)v);
+    else return Ar::mk((double)v);
+  };
+  V H[9], gi[3];
+  if (kUpd == CC_UPDATE_CD) {
+    HT Hb[9];
+    load_block(bsr, up_ptr[i], Hb);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) H[c] = ld(Hb[c]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) H[c] = ld(cpl[k * 32 + 18 + c]);
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) b[c] = warp_sum(b[c]);
-
-  if (lane != 0) return;
-
-  double gi[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    gi[a] = kMixed ? (double)g_hi[3 * (int64_t)i + a] + (double)g_lo[3 * (int64_t)i + a] : g64[3 * (int64_t)i + a];
-  double H[9], L[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) H[q] = (double)Hii[q];
-
-  double dx[3] = {-gi[0], -gi[1], -gi[2]};
+  for (int a = 0; a < 3; ++a) {
+    if constexpr (kMixed) gi[a] = V{g_hi[3 * (int64_t)i + a], g_lo[3 * (int64_t)i + a]};
+    else gi[a] = Ar::mk(g64[3 * (int64_t)i + a]);
+  }
+  V M[9], rhs[3];
   int fb = -1;
   bool done = false;
   if (kUpd != CC_UPDATE_CD) {
+    const int m = sup_ptr[i + 1] - sup_ptr[i];
     if (m == 0) {
       fb = 0;
     } else {
-      double Htd[9], Ad[9], bd[3] = {(double)b[0], (double)b[1], (double)b[2]};
+      const V t0 = ld(cpl[k * 32 + 0]), t1 = ld(cpl[k * 32 + 1]), t2 = ld(cpl[k * 32 + 2]);
+      const V t3 = ld(cpl[k * 32 + 3]), t4 = ld(cpl[k * 32 + 4]), t5 = ld(cpl[k * 32 + 5]);
+      const V Ht[9] = {t0, t1, t2, t1, t3, t4, t2, t4, t5};
+      V b[3];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        Htd[q] = (double)Ht[q];
-        Ad[q] = (double)A[q];
-      }
+      for (int c = 0; c < 3; ++c) b[c] = ld(cpl[k * 32 + 15 + c]);
       if (kUpd == CC_UPDATE_JGS2) {
-        double M[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) M[q] = H[q] + Htd[q];
-        if (chol3(M, L, kPivotRel)) {
-          double r[3] = {-(gi[0] + bd[0]), -(gi[1] + bd[1]), -(gi[2] + bd[2])};
-          chol3_solve(L, r);
-          dx[0] = r[0]; dx[1] = r[1]; dx[2] = r[2];
+        for (int c = 0; c < 9; ++c) M[c] = Ar::add(H[c], Ht[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rhs[c] = Ar::add(gi[c], b[c]);
+        done = true;
+      } else {
+        V adj[6], det;
+        if (sym3_adj<AR>(Ht, rel, adj, &det)) {
+          V A[9];
+#pragma unroll
+          for (int c = 0; c < 9; ++c) A[c] = ld(cpl[k * 32 + 6 + c]);
+          const V inv = Ar::div(Ar::mkf(1.0f), det);
+          V Hi[9] = {adj[0], adj[1], adj[2], adj[1], adj[3], adj[4], adj[2], adj[4], adj[5]};
+#pragma unroll
+          for (int c = 0; c < 9; ++c) Hi[c] = Ar::mul(Hi[c], inv);
+          // W = A Ht^{-1};  S = W A^T;  gt = g_i - W b
+          V W[9];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              W[3 * r + c] = Ar::fma(A[3 * r + 2], Hi[6 + c], Ar::fma(A[3 * r + 1], Hi[3 + c], Ar::mul(A[3 * r], Hi[c])));
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const V Src = Ar::fma(W[3 * r + 2], A[3 * c + 2], Ar::fma(W[3 * r + 1], A[3 * c + 1], Ar::mul(W[3 * r], A[3 * c])));
+              M[3 * r + c] = Ar::sub(H[3 * r + c], Src);
+            }
+            rhs[r] = Ar::sub(gi[r], Ar::fma(W[3 * r + 2], b[2], Ar::fma(W[3 * r + 1], b[1], Ar::mul(W[3 * r], b[0]))));
+          }
           done = true;
         } else {
           fb = 1;
         }
-      } else {
-        double Lt[9];
-        if (chol3(Htd, Lt, kPivotRel)) {
-          // Z = Ht^{-1} A^T (columns = rows of A), y = Ht^{-1} b
-          double Z[9];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            double col[3] = {Ad[3 * c], Ad[3 * c + 1], Ad[3 * c + 2]};
-            chol3_solve(Lt, col);
-            Z[c] = col[0]; Z[3 + c] = col[1]; Z[6 + c] = col[2];
-          }
-          chol3_solve(Lt, bd);
-          double M[9], gt[3];
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              M[3 * r + c] = H[3 * r + c] - (Ad[3 * r] * Z[c] + Ad[3 * r + 1] * Z[3 + c] + Ad[3 * r + 2] * Z[6 + c]);
-            gt[r] = gi[r] - (Ad[3 * r] * bd[0] + Ad[3 * r + 1] * bd[1] + Ad[3 * r + 2] * bd[2]);
-          }
-          if (chol3(M, L, kPivotRel)) {
-            double r[3] = {-gt[0], -gt[1], -gt[2]};
-            chol3_solve(L, r);
-            dx[0] = r[0]; dx[1] = r[1]; dx[2] = r[2];
-            done = true;
-          } else {
-            fb = 2;
-          }
-        } else {
-          fb = 1;
-        }
       }
     }
   }
-  if (!done) {
-    // coordinate descent step: one Newton step on vertex i
-    if (chol3(H, L, 0.0)) {
-      double r[3] = {-gi[0], -gi[1], -gi[2]};
-      chol3_solve(L, r);
-      dx[0] = r[0]; dx[1] = r[1]; dx[2] = r[2];
+  V dx[3];
+  bool ok = false;
+  if (done) {
+    V adj[6], det;
+    if (sym3_adj<AR>(M, rel, adj, &det)) {
+      const V inv = Ar::neg(Ar::div(Ar::mkf(1.0f), det));
+      dx[0] = Ar::mul(inv, Ar::fma(adj[0], rhs[0], Ar::fma(adj[1], rhs[1], Ar::mul(adj[2], rhs[2]))));
+      dx[1] = Ar::mul(inv, Ar::fma(adj[1], rhs[0], Ar::fma(adj[3], rhs[1], Ar::mul(adj[4], rhs[2]))));
+      dx[2] = Ar::mul(inv, Ar::fma(adj[2], rhs[0], Ar::fma(adj[4], rhs[1], Ar::mul(adj[5], rhs[2]))));
+      ok = true;
     } else {
-      dx[0] = dx[1] = dx[2] = __longlong_as_double(0x7ff8000000000000LL);
+      fb = kUpd == CC_UPDATE_JGS2 ? 1 : 2;
+    }
+  }
+  if (!ok) {
+    // coordinate descent step: one Newton step on vertex i
+    V adj[6], det;
+    if (sym3_adj<AR>(H, Ar::mkf(0.0f), adj, &det)) {
+      const V inv = Ar::neg(Ar::div(Ar::mkf(1.0f), det));
+      dx[0] = Ar::mul(inv, Ar::fma(adj[0], gi[0], Ar::fma(adj[1], gi[1], Ar::mul(adj[2], gi[2]))));
+      dx[1] = Ar::mul(inv, Ar::fma(adj[1], gi[0], Ar::fma(adj[3], gi[1], Ar::mul(adj[4], gi[2]))));
+      dx[2] = Ar::mul(inv, Ar::fma(adj[2], gi[0], Ar::fma(adj[4], gi[1], Ar::mul(adj[5], gi[2]))));
+    } else {
+      atomicOr(err, 1ull);
+      return;
     }
   }
   if (fb >= 0) atomicAdd(&fallback[fb], 1ull);
-  if (!(isfinite(dx[0]) && isfinite(dx[1]) && isfinite(dx[2]))) {
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = Ar::to_double(dx[a]);
+  if (!(isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]))) {
     atomicOr(err, 1ull);
     return;
   }
   double xn[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    xn[a] = x[a * n + i] + dx[a];
+    xn[a] = x[a * n + i] + d[a];
     x[a * n + i] = xn[a];
   }
   if (kMixed) {
@@ -253,20 +347,32 @@ __global__ void k_local_solve(const int32_t* __restrict__ verts, int64_t count, 
 
 template <typename HT, bool kMixed, int kUpd>
 void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
-                const float* g_hi, const float* g_lo, double* x, SweepCounters c, cudaStream_t s) {
-  const int wpb = 4;
-  const int hs = m.hash_size > 0 ? m.hash_size : 32;
-  int bits = 0;
-  while ((1 << bits) < hs) ++bits;
-  const int supm = m.sup_max > 0 ? m.sup_max : 1;
-  const size_t smem = (size_t)wpb * warp_smem_bytes<HT>(supm, hs);
-  auto kern = k_local_solve<HT, kMixed, kUpd>;
-  CCG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t blocks = (count + wpb - 1) / wpb;
-  kern<<<(unsigned)blocks, wpb * 32, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_bsr_ptr.p,
-                                                m.d_bsr_col.p, bsr, g64, g_hi, g_lo, m.n, bits, supm, x,
-                                                kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr,
-                                                c.fallback, c.error);
+                const float* g_hi, const float* g_lo, HT* cpl, double* x, SweepCounters c, cudaStream_t s) {
+  float4* xh = kMixed ? m.mx.x_hi.p : nullptr;
+  float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
+  if (kUpd != CC_UPDATE_CD) {
+    const int hs = m.hash_size > 0 ? m.hash_size : 32;
+    int bits = 0;
+    while ((1 << bits) < hs) ++bits;
+    const int supm = m.sup_max > 0 ? m.sup_max : 1;
+    const size_t smem = cta_smem_bytes<HT>(supm, hs);
+    CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+    auto kern = k_couple<HT, kMixed, kUpd>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    kern<<<(unsigned)count, kSolveThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
+                                                      m.d_up_col.p, bsr, g64, g_hi, bits, supm, cpl);
+    CCG_CUDA(cudaGetLastError());
+  }
+  const unsigned grid = (unsigned)((count + 127) / 128);
+  if constexpr (kMixed) {
+    const df rel{1e-12f, (float)(1e-12 - (double)1e-12f)};
+    k_condense<df, HT, kMixed, kUpd><<<grid, 128, 0, s>>>(verts, count, cpl, m.d_sup_ptr.p, m.d_up_ptr.p, bsr, g64,
+                                                         g_hi, g_lo, m.n, x, xh, xl, rel, c.fallback, c.error);
+  } else {
+    k_condense<double, HT, kMixed, kUpd><<<grid, 128, 0, s>>>(verts, count, cpl, m.d_sup_ptr.p, m.d_up_ptr.p, bsr,
+                                                             g64, g_hi, g_lo, m.n, x, xh, xl, 1e-12, c.fallback,
+                                                             c.error);
+  }
   CCG_CUDA(cudaGetLastError());
 }
 
@@ -275,30 +381,32 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
 void launch_local_solve_f64(Mesh& m, cc_update upd, const int32_t* verts, int64_t count, double* x,
                             SweepCounters c, cudaStream_t s) {
   if (count <= 0) return;
+  double* cpl = m.f64.cpl.p;
   switch (upd) {
     case CC_UPDATE_CC:
-      launch_one<double, false, CC_UPDATE_CC>(m, verts, count, m.f64.U.p, m.f64.bsr.p, m.f64.g.p, nullptr, nullptr, x, c, s);
+      launch_one<double, false, CC_UPDATE_CC>(m, verts, count, m.f64.U.p, m.f64.bsr.p, m.f64.g.p, nullptr, nullptr, cpl, x, c, s);
       break;
     case CC_UPDATE_CD:
-      launch_one<double, false, CC_UPDATE_CD>(m, verts, count, m.f64.U.p, m.f64.bsr.p, m.f64.g.p, nullptr, nullptr, x, c, s);
+      launch_one<double, false, CC_UPDATE_CD>(m, verts, count, m.f64.U.p, m.f64.bsr.p, m.f64.g.p, nullptr, nullptr, cpl, x, c, s);
       break;
     default:
-      launch_one<double, false, CC_UPDATE_JGS2>(m, verts, count, m.f64.U.p, m.f64.bsr.p, m.f64.g.p, nullptr, nullptr, x, c, s);
+      launch_one<double, false, CC_UPDATE_JGS2>(m, verts, count, m.f64.U.p, m.f64.bsr.p, m.f64.g.p, nullptr, nullptr, cpl, x, c, s);
   }
 }
 
 void launch_local_solve_mixed(Mesh& m, cc_update upd, const int32_t* verts, int64_t count, double* x,
                               SweepCounters c, cudaStream_t s) {
   if (count <= 0) return;
+  float* cpl = m.mx.cpl.p;
   switch (upd) {
     case CC_UPDATE_CC:
-      launch_one<float, true, CC_UPDATE_CC>(m, verts, count, m.mx.U.p, m.mx.bsr.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, x, c, s);
+      launch_one<float, true, CC_UPDATE_CC>(m, verts, count, m.mx.U.p, m.mx.bsr.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, cpl, x, c, s);
       break;
     case CC_UPDATE_CD:
-      launch_one<float, true, CC_UPDATE_CD>(m, verts, count, m.mx.U.p, m.mx.bsr.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, x, c, s);
+      launch_one<float, true, CC_UPDATE_CD>(m, verts, count, m.mx.U.p, m.mx.bsr.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, cpl, x, c, s);
       break;
     default:
-      launch_one<float, true, CC_UPDATE_JGS2>(m, verts, count, m.mx.U.p, m.mx.bsr.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, x, c, s);
+      launch_one<float, true, CC_UPDATE_JGS2>(m, verts, count, m.mx.U.p, m.mx.bsr.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, cpl, x, c, s);
   }
 }
 

@@ -85,11 +85,13 @@ void build_topology(Mesh& m) {
   for (int64_t v = 0; v < n; ++v)
     m.max_valence = std::max<int32_t>(m.max_valence, (int32_t)(m.vt_ptr[v + 1] - m.vt_ptr[v]));
 
-  // ---- 1-ring neighbours (ascending, self excluded) and block pattern
+  // ---- 1-ring neighbours (ascending, self excluded) and the upper block
+  //      pattern: row j holds columns l >= j of its 1-ring plus j itself,
+  //      ascending, so the diagonal block comes first
   m.nbr_ptr.assign(n + 1, 0);
   m.nbr_idx.clear();
-  m.bsr_ptr.assign(n + 1, 0);
-  m.bsr_col.clear();
+  m.up_ptr.assign(n + 1, 0);
+  m.up_col.clear();
   std::vector<int32_t> tmp;
   for (int64_t v = 0; v < n; ++v) {
     tmp.clear();
@@ -102,58 +104,46 @@ void build_topology(Mesh& m) {
     tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
     m.nbr_idx.insert(m.nbr_idx.end(), tmp.begin(), tmp.end());
     m.nbr_ptr[v + 1] = (int64_t)m.nbr_idx.size();
-    tmp.push_back((int32_t)v);
-    std::sort(tmp.begin(), tmp.end());
-    m.bsr_col.insert(m.bsr_col.end(), tmp.begin(), tmp.end());
-    m.bsr_ptr[v + 1] = (int64_t)m.bsr_col.size();
+    m.up_col.push_back((int32_t)v);
+    for (int32_t u : tmp)
+      if (u > v) m.up_col.push_back(u);
+    m.up_ptr[v + 1] = (int64_t)m.up_col.size();
   }
-  m.nnzb = (int64_t)m.bsr_col.size();
-  std::vector<int32_t> bsr_row(m.nnzb);
-  for (int64_t v = 0; v < n; ++v)
-    for (int64_t b = m.bsr_ptr[v]; b < m.bsr_ptr[v + 1]; ++b) bsr_row[b] = (int32_t)v;
+  m.nnz_up = (int64_t)m.up_col.size();
+  m.nnzb = 2 * m.nnz_up - n;
+  CCG_CHECK(m.max_valence <= 1024, CC_ERR_INVALID_ARG, "vertex valence above 1024 tets");
 
-  // ---- sources of every Hessian block of a free row: entry * 4 + corner w,
-  //      in ascending (entry, w) order
-  std::vector<int32_t> blk_cnt(m.nnzb + 1, 0);
-  auto block_of = [&](int64_t row, int32_t col) -> int64_t {
-    auto b0 = m.bsr_col.begin() + m.bsr_ptr[row], b1 = m.bsr_col.begin() + m.bsr_ptr[row + 1];
-    auto it = std::lower_bound(b0, b1, col);
-    return (int64_t)(it - m.bsr_col.begin());
-  };
-  std::vector<int64_t> src_block(16 * T, -1);
+  // ---- per upper block of a free row, its sources among the row's
+  //      (slot k, corner w) pairs, as local indices 4 k + w (ascending)
+  std::vector<int32_t> rs_ptr(m.nnz_up + 1, 0);
+  std::vector<uint16_t> rs_idx;
   for (int64_t v = 0; v < n; ++v) {
-    if (m.pinned[v]) continue;
-    for (int64_t e = m.vt_ptr[v]; e < m.vt_ptr[v + 1]; ++e) {
-      const int32_t* tv = &m.tets[4 * m.vt_tet[e]];
-      for (int w = 0; w < 4; ++w) {
-        int64_t b = block_of(v, tv[w]);
-        src_block[4 * e + w] = b;
-        blk_cnt[b + 1]++;
-      }
+    const int64_t p0 = m.up_ptr[v], p1 = m.up_ptr[v + 1];
+    if (m.pinned[v]) {
+      for (int64_t p = p0; p < p1; ++p) rs_ptr[p + 1] = (int32_t)rs_idx.size();
+      continue;
     }
-  }
-  for (int64_t b = 0; b < m.nnzb; ++b) blk_cnt[b + 1] += blk_cnt[b];
-  std::vector<int32_t> blk_src(std::max<int64_t>(blk_cnt[m.nnzb], 1));
-  {
-    std::vector<int32_t> cur(blk_cnt.begin(), blk_cnt.end() - 1);
-    for (int64_t k = 0; k < 16 * T; ++k)
-      if (src_block[k] >= 0) blk_src[cur[src_block[k]]++] = (int32_t)k;
+    for (int64_t p = p0; p < p1; ++p) {
+      const int32_t col = m.up_col[p];
+      for (int64_t e = m.vt_ptr[v]; e < m.vt_ptr[v + 1]; ++e) {
+        const int32_t* tv = &m.tets[4 * m.vt_tet[e]];
+        for (int w = 0; w < 4; ++w)
+          if (tv[w] == col) rs_idx.push_back((uint16_t)(4 * (e - m.vt_ptr[v]) + w));
+      }
+      rs_ptr[p + 1] = (int32_t)rs_idx.size();
+    }
   }
 
-  // ---- free rows, their blocks, tets with a free vertex
-  std::vector<int32_t> free_rows, free_blocks, active;
+  // ---- free rows, tets with a free vertex
+  std::vector<int32_t> free_rows, active;
   for (int64_t v = 0; v < n; ++v)
-    if (!m.pinned[v]) {
-      free_rows.push_back((int32_t)v);
-      for (int64_t b = m.bsr_ptr[v]; b < m.bsr_ptr[v + 1]; ++b) free_blocks.push_back((int32_t)b);
-    }
+    if (!m.pinned[v]) free_rows.push_back((int32_t)v);
   for (int64_t t = 0; t < T; ++t) {
     bool any = false;
     for (int c = 0; c < 4; ++c) any |= !m.pinned[m.tets[4 * t + c]];
     if (any) active.push_back((int32_t)t);
   }
   m.n_free = (int64_t)free_rows.size();
-  m.n_free_blocks = (int64_t)free_blocks.size();
   m.n_active_tets = (int64_t)active.size();
 
   // ---- upload
@@ -164,7 +154,6 @@ void build_topology(Mesh& m) {
     Bm_df[k] = make_float2(hi, (float)(Bm[k] - (double)hi));
     Bm32[k] = hi;
   }
-  std::vector<int32_t> i32(n + 1);
   auto to32 = [&](const std::vector<int64_t>& a) {
     std::vector<int32_t> r(a.size());
     for (size_t k = 0; k < a.size(); ++k) r[k] = (int32_t)a[k];
@@ -176,19 +165,43 @@ void build_topology(Mesh& m) {
   m.d_Bm_df.upload(Bm_df, s);
   m.d_Bm32.upload(Bm32, s);
   m.d_vol.upload(vol, s);
-  m.d_mass.upload(m.mass, s);
+  {
+    const double w = m.h > 0.0 ? m.h * m.h : 1.0;
+    std::vector<double> vw(T);
+    std::vector<float> vw32(T);
+    std::vector<float2> vwdf(T);
+    for (int64_t t = 0; t < T; ++t) {
+      vw[t] = vol[t] * w;
+      vw32[t] = (float)vw[t];
+      vwdf[t] = make_float2(vw32[t], (float)(vw[t] - (double)vw32[t]));
+    }
+    m.d_volw.upload(vw, s);
+    m.d_volw32.upload(vw32, s);
+    m.d_volw_df.upload(vwdf, s);
+    std::vector<float> m32(n);
+    std::vector<float2> mdf(n);
+    for (int64_t v = 0; v < n; ++v) {
+      m32[v] = (float)m.mass[v];
+      mdf[v] = make_float2(m32[v], (float)(m.mass[v] - (double)m32[v]));
+    }
+    m.d_mass.upload(m.mass, s);
+    m.d_mass32.upload(m32, s);
+    m.d_mass_df.upload(mdf, s);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
   m.d_pinned.upload(m.pinned, s);
-  auto vt32 = to32(m.vt_ptr), nb32 = to32(m.nbr_ptr), bp32 = to32(m.bsr_ptr);
+  auto vt32 = to32(m.vt_ptr), nb32 = to32(m.nbr_ptr), up32 = to32(m.up_ptr);
   m.d_vt_ptr.upload(vt32, s);
+  m.d_vt_tet.upload(m.vt_tet, s);
+  std::vector<uint8_t> corner8(m.vt_corner.begin(), m.vt_corner.end());
+  m.d_vt_corner.upload(corner8, s);
   m.d_nbr_ptr.upload(nb32, s);
   m.d_nbr_idx.upload(m.nbr_idx, s);
-  m.d_bsr_ptr.upload(bp32, s);
-  m.d_bsr_col.upload(m.bsr_col, s);
-  m.d_bsr_row.upload(bsr_row, s);
-  m.d_blk_ptr.upload(blk_cnt, s);
-  m.d_blk_src.upload(blk_src, s);
+  m.d_up_ptr.upload(up32, s);
+  m.d_up_col.upload(m.up_col, s);
+  m.d_rs_ptr.upload(rs_ptr, s);
+  m.d_rs_idx.upload(rs_idx, s);
   m.d_free_rows.upload(free_rows, s);
-  m.d_free_blocks.upload(free_blocks, s);
   m.d_all_tets.upload(active, s);
   CCG_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
 }

@@ -178,6 +178,26 @@ def test_mixed_solve_reaches_tolerance_and_matches_fp64():
     assert abs(r64.iterations - rmx.iterations) <= 2
 
 
+def test_graph_replay_matches_launch_by_launch_and_profiles():
+    scene = meshgen.stretch_box(8, 8, 8, E=1e5, nu=0.3, factor=1.2, name="cube8_nu03")
+    m = _gpu(scene, 2)
+    out = {}
+    for graph in (False, True):
+        m.profile_enable(True)
+        xd = cc.to_soa(scene.x0)
+        r = m.solve_step(xd, precision="mixed", tol=0.0, max_iters=24, min_iters=24, check_every=8,
+                         use_graph=graph, history=True)
+        prof = m.profile_read()
+        m.profile_enable(False)
+        out[graph] = (cc.from_soa(xd), r.residuals)
+        assert r.iterations == 24
+        for k in ("tet_eval", "gather", "local_solve", "reduce"):
+            assert prof[k]["launches"] > 0 and prof[k]["ms"] > 0, (graph, k)
+        assert prof["total_launches"] >= 24 * 8 * 3
+    np.testing.assert_array_equal(out[False][0], out[True][0])
+    np.testing.assert_array_equal(out[False][1], out[True][1])
+
+
 # ---------------------------------------------------------------- dynamics
 def test_dynamic_step_matches_oracle():
     scene = meshgen.cantilever(3, 3, 8, cell=1 / 16, E=1e5, nu=0.3)
