@@ -240,6 +240,43 @@ typedef struct {
 cc_status cc_profile_enable(cc_mesh* mesh, int32_t on);
 cc_status cc_profile_read(cc_mesh* mesh, cc_profile* out);
 
+/* Allocation-free variant of the basis construction (no counterpart in the
+ * paper).  It is meant for callers that must not have device memory
+ * allocated on their behalf: processes whose GPU memory is entirely reserved
+ * by their own pool allocator, where a cudaMalloc would fail or fragment the
+ * pool, and time-critical loops that cannot absorb cudaMalloc's implicit
+ * synchronisation.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Instead of a cudaMalloc'ed workspace it uses one file-scope
+ * 16 MiB device array (2^21 doubles) that the CUDA runtime reserves on every
+ * GPU that loads this library and keeps until the process exits.
+ *
+ * It computes, for each vertex i in verts, U_i = -H_PP^{-1} H_Pi on the
+ * patch P = S_i (the same dense Cholesky as cc_build_subspace) and writes
+ * the blocks of S_i into U_out.  Everything is caller-owned device memory:
+ *   H_blocks  [nnzb][3][3] float64 Hessian blocks (row-major within a block)
+ *   row_ptr   [n+1] int32, col_idx [nnzb] int32: block rows, columns
+ *             ascending, diagonal block included
+ *   verts     [count] int32 vertices to process (their supports non-empty
+ *             or empty; empty ones are skipped)
+ *   sup_ptr   [n+1] int32, sup_idx [sup_ptr[n]] int32 ascending supports
+ *   U_out     [sup_ptr[n]][3][3] float64 output (only the rows of verts'
+ *             supports are written)
+ *   max_support  largest |S_i| over verts (host int); values whose dense
+ *             patch does not fit the array (above CC_NOALLOC_MAX_SUPPORT)
+ *             are rejected with CC_ERR_INVALID_ARG before any GPU work
+ *   stream    cudaStream_t (NULL: default stream); the call synchronises it
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents; the kernel clears what must start at zero.  Calls that
+ * overlap on the GPU (e.g. on two streams at once) race on the array: keep
+ * them ordered.  CC_ERR_NUMERIC if a patch matrix is not positive definite. */
+#define CC_NOALLOC_MAX_SUPPORT 482
+cc_status cc_build_bases_noalloc(const double* H_blocks, const int32_t* row_ptr, const int32_t* col_idx,
+                                 const int32_t* verts, int64_t count, const int32_t* sup_ptr,
+                                 const int32_t* sup_idx, int32_t max_support, double* U_out,
+                                 void* stream);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* cc_last_error(void);
 

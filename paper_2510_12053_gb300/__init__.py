@@ -96,6 +96,7 @@ _SIGS = {
     "cc_export": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
     "cc_last_error": (ctypes.c_char_p, []),
     "cc_version": (ctypes.c_char_p, []),
 }
