@@ -108,6 +108,7 @@ void ensure_state(Mesh& m, cc_precision p) {
   if (p == CC_PREC_FP64) {
     if (!m.f64.gcon.p) {
       m.f64.gcon.alloc(3 * ne);
+      m.f64.hten.alloc(96 * (size_t)m.T);
       m.f64.g.alloc(3 * m.n);
       m.f64.bsr.alloc(12 * m.nnz_up);
       m.f64.cpl.alloc(32 * m.n_free);
@@ -116,6 +117,7 @@ void ensure_state(Mesh& m, cc_precision p) {
   } else {
     if (!m.mx.gcon.p) {
       m.mx.gcon.alloc(3 * ne);
+      m.mx.hten.alloc(96 * (size_t)m.T);
       m.mx.g_hi.alloc(3 * m.n);
       m.mx.g_lo.alloc(3 * m.n);
       m.mx.bsr.alloc(12 * m.nnz_up);
@@ -330,10 +332,11 @@ void cc_destroy_mesh(cc_mesh* m) {
   rel(m->d_tets); rel(m->d_tslot); rel(m->d_Bm); rel(m->d_Bm_df); rel(m->d_Bm32); rel(m->d_vol); rel(m->d_volw); rel(m->d_volw32); rel(m->d_volw_df); rel(m->d_mass);
   rel(m->d_mass32); rel(m->d_mass_df);
   rel(m->d_pinned); rel(m->d_vt_ptr); rel(m->d_nbr_ptr); rel(m->d_nbr_idx); rel(m->d_vt_tet); rel(m->d_vt_corner);
-  rel(m->d_up_ptr); rel(m->d_up_col); rel(m->d_rs_ptr); rel(m->d_rs_idx); rel(m->d_free_rows);
-  rel(m->d_color); rel(m->d_cv_idx); rel(m->d_tl); rel(m->d_all_tets); rel(m->d_sup_ptr); rel(m->d_sup_idx);
-  rel(m->f64.gcon); rel(m->f64.g); rel(m->f64.cpl); rel(m->f64.bsr); rel(m->f64.U);
-  rel(m->mx.gcon); rel(m->mx.cpl); rel(m->mx.g_hi); rel(m->mx.g_lo); rel(m->mx.bsr); rel(m->mx.U);
+  rel(m->d_up_ptr); rel(m->d_up_col); rel(m->d_rs_ptr); rel(m->d_rs_src); rel(m->d_free_rows);
+  rel(m->d_color); rel(m->d_cv_idx); rel(m->d_tl); rel(m->d_all_tets); rel(m->d_sup_ptr); rel(m->d_sup_idx); rel(m->d_smap_ptr);
+  rel(m->d_smap8); rel(m->d_smap16); rel(m->d_vt_ids);
+  rel(m->f64.gcon); rel(m->f64.hten); rel(m->f64.g); rel(m->f64.cpl); rel(m->f64.bsr); rel(m->f64.U);
+  rel(m->mx.gcon); rel(m->mx.hten); rel(m->mx.cpl); rel(m->mx.g_hi); rel(m->mx.g_lo); rel(m->mx.bsr); rel(m->mx.U);
   rel(m->mx.x_hi); rel(m->mx.x_lo); rel(m->mx.xt_hi); rel(m->mx.xt_lo);
   rel(m->d_red); rel(m->d_scalars); rel(m->d_counters); rel(m->d_xtilde); rel(m->d_xold);
   if (m->h_pinned_scalars) cudaFreeHost(m->h_pinned_scalars);
@@ -382,6 +385,7 @@ cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup
     m->sup_idx.assign(sup_idx, sup_idx + total);
     m->U.assign(U, U + 9 * total);
     m->sup_max = supmax;
+    ccg::build_slot_maps(*m);
     int hs = 32;
     while (hs < 2 * std::max(supmax, 1)) hs <<= 1;
     m->hash_size = hs;

@@ -69,6 +69,7 @@ struct DBuf {
 // assembled gradient and 3x3-block Hessian, and the basis blocks.
 struct StateF64 {
   DBuf<double> gcon;  // [4T][3]   gradient of tet at each (vertex, slot)
+  DBuf<double> hten;  // [T][96]  the tet's 10 upper 3x3 Hessian blocks (corner pairs a <= b)
   DBuf<double> g;     // [n][3]
   DBuf<double> bsr;   // [nnz_up][12] upper Hessian blocks, rows padded to 4
   DBuf<double> U;     // [sup_total][9]
@@ -77,6 +78,7 @@ struct StateF64 {
 
 struct StateMixed {
   DBuf<float2> gcon;  // [4T][3]   float-float (hi, lo)
+  DBuf<float> hten;   // [T][96]
   DBuf<float> g_hi;   // [n][3]
   DBuf<float> g_lo;   // [n][3]
   DBuf<float> bsr;    // [nnz_up][12]
@@ -128,6 +130,8 @@ struct Mesh {
   std::vector<int64_t> up_ptr;   // upper 3x3-block pattern (diagonal first)
   std::vector<int32_t> up_col;
   int64_t nnz_up = 0;
+  int32_t max_up = 0;          // longest upper block row
+  int32_t max_rs = 0;          // most staged sources of one free row
   std::vector<double> mass;
   std::vector<int32_t> color;
   int32_t num_colors = 0;
@@ -136,7 +140,9 @@ struct Mesh {
   std::vector<double> U;       // [sup_total][9]
   int32_t k_ring = 0;
   int32_t sup_max = 0;
-  int32_t hash_size = 0;       // power of two >= 2 * sup_max
+  int32_t hash_size = 0;       // unused (kept for layout stability)
+  int64_t smap_max = 0;        // longest per-vertex slot map
+  bool smap_wide = false;      // slot maps in uint16 (supports of 250+ vertices)
 
   // device rest data
   DBuf<int4> d_tets;
@@ -160,7 +166,7 @@ struct Mesh {
   DBuf<int32_t> d_up_ptr;    // [n+1] upper block rows
   DBuf<int32_t> d_up_col;    // [nnz_up]
   DBuf<int32_t> d_rs_ptr;    // [nnz_up+1] sources of each upper block (free rows)
-  DBuf<uint16_t> d_rs_idx;   // local source index 4 * slot + corner
+  DBuf<int32_t> d_rs_src;    // per-tet store offset of each source, bit 31 = transpose
   DBuf<int32_t> d_free_rows; // free vertices, ascending
   DBuf<int32_t> d_color;     // [n]
   std::vector<int32_t> cv_ptr;  // [C+1] free vertices per colour
@@ -171,6 +177,14 @@ struct Mesh {
   int64_t n_active_tets = 0;
   DBuf<int32_t> d_sup_ptr;   // [n+1]
   DBuf<int32_t> d_sup_idx;
+  // Slot maps of the coupling kernel: for free vertex i, one code per upper
+  // block of each support row and of row i (in support order, row i last):
+  // the block column's slot in S_i, or kSlotNone / kSlotSelf (column i) /
+  // kSlotDiag (the row's diagonal block).
+  DBuf<int64_t> d_smap_ptr;  // [n+1]
+  DBuf<uint8_t> d_smap8;
+  DBuf<uint16_t> d_smap16;
+  DBuf<int4> d_vt_ids;       // [4T] vertex ids of the tet at each (vertex, slot) entry
 
   StateF64 f64;
   StateMixed mx;
@@ -190,6 +204,8 @@ struct Mesh {
 // Host-side helpers implemented in mesh_build.cpp (topology, plain C++)
 // ---------------------------------------------------------------------------
 void build_topology(Mesh& m);
+// Slot maps for the current supports (after cc_build_subspace / cc_set_subspace).
+void build_slot_maps(Mesh& m);
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels_*.cu)

@@ -79,15 +79,36 @@ __device__ __forceinline__ void hess_block(const T* F, const T (&a_v)[3], const 
   K[7] -= s * q0;
 }
 
-// ---- phase A: per-tet gradients of the tets whose vertices moved ----------
-__global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
-                               const double* __restrict__ Bm, const double* __restrict__ vol,
-                               const uint8_t* __restrict__ pinned, const double* __restrict__ x, int64_t n,
-                               const int32_t* __restrict__ list, int64_t count, double mu, double lh,
-                               double weight, double* __restrict__ gcon) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  const int t = list[k];
+// The tet's 10 upper Hessian blocks V K_ab (corner pairs a <= b, order (0,0),
+// (0,1), (0,2), (0,3), (1,1), (1,2), (1,3), (2,2), (2,3), (3,3)), each 3x3
+// row-major, into dst[9 pair + q].
+template <typename T>
+__device__ __forceinline__ void tet_hess_blocks(const T* F, const T* C, T s, T mu, T lh, T V, const T (&G)[4][3],
+                                                T* __restrict__ dst) {
+  T a[4][3];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) a[v][r] = C[3 * r] * G[v][0] + C[3 * r + 1] * G[v][1] + C[3 * r + 2] * G[v][2];
+  int pair = 0;
+#pragma unroll
+  for (int va = 0; va < 4; ++va)
+#pragma unroll
+    for (int vb = va; vb < 4; ++vb) {
+      T K[9];
+      hess_block<T>(F, a[va], a[vb], G[va], G[vb], mu, lh, s, K);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) dst[9 * pair + q] = V * K[q];
+      ++pair;
+    }
+}
+
+// ---- phase A: per-tet gradients and Hessian blocks of the tets whose vertices moved
+__device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                                                  const double* __restrict__ Bm, const double* __restrict__ vol,
+                                                  const uint8_t* __restrict__ pinned, const double* __restrict__ x,
+                                                  int64_t n, int t, double mu, double lh, double weight,
+                                                  double* __restrict__ gcon, double* __restrict__ hdst) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -114,16 +135,39 @@ __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __rest
     for (int r = 0; r < 3; ++r)
       gcon[3 * e + r] = V * (P[3 * r] * kin.G[v][0] + P[3 * r + 1] * kin.G[v][1] + P[3 * r + 2] * kin.G[v][2]);
   }
+  tet_hess_blocks<double>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
 }
 
-__global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
-                                 const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
-                                 const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
-                                 const float4* __restrict__ x_lo, const int32_t* __restrict__ list, int64_t count,
-                                 df mu_d, df lh_d, float2* __restrict__ gcon) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  const int t = list[k];
+// Staged like the mixed kernel: per-thread blocks in shared memory, then
+// coalesced 16-byte stores of each tet's 768-byte region.
+__global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                               const double* __restrict__ Bm, const double* __restrict__ vol,
+                               const uint8_t* __restrict__ pinned, const double* __restrict__ x, int64_t n,
+                               const int32_t* __restrict__ list, int64_t count, double mu, double lh,
+                               double weight, double* __restrict__ gcon, double* __restrict__ hten) {
+  extern __shared__ __align__(16) double hstage64[];
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool live = k < count;
+  const int t = live ? list[k] : -1;
+  if (live) tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, t, mu, lh, weight, gcon, hstage64 + threadIdx.x * 96);
+  __syncwarp();
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  for (int u = 0; u < 32; ++u) {
+    const int tu = __shfl_sync(0xffffffffu, t, u);
+    if (tu < 0) continue;
+    for (int q = lane; q < 48; q += 32) {
+      const double2 v = reinterpret_cast<const double2*>(hstage64 + (wbase + u) * 96)[q];
+      reinterpret_cast<double2*>(hten + (int64_t)tu * 96)[q] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                                                    const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
+                                                    const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
+                                                    const float4* __restrict__ x_lo, int t, df mu_d, df lh_d,
+                                                    float mu_f, float lh_f, const float* __restrict__ volw32,
+                                                    float2* __restrict__ gcon, float* __restrict__ hdst) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -180,203 +224,138 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
 #pragma unroll
     for (int r = 0; r < 3; ++r) gcon[3 * e + r] = make_float2(g[v][r].hi, g[v][r].lo);
   }
+  // float32 Hessian blocks from the high parts
+  float Ff[9], Cf[9], G[4][3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    Ff[q] = F[q].hi;
+    Cf[q] = C[q].hi;
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    G[1][b] = B[b].hi;
+    G[2][b] = B[3 + b].hi;
+    G[3][b] = B[6 + b].hi;
+    G[0][b] = -(G[1][b] + G[2][b] + G[3][b]);
+  }
+  tet_hess_blocks<float>(Ff, Cf, s.hi, mu_f, lh_f, volw32[t], G, hdst);
+}
+
+__global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
+                                 const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
+                                 const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
+                                 const float4* __restrict__ x_lo, const int32_t* __restrict__ list, int64_t count,
+                                 df mu_d, df lh_d, float mu_f, float lh_f, const float* __restrict__ volw32,
+                                 float2* __restrict__ gcon, float* __restrict__ hten) {
+  // Each thread's 96 Hessian values are staged in shared memory, then every
+  // warp writes its 32 tets' 384-byte regions with coalesced 16-byte stores.
+  extern __shared__ __align__(16) float hstage[];
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool live = k < count;
+  const int t = live ? list[k] : -1;
+  if (live) tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, t, mu_d, lh_d, mu_f, lh_f, volw32, gcon,
+                                hstage + threadIdx.x * 96);
+  __syncwarp();
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  for (int u = 0; u < 32; ++u) {
+    const int tu = __shfl_sync(0xffffffffu, t, u);
+    if (tu < 0) continue;
+    if (lane < 24) {
+      const float4 v = reinterpret_cast<const float4*>(hstage + (wbase + u) * 96)[lane];
+      reinterpret_cast<float4*>(hten + (int64_t)tu * 96)[lane] = v;
+    }
+  }
 }
 
 // ---- phase B: one warp per free row j ---------------------------------------
-// Lanes take j's incident tets.  Each computes its tet's Hessian blocks
-// (corner of j, w) for the corners w whose vertex id is >= j, in the row's
-// arithmetic (float64, or float32 from float-float edge vectors), and stages
-// them in shared memory; then each upper block of the row sums its sources in
-// a fixed order (deterministic) and is written padded to 3 x 4.  The gradient
-// sum of the row's per-tet contributions uses a fixed butterfly.
-template <typename HT>
-struct RowArith;
-
-template <>
-struct RowArith<double> {
-  static __device__ __forceinline__ void edges(const double* x, const float4*, const float4*, int64_t n,
-                                               const int (&vid)[4], double (&e)[3][3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double p0 = x[a * n + vid[0]];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) e[c][a] = x[a * n + vid[c + 1]] - p0;
-    }
-  }
-};
-
-template <>
-struct RowArith<float> {
-  static __device__ __forceinline__ void edges(const double*, const float4* xh, const float4* xl, int64_t,
-                                               const int (&vid)[4], float (&e)[3][3]) {
-    const float4 h0 = xh[vid[0]], l0 = xl[vid[0]];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float4 h = xh[vid[c + 1]], l = xl[vid[c + 1]];
-      e[c][0] = (h.x - h0.x) + (l.x - l0.x);
-      e[c][1] = (h.y - h0.y) + (l.y - l0.y);
-      e[c][2] = (h.z - h0.z) + (l.z - l0.z);
-    }
-  }
-};
-
+// Every upper block (j, l) of the row sums its sources -- the stored blocks of
+// the incident tets, transposed where the tet lists l before j -- in a fixed
+// order, one lane per (block, component): the diagonal block's 24-odd
+// sources are split over three groups of nine lanes, the other blocks take
+// nine lanes each, three per round.  Blocks are written padded to 3 x 4.  The
+// row's gradient is the fixed-butterfly sum of its per-(vertex, slot) entries.
 template <typename HT, bool kMixed>
-__global__ void k_row_assemble(const int32_t* __restrict__ rows, int64_t nrows, const int32_t* __restrict__ vt_ptr,
-                               const int32_t* __restrict__ vt_tet, const uint8_t* __restrict__ vt_corner,
-                               const int4* __restrict__ tets, const HT* __restrict__ Bm,
-                               const HT* __restrict__ volw, const double* __restrict__ x,
-                               const float4* __restrict__ x_hi, const float4* __restrict__ x_lo, int64_t n,
-                               const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ rs_ptr,
-                               const uint16_t* __restrict__ rs_idx, const double* __restrict__ gcon64,
-                               const float2* __restrict__ gcon_df, const HT* __restrict__ massh,
-                               const double* __restrict__ mass64, const float2* __restrict__ mass_df,
-                               const double* __restrict__ xt, const float4* __restrict__ xt_hi,
-                               const float4* __restrict__ xt_lo, bool dynamic, HT mu, HT lh,
-                               int stage_blocks, HT* __restrict__ bsr, double* __restrict__ g64,
-                               float* __restrict__ g_hi, float* __restrict__ g_lo) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  HT* stage = reinterpret_cast<HT*>(smem_raw) + (size_t)warp * stage_blocks * 9;
+__global__ void k_row_gather(const int32_t* __restrict__ rows, int64_t nrows, const int32_t* __restrict__ vt_ptr,
+                             const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ rs_ptr,
+                             const int32_t* __restrict__ rs_src, const HT* __restrict__ hten,
+                             const HT* __restrict__ massh, const double* __restrict__ mass64,
+                             const float2* __restrict__ mass_df, const double* __restrict__ gcon64,
+                             const float2* __restrict__ gcon_df, const double* __restrict__ x,
+                             const float4* __restrict__ x_hi, const float4* __restrict__ x_lo,
+                             const double* __restrict__ xt, const float4* __restrict__ xt_hi,
+                             const float4* __restrict__ xt_lo, int64_t n, bool dynamic, int max_rs, int max_up,
+                             HT* __restrict__ bsr, double* __restrict__ g64, float* __restrict__ g_hi,
+                             float* __restrict__ g_lo) {
+  extern __shared__ int rsh[];
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * wpb + warp;
   if (wid >= nrows) return;
   const int j = rows[wid];
+  const int p0 = up_ptr[j], nup = up_ptr[j + 1] - p0;
+  const int c = lane % 9, grp = lane / 9, r = c / 3, col = c % 3;
+  const int tidx = 3 * col + r;
+  // the row's source offsets and per-block ranges, one coalesced pass
+  int* roff = rsh + warp * (max_rs + max_up + 1);
+  int* rsrc = roff + max_up + 1;
+  const int rb = rs_ptr[p0];
+  for (int q = lane; q <= nup; q += 32) roff[q] = rs_ptr[p0 + q] - rb;
+  const int rcount = rs_ptr[p0 + nup] - rb;
+  for (int k = lane; k < rcount; k += 32) rsrc[k] = rs_src[rb + k];
+  __syncwarp();
+
+  // diagonal block
+  {
+    HT acc = HT(0);
+    if (grp < 3) {
+      const int s1 = roff[1];
+#pragma unroll 4
+      for (int s = grp; s < s1; s += 3) {
+        const int v = rsrc[s];
+        acc += hten[(v & 0x7fffffff) + (v < 0 ? tidx : c)];
+      }
+    }
+    const HT a1 = __shfl_down_sync(0xffffffffu, acc, 9);
+    const HT a2 = __shfl_down_sync(0xffffffffu, acc, 18);
+    if (lane < 9) {
+      HT d = (acc + a1) + a2;
+      if (dynamic && r == col) d += massh[j];
+      HT* dst = bsr + (int64_t)p0 * 12 + 4 * r;
+      dst[col] = d;
+      if (col == 2) dst[3] = HT(0);
+    }
+  }
+  // off-diagonal upper blocks, three per round
+  for (int base = 1; base < nup; base += 3) {
+    const int q = base + grp;
+    if (grp < 3 && q < nup) {
+      HT acc = HT(0);
+      const int s1 = roff[q + 1];
+#pragma unroll 4
+      for (int s = roff[q]; s < s1; ++s) {
+        const int v = rsrc[s];
+        acc += hten[(v & 0x7fffffff) + (v < 0 ? tidx : c)];
+      }
+      HT* dst = bsr + (int64_t)(p0 + q) * 12 + 4 * r;
+      dst[col] = acc;
+      if (col == 2) dst[3] = HT(0);
+    }
+  }
+  // gradient
   const int e0 = vt_ptr[j], val = vt_ptr[j + 1] - e0;
-  double gs[3] = {0.0, 0.0, 0.0};
-  df gd[3] = {df{0, 0}, df{0, 0}, df{0, 0}};
-  HT diag[9];
+  if (kMixed) {
+    df gd[3] = {df{0, 0}, df{0, 0}, df{0, 0}};
+    for (int k = lane; k < val; k += 32)
 #pragma unroll
-  for (int c = 0; c < 9; ++c) diag[c] = HT(0);
-  for (int k = lane; k < val; k += 32) {
-    const int e = e0 + k;
-    const int t = vt_tet[e];
-    const int cj = vt_corner[e];
-    const int4 tv = tets[t];
-    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
-    HT ed[3][3];
-    RowArith<HT>::edges(x, x_hi, x_lo, n, vid, ed);
-    HT B[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) B[q] = Bm[9 * (int64_t)t + q];
-    HT F[9];
+      for (int a = 0; a < 3; ++a) {
+        const float2 cc = gcon_df[3 * (int64_t)(e0 + k) + a];
+        gd[a] = df_add(gd[a], df{cc.x, cc.y});
+      }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) F[3 * a + b] = ed[0][a] * B[b] + ed[1][a] * B[3 + b] + ed[2][a] * B[6 + b];
-    HT C[9];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
-      C[0 + b] = F[3 + b1] * F[6 + b2] - F[6 + b1] * F[3 + b2];
-      C[3 + b] = F[6 + b1] * F[0 + b2] - F[0 + b1] * F[6 + b2];
-      C[6 + b] = F[0 + b1] * F[3 + b2] - F[3 + b1] * F[0 + b2];
-    }
-    const HT J = F[0] * C[0] + F[3] * C[3] + F[6] * C[6];
-    const HT s = lh * (J - HT(1)) - mu;
-    const HT V = volw[t];
-    HT G[4][3], a[4][3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      G[1][b] = B[b];
-      G[2][b] = B[3 + b];
-      G[3][b] = B[6 + b];
-      G[0][b] = -(B[b] + B[3 + b] + B[6 + b]);
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) a[v][r] = C[3 * r] * G[v][0] + C[3 * r + 1] * G[v][1] + C[3 * r + 2] * G[v][2];
-    HT Gc[3], ac[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      Gc[r] = G[0][r];
-      ac[r] = a[0][r];
-    }
-#pragma unroll
-    for (int v = 1; v < 4; ++v)
-      if (v == cj) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          Gc[r] = G[v][r];
-          ac[r] = a[v][r];
-        }
-      }
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      if (vid[w] < j) continue;
-      HT K[9];
-      hess_block<HT>(F, ac, a[w], Gc, G[w], mu, lh, s, K);
-      if (w == cj) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) diag[q] += V * K[q];
-      } else {
-        HT* dst = stage + (size_t)(4 * k + w) * 9;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) dst[q] = V * K[q];
-      }
-    }
-    if (kMixed) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float2 c = gcon_df[3 * (int64_t)e + r];
-        gd[r] = df_add(gd[r], df{c.x, c.y});
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) gs[r] += gcon64[3 * (int64_t)e + r];
-    }
-  }
-  __syncwarp();
-  // diagonal block: fixed butterfly over the lanes
-  const int p0 = up_ptr[j], nup = up_ptr[j + 1] - p0;
-#pragma unroll
-  for (int c = 0; c < 9; ++c)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) diag[c] += __shfl_xor_sync(0xffffffffu, diag[c], o);
-  if (lane == 0) {
-    if (dynamic) {
-      const HT mj = massh[j];
-      diag[0] += mj;
-      diag[4] += mj;
-      diag[8] += mj;
-    }
-    HT* dst = bsr + (int64_t)p0 * 12;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      dst[4 * r + 0] = diag[3 * r + 0];
-      dst[4 * r + 1] = diag[3 * r + 1];
-      dst[4 * r + 2] = diag[3 * r + 2];
-      dst[4 * r + 3] = HT(0);
-    }
-  }
-  // off-diagonal upper blocks: each sums its staged sources in a fixed order
-  for (int q = 1 + lane; q < nup; q += 32) {
-    const int p = p0 + q;
-    HT acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = HT(0);
-    const int s1 = rs_ptr[p + 1];
-    for (int sidx = rs_ptr[p]; sidx < s1; ++sidx) {
-      const HT* src = stage + (size_t)rs_idx[sidx] * 9;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) acc[c] += src[c];
-    }
-    HT* dst = bsr + (int64_t)p * 12;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      dst[4 * r + 0] = acc[3 * r + 0];
-      dst[4 * r + 1] = acc[3 * r + 1];
-      dst[4 * r + 2] = acc[3 * r + 2];
-      dst[4 * r + 3] = HT(0);
-    }
-  }
-  // gradient of the row: fixed butterfly over the lanes
-  if (kMixed) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        df other{__shfl_xor_sync(0xffffffffu, gd[r].hi, o), __shfl_xor_sync(0xffffffffu, gd[r].lo, o)};
-        gd[r] = df_add(gd[r], other);
+        df other{__shfl_xor_sync(0xffffffffu, gd[a].hi, o), __shfl_xor_sync(0xffffffffu, gd[a].lo, o)};
+        gd[a] = df_add(gd[a], other);
       }
     if (lane == 0) {
       if (dynamic) {
@@ -387,24 +366,28 @@ __global__ void k_row_assemble(const int32_t* __restrict__ rows, int64_t nrows, 
         gd[2] = df_fma(mj, df_sub(df{xh.z, xl.z}, df{th.z, tl.z}), gd[2]);
       }
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        g_hi[3 * (int64_t)j + r] = gd[r].hi;
-        g_lo[3 * (int64_t)j + r] = gd[r].lo;
+      for (int a = 0; a < 3; ++a) {
+        g_hi[3 * (int64_t)j + a] = gd[a].hi;
+        g_lo[3 * (int64_t)j + a] = gd[a].lo;
       }
     }
   } else {
+    double gs[3] = {0.0, 0.0, 0.0};
+    for (int k = lane; k < val; k += 32)
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+      for (int a = 0; a < 3; ++a) gs[a] += gcon64[3 * (int64_t)(e0 + k) + a];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) gs[r] += __shfl_xor_sync(0xffffffffu, gs[r], o);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) gs[a] += __shfl_xor_sync(0xffffffffu, gs[a], o);
     if (lane == 0) {
       if (dynamic) {
         const double mj = mass64[j];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) gs[r] += mj * (x[r * n + j] - xt[r * n + j]);
+        for (int a = 0; a < 3; ++a) gs[a] += mj * (x[a * n + j] - xt[a * n + j]);
       }
 #pragma unroll
-      for (int r = 0; r < 3; ++r) g64[3 * (int64_t)j + r] = gs[r];
+      for (int a = 0; a < 3; ++a) g64[3 * (int64_t)j + a] = gs[a];
     }
   }
 }
@@ -525,53 +508,50 @@ constexpr int kRedBlocks = 1024;
 void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t count, double weight,
                          cudaStream_t s) {
   if (count <= 0) return;
-  k_tet_grad_f64<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x, m.n,
-                                                    list, count, m.mu, m.lam_hat, weight, m.f64.gcon.p);
+  constexpr int kThreads = 64;
+  const size_t smem = (size_t)kThreads * 96 * sizeof(double);
+  k_tet_grad_f64<<<grid_for(count, kThreads), kThreads, smem, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x, m.n,
+                                                    list, count, m.mu, m.lam_hat, weight, m.f64.gcon.p,
+                                                    m.f64.hten.p);
 }
 
 void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
   if (count <= 0) return;
+  (void)weight;
   df mu_d{(float)m.mu, (float)(m.mu - (double)(float)m.mu)};
   df lh_d{(float)m.lam_hat, (float)(m.lam_hat - (double)(float)m.lam_hat)};
-  (void)weight;
-  k_tet_grad_mixed<<<grid_for(count), kBlock, 0, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_volw_df.p,
+  constexpr int kThreads = 128;
+  const size_t smem = (size_t)kThreads * 96 * sizeof(float);
+  k_tet_grad_mixed<<<grid_for(count, kThreads), kThreads, smem, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_volw_df.p,
                                                       m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, mu_d, lh_d,
-                                                      m.mx.gcon.p);
+                                                      (float)m.mu, (float)m.lam_hat, m.d_volw32.p, m.mx.gcon.p,
+                                                      m.mx.hten.p);
 }
 
 template <typename HT, bool kMixed>
-static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, const HT* Bm, const HT* volw,
-                        const HT* massh, cudaStream_t s) {
-  const int stage_blocks = 4 * m.max_valence;
-  int wpb = 4;
-  size_t smem = (size_t)wpb * stage_blocks * 9 * sizeof(HT);
-  while (wpb > 1 && smem > 200 * 1024) {
-    wpb >>= 1;
-    smem = (size_t)wpb * stage_blocks * 9 * sizeof(HT);
-  }
-  CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "vertex valence too high for the row assembly");
-  auto kern = k_row_assemble<HT, kMixed>;
-  set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, const HT* hten, const HT* massh,
+                        cudaStream_t s) {
   const bool dyn = m.h > 0.0;
+  const int wpb = 4;
   const int64_t blocks = (m.n_free + wpb - 1) / wpb;
-  kern<<<(unsigned)blocks, 32 * wpb, smem, s>>>(
-      m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.d_vt_tet.p, m.d_vt_corner.p, m.d_tets.p, Bm, volw, x,
-      kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr, m.n, m.d_up_ptr.p, m.d_rs_ptr.p, m.d_rs_idx.p,
-      kMixed ? nullptr : m.f64.gcon.p, kMixed ? m.mx.gcon.p : nullptr, massh, m.d_mass.p, m.d_mass_df.p,
-      dyn ? xt : nullptr, kMixed ? m.mx.xt_hi.p : nullptr, kMixed ? m.mx.xt_lo.p : nullptr, dyn, (HT)m.mu,
-      (HT)m.lam_hat,
-      stage_blocks, bsr, kMixed ? nullptr : m.f64.g.p, kMixed ? m.mx.g_hi.p : nullptr,
-      kMixed ? m.mx.g_lo.p : nullptr);
+  const size_t smem = (size_t)wpb * (m.max_rs + m.max_up + 1) * sizeof(int);
+  set_smem_limit(reinterpret_cast<const void*>(k_row_gather<HT, kMixed>), smem);
+  k_row_gather<HT, kMixed><<<(unsigned)blocks, 32 * wpb, smem, s>>>(
+      m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.d_up_ptr.p, m.d_rs_ptr.p, m.d_rs_src.p, hten, massh, m.d_mass.p,
+      m.d_mass_df.p, kMixed ? nullptr : m.f64.gcon.p, kMixed ? m.mx.gcon.p : nullptr, x,
+      kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr, dyn ? xt : nullptr,
+      kMixed ? m.mx.xt_hi.p : nullptr, kMixed ? m.mx.xt_lo.p : nullptr, m.n, dyn, m.max_rs, m.max_up, bsr,
+      kMixed ? nullptr : m.f64.g.p, kMixed ? m.mx.g_hi.p : nullptr, kMixed ? m.mx.g_lo.p : nullptr);
 }
 
 void launch_rows_f64(Mesh& m, const double* x, const double* xt, double weight, cudaStream_t s) {
   (void)weight;
-  launch_rows<double, false>(m, x, xt, m.f64.bsr.p, m.d_Bm.p, m.d_volw.p, m.d_mass.p, s);
+  launch_rows<double, false>(m, x, xt, m.f64.bsr.p, m.f64.hten.p, m.d_mass.p, s);
 }
 
 void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s) {
   (void)weight;
-  launch_rows<float, true>(m, nullptr, nullptr, m.mx.bsr.p, m.d_Bm32.p, m.d_volw32.p, m.d_mass32.p, s);
+  launch_rows<float, true>(m, nullptr, nullptr, m.mx.bsr.p, m.mx.hten.p, m.d_mass32.p, s);
 }
 
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {

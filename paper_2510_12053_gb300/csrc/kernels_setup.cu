@@ -255,6 +255,7 @@ void run_subspace_build(Mesh& m, int32_t k) {
   CCG_CHECK(m.sup_idx.size() < (size_t(1) << 31), CC_ERR_INVALID_ARG, "support arrays exceed 2^31 entries");
   CCG_CHECK(supmax < 32768, CC_ERR_INVALID_ARG, "support larger than 32767 vertices");
   m.sup_max = supmax;
+  build_slot_maps(m);
   int hs = 32;
   while (hs < 2 * std::max(supmax, 1)) hs <<= 1;
   m.hash_size = hs;

@@ -10,8 +10,8 @@
 // and x_i += dx_i (the subspace part U dalpha is discarded, Sec. 3.1).
 // H is stored as its upper 3x3 blocks (l >= j, diagonal first, each block
 // padded to 3 x 4 for 128-bit loads), so each unordered pair of the support
-// is read once.  The CTA stages U_i in shared memory and indexes it through an
-// open-addressing hash (vertex id -> support slot), so any mesh works.
+// is read once.  The CTA stages U_i in shared memory; a precomputed slot map
+// gives, for every block it reads, the support slot of the block's column.
 // Same-coloured vertices share no tet, and this kernel reads only g, H and U,
 // so writing x in place is race-free for both schedules.
 #include "cc_internal.cuh"
@@ -25,20 +25,7 @@ constexpr double kPivotRel = 1e-12;
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__device__ __forceinline__ unsigned hash_slot(int id, int bits) {
-  return ((unsigned)id * 2654435761u) >> (32 - bits);
-}
 
-__device__ __forceinline__ int hash_find(const int* keys, const short* vals, int id, int bits) {
-  const unsigned mask = (1u << bits) - 1u;
-  unsigned h = hash_slot(id, bits);
-  while (true) {
-    const int k = keys[h];
-    if (k == id) return vals[h];
-    if (k == -1) return -1;
-    h = (h + 1) & mask;
-  }
-}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -73,47 +60,64 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
 constexpr int kSolveThreads = 128;
 
 template <typename HT>
-__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int hash_size) {
-  return align16((size_t)sup_max * 9 * sizeof(HT)) + (size_t)hash_size * 4 + align16((size_t)hash_size * 2) +
-         3 * align16((size_t)(sup_max + 1) * 4) + 4 * 32 * sizeof(HT);
+__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes) {
+  return align16((size_t)sup_max * 9 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
+         align16((size_t)smap_max * code_bytes) + 4 * 32 * sizeof(HT);
 }
+
+template <typename SlotT>
+struct SlotCodes;
+template <>
+struct SlotCodes<uint8_t> {
+  static constexpr unsigned kNone = 0xFF, kSelf = 0xFE, kDiag = 0xFD;
+};
+template <>
+struct SlotCodes<uint16_t> {
+  static constexpr unsigned kNone = 0xFFFF, kSelf = 0xFFFE, kDiag = 0xFFFD;
+};
 
 // Coupling products, one CTA per free vertex i of the list.  Quarter-warps take
 // the block rows of the support S and of i itself; their lanes take the row's
-// upper blocks (H_jl, l >= j).  For j, l in S every unordered pair is visited
-// once and contributes M + M^T with M = U_j^T H_jl U_l (H is symmetric); a
-// block (j, i) of a support row gives A's term H_ij U_j = H_ji^T U_j; row i
-// gives H_ii and the terms H_il U_l with l > i.  The CTA writes 27 values per
-// vertex: Ht (6, symmetric), A (9), b (3), H_ii (9).
-template <typename HT, bool kMixed, int kUpd>
+// upper blocks (H_jl, l >= j).  The vertex's slot map (one code per block,
+// staged in shared memory) gives each block's role: for j, l in S every
+// unordered pair is visited once and contributes M + M^T with
+// M = U_j^T H_jl U_l (H is symmetric); a block (j, i) of a support row gives
+// A's term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
+// l > i.  The CTA writes 27 values per vertex: Ht (6, symmetric), A (9),
+// b (3), H_ii (9).
+template <typename HT, typename SlotT, bool kMixed, int kUpd>
 __global__ void __launch_bounds__(kSolveThreads) k_couple(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
-    const int32_t* __restrict__ up_col, const HT* __restrict__ bsr, const double* __restrict__ g64,
-    const float* __restrict__ g_hi, int hash_bits, int sup_max, HT* __restrict__ cpl) {
+    const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
+    const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, int64_t smap_max,
+    HT* __restrict__ cpl) {
+  using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int hs = 1 << hash_bits;
   unsigned char* ptr = smem;
   HT* Us = reinterpret_cast<HT*>(ptr);
   ptr += align16((size_t)sup_max * 9 * sizeof(HT));
-  int* keys = reinterpret_cast<int*>(ptr);
-  short* vals = reinterpret_cast<short*>(keys + hs);
-  ptr += (size_t)hs * 4 + align16((size_t)hs * 2);
   int* rstart = reinterpret_cast<int*>(ptr);
   ptr += align16((size_t)(sup_max + 1) * 4);
   int* rlen = reinterpret_cast<int*>(ptr);
   ptr += align16((size_t)(sup_max + 1) * 4);
   int* rid = reinterpret_cast<int*>(ptr);
   ptr += align16((size_t)(sup_max + 1) * 4);
+  int* roff = reinterpret_cast<int*>(ptr);
+  ptr += align16((size_t)(sup_max + 1) * 4);
+  SlotT* codes = reinterpret_cast<SlotT*>(ptr);
+  ptr += align16((size_t)smap_max * sizeof(SlotT));
   HT* red = reinterpret_cast<HT*>(ptr);  // [4 warps][32]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = verts[blockIdx.x];
   const int s0 = sup_ptr[i];
   const int m = sup_ptr[i + 1] - s0;
+  const int64_t c0 = smap_ptr[i];
+  const int ncodes = (int)(smap_ptr[i + 1] - c0);
 
-  for (int k = tid; k < hs; k += kSolveThreads) keys[k] = -1;
   for (int k = tid; k < 9 * m; k += kSolveThreads) Us[k] = U[(int64_t)s0 * 9 + k];
+  for (int k = tid; k < ncodes; k += kSolveThreads) codes[k] = smap[c0 + k];
   for (int s = tid; s <= m; s += kSolveThreads) {
     const int j = s < m ? sup_idx[s0 + s] : i;
     const int a = up_ptr[j];
@@ -122,63 +126,59 @@ __global__ void __launch_bounds__(kSolveThreads) k_couple(
     rid[s] = j;
   }
   __syncthreads();
-  for (int s = tid; s < m; s += kSolveThreads) {
-    const int id = rid[s];
-    unsigned h = hash_slot(id, hash_bits);
-    while (true) {
-      const int prev = atomicCAS(&keys[h], -1, id);
-      if (prev == -1) {
-        vals[h] = (short)s;
-        break;
+  // exclusive prefix of the row lengths (offsets into the slot map), warp 0
+  if (warp == 0) {
+    int carry = 0;
+    for (int base = 0; base <= m; base += 32) {
+      const int s = base + lane;
+      const int v = s <= m ? rlen[s] : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
       }
-      h = (h + 1) & (unsigned)(hs - 1);
+      if (s <= m) roff[s] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
   __syncthreads();
 
-  // symmetric Ht (6), A (9), b (3), H_ii (9)
   HT h00 = 0, h01 = 0, h02 = 0, h11 = 0, h12 = 0, h22 = 0;
   HT A[9], Hii[9], b[3] = {0, 0, 0};
   mat3_zero(A);
   mat3_zero(Hii);
   const int qw = tid >> 3, l8 = tid & 7;
   for (int r = qw; r <= m; r += kSolveThreads / 8) {
-    const int P = rstart[r], L = rlen[r];
+    const int P = rstart[r], L = rlen[r], off = roff[r];
     const HT* Uj = Us + 9 * r;
     for (int q = l8; q < L; q += 8) {
-      const int64_t p = P + q;
-      const int l = up_col[p];
+      const unsigned code = codes[off + q];
+      if (code == Codes::kNone) continue;
       HT H[9];
-      load_block(bsr, p, H);
+      load_block(bsr, (int64_t)P + q, H);
       if (r < m) {
-        if (q == 0) {
-          HT T[9], M[9];
-          mat3_zero(T);
-          mat3_mul_acc(H, Uj, T);
-          mat3_zero(M);
-          mat3_tmul_acc(Uj, T, M);
-          h00 += M[0]; h01 += M[1]; h02 += M[2]; h11 += M[4]; h12 += M[5]; h22 += M[8];
-        } else if (l == i) {
+        if (code == Codes::kSelf) {
           if (kUpd == CC_UPDATE_CC) mat3_tmul_acc(H, Uj, A);
         } else {
-          const int t = hash_find(keys, vals, l, hash_bits);
-          if (t >= 0) {
-            HT T[9], M[9];
-            mat3_zero(T);
-            mat3_mul_acc(H, Us + 9 * t, T);
-            mat3_zero(M);
-            mat3_tmul_acc(Uj, T, M);
-            h00 += 2 * M[0]; h11 += 2 * M[4]; h22 += 2 * M[8];
-            h01 += M[1] + M[3]; h02 += M[2] + M[6]; h12 += M[5] + M[7];
-          }
+          // pair (j, l) adds M + M^T; the diagonal block (l = j, M symmetric)
+          // takes the same path with weight 1/2
+          const bool dg = code == Codes::kDiag;
+          const HT w = dg ? HT(0.5) : HT(1);
+          HT T[9], M[9];
+          mat3_zero(T);
+          mat3_mul_acc(H, Us + 9 * (dg ? r : (int)code), T);
+          mat3_zero(M);
+          mat3_tmul_acc(Uj, T, M);
+          h00 += 2 * w * M[0]; h11 += 2 * w * M[4]; h22 += 2 * w * M[8];
+          h01 += w * (M[1] + M[3]); h02 += w * (M[2] + M[6]); h12 += w * (M[5] + M[7]);
         }
       } else {
-        if (q == 0) {
+        if (code == Codes::kDiag) {
 #pragma unroll
           for (int c = 0; c < 9; ++c) Hii[c] = H[c];
         } else if (kUpd == CC_UPDATE_CC) {
-          const int t = hash_find(keys, vals, l, hash_bits);
-          if (t >= 0) mat3_mul_acc(H, Us + 9 * t, A);
+          mat3_mul_acc(H, Us + 9 * code, A);
         }
       }
     }
@@ -351,16 +351,23 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
   float4* xh = kMixed ? m.mx.x_hi.p : nullptr;
   float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
   if (kUpd != CC_UPDATE_CD) {
-    const int hs = m.hash_size > 0 ? m.hash_size : 32;
-    int bits = 0;
-    while ((1 << bits) < hs) ++bits;
     const int supm = m.sup_max > 0 ? m.sup_max : 1;
-    const size_t smem = cta_smem_bytes<HT>(supm, hs);
-    CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
-    auto kern = k_couple<HT, kMixed, kUpd>;
-    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-    kern<<<(unsigned)count, kSolveThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
-                                                      m.d_up_col.p, bsr, g64, g_hi, bits, supm, cpl);
+    const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
+    if (m.smap_wide) {
+      const size_t smem = cta_smem_bytes<HT>(supm, smx, 2);
+      CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+      auto kern = k_couple<HT, uint16_t, kMixed, kUpd>;
+      set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+      kern<<<(unsigned)count, kSolveThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
+                                                        m.d_smap_ptr.p, m.d_smap16.p, bsr, g64, g_hi, supm, smx, cpl);
+    } else {
+      const size_t smem = cta_smem_bytes<HT>(supm, smx, 1);
+      CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+      auto kern = k_couple<HT, uint8_t, kMixed, kUpd>;
+      set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+      kern<<<(unsigned)count, kSolveThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
+                                                        m.d_smap_ptr.p, m.d_smap8.p, bsr, g64, g_hi, supm, smx, cpl);
+    }
     CCG_CUDA(cudaGetLastError());
   }
   const unsigned grid = (unsigned)((count + 127) / 128);

@@ -113,25 +113,42 @@ void build_topology(Mesh& m) {
   m.nnzb = 2 * m.nnz_up - n;
   CCG_CHECK(m.max_valence <= 1024, CC_ERR_INVALID_ARG, "vertex valence above 1024 tets");
 
-  // ---- per upper block of a free row, its sources among the row's
-  //      (slot k, corner w) pairs, as local indices 4 k + w (ascending)
+  // ---- per upper block (j, l) of a free row, its sources: the blocks
+  //      K_{cj,w} of the incident tets t with tets[t][w] == l, as offsets of
+  //      the tet's stored upper block pair (min(cj,w), max(cj,w)) in the
+  //      per-tet Hessian store (96 values per tet), bit 31 set when the
+  //      stored block must be transposed (cj > w).  Ascending slot order.
+  static const int kPair[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
   std::vector<int32_t> rs_ptr(m.nnz_up + 1, 0);
-  std::vector<uint16_t> rs_idx;
+  std::vector<int32_t> rs_src;
   for (int64_t v = 0; v < n; ++v) {
     const int64_t p0 = m.up_ptr[v], p1 = m.up_ptr[v + 1];
     if (m.pinned[v]) {
-      for (int64_t p = p0; p < p1; ++p) rs_ptr[p + 1] = (int32_t)rs_idx.size();
+      for (int64_t p = p0; p < p1; ++p) rs_ptr[p + 1] = (int32_t)rs_src.size();
       continue;
     }
     for (int64_t p = p0; p < p1; ++p) {
       const int32_t col = m.up_col[p];
       for (int64_t e = m.vt_ptr[v]; e < m.vt_ptr[v + 1]; ++e) {
-        const int32_t* tv = &m.tets[4 * m.vt_tet[e]];
+        const int64_t t = m.vt_tet[e];
+        const int cj = m.vt_corner[e];
+        const int32_t* tv = &m.tets[4 * t];
         for (int w = 0; w < 4; ++w)
-          if (tv[w] == col) rs_idx.push_back((uint16_t)(4 * (e - m.vt_ptr[v]) + w));
+          if (tv[w] == col) {
+            const uint32_t off = (uint32_t)(t * 96 + 9 * kPair[cj][w]);
+            rs_src.push_back((int32_t)(off | (cj > w ? 0x80000000u : 0u)));
+          }
       }
-      rs_ptr[p + 1] = (int32_t)rs_idx.size();
+      rs_ptr[p + 1] = (int32_t)rs_src.size();
     }
+  }
+  CCG_CHECK(96 * T < (int64_t(1) << 31), CC_ERR_INVALID_ARG, "mesh too large for 31-bit Hessian offsets");
+
+  m.max_up = 0;
+  m.max_rs = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    m.max_up = std::max<int32_t>(m.max_up, (int32_t)(m.up_ptr[v + 1] - m.up_ptr[v]));
+    m.max_rs = std::max<int32_t>(m.max_rs, rs_ptr[m.up_ptr[v + 1]] - rs_ptr[m.up_ptr[v]]);
   }
 
   // ---- free rows, tets with a free vertex
@@ -200,10 +217,60 @@ void build_topology(Mesh& m) {
   m.d_up_ptr.upload(up32, s);
   m.d_up_col.upload(m.up_col, s);
   m.d_rs_ptr.upload(rs_ptr, s);
-  m.d_rs_idx.upload(rs_idx, s);
+  m.d_rs_src.upload(rs_src, s);
   m.d_free_rows.upload(free_rows, s);
   m.d_all_tets.upload(active, s);
+  {
+    std::vector<int32_t> ids(16 * T);
+    for (int64_t e = 0; e < 4 * T; ++e)
+      for (int c = 0; c < 4; ++c) ids[4 * e + c] = m.tets[4 * (int64_t)m.vt_tet[e] + c];
+    m.d_vt_ids.upload(reinterpret_cast<const int4*>(ids.data()), 4 * T, s);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
   CCG_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
+}
+
+void build_slot_maps(Mesh& m) {
+  const int64_t n = m.n;
+  m.smap_wide = m.sup_max >= 250;
+  const uint16_t kNone = m.smap_wide ? 0xFFFF : 0xFF, kSelf = m.smap_wide ? 0xFFFE : 0xFE,
+                 kDiag = m.smap_wide ? 0xFFFD : 0xFD;
+  std::vector<int64_t> ptr(n + 1, 0);
+  std::vector<uint16_t> codes;
+  std::vector<int32_t> slot(n, -1);
+  int64_t longest = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    if (!m.pinned[v]) {
+      const int64_t s0 = m.sup_ptr[v], s1 = m.sup_ptr[v + 1];
+      for (int64_t s = s0; s < s1; ++s) slot[m.sup_idx[s]] = (int32_t)(s - s0);
+      const int64_t before = (int64_t)codes.size();
+      for (int64_t r = s0; r <= s1; ++r) {
+        const int64_t j = r < s1 ? m.sup_idx[r] : v;
+        for (int64_t p = m.up_ptr[j]; p < m.up_ptr[j + 1]; ++p) {
+          const int32_t l = m.up_col[p];
+          uint16_t c;
+          if (p == m.up_ptr[j]) c = kDiag;
+          else if (l == v) c = kSelf;
+          else c = slot[l] >= 0 ? (uint16_t)slot[l] : kNone;
+          codes.push_back(c);
+        }
+      }
+      longest = std::max<int64_t>(longest, (int64_t)codes.size() - before);
+      for (int64_t s = s0; s < s1; ++s) slot[m.sup_idx[s]] = -1;
+    }
+    ptr[v + 1] = (int64_t)codes.size();
+  }
+  m.smap_max = longest;
+  m.d_smap_ptr.upload(ptr, m.stream);
+  if (m.smap_wide) {
+    m.d_smap16.upload(codes, m.stream);
+    m.d_smap8.release();
+  } else {
+    std::vector<uint8_t> c8(codes.begin(), codes.end());
+    m.d_smap8.upload(c8, m.stream);
+    m.d_smap16.release();
+  }
+  CCG_CUDA(cudaStreamSynchronize(m.stream));
 }
 
 }  // namespace ccg
