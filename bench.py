@@ -37,6 +37,37 @@ DIMS = (32, 32, 32)
 K_RING = 2
 MAX_ITERS = 800
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_kernels_cube32.md")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary,
+    or None when the kernel source changed since the capture (hash mismatch)."""
+    import hashlib
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic:"):
+            _, cls, nbytes, src, digest = line.split()
+            if cls != kernel_class:
+                continue
+            path = os.path.join(ROOT, "paper_2510_12053_gb300", "csrc", src)
+            try:
+                cur = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+            except OSError:
+                return None
+            return float(nbytes) if cur == digest else None
+    return None
 
 
 def parse():
@@ -198,6 +229,35 @@ def local_solve_flops(mesh):
     return out
 
 
+def gather_bytes_per_refresh(scene):
+    """Algorithmic bytes of one row-gather launch (all free rows): per row the
+    stored blocks it sums (one 36-byte block per incident tet and corner with
+    a vertex id >= the row's), its 24-byte float-float gradient entries, its
+    upper blocks written and its gradient written."""
+    tets = np.asarray(scene.tets, dtype=np.int64)
+    free = scene.pinned == 0
+    n = scene.n
+    ge = tets[:, None, :] >= tets[:, :, None]          # [T, v, w]: vid[w] >= vid[v]
+    src = np.zeros(n)
+    np.add.at(src, tets.ravel(), ge.sum(axis=2).ravel())
+    val = np.bincount(tets.ravel(), minlength=n)
+    nup = np.zeros(n)
+    pairs = set()
+    for a in range(4):
+        for c in range(4):
+            if a != c:
+                pairs.update(zip(tets[:, a].tolist(), tets[:, c].tolist()))
+    for (j, l) in pairs:
+        if l > j:
+            nup[j] += 1
+    nup += 1
+    per = src * 36 + val * 24 + nup * 36 + 24
+    return float(per[free].sum())
+
+
+TET_BYTES = 16 + 16 + 72 + 12 + 4 * 32 + 4 * 24 + 360   # ids, slots, D_m^-1, V w, positions; gradient + 10 blocks
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2510_12053_gb300 as cc
@@ -277,16 +337,47 @@ def run_ours(args, rank, world):
            for k in cc.PROFILE_CLASSES}
     launches = sum(p["total_launches"] for p in prof)
     dominant = max(cc.PROFILE_CLASSES, key=lambda k: cls[k]["ms"])
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    solves = args.steps * len(meshes)
+    ncol = int(meshes[0].info().num_colors)
+    # units processed in the timed region
+    free_corners = int((scs[0].pinned[scs[0].tets] == 0).sum())
+    active_tets = int((scs[0].pinned[scs[0].tets] == 0).any(axis=1).sum())
+    tet_refreshes = sweeps_total * free_corners + solves * active_tets
+    row_gathers = sweeps_total * ncol + solves
     fl = local_solve_flops(meshes[0])
     flops_per_sweep = float(fl.sum())
+    roof = {}
     ls = cls["local_solve"]
-    achieved = flops_per_sweep * sweeps_total / (ls["ms"] / 1e3) / 1e12 if ls["ms"] > 0 else None
-    roofline = {"kernel": "k_local_solve (coupling SpMM + Schur solve)", "bound": "alu",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "avg_launch_ms": ls["ms"] / max(ls["launches"], 1),
-                "flops_per_sweep": flops_per_sweep}
+    if ls["ms"] > 0:
+        ach = flops_per_sweep * sweeps_total / (ls["ms"] / 1e3) / 1e12
+        tr = [ncu_traffic("k_couple"), ncu_traffic("k_condense")]
+        roof["local_solve"] = {"kernel": "k_couple + k_condense (coupling products + batched Schur solve)",
+                               "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": ach / FP32_PEAK_TFLOPS,
+                               "traffic": (tr[0] + tr[1]) if None not in tr else None,
+                               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                               "algorithmic": f"{flops_per_sweep / meshes[0].info().n_free:.0f} FP32 flop per vertex per sweep",
+                               "avg_launch_ms": ls["ms"] / max(ls["launches"] // 2, 1)}
+    ga = cls["gather"]
+    if ga["ms"] > 0:
+        gb = gather_bytes_per_refresh(scs[0])
+        ach = gb * row_gathers / (ga["ms"] / 1e3) / 1e9
+        roof["gather"] = {"kernel": "k_row_gather (gradient + upper block rows of every free vertex)",
+                          "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                          "traffic": ncu_traffic("k_row_gather"), "peak_source": peak_src,
+                          "algorithmic": f"{gb / 1e6:.1f} MB per launch",
+                          "avg_launch_ms": ga["ms"] / max(ga["launches"], 1)}
+    te = cls["tet_eval"]
+    if te["ms"] > 0:
+        ach = TET_BYTES * tet_refreshes / (te["ms"] / 1e3) / 1e9
+        roof["tet_eval"] = {"kernel": "k_tet_grad_mixed (float-float gradient + float32 Hessian blocks per tet)",
+                            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                            "traffic": ncu_traffic("k_tet_grad_mixed"), "peak_source": peak_src,
+                            "algorithmic": f"{TET_BYTES} B per refreshed tet",
+                            "avg_launch_ms": te["ms"] / max(te["launches"], 1)}
+    roofline = roof.get(dominant) or next(iter(roof.values()), None)
 
     # plain float64 CC on the same solves
     fp64 = None
@@ -343,6 +434,7 @@ def run_ours(args, rank, world):
             if fp64 else None,
             "wall_ms_timed": wall_ms,
             "roofline": roofline,
+            "roofline_all": roof,
             "kernel_ms": {k: round(v["ms"], 3) for k, v in cls.items()},
             "dominant_kernel_class": dominant,
             "gpu_launches": launches,
