@@ -277,6 +277,48 @@ cc_status cc_build_bases_noalloc(const double* H_blocks, const int32_t* row_ptr,
                                  const int32_t* sup_idx, int32_t max_support, double* U_out,
                                  void* stream);
 
+/* A batch: `count` independent meshes solved together (no counterpart in
+ * the paper).  The library stores them as one disjoint union: mesh b's
+ * vertices follow mesh b-1's in the device arrays (offsets in
+ * cc_batch_offsets), tets are renumbered accordingly, and every kernel launch
+ * of a sweep covers all meshes.  Colours, supports and bases of each mesh are
+ * exactly those it would get on its own (components never interact, and the
+ * greedy colouring of the union in ascending id is the per-mesh colouring).
+ * Each mesh keeps its own material; the time step h and gravity are shared. */
+typedef struct {
+  const double* X;       /* host [n][3] */
+  int64_t n;
+  const int32_t* tets;   /* host [T][4], ids local to this mesh */
+  int64_t T;
+  const uint8_t* pinned; /* host [n] or NULL */
+  cc_material mat;
+} cc_mesh_desc;
+
+cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, const double* gravity,
+                         void* stream, cc_mesh** out);
+
+/* Vertex offsets of the meshes of a batch: offsets host [count+1]. */
+cc_status cc_batch_offsets(const cc_mesh* mesh, int64_t* offsets, int32_t* count);
+
+typedef struct {
+  int32_t* iterations;  /* host [count]: sweeps each mesh ran before it stopped */
+  int32_t* status;      /* host [count]: 1 converged, 0 max_iters reached, -1 diverged
+                           (residual non-finite or above 1e6 times its start) */
+  double* g0;           /* host [count]: ||g_free|| at the start */
+  double* g_final;      /* host [count]: ||g_free|| when the mesh stopped */
+  int32_t sweeps;       /* out: sweeps launched until every mesh had stopped */
+  cc_sweep_stats totals;/* out: fallback counts over all meshes */
+} cc_batch_stats;
+
+/* Solves every mesh of a batch (cc_solve_step semantics per mesh): the
+ * residual of each mesh is reduced separately at every check, and a mesh that
+ * converged or diverged stops moving (its vertices are skipped by the
+ * condensation kernel) while the others continue.  x_dev, v_dev: device
+ * [3][n_total] (v_dev NULL for quasistatics).  Returns CC_OK when every mesh
+ * converged, CC_ERR_NOT_CONVERGED otherwise (stats valid). */
+cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_step_opts* opts,
+                         cc_batch_stats* stats);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* cc_last_error(void);
 

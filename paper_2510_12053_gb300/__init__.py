@@ -73,6 +73,17 @@ class MeshInfo(ctypes.Structure):
                 ("max_valence", ctypes.c_int32)]
 
 
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("tets", ctypes.c_void_p), ("T", ctypes.c_int64),
+                ("pinned", ctypes.c_void_p), ("mat", Material)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.POINTER(ctypes.c_int32)), ("status", ctypes.POINTER(ctypes.c_int32)),
+                ("g0", ctypes.POINTER(ctypes.c_double)), ("g_final", ctypes.POINTER(ctypes.c_double)),
+                ("sweeps", ctypes.c_int32), ("totals", SweepStats)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5), ("total_launches", ctypes.c_int64)]
 
@@ -94,6 +105,10 @@ _SIGS = {
     "cc_solve_step": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(StepStats)]),
     "cc_get_info": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
     "cc_export": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "cc_build_batch": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.c_int32, ctypes.c_double, _P, _P,
+                                      ctypes.POINTER(_P)]),
+    "cc_batch_offsets": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "cc_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(BatchStats)]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -178,6 +193,60 @@ class Mesh:
                                    ctypes.byref(out)))
         self._h = out
         self.dynamic = h > 0.0
+
+    @classmethod
+    def from_scenes(cls, scenes, stream=None) -> "Mesh":
+        """A batch: the disjoint union of several meshes, solved together
+        (materials per mesh; time step and gravity of the first scene)."""
+        keep = []
+        descs = (MeshDesc * len(scenes))()
+        for k, sc in enumerate(scenes):
+            X = np.ascontiguousarray(sc.X, dtype=np.float64)
+            T = np.ascontiguousarray(sc.tets, dtype=np.int32)
+            P = np.ascontiguousarray(sc.pinned, dtype=np.uint8)
+            keep += [X, T, P]
+            m = sc.material
+            descs[k] = MeshDesc(X.ctypes.data, X.shape[0], T.ctypes.data, T.shape[0], P.ctypes.data,
+                                Material(m.E, m.nu, m.rho))
+        grav = np.ascontiguousarray(scenes[0].gravity, dtype=np.float64)
+        obj = cls.__new__(cls)
+        obj._h = None
+        out = _P()
+        _check(lib().cc_build_batch(descs, len(scenes), float(scenes[0].h), grav.ctypes.data, _stream_ptr(stream),
+                                    ctypes.byref(out)))
+        obj._h = out
+        obj.n = int(sum(sc.n for sc in scenes))
+        obj.T = int(sum(sc.T for sc in scenes))
+        obj.dynamic = scenes[0].h > 0.0
+        return obj
+
+    def batch_offsets(self) -> np.ndarray:
+        cnt = ctypes.c_int32()
+        _check(lib().cc_batch_offsets(self._h, None, ctypes.byref(cnt)))
+        off = np.zeros(cnt.value + 1, dtype=np.int64)
+        _check(lib().cc_batch_offsets(self._h, off.ctypes.data, ctypes.byref(cnt)))
+        return off
+
+    def solve_batch(self, x, v=None, *, update: str = "cc", schedule: str = "colored", precision: str = "mixed",
+                    tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0, check_every: int = 1,
+                    use_graph: bool = False) -> dict:
+        B = len(self.batch_offsets()) - 1
+        it = np.zeros(B, dtype=np.int32)
+        status = np.zeros(B, dtype=np.int32)
+        g0 = np.zeros(B)
+        gf = np.zeros(B)
+        st = BatchStats(it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        g0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        gf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, SweepStats())
+        o = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters, check_every,
+                     int(use_graph), None)
+        rc = lib().cc_solve_batch(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
+                                  ctypes.byref(st))
+        if rc not in (OK, ERR_NOT_CONVERGED):
+            _check(rc)
+        return {"iterations": it, "status": status, "g0": g0, "g_final": gf, "sweeps": st.sweeps,
+                "updates": st.totals.updates}
 
     @classmethod
     def from_scene(cls, scene, stream=None) -> "Mesh":

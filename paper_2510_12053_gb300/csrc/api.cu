@@ -242,6 +242,63 @@ void check_sweep_opts(const Mesh& m, const cc_sweep_opts& o, int* cb, int* ce) {
   }
 }
 
+
+// Every mesh of a batch takes part again (cc_solve_batch may have stopped some).
+void activate_all(Mesh& m) {
+  const size_t B = m.mesh_vptr.size() - 1;
+  CCG_CUDA(cudaMemcpyAsync(m.d_mesh_active.p, m.d_mesh_ones.p, B * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                           m.stream));
+}
+
+// Runs `chunk` sweeps over colours [cb, ce), each followed by the refresh that
+// makes g and H current, then the residual reduction: the global norm into
+// d_scalars[0] (per_mesh false) or every mesh's squared norm into d_mesh_gsq.
+// With `graph`, the whole chunk is captured once per key and replayed.
+void run_chunk(Mesh& m, double* x, const double* xt, const cc_sweep_opts& so, int cb, int ce, int chunk,
+               bool graph, const std::string& key, bool per_mesh) {
+  cudaStream_t s = m.stream;
+  auto body = [&]() {
+    for (int k = 0; k < chunk; ++k) {
+      sweep_body(m, x, xt, so, cb, ce, true);
+      post_refresh(m, x, xt, so, ce);
+    }
+    if (per_mesh) {
+      const int e0 = prof_event(m);
+      launch_gnorm_mesh(m, so.precision == CC_PREC_MIXED, s);
+      prof_close(m, P_RED, e0, 1);
+    } else {
+      gnorm(m, so.precision, nullptr, m.d_scalars.p);
+    }
+  };
+  if (!graph) {
+    body();
+    CCG_CUDA(cudaGetLastError());
+    return;
+  }
+  if (m.graph_key != key) {
+    drop_graph(m);
+    cudaGraph_t g = nullptr;
+    CCG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    m.prof.capturing = true;
+    try {
+      body();
+    } catch (...) {
+      m.prof.capturing = false;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      drop_graph(m);
+      throw;
+    }
+    m.prof.capturing = false;
+    CCG_CUDA(cudaStreamEndCapture(s, &g));
+    cudaError_t ie = cudaGraphInstantiate(&m.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    CCG_CUDA(ie);
+    m.graph_key = key;
+  }
+  CCG_CUDA(cudaGraphLaunch(m.graph_exec, s));
+}
+
 }  // namespace
 }  // namespace ccg
 
@@ -303,6 +360,9 @@ cc_status cc_build_mesh(const double* X, int64_t n, const int32_t* tets, int64_t
     m->pinned.assign(n, 0);
     if (pinned)
       for (int64_t v = 0; v < n; ++v) m->pinned[v] = pinned[v] ? 1 : 0;
+    m->tet_mu.assign(T, m->mu);
+    m->tet_lh.assign(T, m->lam_hat);
+    m->tet_rho.assign(T, m->rho);
     ccg::build_topology(*m);
     CCG_CHECK(m->n_free > 0, CC_ERR_INVALID_ARG, "every vertex is pinned");
     m->d_red.alloc(4096);
@@ -329,7 +389,8 @@ void cc_destroy_mesh(cc_mesh* m) {
   drop_graph(*m);
   for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
   auto rel = [](auto& b) { b.release(); };
-  rel(m->d_tets); rel(m->d_tslot); rel(m->d_Bm); rel(m->d_Bm_df); rel(m->d_Bm32); rel(m->d_vol); rel(m->d_volw); rel(m->d_volw32); rel(m->d_volw_df); rel(m->d_mass);
+  rel(m->d_tets); rel(m->d_tslot); rel(m->d_Bm); rel(m->d_Bm_df); rel(m->d_Bm32); rel(m->d_vol); rel(m->d_mat64); rel(m->d_matdf); rel(m->d_vert_mesh);
+  rel(m->d_mesh_fptr); rel(m->d_mesh_active); rel(m->d_mesh_ones); rel(m->d_mesh_gsq); rel(m->d_volw); rel(m->d_volw32); rel(m->d_volw_df); rel(m->d_mass);
   rel(m->d_mass32); rel(m->d_mass_df);
   rel(m->d_pinned); rel(m->d_vt_ptr); rel(m->d_nbr_ptr); rel(m->d_nbr_idx); rel(m->d_vt_tet); rel(m->d_vt_corner);
   rel(m->d_up_ptr); rel(m->d_up_col); rel(m->d_rs_ptr); rel(m->d_rs_src); rel(m->d_free_rows);
@@ -435,6 +496,7 @@ cc_status cc_sweep(cc_mesh* m, double* x, const double* xt, const cc_sweep_opts*
     ensure_state(*m, opts->precision);
     cudaStream_t s = m->stream;
     CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
+    activate_all(*m);
     if (opts->precision == CC_PREC_MIXED) {
       split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
       if (m->h > 0.0) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
@@ -474,6 +536,7 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
       xt = m->d_xtilde.p;
     }
     CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
+    activate_all(*m);
     if (o->precision == CC_PREC_MIXED) {
       split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
       if (dyn) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
@@ -498,52 +561,17 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
     std::string key;
     if (graph) {
       char buf[256];
-      std::snprintf(buf, sizeof(buf), "%p %p %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
+      std::snprintf(buf, sizeof(buf), "step %p %p %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
                     (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0);
       key = buf;
     }
     while (!conv && it < o->max_iters) {
       const int chunk = std::min(every, o->max_iters - it);
-      if (graph && chunk == every && it > 0) {
-        if (m->graph_key != key) {
-          drop_graph(*m);
-          cudaGraph_t g = nullptr;
-          CCG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-          m->prof.capturing = true;
-          try {
-            for (int k = 0; k < chunk; ++k) {
-              sweep_body(*m, x, xt, so, cb, ce, true);
-              post_refresh(*m, x, xt, so, ce);
-            }
-            gnorm(*m, o->precision, nullptr, m->d_scalars.p);
-          } catch (...) {
-            m->prof.capturing = false;
-            cudaStreamEndCapture(s, &g);
-            if (g) cudaGraphDestroy(g);
-            drop_graph(*m);
-            throw;
-          }
-          m->prof.capturing = false;
-          CCG_CUDA(cudaStreamEndCapture(s, &g));
-          cudaError_t ie = cudaGraphInstantiate(&m->graph_exec, g, 0);
-          cudaGraphDestroy(g);
-          CCG_CUDA(ie);
-          m->graph_key = key;
-        }
-        CCG_CUDA(cudaGraphLaunch(m->graph_exec, s));
-        it += chunk;
-        gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
-        prof_after_replay(*m);
-      } else {
-        for (int k = 0; k < chunk; ++k) {
-          sweep_body(*m, x, xt, so, cb, ce, true);
-          post_refresh(*m, x, xt, so, ce);
-        }
-        CCG_CUDA(cudaGetLastError());
-        it += chunk;
-        gnorm(*m, o->precision, nullptr, m->d_scalars.p);
-        gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
-      }
+      const bool replay = graph && chunk == every && it > 0;
+      run_chunk(*m, x, xt, so, cb, ce, chunk, replay, key, false);
+      it += chunk;
+      gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
+      if (replay) prof_after_replay(*m);
       if (o->residual_history) o->residual_history[it] = gcur;
       CCG_CHECK(std::isfinite(gcur), CC_ERR_NUMERIC, "non-finite residual");
       if (it >= o->min_iters && gcur <= o->tol * g0) conv = true;
@@ -576,6 +604,211 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
     return f.st;
   } catch (...) {
     ccg::g_last_error = "cc_solve_step: unexpected error";
+    return CC_ERR_STATE;
+  }
+}
+
+cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, const double* gravity, void* stream,
+                         cc_mesh** out) {
+  cc_mesh* m = nullptr;
+  try {
+    ccg::g_last_error.clear();
+    CCG_CHECK(out != nullptr, CC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    CCG_CHECK(meshes && count >= 1, CC_ERR_INVALID_ARG, "need at least one mesh");
+    CCG_CHECK(h >= 0 && std::isfinite(h), CC_ERR_INVALID_ARG, "bad time step");
+    int64_t n = 0, T = 0;
+    for (int32_t b = 0; b < count; ++b) {
+      const cc_mesh_desc& d = meshes[b];
+      CCG_CHECK(d.X && d.tets && d.n >= 4 && d.T >= 1, CC_ERR_INVALID_ARG, "bad mesh in batch");
+      CCG_CHECK(d.mat.E > 0 && d.mat.nu > -1.0 && d.mat.nu < 0.5 && d.mat.rho >= 0 && std::isfinite(d.mat.E),
+                CC_ERR_INVALID_ARG, "bad material in batch");
+      n += d.n;
+      T += d.T;
+    }
+    CCG_CHECK(n < (int64_t(1) << 31) && T < (int64_t(1) << 29), CC_ERR_INVALID_ARG, "batch too large");
+    m = new cc_mesh();
+    m->n = n;
+    m->T = T;
+    const cc_material& m0 = meshes[0].mat;
+    m->E = m0.E;
+    m->nu = m0.nu;
+    m->rho = m0.rho;
+    m->mu = m0.E / (2.0 * (1.0 + m0.nu));
+    m->lam_hat = m0.E * m0.nu / ((1.0 + m0.nu) * (1.0 - 2.0 * m0.nu)) + m->mu;
+    m->h = h;
+    if (gravity && h > 0)
+      for (int a = 0; a < 3; ++a) m->grav[a] = gravity[a];
+    m->stream = (cudaStream_t)stream;
+    m->X.resize(3 * n);
+    m->tets.resize(4 * T);
+    m->pinned.assign(n, 0);
+    m->tet_mu.resize(T);
+    m->tet_lh.resize(T);
+    m->tet_rho.resize(T);
+    m->mesh_vptr.assign(count + 1, 0);
+    m->mesh_tptr.assign(count + 1, 0);
+    int64_t vo = 0, to = 0;
+    for (int32_t b = 0; b < count; ++b) {
+      const cc_mesh_desc& d = meshes[b];
+      for (int64_t k = 0; k < 3 * d.n; ++k) {
+        CCG_CHECK(std::isfinite(d.X[k]), CC_ERR_INVALID_ARG, "non-finite rest position");
+        m->X[3 * vo + k] = d.X[k];
+      }
+      for (int64_t k = 0; k < 4 * d.T; ++k) {
+        CCG_CHECK(d.tets[k] >= 0 && d.tets[k] < d.n, CC_ERR_INVALID_ARG, "tet vertex id out of range");
+        m->tets[4 * to + k] = (int32_t)(d.tets[k] + vo);
+      }
+      if (d.pinned)
+        for (int64_t v = 0; v < d.n; ++v) m->pinned[vo + v] = d.pinned[v] ? 1 : 0;
+      const double mu = d.mat.E / (2.0 * (1.0 + d.mat.nu));
+      const double lh = d.mat.E * d.mat.nu / ((1.0 + d.mat.nu) * (1.0 - 2.0 * d.mat.nu)) + mu;
+      for (int64_t t = 0; t < d.T; ++t) {
+        m->tet_mu[to + t] = mu;
+        m->tet_lh[to + t] = lh;
+        m->tet_rho[to + t] = d.mat.rho;
+      }
+      vo += d.n;
+      to += d.T;
+      m->mesh_vptr[b + 1] = vo;
+      m->mesh_tptr[b + 1] = to;
+    }
+    ccg::build_topology(*m);
+    CCG_CHECK(m->n_free > 0, CC_ERR_INVALID_ARG, "every vertex is pinned");
+    m->d_red.alloc(4096);
+    m->d_scalars.alloc(8);
+    m->d_counters.alloc(8);
+    CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), m->stream));
+    CCG_CUDA(cudaMallocHost((void**)&m->h_pinned_scalars, 8 * sizeof(double)));
+    *out = m;
+    return CC_OK;
+  } catch (const ccg::Fail& f) {
+    cc_destroy_mesh(m);
+    return f.st;
+  } catch (...) {
+    cc_destroy_mesh(m);
+    ccg::g_last_error = "cc_build_batch: unexpected error";
+    return CC_ERR_STATE;
+  }
+}
+
+cc_status cc_batch_offsets(const cc_mesh* m, int64_t* offsets, int32_t* count) {
+  CC_API_BODY("cc_batch_offsets", {
+    CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    const int32_t B = (int32_t)m->mesh_vptr.size() - 1;
+    if (count) *count = B;
+    if (offsets) std::memcpy(offsets, m->mesh_vptr.data(), (B + 1) * sizeof(int64_t));
+  })
+}
+
+cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o, cc_batch_stats* st) {
+  try {
+    ccg::g_last_error.clear();
+    CCG_CHECK(m && x && o && st && st->iterations && st->status && st->g0 && st->g_final, CC_ERR_INVALID_ARG,
+              "NULL argument");
+    CCG_CHECK(o->max_iters >= 0 && o->min_iters >= 0 && o->tol >= 0, CC_ERR_INVALID_ARG, "bad iteration limits");
+    CCG_CHECK((m->h > 0.0) == (v != nullptr), CC_ERR_INVALID_ARG,
+              "v must be given exactly for dynamic meshes (h > 0)");
+    cc_sweep_opts so{o->update, o->schedule, o->precision, 0, -1};
+    int cb, ce;
+    check_sweep_opts(*m, so, &cb, &ce);
+    ensure_state(*m, o->precision);
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n;
+    const int32_t B = (int32_t)m->mesh_vptr.size() - 1;
+    const bool dyn = m->h > 0.0;
+    const double* xt = nullptr;
+    if (dyn) {
+      if (!m->d_xtilde.p) {
+        m->d_xtilde.alloc(3 * n);
+        m->d_xold.alloc(3 * n);
+      }
+      CCG_CUDA(cudaMemcpyAsync(m->d_xold.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      launch_inertial_target(x, v, n, m->h, m->grav, m->d_xtilde.p, s);
+      xt = m->d_xtilde.p;
+    }
+    CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
+    activate_all(*m);
+    if (o->precision == CC_PREC_MIXED) {
+      split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
+      if (dyn) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
+    }
+    refresh_all(*m, o->precision, x, xt);
+    launch_gnorm_mesh(*m, o->precision == CC_PREC_MIXED, s);
+    std::vector<double> gsq(B);
+    std::vector<int32_t> active(B, 1);
+    CCG_CUDA(cudaMemcpyAsync(gsq.data(), m->d_mesh_gsq.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    int32_t live = 0;
+    for (int32_t b = 0; b < B; ++b) {
+      st->g0[b] = std::sqrt(gsq[b]);
+      st->g_final[b] = st->g0[b];
+      st->iterations[b] = 0;
+      st->status[b] = 0;
+      if (!(st->g0[b] > 0.0)) {
+        active[b] = 0;
+        st->status[b] = std::isfinite(st->g0[b]) ? 1 : -1;
+      } else {
+        ++live;
+      }
+    }
+    const int every = std::max(1, o->check_every);
+    const bool graph = o->use_graph && s != nullptr;
+    std::string key;
+    if (graph) {
+      char buf[256];
+      std::snprintf(buf, sizeof(buf), "batch %p %p %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
+                    (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0);
+      key = buf;
+    }
+    int it = 0;
+    while (live > 0 && it < o->max_iters) {
+      CCG_CUDA(cudaMemcpyAsync(m->d_mesh_active.p, active.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      const int chunk = std::min(every, o->max_iters - it);
+      const bool replay = graph && chunk == every && it > 0;
+      run_chunk(*m, x, xt, so, cb, ce, chunk, replay, key, true);
+      it += chunk;
+      CCG_CUDA(cudaMemcpyAsync(gsq.data(), m->d_mesh_gsq.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CCG_CUDA(cudaStreamSynchronize(s));
+      if (replay) prof_after_replay(*m);
+      for (int32_t b = 0; b < B; ++b) {
+        if (!active[b]) continue;
+        const double g = std::sqrt(gsq[b]);
+        st->iterations[b] = it;
+        st->g_final[b] = g;
+        if (!std::isfinite(g) || g > 1e6 * st->g0[b]) {
+          st->status[b] = -1;
+        } else if (it >= o->min_iters && g <= o->tol * st->g0[b]) {
+          st->status[b] = 1;
+        } else {
+          continue;
+        }
+        active[b] = 0;
+        --live;
+      }
+    }
+    activate_all(*m);
+    if (dyn) launch_velocity(x, m->d_xold.p, n, m->h, v, s);
+    unsigned long long h8[8];
+    CCG_CUDA(cudaMemcpyAsync(h8, m->d_counters.p, sizeof(h8), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    st->sweeps = it;
+    st->totals.updates = (int64_t)it * m->n_free;
+    st->totals.fallback_empty = (int64_t)h8[0];
+    st->totals.fallback_reduced = (int64_t)h8[1];
+    st->totals.fallback_schur = (int64_t)h8[2];
+    bool all = true;
+    for (int32_t b = 0; b < B; ++b) all &= st->status[b] == 1;
+    if (!all) {
+      ccg::g_last_error = "cc_solve_batch: some meshes did not converge";
+      return CC_ERR_NOT_CONVERGED;
+    }
+    return CC_OK;
+  } catch (const ccg::Fail& f) {
+    if (ccg::g_last_error.empty()) ccg::g_last_error = "cc_solve_batch";
+    return f.st;
+  } catch (...) {
+    ccg::g_last_error = "cc_solve_batch: unexpected error";
     return CC_ERR_STATE;
   }
 }

@@ -133,6 +133,15 @@ struct Mesh {
   int32_t max_up = 0;          // longest upper block row
   int32_t max_rs = 0;          // most staged sources of one free row
   std::vector<double> mass;
+  std::vector<double> tet_mu, tet_lh, tet_rho;   // per-tet material (a batch mixes materials)
+  // batches: mesh b owns vertices [mesh_vptr[b], mesh_vptr[b+1]) and tets [mesh_tptr[b], mesh_tptr[b+1])
+  std::vector<int64_t> mesh_vptr, mesh_tptr;
+  std::vector<int32_t> mesh_fptr;                // free rows of mesh b: [mesh_fptr[b], mesh_fptr[b+1])
+  DBuf<int32_t> d_vert_mesh;                     // [n] mesh of every vertex
+  DBuf<int32_t> d_mesh_fptr;                     // [B+1]
+  DBuf<int32_t> d_mesh_active;                   // [B] 1 while the mesh is still being solved
+  DBuf<int32_t> d_mesh_ones;                     // [B] all ones (resets d_mesh_active)
+  DBuf<double> d_mesh_gsq;                       // [B] squared free gradient norm per mesh
   std::vector<int32_t> color;
   int32_t num_colors = 0;
   std::vector<int64_t> sup_ptr;
@@ -151,6 +160,8 @@ struct Mesh {
   DBuf<float2> d_Bm_df;      // [T][9] float-float copy
   DBuf<float> d_Bm32;        // [T][9]
   DBuf<double> d_vol;        // [T]
+  DBuf<double2> d_mat64;     // [T] (mu, lam_hat) of the tet's material
+  DBuf<float4> d_matdf;      // [T] (mu hi, mu lo, lam_hat hi, lam_hat lo)
   DBuf<double> d_volw;       // [T] vol * elastic weight (h^2 or 1), float64
   DBuf<float> d_volw32;      // [T] same, float32
   DBuf<float2> d_volw_df;    // [T] same, float-float
@@ -232,6 +243,7 @@ void launch_energy(Mesh& m, const double* x, const double* xt, double* out_scala
                    cudaStream_t s);
 void launch_gnorm_f64(Mesh& m, double* grad_out, double* out_scalar, cudaStream_t s);
 void launch_gnorm_mixed(Mesh& m, double* grad_out, double* out_scalar, cudaStream_t s);
+void launch_gnorm_mesh(Mesh& m, bool mixed, cudaStream_t s);  // per-mesh squared norms -> d_mesh_gsq
 // mirrors and small vector ops
 void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStream_t s);
 void launch_inertial_target(const double* x, const double* v, int64_t n, double h,

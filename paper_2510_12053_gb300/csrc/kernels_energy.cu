@@ -143,13 +143,16 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
 __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                const double* __restrict__ Bm, const double* __restrict__ vol,
                                const uint8_t* __restrict__ pinned, const double* __restrict__ x, int64_t n,
-                               const int32_t* __restrict__ list, int64_t count, double mu, double lh,
+                               const int32_t* __restrict__ list, int64_t count, const double2* __restrict__ mat,
                                double weight, double* __restrict__ gcon, double* __restrict__ hten) {
   extern __shared__ __align__(16) double hstage64[];
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < count;
   const int t = live ? list[k] : -1;
-  if (live) tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, t, mu, lh, weight, gcon, hstage64 + threadIdx.x * 96);
+  if (live) {
+    const double2 ml = mat[t];
+    tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, t, ml.x, ml.y, weight, gcon, hstage64 + threadIdx.x * 96);
+  }
   __syncwarp();
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   for (int u = 0; u < 32; ++u) {
@@ -245,7 +248,7 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
                                  const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
                                  const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
                                  const float4* __restrict__ x_lo, const int32_t* __restrict__ list, int64_t count,
-                                 df mu_d, df lh_d, float mu_f, float lh_f, const float* __restrict__ volw32,
+                                 const float4* __restrict__ matdf, const float* __restrict__ volw32,
                                  float2* __restrict__ gcon, float* __restrict__ hten) {
   // Each thread's 96 Hessian values are staged in shared memory, then every
   // warp writes its 32 tets' 384-byte regions with coalesced 16-byte stores.
@@ -253,8 +256,11 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < count;
   const int t = live ? list[k] : -1;
-  if (live) tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, t, mu_d, lh_d, mu_f, lh_f, volw32, gcon,
-                                hstage + threadIdx.x * 96);
+  if (live) {
+    const float4 ml = matdf[t];  // (mu hi, mu lo, lam_hat hi, lam_hat lo)
+    tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, t, df{ml.x, ml.y}, df{ml.z, ml.w}, ml.x, ml.z,
+                        volw32, gcon, hstage + threadIdx.x * 96);
+  }
   __syncwarp();
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   for (int u = 0; u < 32; ++u) {
@@ -420,7 +426,7 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t count, d
 
 __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __restrict__ Bm,
                               const double* __restrict__ vol, const double* __restrict__ x, int64_t n,
-                              int64_t T, double mu, double lh, double weight, double* __restrict__ part) {
+                              int64_t T, const double2* __restrict__ mat, double weight, double* __restrict__ part) {
   double e = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
     const int4 tv = tets[t];
@@ -439,6 +445,7 @@ __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __res
 #pragma unroll
     for (int q = 0; q < 9; ++q) I += kin.F[q] * kin.F[q];
     const double Jm1 = kin.J - 1.0;
+    const double mu = mat[t].x, lh = mat[t].y;
     e += weight * vol[t] * (0.5 * mu * (I - 3.0) - mu * Jm1 + 0.5 * lh * Jm1 * Jm1);
   }
   e = block_sum(e);
@@ -473,6 +480,27 @@ __global__ void k_gnorm(const int32_t* __restrict__ free_rows, int64_t nfree, co
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// Squared free gradient norm of every mesh of a batch: one CTA per mesh over
+// its contiguous range of free rows, fixed-order block reduction.
+template <bool kMixed>
+__global__ void k_gnorm_mesh(const int32_t* __restrict__ fptr, const int32_t* __restrict__ free_rows,
+                             const double* __restrict__ g64, const float* __restrict__ g_hi,
+                             const float* __restrict__ g_lo, double* __restrict__ gsq) {
+  const int b = blockIdx.x;
+  double acc = 0.0;
+  for (int k = fptr[b] + threadIdx.x; k < fptr[b + 1]; k += blockDim.x) {
+    const int j = free_rows[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double v = kMixed ? (double)g_hi[3 * (int64_t)j + a] + (double)g_lo[3 * (int64_t)j + a]
+                              : g64[3 * (int64_t)j + a];
+      acc += v * v;
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) gsq[b] = acc;
 }
 
 __global__ void k_split_df(const double* __restrict__ x, int64_t n, float4* __restrict__ hi,
@@ -511,20 +539,18 @@ void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t 
   constexpr int kThreads = 64;
   const size_t smem = (size_t)kThreads * 96 * sizeof(double);
   k_tet_grad_f64<<<grid_for(count, kThreads), kThreads, smem, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x, m.n,
-                                                    list, count, m.mu, m.lam_hat, weight, m.f64.gcon.p,
+                                                    list, count, m.d_mat64.p, weight, m.f64.gcon.p,
                                                     m.f64.hten.p);
 }
 
 void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
   if (count <= 0) return;
   (void)weight;
-  df mu_d{(float)m.mu, (float)(m.mu - (double)(float)m.mu)};
-  df lh_d{(float)m.lam_hat, (float)(m.lam_hat - (double)(float)m.lam_hat)};
   constexpr int kThreads = 128;
   const size_t smem = (size_t)kThreads * 96 * sizeof(float);
   k_tet_grad_mixed<<<grid_for(count, kThreads), kThreads, smem, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_volw_df.p,
-                                                      m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, mu_d, lh_d,
-                                                      (float)m.mu, (float)m.lam_hat, m.d_volw32.p, m.mx.gcon.p,
+                                                      m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, m.d_matdf.p,
+                                                      m.d_volw32.p, m.mx.gcon.p,
                                                       m.mx.hten.p);
 }
 
@@ -556,7 +582,7 @@ void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s) {
 
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {
   const double w = m.h > 0.0 ? m.h * m.h : 1.0;
-  k_energy_tets<<<kRedBlocks, kBlock, 0, s>>>(m.d_tets.p, m.d_Bm.p, m.d_vol.p, x, m.n, m.T, m.mu, m.lam_hat, w,
+  k_energy_tets<<<kRedBlocks, kBlock, 0, s>>>(m.d_tets.p, m.d_Bm.p, m.d_vol.p, x, m.n, m.T, m.d_mat64.p, w,
                                               m.d_red.p);
   if (m.h > 0.0 && xt) {
     k_energy_inertia<<<kRedBlocks, kBlock, 0, s>>>(m.d_mass.p, x, xt, m.n, m.d_red.p + kRedBlocks);
@@ -576,6 +602,16 @@ void launch_gnorm_mixed(Mesh& m, double* grad_out, double* out, cudaStream_t s) 
   k_gnorm<true><<<kRedBlocks, kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, m.n,
                                               grad_out, m.d_red.p);
   k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+}
+
+void launch_gnorm_mesh(Mesh& m, bool mixed, cudaStream_t s) {
+  const unsigned B = (unsigned)(m.mesh_vptr.size() - 1);
+  if (mixed)
+    k_gnorm_mesh<true><<<B, 256, 0, s>>>(m.d_mesh_fptr.p, m.d_free_rows.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p,
+                                         m.d_mesh_gsq.p);
+  else
+    k_gnorm_mesh<false><<<B, 256, 0, s>>>(m.d_mesh_fptr.p, m.d_free_rows.p, m.f64.g.p, nullptr, nullptr,
+                                          m.d_mesh_gsq.p);
 }
 
 void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStream_t s) {

@@ -218,13 +218,14 @@ __global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, con
                            const HT* __restrict__ bsr, const double* __restrict__ g64,
                            const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
                            double* __restrict__ x, float4* __restrict__ x_hi, float4* __restrict__ x_lo,
-                           AR rel, unsigned long long* __restrict__ fallback,
-                           unsigned long long* __restrict__ err) {
+                           AR rel, const int32_t* __restrict__ vert_mesh, const int32_t* __restrict__ active,
+                           unsigned long long* __restrict__ fallback, unsigned long long* __restrict__ err) {
   using Ar = Arith<AR>;
   using V = typename Ar::V;
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= count) return;
   const int i = verts[k];
+  if (active[vert_mesh[i]] == 0) return;  // this mesh of the batch has stopped
   auto ld = [](HT v) -> V {
     if constexpr (sizeof(HT) == 4) return Ar::mkf((float)v);
     else return Ar::mk((double)v);
@@ -374,11 +375,12 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
   if constexpr (kMixed) {
     const df rel{1e-12f, (float)(1e-12 - (double)1e-12f)};
     k_condense<df, HT, kMixed, kUpd><<<grid, 128, 0, s>>>(verts, count, cpl, m.d_sup_ptr.p, m.d_up_ptr.p, bsr, g64,
-                                                         g_hi, g_lo, m.n, x, xh, xl, rel, c.fallback, c.error);
+                                                         g_hi, g_lo, m.n, x, xh, xl, rel, m.d_vert_mesh.p,
+                                                         m.d_mesh_active.p, c.fallback, c.error);
   } else {
     k_condense<double, HT, kMixed, kUpd><<<grid, 128, 0, s>>>(verts, count, cpl, m.d_sup_ptr.p, m.d_up_ptr.p, bsr,
-                                                             g64, g_hi, g_lo, m.n, x, xh, xl, 1e-12, c.fallback,
-                                                             c.error);
+                                                             g64, g_hi, g_lo, m.n, x, xh, xl, 1e-12,
+                                                             m.d_vert_mesh.p, m.d_mesh_active.p, c.fallback, c.error);
   }
   CCG_CUDA(cudaGetLastError());
 }

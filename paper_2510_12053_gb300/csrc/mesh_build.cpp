@@ -59,7 +59,7 @@ void build_topology(Mesh& m) {
     inverse3(Dm, inv, &d2);
     std::memcpy(&Bm[9 * t], inv, sizeof(inv));
     vol[t] = det / 6.0;
-    for (int c = 0; c < 4; ++c) m.mass[tv[c]] += m.rho * vol[t] / 4.0;
+    for (int c = 0; c < 4; ++c) m.mass[tv[c]] += m.tet_rho[t] * vol[t] / 4.0;
   }
 
   // ---- vertex -> tet lists (ascending tet id) and the entry of every corner
@@ -183,6 +183,19 @@ void build_topology(Mesh& m) {
   m.d_Bm32.upload(Bm32, s);
   m.d_vol.upload(vol, s);
   {
+    std::vector<double2> m64(T);
+    std::vector<float4> mdf(T);
+    for (int64_t t = 0; t < T; ++t) {
+      const double mu = m.tet_mu[t], lh = m.tet_lh[t];
+      m64[t] = make_double2(mu, lh);
+      const float mh = (float)mu, lhh = (float)lh;
+      mdf[t] = make_float4(mh, (float)(mu - (double)mh), lhh, (float)(lh - (double)lhh));
+    }
+    m.d_mat64.upload(m64, s);
+    m.d_matdf.upload(mdf, s);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
+  {
     const double w = m.h > 0.0 ? m.h * m.h : 1.0;
     std::vector<double> vw(T);
     std::vector<float> vw32(T);
@@ -220,6 +233,30 @@ void build_topology(Mesh& m) {
   m.d_rs_src.upload(rs_src, s);
   m.d_free_rows.upload(free_rows, s);
   m.d_all_tets.upload(active, s);
+  {
+    if (m.mesh_vptr.empty()) {
+      m.mesh_vptr = {0, n};
+      m.mesh_tptr = {0, T};
+    }
+    const int64_t B = (int64_t)m.mesh_vptr.size() - 1;
+    std::vector<int32_t> vmesh(n);
+    m.mesh_fptr.assign(B + 1, 0);
+    for (int64_t b = 0; b < B; ++b)
+      for (int64_t v = m.mesh_vptr[b]; v < m.mesh_vptr[b + 1]; ++v) vmesh[v] = (int32_t)b;
+    // free rows ascend, and vertex ranges ascend with b, so each mesh's free rows are contiguous
+    int64_t f = 0;
+    for (int64_t b = 0; b < B; ++b) {
+      while (f < (int64_t)free_rows.size() && free_rows[f] < m.mesh_vptr[b + 1]) ++f;
+      m.mesh_fptr[b + 1] = (int32_t)f;
+    }
+    m.d_vert_mesh.upload(vmesh, s);
+    m.d_mesh_fptr.upload(m.mesh_fptr, s);
+    std::vector<int32_t> ones(B, 1);
+    m.d_mesh_active.upload(ones, s);
+    m.d_mesh_ones.upload(ones, s);
+    m.d_mesh_gsq.alloc(B);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
   {
     std::vector<int32_t> ids(16 * T);
     for (int64_t e = 0; e < 4 * T; ++e)
