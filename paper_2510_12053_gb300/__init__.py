@@ -84,6 +84,11 @@ class BatchStats(ctypes.Structure):
                 ("sweeps", ctypes.c_int32), ("totals", SweepStats)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("couple_threads", ctypes.c_int32), ("gather_warps", ctypes.c_int32),
+                ("couple_ms", ctypes.c_double * 3), ("gather_ms", ctypes.c_double * 3)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5), ("total_launches", ctypes.c_int64)]
 
@@ -109,6 +114,7 @@ _SIGS = {
                                       ctypes.POINTER(_P)]),
     "cc_batch_offsets": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "cc_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(BatchStats)]),
+    "cc_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -293,6 +299,14 @@ class Mesh:
         out = np.empty(max(cnt.value, 1), dtype=dt)
         _check(lib().cc_export(self._h, which, out.ctypes.data, out.size, ctypes.byref(cnt)))
         return out[:cnt.value]
+
+    def autotune(self, x, xtilde=None, precision: str = "mixed", sweeps: int = 4) -> dict:
+        """Pick the fastest launch shapes for this mesh (x is not modified)."""
+        r = TuneResult()
+        _check(lib().cc_autotune(self._h, _dev3n(x, self.n, "x"), _dev3n(xtilde, self.n, "xtilde"), PREC[precision],
+                                 int(sweeps), ctypes.byref(r)))
+        return {"couple_threads": r.couple_threads, "gather_warps": r.gather_warps,
+                "couple_ms": list(r.couple_ms), "gather_ms": list(r.gather_ms)}
 
     def profile_enable(self, on: bool = True):
         _check(lib().cc_profile_enable(self._h, int(on)))

@@ -813,6 +813,80 @@ cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o
   }
 }
 
+cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precision p, int32_t sweeps,
+                      cc_tune_result* out) {
+  CC_API_BODY("cc_autotune", {
+    CCG_CHECK(m && x && out, CC_ERR_INVALID_ARG, "NULL argument");
+    CCG_CHECK(sweeps >= 1 && sweeps <= 1000, CC_ERR_INVALID_ARG, "sweeps must be in [1, 1000]");
+    CCG_CHECK(m->h == 0.0 || xt, CC_ERR_INVALID_ARG, "dynamic mesh needs xtilde");
+    cc_sweep_opts so{CC_UPDATE_CC, CC_SCHED_COLORED, p, 0, -1};
+    int cb, ce;
+    check_sweep_opts(*m, so, &cb, &ce);
+    ensure_state(*m, p);
+    cudaStream_t s = m->stream;
+    DBuf<double> tmp;
+    tmp.alloc(3 * m->n);
+    cudaEvent_t e0, e1;
+    CCG_CUDA(cudaEventCreate(&e0));
+    CCG_CUDA(cudaEventCreate(&e1));
+    const bool prof = m->prof.on;
+    m->prof.on = false;
+    auto time_sweeps = [&]() -> double {
+      CCG_CUDA(cudaMemcpyAsync(tmp.p, x, 3 * m->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      activate_all(*m);
+      if (p == CC_PREC_MIXED) {
+        split(*m, tmp.p, m->mx.x_hi.p, m->mx.x_lo.p);
+        if (m->h > 0.0) split(*m, xt, m->mx.xt_hi.p, m->mx.xt_lo.p);
+      }
+      refresh_all(*m, p, tmp.p, xt);
+      sweep_body(*m, tmp.p, xt, so, cb, ce, true);  // warm-up sweep
+      post_refresh(*m, tmp.p, xt, so, ce);
+      CCG_CUDA(cudaEventRecord(e0, s));
+      for (int k = 0; k < sweeps; ++k) {
+        sweep_body(*m, tmp.p, xt, so, cb, ce, true);
+        post_refresh(*m, tmp.p, xt, so, ce);
+      }
+      CCG_CUDA(cudaEventRecord(e1, s));
+      CCG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CCG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return ms / sweeps;
+    };
+    try {
+      const int ct[3] = {64, 128, 256}, gw[3] = {2, 4, 8};
+      for (int k = 0; k < 3; ++k) {
+        m->tune_couple_threads = ct[k];
+        out->couple_ms[k] = time_sweeps();
+      }
+      int best = 0;
+      for (int k = 1; k < 3; ++k)
+        if (out->couple_ms[k] < out->couple_ms[best]) best = k;
+      m->tune_couple_threads = ct[best];
+      for (int k = 0; k < 3; ++k) {
+        m->tune_gather_wpb = gw[k];
+        out->gather_ms[k] = time_sweeps();
+      }
+      best = 0;
+      for (int k = 1; k < 3; ++k)
+        if (out->gather_ms[k] < out->gather_ms[best]) best = k;
+      m->tune_gather_wpb = gw[best];
+    } catch (...) {
+      m->prof.on = prof;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    m->prof.on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_graph(*m);
+    CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    out->couple_threads = m->tune_couple_threads;
+    out->gather_warps = m->tune_gather_wpb;
+  })
+}
+
 cc_status cc_get_info(const cc_mesh* m, cc_mesh_info* info) {
   CC_API_BODY("cc_get_info", {
     CCG_CHECK(m && info, CC_ERR_INVALID_ARG, "NULL argument");

@@ -113,6 +113,9 @@ void set_smem_limit(const void* kernel, size_t bytes);
 
 struct Mesh {
   Prof prof;
+  // launch configurations chosen by cc_autotune (defaults before tuning)
+  int tune_couple_threads = 128;  // threads per vertex in the coupling kernel
+  int tune_gather_wpb = 4;        // warps (rows) per block in the row gather
   int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
   int32_t max_valence = 0;
   double E = 0, nu = 0, rho = 0, mu = 0, lam_hat = 0, h = 0;

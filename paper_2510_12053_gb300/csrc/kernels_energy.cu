@@ -558,7 +558,7 @@ template <typename HT, bool kMixed>
 static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, const HT* hten, const HT* massh,
                         cudaStream_t s) {
   const bool dyn = m.h > 0.0;
-  const int wpb = 4;
+  const int wpb = m.tune_gather_wpb > 0 ? m.tune_gather_wpb : 4;
   const int64_t blocks = (m.n_free + wpb - 1) / wpb;
   const size_t smem = (size_t)wpb * (m.max_rs + m.max_up + 1) * sizeof(int);
   set_smem_limit(reinterpret_cast<const void*>(k_row_gather<HT, kMixed>), smem);

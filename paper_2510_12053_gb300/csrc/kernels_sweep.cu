@@ -57,12 +57,11 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
   }
 }
 
-constexpr int kSolveThreads = 128;
 
 template <typename HT>
-__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes) {
+__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps) {
   return align16((size_t)sup_max * 9 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
-         align16((size_t)smap_max * code_bytes) + 4 * 32 * sizeof(HT);
+         align16((size_t)smap_max * code_bytes) + (size_t)nwarps * 32 * sizeof(HT);
 }
 
 template <typename SlotT>
@@ -85,8 +84,8 @@ struct SlotCodes<uint16_t> {
 // A's term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
 // l > i.  The CTA writes 27 values per vertex: Ht (6, symmetric), A (9),
 // b (3), H_ii (9).
-template <typename HT, typename SlotT, bool kMixed, int kUpd>
-__global__ void __launch_bounds__(kSolveThreads) k_couple(
+template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_couple(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_couple(
   ptr += align16((size_t)(sup_max + 1) * 4);
   SlotT* codes = reinterpret_cast<SlotT*>(ptr);
   ptr += align16((size_t)smap_max * sizeof(SlotT));
-  HT* red = reinterpret_cast<HT*>(ptr);  // [4 warps][32]
+  HT* red = reinterpret_cast<HT*>(ptr);  // [warps][32]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = verts[blockIdx.x];
@@ -116,9 +115,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_couple(
   const int64_t c0 = smap_ptr[i];
   const int ncodes = (int)(smap_ptr[i + 1] - c0);
 
-  for (int k = tid; k < 9 * m; k += kSolveThreads) Us[k] = U[(int64_t)s0 * 9 + k];
-  for (int k = tid; k < ncodes; k += kSolveThreads) codes[k] = smap[c0 + k];
-  for (int s = tid; s <= m; s += kSolveThreads) {
+  for (int k = tid; k < 9 * m; k += kThreads) Us[k] = U[(int64_t)s0 * 9 + k];
+  for (int k = tid; k < ncodes; k += kThreads) codes[k] = smap[c0 + k];
+  for (int s = tid; s <= m; s += kThreads) {
     const int j = s < m ? sup_idx[s0 + s] : i;
     const int a = up_ptr[j];
     rstart[s] = a;
@@ -149,7 +148,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_couple(
   mat3_zero(A);
   mat3_zero(Hii);
   const int qw = tid >> 3, l8 = tid & 7;
-  for (int r = qw; r <= m; r += kSolveThreads / 8) {
+  for (int r = qw; r <= m; r += kThreads / 8) {
     const int P = rstart[r], L = rlen[r], off = roff[r];
     const HT* Uj = Us + 9 * r;
     for (int q = l8; q < L; q += 8) {
@@ -202,8 +201,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_couple(
     for (int v = 0; v < 27; ++v) red[warp * 32 + v] = vals27[v];
   __syncthreads();
   if (tid >= 27) return;
-  // fixed-order sum of the four warps' partials
-  cpl[(int64_t)blockIdx.x * 32 + tid] = ((red[tid] + red[32 + tid]) + red[64 + tid]) + red[96 + tid];
+  // fixed-order sum of the warps' partials
+  HT tot = red[tid];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w) tot += red[32 * w + tid];
+  cpl[(int64_t)blockIdx.x * 32 + tid] = tot;
 }
 
 // Batched condensation (Eq. 9-12), one free vertex per thread: a warp
@@ -346,30 +348,38 @@ __global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, con
   }
 }
 
+template <typename HT, bool kMixed, int kUpd, int kThreads>
+void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
+                   const float* g_hi, HT* cpl, cudaStream_t s) {
+  const int supm = m.sup_max > 0 ? m.sup_max : 1;
+  const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
+  const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
+  CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+  if (m.smap_wide) {
+    auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    kern<<<(unsigned)count, kThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
+                                                 m.d_smap_ptr.p, m.d_smap16.p, bsr, g64, g_hi, supm, smx, cpl);
+  } else {
+    auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    kern<<<(unsigned)count, kThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
+                                                 m.d_smap_ptr.p, m.d_smap8.p, bsr, g64, g_hi, supm, smx, cpl);
+  }
+  CCG_CUDA(cudaGetLastError());
+}
+
 template <typename HT, bool kMixed, int kUpd>
 void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
                 const float* g_hi, const float* g_lo, HT* cpl, double* x, SweepCounters c, cudaStream_t s) {
   float4* xh = kMixed ? m.mx.x_hi.p : nullptr;
   float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
   if (kUpd != CC_UPDATE_CD) {
-    const int supm = m.sup_max > 0 ? m.sup_max : 1;
-    const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
-    if (m.smap_wide) {
-      const size_t smem = cta_smem_bytes<HT>(supm, smx, 2);
-      CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
-      auto kern = k_couple<HT, uint16_t, kMixed, kUpd>;
-      set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-      kern<<<(unsigned)count, kSolveThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
-                                                        m.d_smap_ptr.p, m.d_smap16.p, bsr, g64, g_hi, supm, smx, cpl);
-    } else {
-      const size_t smem = cta_smem_bytes<HT>(supm, smx, 1);
-      CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
-      auto kern = k_couple<HT, uint8_t, kMixed, kUpd>;
-      set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-      kern<<<(unsigned)count, kSolveThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
-                                                        m.d_smap_ptr.p, m.d_smap8.p, bsr, g64, g_hi, supm, smx, cpl);
+    switch (m.tune_couple_threads) {
+      case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
+      case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
+      default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, s);
     }
-    CCG_CUDA(cudaGetLastError());
   }
   const unsigned grid = (unsigned)((count + 127) / 128);
   if constexpr (kMixed) {
