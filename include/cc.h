@@ -337,6 +337,16 @@ typedef struct {
 cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev, cc_precision precision,
                       int32_t sweeps, cc_tune_result* out);
 
+/* Dense BF16 tensor-core GEMM used by the learned-subspace MLP (no
+ * counterpart in the paper), exposed for testing: C = A . B^T with
+ * A [M x K], B [N x K] row-major BF16 device arrays (leading dimensions lda,
+ * ldb in elements, multiples of 8, base addresses 16-byte aligned) and
+ * C [M x N] float32 (leading dimension ldc).  tcgen05 MMA with TMA-loaded,
+ * 128-byte-swizzled tiles and a float32 accumulator in tensor memory.
+ * CC_ERR_TIMEOUT if a bounded device wait expired. */
+cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
+                          int32_t K, float* C, int64_t ldc, void* stream);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* cc_last_error(void);
 

@@ -115,6 +115,8 @@ _SIGS = {
     "cc_batch_offsets": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "cc_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(BatchStats)]),
     "cc_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
+    "cc_gemm_bf16_tn": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, _P, ctypes.c_int64, _P]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -352,6 +354,18 @@ class Mesh:
         return SolveResult(st.iterations, bool(st.converged), st.g0, st.g_final, st.energy_final,
                            st.sweeps.updates, st.sweeps.fallback_empty, st.sweeps.fallback_reduced,
                            st.sweeps.fallback_schur, hist)
+
+
+def gemm_bf16_tn(A, B, out=None, stream=None):
+    """C = A . B^T on the tcgen05 kernel (A [M, K], B [N, K] bf16 CUDA tensors)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().cc_gemm_bf16_tn(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), M, N, K, C.data_ptr(),
+                                 C.stride(0), _stream_ptr(st)))
+    return C
 
 
 def version() -> str:

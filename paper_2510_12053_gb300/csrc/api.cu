@@ -9,6 +9,7 @@
 #include <string>
 
 #include "cc_internal.cuh"
+#include "mlp.cuh"
 
 namespace ccg {
 
@@ -884,6 +885,25 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
     CCG_CUDA(cudaStreamSynchronize(s));
     out->couple_threads = m->tune_couple_threads;
     out->gather_warps = m->tune_gather_wpb;
+  })
+}
+
+cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N, int32_t K,
+                          float* C, int64_t ldc, void* stream) {
+  CC_API_BODY("cc_gemm_bf16_tn", {
+    CCG_CHECK(A && B && C && ldc >= N, CC_ERR_INVALID_ARG, "bad GEMM arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<int> err;
+    err.alloc(1);
+    CCG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    GemmEpilogue ep;
+    ep.c32 = C;
+    ep.ldc = ldc;
+    gemm_tn(A, lda, B, ldb, M, N, K, kEpiF32, ep, err.p, s);
+    int h = 0;
+    CCG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    CCG_CHECK(h == 0, CC_ERR_TIMEOUT, "a bounded wait in the GEMM kernel expired");
   })
 }
 
