@@ -259,9 +259,10 @@ def cube32_stretch(E: float = 1e5, seed: int = 0, init: str = "linear") -> Scene
                        name="cube32_stretch")
 
 
-def cube48_stretch(E: float = 1e6, seed: int = 0, init: str = "linear") -> Scene:
+def cube48_stretch(E: float = 1e6, seed: int = 0, init: str = "linear", nu: float = 0.45,
+                   jitter_amount: float = 0.05) -> Scene:
     """48x48x48-cell unit cube (117 649 vertices, 663 552 tets)."""
-    return stretch_box(48, 48, 48, E=E, nu=0.45, jitter_amount=0.05, seed=seed, init=init,
+    return stretch_box(48, 48, 48, E=E, nu=nu, jitter_amount=jitter_amount, seed=seed, init=init,
                        name="cube48_stretch")
 
 
@@ -269,3 +270,51 @@ def beam_dynamic(nx: int = 64, ny: int = 64, nz: int = 256) -> Scene:
     """Cantilever of 1/64 m cells (64x64x256 cells: 1 085 825 vertices, 6 291 456 tets)."""
     return cantilever(nx, ny, nz, cell=1.0 / 64.0, E=1e7, nu=0.45, rho=1000.0, h=1.0 / 60.0,
                       name=f"beam{nx}x{ny}x{nz}")
+
+
+# ---------------------------------------------------------------------------
+# Learned-subspace inputs: training meshes, initial weights, minibatch draws
+# ---------------------------------------------------------------------------
+def training_boxes(count: int, seed: int, side_lo: int = 4, side_hi: int = 12,
+                   jitter_amount: float = 0.05) -> List[Scene]:
+    """Jittered random boxes for training the subspace network: sides uniform
+    in ``{side_lo..side_hi}`` cells, otherwise the batch family of
+    :func:`random_box` (random clamped face, stretch, ``E``, ``nu``)."""
+    return [random_box(i, seed, side_lo=side_lo, side_hi=side_hi, jitter_amount=jitter_amount)
+            for i in range(count)]
+
+
+def mlp_dims(hidden: int = 256, layers: int = 3, slots: int = 64, channels: int = 4,
+             extra: int = 2, out_per_slot: int = 9) -> List[int]:
+    """Layer widths of the subspace network: input, ``layers`` hidden widths, output."""
+    return [slots * channels + extra] + [hidden] * layers + [slots * out_per_slot]
+
+
+def mlp_param_count(dims: List[int]) -> int:
+    return sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(len(dims) - 1))
+
+
+def mlp_init(dims: List[int], seed: int, out_scale: float = 0.1) -> np.ndarray:
+    """Initial parameters as one float32 vector, layer by layer: W_l row-major
+    ``[dims[l+1], dims[l]]`` followed by b_l ``[dims[l+1]]``.  Hidden weights
+    are normal with variance 2 / fan_in (He et al. 2015), the output layer's
+    are scaled by ``out_scale``; biases start at zero."""
+    parts, ctr = [], 0
+    L = len(dims) - 1
+    for l in range(L):
+        n_out, n_in = dims[l + 1], dims[l]
+        z = normal(seed, np.arange(ctr, ctr + n_out * n_in, dtype=np.uint64))
+        ctr += n_out * n_in
+        std = np.sqrt(2.0 / n_in) * (out_scale if l == L - 1 else 1.0)
+        parts.append((z * std).astype(np.float32))
+        parts.append(np.zeros(n_out, dtype=np.float32))
+    return np.concatenate(parts)
+
+
+def batch_indices(seed: int, step0: int, steps: int, batch: int, n: int) -> np.ndarray:
+    """Minibatch sample indices ``[steps, batch]`` int32 for training steps
+    ``step0 .. step0 + steps - 1``, drawn uniformly with replacement from
+    ``n`` samples (counter ``step * batch + b``)."""
+    c = np.arange(step0 * batch, (step0 + steps) * batch, dtype=np.uint64)
+    idx = np.minimum((uniform01(seed, c) * n).astype(np.int64), n - 1)
+    return idx.astype(np.int32).reshape(steps, batch)

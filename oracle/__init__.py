@@ -23,6 +23,11 @@ Modules
 ``solvers``   coordinate descent (Eq. 3), JGS2 (Eq. 7), Coordinate
               Condensation (Eq. 9-12, Algorithm 1), Newton, line search,
               termination measures (Sec. 4.1).
+``mlp``       the subspace network (no counterpart in the paper): forward and
+              backward passes with the bfloat16 rounding points of the
+              tensor-core path, mean squared error, Adam.
+``learned``   stencil slots, network inputs and targets, assembly of learned
+              bases, and the per-vertex fallback rule (residual of Eq. 5).
 
 Parity status: every function listed above is pinned by ``tests/test_oracle_*``
 against finite differences, invariants, textbook formulas or brute force,
