@@ -337,15 +337,134 @@ typedef struct {
 cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev, cc_precision precision,
                       int32_t sweeps, cc_tune_result* out);
 
-/* Dense BF16 tensor-core GEMM used by the learned-subspace MLP (no
- * counterpart in the paper), exposed for testing: C = A . B^T with
- * A [M x K], B [N x K] row-major BF16 device arrays (leading dimensions lda,
- * ldb in elements, multiples of 8, base addresses 16-byte aligned) and
- * C [M x N] float32 (leading dimension ldc).  tcgen05 MMA with TMA-loaded,
- * 128-byte-swizzled tiles and a float32 accumulator in tensor memory.
- * CC_ERR_TIMEOUT if a bounded device wait expired. */
+/* ======================================================================
+ * Learned perturbation bases.  The paper builds every U_i by the patch
+ * solve of Eq. 5 (Sec. 3.1) and has no learned component: everything below
+ * is an addition.  A multilayer perceptron maps the rest geometry of a
+ * vertex's 2-ring and its material to U_i on the 2-ring support (k = 2);
+ * bases whose Eq. 5 residual is no better than U_i = 0 fall back to the
+ * computed patch solve, vertex by vertex.
+ * ====================================================================== */
+
+/* Dense BF16 tensor-core GEMM used by the network, exposed for testing:
+ * C = A . B^T with A [M x K], B [N x K] row-major BF16 device arrays
+ * (leading dimensions lda, ldb in elements, multiples of 8, base addresses
+ * 16-byte aligned) and C [M x N] float32 device (leading dimension ldc).
+ * tcgen05 MMA with TMA-loaded, 128-byte-swizzled tiles and a float32
+ * accumulator in tensor memory.  n_tile in {0 (automatic), 64, 128, 192,
+ * 256}; k_splits >= 1 splits K over CTAs (partial products summed in a fixed
+ * order afterwards), 0 = 1.  CC_ERR_TIMEOUT if a bounded device wait
+ * expired. */
 cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
-                          int32_t K, float* C, int64_t ldc, void* stream);
+                          int32_t K, float* C, int64_t ldc, int32_t n_tile, int32_t k_splits, void* stream);
+
+/* Network inputs: 64 stencil slots x 4 channels + 2 material channels. */
+#define CC_LEARNED_D_IN 258
+/* Network outputs: 64 slots x one 3x3 block. */
+#define CC_LEARNED_D_OUT 576
+/* Leading dimension of an input row (CC_LEARNED_D_IN rounded up to 8). */
+#define CC_LEARNED_LDX 264
+
+typedef struct cc_mlp cc_mlp;
+
+typedef struct {
+  int32_t d_in;       /* input width (CC_LEARNED_D_IN for bases) */
+  int32_t hidden;     /* width of every hidden layer, multiple of 8 */
+  int32_t layers;     /* number of hidden layers, >= 1 */
+  int32_t d_out;      /* output width, multiple of 8 (CC_LEARNED_D_OUT) */
+  int32_t max_batch;  /* largest training minibatch (rows) */
+} cc_mlp_config;
+
+typedef struct {
+  float lr, beta1, beta2, eps;  /* Adam (Kingma and Ba 2015, bias-corrected) */
+} cc_adam;
+
+/* Network with float32 master parameters, BF16 copies of every weight
+ * matrix in both orientations, Adam moments and a training workspace for
+ * max_batch rows, all on the current device.  Layers: H = GELU(H W^T + b)
+ * (erf form) for the hidden layers, linear output.  Parameters start at
+ * zero; load them with cc_mlp_set_params.  stream: cudaStream_t or NULL. */
+cc_status cc_mlp_create(const cc_mlp_config* cfg, void* stream, cc_mlp** out);
+void cc_mlp_destroy(cc_mlp* net);
+
+/* Number of parameters: sum over layers of d_out_l * d_in_l + d_out_l. */
+int64_t cc_mlp_param_count(const cc_mlp* net);
+
+/* Host float32 parameters, layer by layer: W_l row-major [d_out_l][d_in_l],
+ * then b_l [d_out_l].  Setting them also resets Adam's moments and step. */
+cc_status cc_mlp_set_params(cc_mlp* net, const float* params, int64_t count);
+cc_status cc_mlp_get_params(const cc_mlp* net, float* params, int64_t count);
+
+/* Y [rows x d_out] float32 (device, leading dimension ldy) of the inputs
+ * X [rows x d_in] BF16 (device, leading dimension ldx, multiple of 8).
+ * Any number of rows; the inference workspace grows as needed. */
+cc_status cc_mlp_forward(cc_mlp* net, const void* X, int64_t ldx, int64_t rows, float* Y, int64_t ldy);
+
+/* Mean squared error over rows x d_out against T (device float32 [rows x
+ * ldt]) and its gradient with respect to every parameter, written to grad
+ * (device float32 [param_count], parameter layout) unless NULL.  BF16 is
+ * stored at the inputs, the weights, the hidden activations, the output
+ * gradient and every pre-activation gradient; products accumulate in
+ * float32.  rows <= max_batch. */
+cc_status cc_mlp_loss_grad(cc_mlp* net, const void* X, int64_t ldx, const float* T, int64_t ldt,
+                           int32_t rows, double* loss, float* grad);
+
+/* One Adam step with a caller-supplied gradient (device float32). */
+cc_status cc_mlp_adam_step(cc_mlp* net, const float* grad, const cc_adam* opt);
+
+/* `steps` training steps: step s gathers the rows idx[s*batch .. s*batch +
+ * batch) (device int32, each < n_samples) of X (device BF16 [n_samples x
+ * ldx]) and T (device float32 [n_samples x ldt]), runs forward, backward
+ * and one Adam step.  losses (host [steps], or NULL) receives every step's
+ * loss.  batch <= max_batch. */
+cc_status cc_mlp_train(cc_mlp* net, const void* X, int64_t ldx, const float* T, int64_t ldt,
+                       int64_t n_samples, const int32_t* idx, int32_t steps, int32_t batch,
+                       const cc_adam* opt, double* losses);
+
+/* Network inputs (and optionally targets) of every free vertex of a mesh
+ * built on a Kuhn lattice, in ascending vertex id:
+ *   l_i = mean over the 1-ring of max_a |X_j[a] - X_i[a]| (the cell size);
+ *   for every j within 2 hops: q = (X_j - X_i) / l_i, o = floor(q + 1/2),
+ *   slot s = position of o in the 64 offsets of the lattice's 2-ring (the 14
+ *   1-ring offsets first, each group in lexicographic order); channels
+ *   4s..4s+2 = 8 (q - o), 4s+3 = +1 free / -1 pinned; absent slots zero;
+ *   channel 256 = (log10 E - 5.5) / 1.5, channel 257 = 10 (nu - 0.4).
+ * X: device BF16 [rows_cap x ldx] (ldx >= CC_LEARNED_LDX, multiple of 8,
+ * columns 258.. written as zero).  T: device float32 [rows_cap x ldt] or
+ * NULL; when given, the mesh must hold computed k = 2 bases
+ * (cc_build_subspace(mesh, 2)) and row r gets U_i[j] at columns
+ * 9 s(j) .. 9 s(j) + 8 for j in S_i, zero elsewhere.  rows: host out,
+ * number of free vertices.  CC_ERR_INVALID_ARG when a vertex within 2 hops
+ * is off the stencil or two share a slot (not a Kuhn lattice). */
+cc_status cc_learned_inputs(cc_mesh* mesh, void* X, int64_t ldx, float* T, int64_t ldt, int64_t rows_cap,
+                            int64_t* rows);
+
+typedef struct {
+  int64_t n_free;      /* vertices with a basis */
+  int64_t n_fallback;  /* of them, rebuilt by the patch solve */
+  double rho_max;      /* largest Eq. 5 residual of a kept learned basis */
+  double rho_mean;     /* mean residual of the learned bases, before fallback */
+  double ms_supports;  /* 2-ring supports (host breadth-first search) */
+  double ms_inputs;    /* network inputs */
+  double ms_infer;     /* network forward */
+  double ms_assemble;  /* predictions -> bases */
+  double ms_residual;  /* rest Hessian + Eq. 5 residuals */
+  double ms_fallback;  /* patch solves of the fallback set */
+  double ms_total;     /* wall time of the whole call */
+} cc_learned_stats;
+
+/* Replaces the mesh's bases by learned ones on the k = 2 supports: network
+ * inputs of every free vertex, one forward pass, bases assembled from the
+ * predictions, then the residual of Eq. 5 at rest,
+ *   rho_i = ||H_PP U_i + H_Pi||_F / ||H_Pi||_F,
+ * for every free vertex; those with rho_i >= tau (tau = 1: no better than
+ * U_i = 0, i.e. plain coordinate descent) get the computed basis from the
+ * patch solve.  rho (device float64 [n_free], may be NULL) receives every
+ * learned basis's residual.  Quasistatic meshes only (h = 0); needs
+ * cc_color first.  The network must have d_in = CC_LEARNED_D_IN and
+ * d_out = CC_LEARNED_D_OUT. */
+cc_status cc_build_learned_subspace(cc_mesh* mesh, cc_mlp* net, double tau, double* rho,
+                                    cc_learned_stats* stats);
 
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* cc_last_error(void);

@@ -93,7 +93,25 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5), ("total_launches", ctypes.c_int64)]
 
 
+class MlpConfig(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_int32), ("hidden", ctypes.c_int32), ("layers", ctypes.c_int32),
+                ("d_out", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
+class LearnedStats(ctypes.Structure):
+    _fields_ = [("n_free", ctypes.c_int64), ("n_fallback", ctypes.c_int64), ("rho_max", ctypes.c_double),
+                ("rho_mean", ctypes.c_double), ("ms_supports", ctypes.c_double), ("ms_inputs", ctypes.c_double),
+                ("ms_infer", ctypes.c_double), ("ms_assemble", ctypes.c_double), ("ms_residual", ctypes.c_double),
+                ("ms_fallback", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+
 PROFILE_CLASSES = ["tet_eval", "gather", "local_solve", "reduce", "other"]
+LEARNED_D_IN, LEARNED_D_OUT, LEARNED_LDX = 258, 576, 264
 
 _lib_handle = None
 
@@ -116,7 +134,21 @@ _SIGS = {
     "cc_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(BatchStats)]),
     "cc_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
     "cc_gemm_bf16_tn": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, _P, ctypes.c_int64, _P]),
+                                       ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]),
+    "cc_mlp_create": (ctypes.c_int, [ctypes.POINTER(MlpConfig), _P, ctypes.POINTER(_P)]),
+    "cc_mlp_destroy": (None, [_P]),
+    "cc_mlp_param_count": (ctypes.c_int64, [_P]),
+    "cc_mlp_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "cc_mlp_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "cc_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64]),
+    "cc_mlp_loss_grad": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_double), _P]),
+    "cc_mlp_adam_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(Adam)]),
+    "cc_mlp_train": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64, _P,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Adam), _P]),
+    "cc_learned_inputs": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64)]),
+    "cc_build_learned_subspace": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(LearnedStats)]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -289,6 +321,29 @@ class Mesh:
         _check(lib().cc_set_subspace(self._h, sp.ctypes.data, si.ctypes.data if si.size else None,
                                      Ub.ctypes.data))
 
+    def learned_inputs(self, X=None, T=None, targets: bool = False):
+        """Network inputs (and with ``targets`` the computed k = 2 bases in
+        slot order) of every free vertex: (X [n_free, 264] bf16, T or None)."""
+        import torch
+        nf = int(self.info().n_free)
+        if X is None:
+            X = torch.empty((nf, LEARNED_LDX), dtype=torch.bfloat16, device="cuda")
+        if targets and T is None:
+            T = torch.empty((nf, LEARNED_D_OUT), dtype=torch.float32, device="cuda")
+        rows = ctypes.c_int64()
+        _check(lib().cc_learned_inputs(self._h, _dev(X, torch.bfloat16, "X", LEARNED_LDX), X.stride(0),
+                                       _dev(T, torch.float32, "T", LEARNED_D_OUT) if T is not None else None,
+                                       T.stride(0) if T is not None else 0, X.shape[0], ctypes.byref(rows)))
+        return X, T
+
+    def build_learned_subspace(self, net: "MLP", tau: float = 1.0, want_rho: bool = False):
+        """Learned k = 2 bases with the per-vertex fallback; returns (stats dict, rho or None)."""
+        import torch
+        st = LearnedStats()
+        rho = torch.empty(int(self.info().n_free), dtype=torch.float64, device="cuda") if want_rho else None
+        _check(lib().cc_build_learned_subspace(self._h, net._h, float(tau), _ptr(rho), ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in LearnedStats._fields_}, rho
+
     def info(self) -> MeshInfo:
         inf = MeshInfo()
         _check(lib().cc_get_info(self._h, ctypes.byref(inf)))
@@ -356,7 +411,7 @@ class Mesh:
                            st.sweeps.fallback_schur, hist)
 
 
-def gemm_bf16_tn(A, B, out=None, stream=None):
+def gemm_bf16_tn(A, B, out=None, stream=None, n_tile: int = 0, k_splits: int = 0):
     """C = A . B^T on the tcgen05 kernel (A [M, K], B [N, K] bf16 CUDA tensors)."""
     import torch
     M, K = A.shape
@@ -364,8 +419,91 @@ def gemm_bf16_tn(A, B, out=None, stream=None):
     C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().cc_gemm_bf16_tn(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), M, N, K, C.data_ptr(),
-                                 C.stride(0), _stream_ptr(st)))
+                                 C.stride(0), int(n_tile), int(k_splits), _stream_ptr(st)))
     return C
+
+
+def _dev(t, dtype, name, cols=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.dim() == 2 and t.stride(1) == 1):
+        raise CCError(ERR_INVALID_ARG, f"{name} must be a row-major 2-D {dtype} CUDA tensor")
+    if cols is not None and t.shape[1] < cols:
+        raise CCError(ERR_INVALID_ARG, f"{name} needs at least {cols} columns")
+    return t.data_ptr()
+
+
+class MLP:
+    """The subspace network on the GPU (owns the library's ``cc_mlp``)."""
+
+    def __init__(self, d_in: int = LEARNED_D_IN, hidden: int = 256, layers: int = 3, d_out: int = LEARNED_D_OUT,
+                 max_batch: int = 8192, stream=None):
+        cfg = MlpConfig(d_in, hidden, layers, d_out, max_batch)
+        out = _P()
+        self._h = None
+        _check(lib().cc_mlp_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(out)))
+        self._h = out
+        self.dims = [d_in] + [hidden] * layers + [d_out]
+        self.max_batch = max_batch
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().cc_mlp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self) -> int:
+        return int(lib().cc_mlp_param_count(self._h))
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().cc_mlp_set_params(self._h, p.ctypes.data, p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.param_count, dtype=np.float32)
+        _check(lib().cc_mlp_get_params(self._h, p.ctypes.data, p.size))
+        return p
+
+    def forward(self, X, out=None):
+        """Y [rows, d_out] float32 for BF16 inputs X [rows, >= d_in] (row stride a multiple of 8)."""
+        import torch
+        rows = X.shape[0]
+        Y = out if out is not None else torch.empty((rows, self.dims[-1]), dtype=torch.float32, device=X.device)
+        _check(lib().cc_mlp_forward(self._h, _dev(X, torch.bfloat16, "X"), X.stride(0), rows,
+                                    _dev(Y, torch.float32, "Y", self.dims[-1]), Y.stride(0)))
+        return Y
+
+    def loss_grad(self, X, T, want_grad: bool = True):
+        """(mean squared error, gradient as a float32 CUDA tensor or None)."""
+        import torch
+        g = torch.empty(self.param_count, dtype=torch.float32, device=X.device) if want_grad else None
+        loss = ctypes.c_double()
+        _check(lib().cc_mlp_loss_grad(self._h, _dev(X, torch.bfloat16, "X"), X.stride(0),
+                                      _dev(T, torch.float32, "T", self.dims[-1]), T.stride(0), X.shape[0],
+                                      ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def adam_step(self, grad, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        _check(lib().cc_mlp_adam_step(self._h, grad.data_ptr(), ctypes.byref(Adam(lr, beta1, beta2, eps))))
+
+    def train(self, X, T, idx, batch: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8) -> np.ndarray:
+        """Steps over minibatches idx [steps, batch] (int32 CUDA tensor); returns the losses."""
+        import torch
+        steps = idx.shape[0]
+        if not (idx.is_cuda and idx.dtype == torch.int32 and idx.is_contiguous() and idx.shape[1] == batch):
+            raise CCError(ERR_INVALID_ARG, "idx must be a contiguous int32 CUDA tensor [steps, batch]")
+        losses = np.zeros(max(steps, 1))
+        _check(lib().cc_mlp_train(self._h, _dev(X, torch.bfloat16, "X"), X.stride(0),
+                                  _dev(T, torch.float32, "T", self.dims[-1]), T.stride(0), X.shape[0],
+                                  idx.data_ptr(), steps, batch, ctypes.byref(Adam(lr, beta1, beta2, eps)),
+                                  losses.ctypes.data))
+        return losses[:steps]
 
 
 def version() -> str:

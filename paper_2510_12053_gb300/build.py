@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-O3", "-I" + os.path.join(HERE, "..", "include")]
-SOURCES = ["api.cu", "mesh_build.cpp", "kernels_energy.cu", "kernels_sweep.cu", "kernels_setup.cu", "noalloc.cu", "mlp_gemm.cu"]
+SOURCES = ["api.cu", "mesh_build.cpp", "kernels_energy.cu", "kernels_sweep.cu", "kernels_setup.cu", "noalloc.cu", "mlp_gemm.cu", "mlp.cu"]
 
 
 def _nvcc() -> str:

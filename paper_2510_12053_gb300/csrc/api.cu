@@ -16,6 +16,8 @@ namespace ccg {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+bool error_empty() { return g_last_error.empty(); }
 
 void set_smem_limit(const void* kernel, size_t bytes) {
   static std::mutex mu;
@@ -28,6 +30,51 @@ void set_smem_limit(const void* kernel, size_t bytes) {
   if (have >= bytes) return;
   CCG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   have = bytes;
+}
+
+void drop_graph(Mesh& m) {
+  if (m.graph_exec) cudaGraphExecDestroy(m.graph_exec);
+  m.graph_exec = nullptr;
+  m.graph_key.clear();
+  for (cudaEvent_t e : m.prof.gpool) cudaEventDestroy(e);
+  m.prof.gpool.clear();
+  m.prof.gmark_cls.clear();
+  m.prof.gmark_begin.clear();
+  m.prof.gmark_end.clear();
+  m.prof.gmark_launches.clear();
+  m.prof.graph_launches = 0;
+}
+
+void ensure_state(Mesh& m, cc_precision p) {
+  cudaStream_t s = m.stream;
+  const size_t ne = 4 * (size_t)m.T;
+  if (p == CC_PREC_FP64) {
+    if (!m.f64.gcon.p) {
+      m.f64.gcon.alloc(3 * ne);
+      m.f64.hten.alloc(96 * (size_t)m.T);
+      m.f64.g.alloc(3 * m.n);
+      m.f64.bsr.alloc(12 * m.nnz_up);
+      m.f64.cpl.alloc(32 * m.n_free);
+      CCG_CUDA(cudaMemsetAsync(m.f64.g.p, 0, 3 * m.n * sizeof(double), s));
+    }
+  } else {
+    if (!m.mx.gcon.p) {
+      m.mx.gcon.alloc(3 * ne);
+      m.mx.hten.alloc(96 * (size_t)m.T);
+      m.mx.g_hi.alloc(3 * m.n);
+      m.mx.g_lo.alloc(3 * m.n);
+      m.mx.bsr.alloc(12 * m.nnz_up);
+      m.mx.cpl.alloc(32 * m.n_free);
+      m.mx.x_hi.alloc(m.n);
+      m.mx.x_lo.alloc(m.n);
+      m.mx.xt_hi.alloc(m.n);
+      m.mx.xt_lo.alloc(m.n);
+      CCG_CUDA(cudaMemsetAsync(m.mx.g_hi.p, 0, 3 * m.n * sizeof(float), s));
+      CCG_CUDA(cudaMemsetAsync(m.mx.g_lo.p, 0, 3 * m.n * sizeof(float), s));
+      CCG_CUDA(cudaMemsetAsync(m.mx.xt_hi.p, 0, m.n * sizeof(float4), s));
+      CCG_CUDA(cudaMemsetAsync(m.mx.xt_lo.p, 0, m.n * sizeof(float4), s));
+    }
+  }
 }
 
 namespace {
@@ -88,52 +135,8 @@ void prof_after_replay(Mesh& m) {
   }
 }
 
-void drop_graph(Mesh& m) {
-  if (m.graph_exec) cudaGraphExecDestroy(m.graph_exec);
-  m.graph_exec = nullptr;
-  m.graph_key.clear();
-  for (cudaEvent_t e : m.prof.gpool) cudaEventDestroy(e);
-  m.prof.gpool.clear();
-  m.prof.gmark_cls.clear();
-  m.prof.gmark_begin.clear();
-  m.prof.gmark_end.clear();
-  m.prof.gmark_launches.clear();
-  m.prof.graph_launches = 0;
-}
 
 double elastic_weight(const Mesh& m) { return m.h > 0.0 ? m.h * m.h : 1.0; }
-
-void ensure_state(Mesh& m, cc_precision p) {
-  cudaStream_t s = m.stream;
-  const size_t ne = 4 * (size_t)m.T;
-  if (p == CC_PREC_FP64) {
-    if (!m.f64.gcon.p) {
-      m.f64.gcon.alloc(3 * ne);
-      m.f64.hten.alloc(96 * (size_t)m.T);
-      m.f64.g.alloc(3 * m.n);
-      m.f64.bsr.alloc(12 * m.nnz_up);
-      m.f64.cpl.alloc(32 * m.n_free);
-      CCG_CUDA(cudaMemsetAsync(m.f64.g.p, 0, 3 * m.n * sizeof(double), s));
-    }
-  } else {
-    if (!m.mx.gcon.p) {
-      m.mx.gcon.alloc(3 * ne);
-      m.mx.hten.alloc(96 * (size_t)m.T);
-      m.mx.g_hi.alloc(3 * m.n);
-      m.mx.g_lo.alloc(3 * m.n);
-      m.mx.bsr.alloc(12 * m.nnz_up);
-      m.mx.cpl.alloc(32 * m.n_free);
-      m.mx.x_hi.alloc(m.n);
-      m.mx.x_lo.alloc(m.n);
-      m.mx.xt_hi.alloc(m.n);
-      m.mx.xt_lo.alloc(m.n);
-      CCG_CUDA(cudaMemsetAsync(m.mx.g_hi.p, 0, 3 * m.n * sizeof(float), s));
-      CCG_CUDA(cudaMemsetAsync(m.mx.g_lo.p, 0, 3 * m.n * sizeof(float), s));
-      CCG_CUDA(cudaMemsetAsync(m.mx.xt_hi.p, 0, m.n * sizeof(float4), s));
-      CCG_CUDA(cudaMemsetAsync(m.mx.xt_lo.p, 0, m.n * sizeof(float4), s));
-    }
-  }
-}
 
 // Re-evaluates the per-tet derivatives for a tet list and re-gathers g, H.
 void refresh(Mesh& m, cc_precision p, const double* x, const double* xt, const int32_t* list, int64_t count) {
@@ -307,22 +310,6 @@ using namespace ccg;
 
 struct cc_mesh : public ccg::Mesh {};
 
-#define CC_API_BODY(name, ...)                                   \
-  try {                                                           \
-    ccg::g_last_error.clear();                                    \
-    __VA_ARGS__;                                                  \
-    return CC_OK;                                                 \
-  } catch (const ccg::Fail& f) {                                  \
-    if (ccg::g_last_error.empty()) ccg::g_last_error = name;      \
-    return f.st;                                                  \
-  } catch (const std::bad_alloc&) {                               \
-    ccg::g_last_error = std::string(name) + ": host out of memory"; \
-    return CC_ERR_OOM;                                            \
-  } catch (...) {                                                 \
-    ccg::g_last_error = std::string(name) + ": unexpected error"; \
-    return CC_ERR_STATE;                                          \
-  }
-
 extern "C" {
 
 const char* cc_last_error(void) { return ccg::g_last_error.c_str(); }
@@ -364,6 +351,8 @@ cc_status cc_build_mesh(const double* X, int64_t n, const int32_t* tets, int64_t
     m->tet_mu.assign(T, m->mu);
     m->tet_lh.assign(T, m->lam_hat);
     m->tet_rho.assign(T, m->rho);
+    m->tet_E.assign(T, mat->E);
+    m->tet_nu.assign(T, mat->nu);
     ccg::build_topology(*m);
     CCG_CHECK(m->n_free > 0, CC_ERR_INVALID_ARG, "every vertex is pinned");
     m->d_red.alloc(4096);
@@ -408,6 +397,7 @@ void cc_destroy_mesh(cc_mesh* m) {
 cc_status cc_color(cc_mesh* m, int32_t* colors_out, int32_t* num_colors) {
   CC_API_BODY("cc_color", {
     CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    drop_graph(*m);
     ccg::run_coloring(*m);
     if (colors_out) std::memcpy(colors_out, m->color.data(), m->n * sizeof(int32_t));
     if (num_colors) *num_colors = m->num_colors;
@@ -420,6 +410,7 @@ cc_status cc_build_subspace(cc_mesh* m, int32_t k) {
     CCG_CHECK(k >= 1 && k <= 4, CC_ERR_INVALID_ARG, "k_ring must be in [1, 4]");
     CCG_CHECK(m->num_colors > 0, CC_ERR_STATE, "cc_color must run before cc_build_subspace");
     ensure_state(*m, CC_PREC_FP64);
+    drop_graph(*m);
     ccg::run_subspace_build(*m, k);
   })
 }
@@ -443,9 +434,9 @@ cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup
     }
     const int64_t total = sup_ptr[n];
     CCG_CHECK(total < (int64_t(1) << 31) && supmax < 32768, CC_ERR_INVALID_ARG, "support too large");
+    drop_graph(*m);
     m->sup_ptr.assign(sup_ptr, sup_ptr + n + 1);
     m->sup_idx.assign(sup_idx, sup_idx + total);
-    m->U.assign(U, U + 9 * total);
     m->sup_max = supmax;
     ccg::build_slot_maps(*m);
     int hs = 32;
@@ -456,10 +447,10 @@ cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup
     for (int64_t v = 0; v <= n; ++v) sp32[v] = (int32_t)sup_ptr[v];
     m->d_sup_ptr.upload(sp32, m->stream);
     m->d_sup_idx.upload(m->sup_idx, m->stream);
-    m->f64.U.upload(m->U, m->stream);
-    std::vector<float> u32(9 * std::max<int64_t>(total, 1), 0.f);
-    for (int64_t q = 0; q < 9 * total; ++q) u32[q] = (float)m->U[q];
-    m->mx.U.upload(u32, m->stream);
+    m->f64.U.alloc(9 * std::max<int64_t>(total, 1));
+    if (total) CCG_CUDA(cudaMemcpyAsync(m->f64.U.p, U, 9 * total * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    m->mx.U.alloc(9 * std::max<int64_t>(total, 1));
+    ccg::bases_to_f32(*m);
     CCG_CUDA(cudaStreamSynchronize(m->stream));
   })
 }
@@ -647,6 +638,8 @@ cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, co
     m->tet_mu.resize(T);
     m->tet_lh.resize(T);
     m->tet_rho.resize(T);
+    m->tet_E.resize(T);
+    m->tet_nu.resize(T);
     m->mesh_vptr.assign(count + 1, 0);
     m->mesh_tptr.assign(count + 1, 0);
     int64_t vo = 0, to = 0;
@@ -668,6 +661,8 @@ cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, co
         m->tet_mu[to + t] = mu;
         m->tet_lh[to + t] = lh;
         m->tet_rho[to + t] = d.mat.rho;
+        m->tet_E[to + t] = d.mat.E;
+        m->tet_nu[to + t] = d.mat.nu;
       }
       vo += d.n;
       to += d.T;
@@ -888,25 +883,6 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
   })
 }
 
-cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N, int32_t K,
-                          float* C, int64_t ldc, void* stream) {
-  CC_API_BODY("cc_gemm_bf16_tn", {
-    CCG_CHECK(A && B && C && ldc >= N, CC_ERR_INVALID_ARG, "bad GEMM arguments");
-    cudaStream_t s = (cudaStream_t)stream;
-    DBuf<int> err;
-    err.alloc(1);
-    CCG_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    GemmEpilogue ep;
-    ep.c32 = C;
-    ep.ldc = ldc;
-    gemm_tn(A, lda, B, ldb, M, N, K, kEpiF32, ep, err.p, s);
-    int h = 0;
-    CCG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CCG_CUDA(cudaStreamSynchronize(s));
-    CCG_CHECK(h == 0, CC_ERR_TIMEOUT, "a bounded wait in the GEMM kernel expired");
-  })
-}
-
 cc_status cc_get_info(const cc_mesh* m, cc_mesh_info* info) {
   CC_API_BODY("cc_get_info", {
     CCG_CHECK(m && info, CC_ERR_INVALID_ARG, "NULL argument");
@@ -944,9 +920,20 @@ cc_status cc_export(const cc_mesh* m, cc_array which, void* dst, int64_t cap, in
       case CC_ARR_SUP_IDX:
         CCG_CHECK(m->k_ring != 0, CC_ERR_STATE, "no subspace yet");
         src = m->sup_idx.data(); len = (int64_t)m->sup_idx.size(); esz = 4; break;
-      case CC_ARR_U:
+      case CC_ARR_U: {
         CCG_CHECK(m->k_ring != 0, CC_ERR_STATE, "no subspace yet");
-        src = m->U.data(); len = (int64_t)m->U.size(); esz = 8; break;
+        // the bases live on the device only
+        len = 9 * (int64_t)m->sup_idx.size();
+        if (count) *count = len;
+        if (dst) {
+          CCG_CHECK(cap >= len, CC_ERR_INVALID_ARG, "destination too small");
+          if (len) {
+            CCG_CUDA(cudaStreamSynchronize(m->stream));
+            CCG_CUDA(cudaMemcpy(dst, m->f64.U.p, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost));
+          }
+        }
+        return CC_OK;
+      }
       case CC_ARR_MASS: src = m->mass.data(); len = (int64_t)m->mass.size(); esz = 8; break;
       default: CCG_CHECK(false, CC_ERR_INVALID_ARG, "unknown array");
     }

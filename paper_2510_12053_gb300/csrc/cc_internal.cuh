@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -44,6 +45,24 @@ template <typename T>
 struct DBuf {
   T* p = nullptr;
   size_t count = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), count(o.count) {
+    o.p = nullptr;
+    o.count = 0;
+  }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      count = o.count;
+      o.p = nullptr;
+      o.count = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
   void alloc(size_t c) {
     release();
     if (c == 0) c = 1;
@@ -137,6 +156,7 @@ struct Mesh {
   int32_t max_rs = 0;          // most staged sources of one free row
   std::vector<double> mass;
   std::vector<double> tet_mu, tet_lh, tet_rho;   // per-tet material (a batch mixes materials)
+  std::vector<double> tet_E, tet_nu;             // the same as given (Young's modulus, Poisson ratio)
   // batches: mesh b owns vertices [mesh_vptr[b], mesh_vptr[b+1]) and tets [mesh_tptr[b], mesh_tptr[b+1])
   std::vector<int64_t> mesh_vptr, mesh_tptr;
   std::vector<int32_t> mesh_fptr;                // free rows of mesh b: [mesh_fptr[b], mesh_fptr[b+1])
@@ -149,7 +169,6 @@ struct Mesh {
   int32_t num_colors = 0;
   std::vector<int64_t> sup_ptr;
   std::vector<int32_t> sup_idx;
-  std::vector<double> U;       // [sup_total][9]
   int32_t k_ring = 0;
   int32_t sup_max = 0;
   int32_t hash_size = 0;       // unused (kept for layout stability)
@@ -256,5 +275,32 @@ void launch_velocity(const double* x, const double* xold, int64_t n, double h, d
 // colouring and subspace build
 void run_coloring(Mesh& m);
 void run_subspace_build(Mesh& m, int32_t k);
+void build_supports(Mesh& m, int32_t k);
+void rest_hessian_f64(Mesh& m);
+void patch_solves(Mesh& m, const int32_t* d_verts, int64_t count);
+void bases_to_f32(Mesh& m);
+// solver state of one precision (allocated once, on first use)
+void ensure_state(Mesh& m, cc_precision p);
+// forgets the captured sweep graph (its nodes hold buffer pointers)
+void drop_graph(Mesh& m);
+void clear_error();
+bool error_empty();
+
+// Body of a C entry point: runs the statements, maps exceptions to status codes.
+#define CC_API_BODY(name, ...)                                              \
+  try {                                                                      \
+    ::ccg::clear_error();                                                    \
+    __VA_ARGS__;                                                             \
+    return CC_OK;                                                            \
+  } catch (const ::ccg::Fail& f) {                                           \
+    if (::ccg::error_empty()) ::ccg::set_error(name);                        \
+    return f.st;                                                             \
+  } catch (const std::bad_alloc&) {                                          \
+    ::ccg::set_error(std::string(name) + ": host out of memory");            \
+    return CC_ERR_OOM;                                                       \
+  } catch (...) {                                                            \
+    ::ccg::set_error(std::string(name) + ": unexpected error");              \
+    return CC_ERR_STATE;                                                     \
+  }
 
 }  // namespace ccg

@@ -219,9 +219,9 @@ void run_coloring(Mesh& m) {
   CCG_CUDA(cudaStreamSynchronize(s));
 }
 
-// k-ring supports on the host (breadth-first over the 1-ring CSR), then the
-// rest Hessian and one dense Cholesky per patch on the GPU.
-void run_subspace_build(Mesh& m, int32_t k) {
+// k-ring supports on the host: breadth-first over the 1-ring CSR, free
+// vertices only, i excluded, ascending.  Uploads them and the slot maps.
+void build_supports(Mesh& m, int32_t k) {
   cudaStream_t s = m.stream;
   const int64_t n = m.n;
   m.sup_ptr.assign(n + 1, 0);
@@ -264,33 +264,44 @@ void run_subspace_build(Mesh& m, int32_t k) {
   for (int64_t v = 0; v <= n; ++v) sp32[v] = (int32_t)m.sup_ptr[v];
   m.d_sup_ptr.upload(sp32, s);
   m.d_sup_idx.upload(m.sup_idx, s);
-
-  // rest Hessian in float64 (dynamic meshes: M + h^2 K)
   const int64_t total = (int64_t)m.sup_idx.size();
-  DBuf<double> Xs;
-  {
-    std::vector<double> soa(3 * n);
-    for (int64_t j = 0; j < n; ++j)
-      for (int a = 0; a < 3; ++a) soa[a * n + j] = m.X[3 * j + a];
-    Xs.upload(soa, s);
-    const double w = m.h > 0.0 ? m.h * m.h : 1.0;
-    launch_tet_grad_f64(m, Xs.p, m.d_all_tets.p, m.n_active_tets, w, s);
-    launch_rows_f64(m, Xs.p, Xs.p, w, s);
-    CCG_CUDA(cudaStreamSynchronize(s));
-  }
   m.f64.U.alloc(9 * std::max<int64_t>(total, 1));
-  const int Nmax = 3 * std::max(supmax, 1);
+  m.mx.U.alloc(9 * std::max<int64_t>(total, 1));
+}
+
+// Rest Hessian of E in float64 into the float64 block rows (dynamic meshes:
+// M + h^2 K).  The float64 solver state must exist.
+void rest_hessian_f64(Mesh& m) {
+  cudaStream_t s = m.stream;
+  const int64_t n = m.n;
+  DBuf<double> Xs;
+  std::vector<double> soa(3 * n);
+  for (int64_t j = 0; j < n; ++j)
+    for (int a = 0; a < 3; ++a) soa[a * n + j] = m.X[3 * j + a];
+  Xs.upload(soa, s);
+  const double w = m.h > 0.0 ? m.h * m.h : 1.0;
+  launch_tet_grad_f64(m, Xs.p, m.d_all_tets.p, m.n_active_tets, w, s);
+  launch_rows_f64(m, Xs.p, Xs.p, w, s);
+  CCG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Dense patch solves (Eq. 5 on P = S_i) for a device list of free vertices,
+// written into the float64 bases.  Needs the rest Hessian in the block rows.
+void patch_solves(Mesh& m, const int32_t* d_verts, int64_t count) {
+  cudaStream_t s = m.stream;
+  if (count <= 0) return;
+  const int Nmax = 3 * std::max(m.sup_max, 1);
   const size_t per = (size_t)Nmax * Nmax + 3 * (size_t)Nmax;
   int64_t batch = std::max<int64_t>(1, (int64_t)((size_t(1) << 30) / (per * sizeof(double))));
-  batch = std::min<int64_t>(batch, m.n_free);
+  batch = std::min<int64_t>(batch, count);
   DBuf<double> scratch;
   scratch.alloc(per * std::max<int64_t>(batch, 1));
   DBuf<int32_t> fail;
   fail.alloc(1);
   CCG_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int32_t), s));
-  for (int64_t b0 = 0; b0 < m.n_free; b0 += batch) {
-    const int64_t cnt = std::min<int64_t>(batch, m.n_free - b0);
-    k_patch_basis<<<(unsigned)cnt, 256, 0, s>>>(m.d_free_rows.p + b0, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_up_ptr.p,
+  for (int64_t b0 = 0; b0 < count; b0 += batch) {
+    const int64_t cnt = std::min<int64_t>(batch, count - b0);
+    k_patch_basis<<<(unsigned)cnt, 256, 0, s>>>(d_verts + b0, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_up_ptr.p,
                                                  m.d_up_col.p, m.f64.bsr.p, Nmax, scratch.p, m.f64.U.p, fail.p);
     CCG_CUDA(cudaGetLastError());
   }
@@ -298,12 +309,30 @@ void run_subspace_build(Mesh& m, int32_t k) {
   CCG_CUDA(cudaMemcpyAsync(&nfail, fail.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CCG_CUDA(cudaStreamSynchronize(s));
   CCG_CHECK(nfail == 0, CC_ERR_NUMERIC, "a patch Hessian was not positive definite");
-  m.U.assign(9 * total, 0.0);
-  if (total) CCG_CUDA(cudaMemcpy(m.U.data(), m.f64.U.p, 9 * total * sizeof(double), cudaMemcpyDeviceToHost));
-  std::vector<float> u32(9 * std::max<int64_t>(total, 1), 0.f);
-  for (int64_t q = 0; q < 9 * total; ++q) u32[q] = (float)m.U[q];
-  m.mx.U.upload(u32, s);
-  CCG_CUDA(cudaStreamSynchronize(s));
+}
+
+namespace {
+__global__ void k_f64_to_f32(const double* __restrict__ a, int64_t count, float* __restrict__ b) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+    b[k] = (float)a[k];
+}
+}  // namespace
+
+// float32 copy of the float64 bases (used by the mixed-precision sweep).
+void bases_to_f32(Mesh& m) {
+  const int64_t count = 9 * (int64_t)m.sup_idx.size();
+  if (count == 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16);
+  k_f64_to_f32<<<grid, 256, 0, m.stream>>>(m.f64.U.p, count, m.mx.U.p);
+  CCG_CUDA(cudaGetLastError());
+}
+
+void run_subspace_build(Mesh& m, int32_t k) {
+  build_supports(m, k);
+  rest_hessian_f64(m);
+  patch_solves(m, m.d_free_rows.p, m.n_free);
+  bases_to_f32(m);
+  CCG_CUDA(cudaStreamSynchronize(m.stream));
 }
 
 }  // namespace ccg

@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -120,7 +121,7 @@ __device__ __forceinline__ float gelu_grad(float z) {
 template <int BN, int EPI>
 __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtensorMap mapA,
                                                  const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
-                                                 GemmEpilogue ep, int* __restrict__ err) {
+                                                 int kt_per_split, GemmEpilogue ep, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment of the tile ring (128-byte swizzle atoms)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -140,7 +141,10 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int ktiles = (K + kBK - 1) / kBK;
+  // this split's K tiles: [kt0, kt0 + ktiles)
+  const int kt_all = (K + kBK - 1) / kBK;
+  const int kt0 = blockIdx.z * kt_per_split;
+  const int ktiles = max(0, min(kt_all - kt0, kt_per_split));
 
   if (threadIdx.x == 0) {
     failed = 0;
@@ -166,8 +170,8 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
     // prologue: fill the ring
     for (int s = 0; s < kStages && s < ktiles; ++s) {
       mbar_expect_tx(&bar_full[s], kABytes + kBBytes);
-      tma_load_2d(tileA[s], &mapA, &bar_full[s], s * kBK, m0);
-      tma_load_2d(tileB[s], &mapB, &bar_full[s], s * kBK, n0);
+      tma_load_2d(tileA[s], &mapA, &bar_full[s], (kt0 + s) * kBK, m0);
+      tma_load_2d(tileB[s], &mapB, &bar_full[s], (kt0 + s) * kBK, n0);
     }
     for (int kt = 0; kt < ktiles; ++kt) {
       const int s = kt % kStages;
@@ -190,8 +194,8 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
           break;
         }
         mbar_expect_tx(&bar_full[s], kABytes + kBBytes);
-        tma_load_2d(tileA[s], &mapA, &bar_full[s], nk * kBK, m0);
-        tma_load_2d(tileB[s], &mapB, &bar_full[s], nk * kBK, n0);
+        tma_load_2d(tileA[s], &mapA, &bar_full[s], (kt0 + nk) * kBK, m0);
+        tma_load_2d(tileB[s], &mapB, &bar_full[s], (kt0 + nk) * kBK, n0);
       }
     }
   }
@@ -209,33 +213,68 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
   if (ok) {
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    float* c32 = ep.c32;
+    if (EPI == kEpiF32 && c32) c32 += (int64_t)blockIdx.z * ep.split_stride;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tmem_ld16(lane_base + c, v);
       if (row >= M) continue;
+      const int col0 = n0 + c;
+      if (col0 >= N) continue;
+      const bool full = col0 + 16 <= N;
+      if (EPI == kEpiF32 || EPI == kEpiBiasF32) {
+        if (EPI == kEpiBiasF32) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int col = n0 + c + k;
-        if (col >= N) continue;
-        float z = v[k];
-        if (EPI == kEpiF32) {
-          ep.c32[(int64_t)row * ep.ldc + col] = z;
-        } else if (EPI == kEpiBiasF32) {
-          ep.c32[(int64_t)row * ep.ldc + col] = z + ep.bias[col];
-        } else if (EPI == kEpiBiasGelu) {
-          z += ep.bias[col];
-          const __nv_bfloat16 zb = __float2bfloat16_rn(z);
-          const __nv_bfloat16 hb = __float2bfloat16_rn(gelu(__bfloat162float(zb)));
-          ep.z16[(int64_t)row * ep.ldz + col] = zb;
-          ep.h16[(int64_t)row * ep.ldh + col] = hb;
-          if (ep.ht16) ep.ht16[(int64_t)col * ep.ldt + row] = hb;
-        } else {  // kEpiGeluGrad: dZ = C * gelu'(Z)
-          const float zz = __bfloat162float(ep.z16[(int64_t)row * ep.ldz + col]);
-          const __nv_bfloat16 gb = __float2bfloat16_rn(z * gelu_grad(zz));
-          ep.h16[(int64_t)row * ep.ldh + col] = gb;
-          if (ep.ht16) ep.ht16[(int64_t)col * ep.ldt + row] = gb;
+          for (int k = 0; k < 16; ++k) v[k] += (col0 + k < N) ? ep.bias[col0 + k] : 0.0f;
         }
+        float* dst = c32 + (int64_t)row * ep.ldc + col0;
+        if (full && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+          for (int k = 0; k < 16; k += 4) *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+        } else {
+          for (int k = 0; k < 16 && col0 + k < N; ++k) dst[k] = v[k];
+        }
+        continue;
+      }
+      __nv_bfloat16 hb[16];
+      if (EPI == kEpiBiasGelu) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float z = v[k] + ((col0 + k < N) ? ep.bias[col0 + k] : 0.0f);
+          v[k] = z;
+          hb[k] = __float2bfloat16_rn(gelu(z));
+        }
+        if (ep.z32) {  // pre-activations are kept for training only
+          float* zdst = ep.z32 + (int64_t)row * ep.ldz + col0;
+          if (full && ((reinterpret_cast<uintptr_t>(zdst) & 15) == 0)) {
+#pragma unroll
+            for (int k = 0; k < 16; k += 4)
+              *reinterpret_cast<float4*>(zdst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+          } else {
+            for (int k = 0; k < 16 && col0 + k < N; ++k) zdst[k] = v[k];
+          }
+        }
+      } else {  // kEpiGeluGrad: dZ = C * gelu'(Z)
+        const float* zsrc = ep.z32 + (int64_t)row * ep.ldz + col0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float z = (col0 + k < N) ? zsrc[k] : 0.0f;
+          hb[k] = __float2bfloat16_rn(v[k] * gelu_grad(z));
+        }
+      }
+      __nv_bfloat16* hdst = ep.h16 + (int64_t)row * ep.ldh + col0;
+      if (full && ((reinterpret_cast<uintptr_t>(hdst) & 15) == 0)) {
+        uint4 w[2];
+        memcpy(w, hb, sizeof(w));
+        reinterpret_cast<uint4*>(hdst)[0] = w[0];
+        reinterpret_cast<uint4*>(hdst)[1] = w[1];
+      } else {
+        for (int k = 0; k < 16 && col0 + k < N; ++k) hdst[k] = hb[k];
+      }
+      if (ep.ht16) {
+        // transposed copy: consecutive lanes write consecutive rows
+        for (int k = 0; k < 16 && col0 + k < N; ++k) ep.ht16[(int64_t)(col0 + k) * ep.ldt + row] = hb[k];
       }
     }
   }
@@ -283,46 +322,75 @@ CUtensorMap make_map(const void* ptr, int64_t rows, int64_t cols, int64_t ld, in
 }
 
 template <int BN, int EPI>
-void launch_bn(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, const GemmEpilogue& ep, int* err,
-               cudaStream_t s) {
+void launch_bn(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int splits, const GemmEpilogue& ep,
+               int* err, cudaStream_t s) {
   const size_t smem = (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
   auto kern = k_gemm_tn<BN, EPI>;
   set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-  const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN));
-  kern<<<grid, 128, smem, s>>>(a, b, M, N, K, ep, err);
+  const int kt_all = (K + kBK - 1) / kBK;
+  const int per = (kt_all + splits - 1) / splits;
+  const int z = (kt_all + per - 1) / per;  // every split gets at least one K tile
+  const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN), (unsigned)z);
+  kern<<<grid, 128, smem, s>>>(a, b, M, N, K, per, ep, err);
   CCG_CUDA(cudaGetLastError());
 }
 
 template <int EPI>
-void launch_epi(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, int bn,
+void launch_epi(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, GemmShape sh,
                 const GemmEpilogue& ep, int* err, cudaStream_t s) {
   const CUtensorMap ma = make_map(A, M, K, lda, kBM);
-  switch (bn) {
-    case 64: launch_bn<64, EPI>(ma, make_map(B, N, K, ldb, 64), M, N, K, ep, err, s); break;
-    case 128: launch_bn<128, EPI>(ma, make_map(B, N, K, ldb, 128), M, N, K, ep, err, s); break;
-    case 192: launch_bn<192, EPI>(ma, make_map(B, N, K, ldb, 192), M, N, K, ep, err, s); break;
-    default: launch_bn<256, EPI>(ma, make_map(B, N, K, ldb, 256), M, N, K, ep, err, s); break;
+  switch (sh.bn) {
+    case 64: launch_bn<64, EPI>(ma, make_map(B, N, K, ldb, 64), M, N, K, sh.splits, ep, err, s); break;
+    case 128: launch_bn<128, EPI>(ma, make_map(B, N, K, ldb, 128), M, N, K, sh.splits, ep, err, s); break;
+    case 192: launch_bn<192, EPI>(ma, make_map(B, N, K, ldb, 192), M, N, K, sh.splits, ep, err, s); break;
+    default: launch_bn<256, EPI>(ma, make_map(B, N, K, ldb, 256), M, N, K, sh.splits, ep, err, s); break;
   }
 }
 
 }  // namespace
 
-int gemm_pick_bn(int N) {
-  if (N % 256 == 0) return 256;
-  if (N % 192 == 0) return 192;
-  if (N % 128 == 0) return 128;
-  return 64;
+GemmShape gemm_pick_shape(int M, int N, int K, bool allow_split) {
+  constexpr int kSlots = 2 * 152;  // about two resident CTAs per SM
+  GemmShape sh;
+  const int mt = (M + kBM - 1) / kBM;
+  const int cands[4] = {256, 192, 128, 64};
+  sh.bn = 64;
+  for (int bn : cands) {
+    if (N % bn != 0 && bn != 64) continue;
+    if ((int64_t)mt * ((N + bn - 1) / bn) >= kSlots || allow_split) {
+      sh.bn = bn;
+      break;
+    }
+  }
+  if (allow_split) {
+    const int tiles = mt * ((N + sh.bn - 1) / sh.bn);
+    const int kt = (K + kBK - 1) / kBK;
+    const int want = (kSlots + tiles - 1) / tiles;
+    sh.splits = std::max(1, std::min(want, kt / 4));
+  }
+  return sh;
 }
 
 void gemm_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, int epi,
-             const GemmEpilogue& ep, int* err, cudaStream_t s) {
+             const GemmEpilogue& ep, int* err, cudaStream_t s, GemmShape sh) {
   CCG_CHECK(M > 0 && N > 0 && K > 0, CC_ERR_INVALID_ARG, "GEMM sizes must be positive");
-  const int bn = gemm_pick_bn(N);
+  CCG_CHECK(sh.bn == 64 || sh.bn == 128 || sh.bn == 192 || sh.bn == 256, CC_ERR_INVALID_ARG, "bad GEMM N tile");
+  CCG_CHECK(sh.splits >= 1 && (sh.splits == 1 || epi == kEpiF32), CC_ERR_INVALID_ARG,
+            "split K needs the float32 epilogue");
+  // every buffer an epilogue writes or reads must be present
+  const bool f32 = epi == kEpiF32 || epi == kEpiBiasF32;
+  CCG_CHECK(!f32 || (ep.c32 && ep.ldc >= N), CC_ERR_INVALID_ARG, "GEMM epilogue: missing float32 output");
+  CCG_CHECK(!(epi == kEpiBiasF32 || epi == kEpiBiasGelu) || ep.bias, CC_ERR_INVALID_ARG, "GEMM epilogue: missing bias");
+  CCG_CHECK(f32 || (ep.h16 && ep.ldh >= N), CC_ERR_INVALID_ARG, "GEMM epilogue: missing BF16 output");
+  CCG_CHECK(epi != kEpiGeluGrad || (ep.z32 && ep.ldz >= N), CC_ERR_INVALID_ARG,
+            "GEMM epilogue: missing pre-activations");
+  CCG_CHECK(!ep.z32 || ep.ldz >= N, CC_ERR_INVALID_ARG, "GEMM epilogue: bad pre-activation stride");
+  CCG_CHECK(!ep.ht16 || ep.ldt >= M, CC_ERR_INVALID_ARG, "GEMM epilogue: transposed copy too narrow");
   switch (epi) {
-    case kEpiF32: launch_epi<kEpiF32>(A, lda, B, ldb, M, N, K, bn, ep, err, s); break;
-    case kEpiBiasF32: launch_epi<kEpiBiasF32>(A, lda, B, ldb, M, N, K, bn, ep, err, s); break;
-    case kEpiBiasGelu: launch_epi<kEpiBiasGelu>(A, lda, B, ldb, M, N, K, bn, ep, err, s); break;
-    default: launch_epi<kEpiGeluGrad>(A, lda, B, ldb, M, N, K, bn, ep, err, s); break;
+    case kEpiF32: launch_epi<kEpiF32>(A, lda, B, ldb, M, N, K, sh, ep, err, s); break;
+    case kEpiBiasF32: launch_epi<kEpiBiasF32>(A, lda, B, ldb, M, N, K, sh, ep, err, s); break;
+    case kEpiBiasGelu: launch_epi<kEpiBiasGelu>(A, lda, B, ldb, M, N, K, sh, ep, err, s); break;
+    default: launch_epi<kEpiGeluGrad>(A, lda, B, ldb, M, N, K, sh, ep, err, s); break;
   }
 }
 

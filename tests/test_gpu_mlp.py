@@ -1,33 +1,298 @@
-"""Learned-subspace MLP on the GPU: the tcgen05 BF16 GEMM against an exact
-product of the same BF16 inputs, and (below) the network's gradients against
-the FP64 oracle."""
+"""Learned-subspace network and bases on the GPU against the FP64 oracle.
+
+* the tcgen05 BF16 GEMM against an exact product of the same BF16 inputs
+  (every N tile, split K);
+* forward pass, loss and gradients against ``oracle.mlp`` evaluated with the
+  same BF16 rounding points.  The GPU accumulates in float32 and rounds to
+  BF16 where the oracle rounds a float64 value, so a handful of stored BF16
+  values differ by one unit in the last place; the tolerances below (1e-3
+  relative per tensor) bound that effect;
+* Adam against the oracle's update on the same gradient;
+* network inputs (bit for bit, the two material channels within one BF16
+  step), targets, Eq. 5 residuals and the fallback set against
+  ``oracle.learned``;
+* a trained network against the method without it.
+"""
 import numpy as np
 import pytest
 
 import meshgen
+from oracle import fem, learned, mlp, solvers, subspace, topology
 
 torch = pytest.importorskip("torch")
 import paper_2510_12053_gb300 as cc  # noqa: E402
+from paper_2510_12053_gb300 import learned as cclearn  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 
-def _bf16(rows, cols, seed, ld=None):
-    a = meshgen.normal(seed, np.arange(rows * cols)).reshape(rows, cols).astype(np.float32)
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _bf16(rows, cols, seed, ld=None, scale=1.0):
+    """(CUDA bf16 tensor [rows, ld], float64 numpy of its first cols columns)."""
+    a = (scale * meshgen.normal(seed, np.arange(rows * cols))).reshape(rows, cols).astype(np.float32)
     t = torch.zeros((rows, ld or cols), dtype=torch.bfloat16)
     t[:, :cols] = torch.from_numpy(a).to(torch.bfloat16)
-    return t
+    return t.cuda(), t[:, :cols].double().numpy()
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (300, 256, 320), (1000, 576, 256), (257, 192, 200),
-                                   (8192, 256, 576), (64, 128, 1000)])
-def test_gemm_bf16_matches_exact_product(M, N, K):
-    assert torch.cuda.is_available()
+# ---------------------------------------------------------------- GEMM
+@pytest.mark.parametrize("M,N,K,tile,splits", [
+    (128, 64, 64, 0, 0), (300, 256, 320, 0, 0), (1000, 576, 256, 0, 0), (257, 192, 200, 0, 0),
+    (8192, 256, 576, 0, 0), (64, 128, 1000, 0, 0), (300, 256, 320, 64, 0), (300, 256, 320, 128, 0),
+    (576, 256, 8192, 0, 16), (256, 258, 1000, 64, 5), (256, 256, 4096, 128, 64)])
+def test_gemm_bf16_matches_exact_product(M, N, K, tile, splits):
     ld = (K + 7) // 8 * 8
-    A = _bf16(M, K, 1 + M, ld)
-    B = _bf16(N, K, 2 + N, ld)
-    C = cc.gemm_bf16_tn(A.cuda()[:, :K], B.cuda()[:, :K])
+    A, An = _bf16(M, K, 1 + M, ld)
+    B, Bn = _bf16(N, K, 2 + N, ld)
+    C = cc.gemm_bf16_tn(A[:, :K], B[:, :K], n_tile=tile, k_splits=splits)
     torch.cuda.synchronize()
-    ref = A[:, :K].double() @ B[:, :K].double().T
-    err = (C.cpu().double() - ref).abs().max().item()
-    assert err <= 1e-5 * ref.abs().max().item() + 1e-6, err
+    ref = An @ Bn.T
+    err = np.abs(C.cpu().double().numpy() - ref).max()
+    assert err <= 1e-5 * np.abs(ref).max() + 1e-6, err
+
+
+# ---------------------------------------------------------------- network
+def _net(dims, max_batch, seed):
+    net = cc.MLP(dims[0], dims[1], len(dims) - 2, dims[-1], max_batch=max_batch)
+    p = meshgen.mlp_init(dims, seed, out_scale=1.0)
+    p += (0.05 * meshgen.normal(seed + 7, np.arange(p.size))).astype(np.float32) * _bias_mask(dims)
+    net.set_params(p)
+    return net, p.astype(np.float64)
+
+
+def _bias_mask(dims):
+    m = np.zeros(meshgen.mlp_param_count(dims), dtype=np.float32)
+    for _, sb in mlp.layer_slices(dims):
+        m[sb] = 1.0
+    return m
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+DIMS = [meshgen.mlp_dims(), [30, 40, 40, 24], [258, 64, 16]]
+
+
+@pytest.mark.parametrize("dims", DIMS, ids=["full", "small", "one-hidden"])
+def test_forward_matches_oracle(dims):
+    rows = 1000
+    net, p = _net(dims, 64, 3)
+    X, Xn = _bf16(rows, dims[0], 11, (dims[0] + 7) // 8 * 8)
+    Y = net.forward(X).cpu().double().numpy()
+    Yo, _ = mlp.forward(p, dims, Xn, rounding=True)
+    assert _rel(Y, Yo) <= 1e-3
+    assert np.abs(Y - Yo).max() <= 1e-2 * np.abs(Yo).max()
+
+
+@pytest.mark.parametrize("dims,B", [(DIMS[0], 1000), (DIMS[0], 4096), (DIMS[1], 77), (DIMS[2], 333)],
+                         ids=["full-1000", "full-4096", "small-77", "one-hidden-333"])
+def test_loss_and_gradient_match_oracle(dims, B):
+    net, p = _net(dims, B, 5)
+    X, Xn = _bf16(B, dims[0], 13, (dims[0] + 7) // 8 * 8)
+    Tn = (0.3 * meshgen.normal(17, np.arange(B * dims[-1]))).reshape(B, dims[-1]).astype(np.float32)
+    loss, g = net.loss_grad(X, torch.from_numpy(Tn).cuda())
+    g = g.cpu().double().numpy()
+    lo, go = mlp.loss_and_grad(p, dims, Xn, Tn.astype(np.float64), rounding=True)
+    assert abs(loss - lo) <= 1e-5 * lo
+    for l, (sw, sb) in enumerate(mlp.layer_slices(dims)):
+        assert _rel(g[sw], go[sw]) <= 1e-3, (l, "W", _rel(g[sw], go[sw]))
+        assert _rel(g[sb], go[sb]) <= 1e-3, (l, "b", _rel(g[sb], go[sb]))
+
+
+def test_adam_step_matches_oracle():
+    dims = DIMS[1]
+    net, p = _net(dims, 16, 9)
+    m = v = np.zeros_like(p)
+    for t in range(1, 4):
+        g = (meshgen.normal(40 + t, np.arange(p.size)) * 10.0 ** (-t)).astype(np.float32)
+        net.adam_step(torch.from_numpy(g).cuda(), lr=1e-2)
+        p, m, v = mlp.adam_step(p, g.astype(np.float64), m, v, t, 1e-2)
+        np.testing.assert_allclose(net.get_params(), p, rtol=0, atol=1e-6)
+
+
+def test_training_losses_follow_the_oracle():
+    dims = DIMS[1]
+    n, B, steps, lr = 96, 32, 5, 1e-3
+    net, p = _net(dims, B, 21)
+    X, Xn = _bf16(n, dims[0], 23, 32)
+    Tn = (0.3 * meshgen.normal(29, np.arange(n * dims[-1]))).reshape(n, dims[-1]).astype(np.float32)
+    idx = meshgen.batch_indices(31, 0, steps, B, n)
+    losses = net.train(X, torch.from_numpy(Tn).cuda(), torch.from_numpy(idx).cuda(), B, lr=lr)
+    m = v = np.zeros_like(p)
+    for t in range(steps):
+        lo, go = mlp.loss_and_grad(p, dims, Xn[idx[t]], Tn[idx[t]].astype(np.float64), rounding=True)
+        assert abs(losses[t] - lo) <= 1e-3 * lo, (t, losses[t], lo)
+        p, m, v = mlp.adam_step(p, go, m, v, t + 1, lr)
+
+
+def test_training_reduces_the_loss():
+    dims = [30, 64, 64, 24]
+    n, B = 4096, 512
+    teacher, _ = _net(dims, 8, 77)
+    X, _ = _bf16(n, dims[0], 41, 32)
+    T = teacher.forward(X)
+    net, _ = _net(dims, B, 78)
+    idx = torch.from_numpy(meshgen.batch_indices(43, 0, 400, B, n)).cuda()
+    losses = net.train(X, T, idx, B, lr=3e-3)
+    assert np.all(np.isfinite(losses))
+    assert losses[-20:].mean() < 0.2 * losses[:5].mean()
+
+
+# ---------------------------------------------------------------- inputs and targets
+def _train_scenes(count, seed, lo=4, hi=7):
+    return meshgen.training_boxes(count, seed, side_lo=lo, side_hi=hi)
+
+
+@pytest.mark.parametrize("which", ["single", "union"])
+def test_learned_inputs_and_targets_match_oracle(which):
+    scenes = _train_scenes(3, 5) if which == "union" else [meshgen.stretch_box(5, 4, 4, E=3e5, nu=0.33,
+                                                                               jitter_amount=0.05, seed=6)]
+    m = cc.Mesh.from_scenes(scenes) if which == "union" else cc.Mesh.from_scene(scenes[0])
+    m.color()
+    m.build_subspace(2)
+    X, T = m.learned_inputs(targets=True)
+    X = X.cpu()[:, :learned.D_IN + 6].double().numpy()
+    T = T.cpu().double().numpy()
+    r0 = 0
+    for sc in scenes:
+        pb = fem.problem_from_scene(sc)
+        topo = topology.Topology(pb.n, pb.tets, pb.free)
+        rows, _, Fb = learned.features(pb, topo)
+        sup, bases = subspace.build_local_bases(pb, topo, 2)
+        To = learned.targets(pb, topo, sup, bases)
+        nr = len(rows)
+        Xg, Tg = X[r0:r0 + nr], T[r0:r0 + nr]
+        np.testing.assert_array_equal(Xg[:, :256], Fb[:, :256])
+        assert np.all(Xg[:, 258:] == 0.0)
+        np.testing.assert_allclose(Xg[:, 256:258], Fb[:, 256:258], rtol=2.0 ** -7, atol=0)
+        np.testing.assert_allclose(Tg, To, rtol=0, atol=1e-6 * max(1.0, np.abs(To).max()))
+        np.testing.assert_array_equal(Tg == 0.0, To == 0.0)
+        r0 += nr
+    assert r0 == X.shape[0]
+
+
+def test_inputs_reject_a_mesh_off_the_lattice():
+    sc = meshgen.stretch_box(4, 4, 4, E=1e5, nu=0.3, jitter_amount=0.0)
+    X = sc.X.copy()
+    X[:, 0] *= 2.7        # cells 2.7 times longer in x: offsets leave the stencil
+    m = cc.Mesh(X, sc.tets, sc.pinned, E=1e5, nu=0.3)
+    m.color()
+    with pytest.raises(cc.CCError) as e:
+        m.learned_inputs()
+    assert e.value.status == cc.ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- residuals and fallback
+def _constant_net(pattern_seed=3):
+    """A network whose output is its last bias (all weights zero): every
+    vertex receives the same 64 blocks, exactly representable on both sides."""
+    dims = meshgen.mlp_dims()
+    p = np.zeros(meshgen.mlp_param_count(dims), dtype=np.float32)
+    b = np.zeros(576, dtype=np.float32)
+    st = learned.stencil()
+    for s in range(64):
+        c = 0.45 if s < 14 else 0.12
+        blk = c * np.eye(3) + 0.02 * meshgen.normal(pattern_seed, np.arange(9 * s, 9 * s + 9)).reshape(3, 3)
+        b[9 * s:9 * s + 9] = blk.ravel()
+    p[mlp.layer_slices(dims)[-1][1]] = b
+    net = cc.MLP(max_batch=256)
+    net.set_params(p)
+    return net, b.astype(np.float64)
+
+
+def test_learned_bases_residuals_and_fallback_match_oracle():
+    sc = meshgen.stretch_box(5, 4, 4, E=1e5, nu=0.3, factor=1.2, jitter_amount=0.05, seed=8)
+    net, b = _constant_net()
+    m = cc.Mesh.from_scene(sc)
+    m.color()
+    stats, rho = m.build_learned_subspace(net, tau=1.0, want_rho=True)
+    rho = rho.cpu().numpy()
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    rows = np.flatnonzero(pb.free)
+    sup, lb = learned.assemble(pb, topo, np.tile(b, (len(rows), 1)))
+    out, F, rho_o = learned.with_fallback(pb, sup, lb, tau=1.0)
+    np.testing.assert_allclose(rho, rho_o[rows], rtol=1e-10, atol=1e-14)
+    near = np.abs(rho_o - 1.0) <= 1e-9
+    Fg = {int(rows[r]) for r in range(len(rows)) if len(sup[rows[r]]) and rho[r] >= 1.0}
+    assert {int(i) for i in F if not near[i]} == {i for i in Fg if not near[i]}
+    assert stats["n_fallback"] == len(Fg) and 0 < len(Fg) < len(rows)
+    sp, si, Ug = m.export("sup_ptr"), m.export("sup_idx"), m.export("U").reshape(-1, 3, 3)
+    for i in rows:
+        np.testing.assert_array_equal(si[sp[i]:sp[i + 1]], sup[i])
+        if len(sup[i]):
+            np.testing.assert_allclose(Ug[sp[i]:sp[i + 1]], out[i], rtol=0,
+                                       atol=1e-10 * max(1.0, np.abs(out[i]).max()))
+
+
+def test_learned_subspace_rejects_dynamic_meshes_and_wrong_networks():
+    sc = meshgen.cantilever(2, 2, 4, cell=0.25, E=1e5, nu=0.3, h=0.01)
+    m = cc.Mesh.from_scene(sc)
+    m.color()
+    net, _ = _constant_net()
+    with pytest.raises(cc.CCError):
+        m.build_learned_subspace(net)
+    sq = cc.Mesh.from_scene(meshgen.stretch_box(3, 3, 3, E=1e5, nu=0.3))
+    sq.color()
+    with pytest.raises(cc.CCError):
+        sq.build_learned_subspace(cc.MLP(30, 16, 1, 24, max_batch=8))
+
+
+# ---------------------------------------------------------------- what the network gains
+def _indices(seed):
+    return lambda s0, cnt, batch, n: meshgen.batch_indices(seed, s0, cnt, batch, n)
+
+
+def test_trained_network_gains_over_the_method_without_it():
+    """Train on computed bases of 120 jittered boxes, evaluate on a held-out
+    stretch box: the learned bases keep most vertices off the patch solve,
+    converge like the computed ones (and like the oracle's curve), and far
+    faster than coordinate descent, the method without any subspace."""
+    scenes = _train_scenes(120, 2024, 4, 8)
+    X, T, _ = cclearn.training_set(scenes)
+    net = cc.MLP(max_batch=2048)
+    net.set_params(meshgen.mlp_init(meshgen.mlp_dims(), 1))
+    untrained = cc.MLP(max_batch=256)
+    untrained.set_params(meshgen.mlp_init(meshgen.mlp_dims(), 1))
+    losses, secs = cclearn.train(net, X, T, _indices(7), steps=3000, batch=2048, lr=1e-3)
+    assert losses[-50:].mean() < 0.05 * losses[:10].mean()
+
+    sc = meshgen.stretch_box(6, 6, 6, E=1e6, nu=0.3, factor=1.3, jitter_amount=0.05, seed=99)
+    xs = cc.to_soa(sc.x0)
+
+    def run(kind):
+        m = cc.Mesh.from_scene(sc)
+        m.color()
+        st = None
+        if kind == "learned":
+            st, _ = m.build_learned_subspace(net)
+        elif kind == "untrained":
+            st, _ = m.build_learned_subspace(untrained)
+        elif kind == "computed":
+            m.build_subspace(2)
+        x = xs.clone()
+        r = m.solve_step(x, update="cd" if kind == "cd" else "cc", precision="mixed", tol=1e-6, max_iters=400,
+                         history=True)
+        return r, st
+
+    rL, sL = run("learned")
+    rU, sU = run("untrained")
+    rC, _ = run("computed")
+    rD, _ = run("cd")
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, bases = subspace.build_local_bases(pb, topo, 2)
+    _, hist = solvers.solve(pb, topo, sup, bases, sc.x0, kind="cc", tol=1e-6, max_iters=200)
+    print(f"\nlearned: {rL.iterations} sweeps, fallback {sL['n_fallback']}/{sL['n_free']}; untrained fallback "
+          f"{sU['n_fallback']}; computed {rC.iterations}; oracle computed {hist.iterations}; "
+          f"cd {rD.iterations} (converged {rD.converged}); training {secs:.2f}s")
+    assert rL.converged and rC.converged and hist.converged
+    assert sL["n_fallback"] <= 0.25 * sL["n_free"]          # most patch solves avoided
+    assert sU["n_fallback"] >= 2 * max(sL["n_fallback"], 1)  # training is what avoids them
+    assert rL.iterations <= 1.5 * hist.iterations + 2        # near the oracle's computed-basis curve
+    assert (not rD.converged) or rD.iterations >= 2 * rL.iterations
