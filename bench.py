@@ -84,6 +84,11 @@ def parse():
     p.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of CUDA graphs")
     p.add_argument("--no-batch", action="store_true", help="skip the 256-mesh batched solve")
     p.add_argument("--batch-count", type=int, default=256)
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-basis workload")
+    p.add_argument("--train-meshes", type=int, default=2000)
+    p.add_argument("--train-steps", type=int, default=4000)
+    p.add_argument("--train-batch", type=int, default=8192)
+    p.add_argument("--learned-max-iters", type=int, default=2000, help="sweep cap of the 48^3 solves")
     return p.parse_args()
 
 
@@ -324,6 +329,152 @@ def run_batch(args, stream, dev):
     return out
 
 
+def mlp_flops(dims, rows, backward=False):
+    """Algorithmic GEMM FLOPs of the network over ``rows`` rows: 2 rows N K
+    per layer forward; backward adds the weight gradients (2 rows N K per
+    layer) and the input gradients of every layer but the first."""
+    nk = [dims[l + 1] * dims[l] for l in range(len(dims) - 1)]
+    f = 2.0 * rows * sum(nk)
+    if backward:
+        f += 2.0 * rows * sum(nk) + 2.0 * rows * sum(nk[1:])
+    return f
+
+
+def run_learned(args, stream, dev):
+    """Learned bases (configuration 5): train the network on computed 2-ring
+    bases of jittered random boxes (sides U{4..12}, batch-family materials and
+    boundary conditions, seed 0; the last 10% held out), then solve the
+    48x48x48-cell stretch cube (E = 1e6, jitter 5%) with learned bases (with
+    the per-vertex fallback), with computed bases, in plain float64 with
+    computed bases, and with coordinate descent.  Wall time = basis
+    acquisition + solve."""
+    import torch
+    import meshgen
+    import paper_2510_12053_gb300 as cc
+    from paper_2510_12053_gb300 import learned as cl
+    peaks, peak_src = measured_peaks()
+    dims = meshgen.mlp_dims()
+    out = {"network": {"dims": dims, "params": meshgen.mlp_param_count(dims), "activation": "GELU (erf)",
+                       "storage": "BF16 weights/activations, float32 accumulation and master weights"}}
+    boxes = meshgen.training_boxes(args.train_meshes, seed=0, side_lo=4, side_hi=12)
+    n_hold = max(1, len(boxes) // 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, T, counts = cl.training_set(boxes, stream=stream)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n_train = int(counts[:-n_hold].sum())
+    Xtr, Ttr, Xho, Tho = X[:n_train], T[:n_train], X[n_train:], T[n_train:]
+    net = cc.MLP(max_batch=args.train_batch, stream=stream)
+    net.set_params(meshgen.mlp_init(dims, 1))
+    ho0 = cl.evaluate(net, Xho, Tho)
+    losses, train_s = cl.train(net, Xtr, Ttr, lambda s0, c, b, n: meshgen.batch_indices(17, s0, c, b, n),
+                               steps=args.train_steps, batch=args.train_batch, lr=2e-3, lr_final=2e-5)
+    ho1 = cl.evaluate(net, Xho, Tho)
+    tr_flops = mlp_flops(dims, args.train_batch, backward=True) * args.train_steps
+    out["training"] = {"meshes": len(boxes) - n_hold, "held_out_meshes": n_hold, "samples": n_train,
+                       "held_out_samples": int(X.shape[0] - n_train), "data_generation_s": gen_s,
+                       "steps": args.train_steps, "batch": args.train_batch, "train_s": train_s,
+                       "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean()),
+                       "held_out_mse_before": ho0, "held_out_mse_after": ho1,
+                       "target_mean_square": float((Tho ** 2).mean().item()),
+                       "tflops": tr_flops / train_s / 1e12}
+    del X, T, Xtr, Ttr, Xho, Tho
+
+    sc = meshgen.cube48_stretch(E=1e6, nu=args.nu)
+    x0 = cc.to_soa(sc.x0, device=dev)
+    n_free = int((sc.pinned == 0).sum())
+
+    def solve(mesh, precision, update="cc"):
+        x = x0.clone()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        try:
+            r = mesh.solve_step(x, update=update, precision=precision, tol=1e-6, max_iters=args.learned_max_iters,
+                                check_every=args.check_every, use_graph=not args.no_graph, history=True)
+        except cc.CCError as e:   # a diverging solve (non-finite residual) is reported, not fatal
+            torch.cuda.synchronize()
+            return {"ms": None, "sweeps": None, "converged": False, "error": str(e)}
+        ev1.record(stream)
+        ev1.synchronize()
+        h = r.residuals[:r.iterations + 1]
+        checked = [k for k in range(len(h)) if h[k] >= 0.0]   # residual read every check_every sweeps
+        keep = checked[::max(1, len(checked) // 24)] + checked[-1:]
+        curve = {int(k): float(h[k] / r.g0) for k in keep}
+        return {"ms": ev0.elapsed_time(ev1), "sweeps": r.iterations, "converged": r.converged,
+                "vertex_updates_per_s": n_free * r.iterations / (ev0.elapsed_time(ev1) / 1e3),
+                "rel_residual_curve": curve}
+
+    def fresh():
+        m = cc.Mesh.from_scene(sc, stream=stream)
+        m.color()
+        return m
+
+    res = {}
+    # computed bases (mixed), warm once then timed
+    m = fresh()
+    m.build_subspace(K_RING)
+    solve(m, "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.build_subspace(K_RING)
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    res["computed_mixed"] = dict(solve(m, "mixed"), acquisition_ms=build_ms)
+    res["plain_fp64"] = dict(solve(m, "fp64"), acquisition_ms=build_ms)
+    m.close()
+    # learned bases (mixed)
+    m = fresh()
+    m.build_learned_subspace(net)
+    solve(m, "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, rho = m.build_learned_subspace(net, tau=1.0, want_rho=True)
+    torch.cuda.synchronize()
+    acq_ms = 1e3 * (time.perf_counter() - t0)
+    rq = np.quantile(rho.cpu().numpy(), [0.5, 0.9, 0.99, 1.0])
+    res["learned_mixed"] = dict(solve(m, "mixed"), acquisition_ms=acq_ms,
+                                fallback=int(st["n_fallback"]), fallback_frac=st["n_fallback"] / max(st["n_free"], 1),
+                                rho_mean=st["rho_mean"], rho_max_kept=st["rho_max"],
+                                rho_quantiles={"p50": rq[0], "p90": rq[1], "p99": rq[2], "max": rq[3]},
+                                acquisition_split_ms={k[3:]: st[k] for k in st if k.startswith("ms_")})
+    # the network's forward pass alone on the cube's inputs (tensor pipe)
+    Xc, _ = m.learned_inputs()
+    Yc = net.forward(Xc)
+    times = []
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.forward(Xc, out=Yc)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    inf_ms = statistics.median(times)
+    inf_tf = mlp_flops(dims, Xc.shape[0]) / (inf_ms / 1e3) / 1e12
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    out["inference_roofline"] = {"kernel": "k_gemm_tn (4 tcgen05 GEMMs, fused bias/GELU epilogues)", "bound": "tensor",
+                                 "achieved": inf_tf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": inf_tf / bf16_peak,
+                                 "rows": int(Xc.shape[0]), "ms": inf_ms, "peak_source": peak_src + " (bf16, burst)"}
+    m.close()
+    # coordinate descent: the method without any subspace
+    m = fresh()
+    res["cd_mixed"] = dict(solve(m, "mixed", update="cd"), acquisition_ms=0.0)
+    m.close()
+    for v in res.values():
+        v["wall_ms"] = v["acquisition_ms"] + v["ms"] if v.get("ms") is not None else None
+    out["cube48"] = {"workload": f"cube48_stretch: 48x48x48 cells ({sc.n} vertices, {sc.T} tets), E=1e6, "
+                                 f"nu={args.nu}, jitter 5%, tol 1e-6 rel grad-norm, "
+                                 f"at most {args.learned_max_iters} sweeps", "n_free": n_free, **res}
+
+    def ratio(a, b):
+        wa, wb = res[a].get("wall_ms"), res[b].get("wall_ms")
+        return wa / wb if (wa and wb and res[a]["converged"] and res[b]["converged"]) else None
+    out["learned_vs_plain_fp64_wall"] = ratio("plain_fp64", "learned_mixed")
+    out["learned_vs_computed_mixed_wall"] = ratio("computed_mixed", "learned_mixed")
+    net.close()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2510_12053_gb300 as cc
@@ -481,6 +632,9 @@ def run_ours(args, rank, world):
     batch_res = None
     if not args.no_batch:
         batch_res = run_batch(args, stream, dev)
+    learned_res = None
+    if not args.no_learned:
+        learned_res = run_learned(args, stream, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -513,6 +667,7 @@ def run_ours(args, rank, world):
                     "d2h_bytes_per_step": 24 * n * len(meshes)},
             "cpu_baseline": cpu,
             "batch": batch_res,
+            "learned": learned_res,
         }
         print(json.dumps(line), flush=True)
     for m in meshes:
