@@ -89,6 +89,22 @@ def test_forward_matches_oracle(dims):
     assert np.abs(Y - Yo).max() <= 1e-2 * np.abs(Yo).max()
 
 
+def test_forward_at_full_size_on_sampled_rows():
+    """Inference over the 112 847 free vertices of the 48^3 cube: 257 sampled
+    rows against the oracle, evaluated one by one."""
+    dims = DIMS[0]
+    rows = 112847
+    net, p = _net(dims, 64, 4)
+    X, Xn = _bf16(rows, dims[0], 12, 264)
+    Y = net.forward(X)
+    torch.cuda.synchronize()
+    pick = np.unique((meshgen.uniform01(13, np.arange(256)) * rows).astype(np.int64).tolist() + [rows - 1])
+    Yo, _ = mlp.forward(p, dims, Xn[pick], rounding=True)
+    Ys = Y[torch.from_numpy(pick).cuda()].cpu().double().numpy()
+    assert _rel(Ys, Yo) <= 1e-3
+    assert np.abs(Ys - Yo).max() <= 1e-2 * np.abs(Yo).max()
+
+
 @pytest.mark.parametrize("dims,B", [(DIMS[0], 1000), (DIMS[0], 4096), (DIMS[1], 77), (DIMS[2], 333)],
                          ids=["full-1000", "full-4096", "small-77", "one-hidden-333"])
 def test_loss_and_gradient_match_oracle(dims, B):
