@@ -322,7 +322,7 @@ cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_s
 /* Launch-configuration autotuner (no counterpart in the paper).  Times
  * `sweeps` coloured CC sweeps from x_dev for each candidate configuration of
  * the two kernels whose best shape depends on the mesh: threads per vertex of
- * the coupling kernel (64, 128, 256) and block rows per CTA of the row
+ * the coupling kernel (32 = one warp per vertex, 64, 128, 256) and block rows per CTA of the row
  * gather (2, 4, 8 warps), and keeps the fastest for this mesh.  x_dev is not
  * modified (the sweeps run on a private copy).  Requires cc_color and a
  * subspace.  Results with different configurations agree to float32
@@ -330,12 +330,18 @@ cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_s
 typedef struct {
   int32_t couple_threads;
   int32_t gather_warps;
-  double couple_ms[3]; /* ms per sweep with 64, 128, 256 threads per vertex */
+  double couple_ms[4]; /* ms per sweep with 32, 64, 128, 256 threads per vertex */
   double gather_ms[3]; /* ms per sweep with 2, 4, 8 warps per block */
 } cc_tune_result;
 
 cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev, cc_precision precision,
                       int32_t sweeps, cc_tune_result* out);
+
+/* Sets the launch shapes cc_autotune chooses among (no counterpart in the
+ * paper): couple_threads in {32 (one warp per vertex), 64, 128, 256},
+ * gather_warps in {2, 4, 8}; 0 keeps the current value.  CC_ERR_INVALID_ARG
+ * for any other value. */
+cc_status cc_set_launch_shape(cc_mesh* mesh, int32_t couple_threads, int32_t gather_warps);
 
 /* ======================================================================
  * Learned perturbation bases.  The paper builds every U_i by the patch

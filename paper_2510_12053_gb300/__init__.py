@@ -86,7 +86,7 @@ class BatchStats(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("couple_threads", ctypes.c_int32), ("gather_warps", ctypes.c_int32),
-                ("couple_ms", ctypes.c_double * 3), ("gather_ms", ctypes.c_double * 3)]
+                ("couple_ms", ctypes.c_double * 4), ("gather_ms", ctypes.c_double * 3)]
 
 
 class Profile(ctypes.Structure):
@@ -149,6 +149,7 @@ _SIGS = {
     "cc_learned_inputs": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]),
     "cc_build_learned_subspace": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(LearnedStats)]),
+    "cc_set_launch_shape": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -364,6 +365,10 @@ class Mesh:
                                  int(sweeps), ctypes.byref(r)))
         return {"couple_threads": r.couple_threads, "gather_warps": r.gather_warps,
                 "couple_ms": list(r.couple_ms), "gather_ms": list(r.gather_ms)}
+
+    def set_launch_shape(self, couple_threads: int = 0, gather_warps: int = 0):
+        """Pins the coupling kernel's threads per vertex (32 = one warp) and the gather's warps per block."""
+        _check(lib().cc_set_launch_shape(self._h, int(couple_threads), int(gather_warps)))
 
     def profile_enable(self, on: bool = True):
         _check(lib().cc_profile_enable(self._h, int(on)))

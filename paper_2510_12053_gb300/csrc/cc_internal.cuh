@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <new>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -133,7 +134,7 @@ void set_smem_limit(const void* kernel, size_t bytes);
 struct Mesh {
   Prof prof;
   // launch configurations chosen by cc_autotune (defaults before tuning)
-  int tune_couple_threads = 128;  // threads per vertex in the coupling kernel
+  int tune_couple_threads = 64;   // threads per vertex in the coupling kernel (32: one warp)
   int tune_gather_wpb = 4;        // warps (rows) per block in the row gather
   int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
   int32_t max_valence = 0;
@@ -232,6 +233,41 @@ struct Mesh {
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key;
 };
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch (opt-in, see pdl_enabled).  A kernel started
+// by pdl_launch may be scheduled while its predecessor in the stream is still
+// finishing: its
+// launch and CTA dispatch overlap the predecessor's tail.  Every such kernel
+// begins with pdl_entry(): it lets its own successor be scheduled once all of
+// its CTAs have started, then waits until the predecessor has completed and
+// its writes are visible, before touching global memory (for an ordinary
+// launch the wait returns at once).  Because each kernel waits for the
+// previous one, completion is transitive along the stream.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+bool pdl_enabled();  // true when CC_GB300_PDL is set in the environment (default: ordinary launches)
+
+template <typename... KArgs, typename... Args>
+void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  CCG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
 
 // ---------------------------------------------------------------------------
 // Host-side helpers implemented in mesh_build.cpp (topology, plain C++)

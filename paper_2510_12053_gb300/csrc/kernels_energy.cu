@@ -145,6 +145,7 @@ __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __rest
                                const uint8_t* __restrict__ pinned, const double* __restrict__ x, int64_t n,
                                const int32_t* __restrict__ list, int64_t count, const double2* __restrict__ mat,
                                double weight, double* __restrict__ gcon, double* __restrict__ hten) {
+  pdl_entry();
   extern __shared__ __align__(16) double hstage64[];
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < count;
@@ -250,6 +251,7 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
                                  const float4* __restrict__ x_lo, const int32_t* __restrict__ list, int64_t count,
                                  const float4* __restrict__ matdf, const float* __restrict__ volw32,
                                  float2* __restrict__ gcon, float* __restrict__ hten) {
+  pdl_entry();
   // Each thread's 96 Hessian values are staged in shared memory, then every
   // warp writes its 32 tets' 384-byte regions with coalesced 16-byte stores.
   extern __shared__ __align__(16) float hstage[];
@@ -292,6 +294,7 @@ __global__ void k_row_gather(const int32_t* __restrict__ rows, int64_t nrows, co
                              const float4* __restrict__ xt_lo, int64_t n, bool dynamic, int max_rs, int max_up,
                              HT* __restrict__ bsr, double* __restrict__ g64, float* __restrict__ g_hi,
                              float* __restrict__ g_lo) {
+  pdl_entry();
   extern __shared__ int rsh[];
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * wpb + warp;
@@ -418,6 +421,7 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Stage 2: sums `count` partials in a fixed order, out[0] = result.
 __global__ void k_reduce_final(const double* __restrict__ part, int64_t count, double* __restrict__ out) {
+  pdl_entry();
   double v = 0.0;
   for (int64_t k = threadIdx.x; k < count; k += blockDim.x) v += part[k];
   v = block_sum(v);
@@ -427,6 +431,7 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t count, d
 __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __restrict__ Bm,
                               const double* __restrict__ vol, const double* __restrict__ x, int64_t n,
                               int64_t T, const double2* __restrict__ mat, double weight, double* __restrict__ part) {
+  pdl_entry();
   double e = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
     const int4 tv = tets[t];
@@ -454,6 +459,7 @@ __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __res
 
 __global__ void k_energy_inertia(const double* __restrict__ mass, const double* __restrict__ x,
                                  const double* __restrict__ xt, int64_t n, double* __restrict__ part) {
+  pdl_entry();
   double e = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     double d0 = x[j] - xt[j], d1 = x[n + j] - xt[n + j], d2 = x[2 * n + j] - xt[2 * n + j];
@@ -467,6 +473,7 @@ template <bool kMixed>
 __global__ void k_gnorm(const int32_t* __restrict__ free_rows, int64_t nfree, const double* __restrict__ g64,
                         const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
                         double* __restrict__ grad_out, double* __restrict__ part) {
+  pdl_entry();
   double acc = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nfree; k += (int64_t)gridDim.x * blockDim.x) {
     const int j = free_rows[k];
@@ -488,6 +495,7 @@ template <bool kMixed>
 __global__ void k_gnorm_mesh(const int32_t* __restrict__ fptr, const int32_t* __restrict__ free_rows,
                              const double* __restrict__ g64, const float* __restrict__ g_hi,
                              const float* __restrict__ g_lo, double* __restrict__ gsq) {
+  pdl_entry();
   const int b = blockIdx.x;
   double acc = 0.0;
   for (int k = fptr[b] + threadIdx.x; k < fptr[b + 1]; k += blockDim.x) {
@@ -505,6 +513,7 @@ __global__ void k_gnorm_mesh(const int32_t* __restrict__ fptr, const int32_t* __
 
 __global__ void k_split_df(const double* __restrict__ x, int64_t n, float4* __restrict__ hi,
                            float4* __restrict__ lo) {
+  pdl_entry();
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   df a = df_from_double(x[j]), b = df_from_double(x[n + j]), c = df_from_double(x[2 * n + j]);
@@ -538,9 +547,8 @@ void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t 
   if (count <= 0) return;
   constexpr int kThreads = 64;
   const size_t smem = (size_t)kThreads * 96 * sizeof(double);
-  k_tet_grad_f64<<<grid_for(count, kThreads), kThreads, smem, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm.p, m.d_vol.p, m.d_pinned.p, x, m.n,
-                                                    list, count, m.d_mat64.p, weight, m.f64.gcon.p,
-                                                    m.f64.hten.p);
+  pdl_launch(k_tet_grad_f64, grid_for(count, kThreads), kThreads, smem, s, m.d_tets.p, m.d_tslot.p, m.d_Bm.p,
+             m.d_vol.p, m.d_pinned.p, x, m.n, list, count, m.d_mat64.p, weight, m.f64.gcon.p, m.f64.hten.p);
 }
 
 void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
@@ -548,10 +556,9 @@ void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double w
   (void)weight;
   constexpr int kThreads = 128;
   const size_t smem = (size_t)kThreads * 96 * sizeof(float);
-  k_tet_grad_mixed<<<grid_for(count, kThreads), kThreads, smem, s>>>(m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p, m.d_volw_df.p,
-                                                      m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, m.d_matdf.p,
-                                                      m.d_volw32.p, m.mx.gcon.p,
-                                                      m.mx.hten.p);
+  pdl_launch(k_tet_grad_mixed, grid_for(count, kThreads), kThreads, smem, s, m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p,
+             m.d_volw_df.p, m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, m.d_matdf.p, m.d_volw32.p,
+             m.mx.gcon.p, m.mx.hten.p);
 }
 
 template <typename HT, bool kMixed>
@@ -562,7 +569,7 @@ static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, con
   const int64_t blocks = (m.n_free + wpb - 1) / wpb;
   const size_t smem = (size_t)wpb * (m.max_rs + m.max_up + 1) * sizeof(int);
   set_smem_limit(reinterpret_cast<const void*>(k_row_gather<HT, kMixed>), smem);
-  k_row_gather<HT, kMixed><<<(unsigned)blocks, 32 * wpb, smem, s>>>(
+  pdl_launch(k_row_gather<HT, kMixed>, (unsigned)blocks, 32 * wpb, smem, s,
       m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.d_up_ptr.p, m.d_rs_ptr.p, m.d_rs_src.p, hten, massh, m.d_mass.p,
       m.d_mass_df.p, kMixed ? nullptr : m.f64.gcon.p, kMixed ? m.mx.gcon.p : nullptr, x,
       kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr, dyn ? xt : nullptr,
@@ -582,40 +589,40 @@ void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s) {
 
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {
   const double w = m.h > 0.0 ? m.h * m.h : 1.0;
-  k_energy_tets<<<kRedBlocks, kBlock, 0, s>>>(m.d_tets.p, m.d_Bm.p, m.d_vol.p, x, m.n, m.T, m.d_mat64.p, w,
-                                              m.d_red.p);
+  pdl_launch(k_energy_tets, kRedBlocks, kBlock, 0, s, m.d_tets.p, m.d_Bm.p, m.d_vol.p, x, m.n, m.T, m.d_mat64.p, w,
+             m.d_red.p);
   if (m.h > 0.0 && xt) {
-    k_energy_inertia<<<kRedBlocks, kBlock, 0, s>>>(m.d_mass.p, x, xt, m.n, m.d_red.p + kRedBlocks);
-    k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, 2 * kRedBlocks, out);
+    pdl_launch(k_energy_inertia, kRedBlocks, kBlock, 0, s, m.d_mass.p, x, xt, m.n, m.d_red.p + kRedBlocks);
+    pdl_launch(k_reduce_final, 1, 1024, 0, s, m.d_red.p, (int64_t)(2 * kRedBlocks), out);
   } else {
-    k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+    pdl_launch(k_reduce_final, 1, 1024, 0, s, m.d_red.p, (int64_t)kRedBlocks, out);
   }
 }
 
 void launch_gnorm_f64(Mesh& m, double* grad_out, double* out, cudaStream_t s) {
-  k_gnorm<false><<<kRedBlocks, kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, m.f64.g.p, nullptr, nullptr, m.n, grad_out,
-                                               m.d_red.p);
-  k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+  pdl_launch(k_gnorm<false>, kRedBlocks, kBlock, 0, s, m.d_free_rows.p, m.n_free, (const double*)m.f64.g.p,
+             (const float*)nullptr, (const float*)nullptr, m.n, grad_out, m.d_red.p);
+  pdl_launch(k_reduce_final, 1, 1024, 0, s, m.d_red.p, (int64_t)kRedBlocks, out);
 }
 
 void launch_gnorm_mixed(Mesh& m, double* grad_out, double* out, cudaStream_t s) {
-  k_gnorm<true><<<kRedBlocks, kBlock, 0, s>>>(m.d_free_rows.p, m.n_free, nullptr, m.mx.g_hi.p, m.mx.g_lo.p, m.n,
-                                              grad_out, m.d_red.p);
-  k_reduce_final<<<1, 1024, 0, s>>>(m.d_red.p, kRedBlocks, out);
+  pdl_launch(k_gnorm<true>, kRedBlocks, kBlock, 0, s, m.d_free_rows.p, m.n_free, (const double*)nullptr,
+             (const float*)m.mx.g_hi.p, (const float*)m.mx.g_lo.p, m.n, grad_out, m.d_red.p);
+  pdl_launch(k_reduce_final, 1, 1024, 0, s, m.d_red.p, (int64_t)kRedBlocks, out);
 }
 
 void launch_gnorm_mesh(Mesh& m, bool mixed, cudaStream_t s) {
   const unsigned B = (unsigned)(m.mesh_vptr.size() - 1);
   if (mixed)
-    k_gnorm_mesh<true><<<B, 256, 0, s>>>(m.d_mesh_fptr.p, m.d_free_rows.p, nullptr, m.mx.g_hi.p, m.mx.g_lo.p,
-                                         m.d_mesh_gsq.p);
+    pdl_launch(k_gnorm_mesh<true>, B, 256, 0, s, m.d_mesh_fptr.p, m.d_free_rows.p, (const double*)nullptr,
+               (const float*)m.mx.g_hi.p, (const float*)m.mx.g_lo.p, m.d_mesh_gsq.p);
   else
-    k_gnorm_mesh<false><<<B, 256, 0, s>>>(m.d_mesh_fptr.p, m.d_free_rows.p, m.f64.g.p, nullptr, nullptr,
-                                          m.d_mesh_gsq.p);
+    pdl_launch(k_gnorm_mesh<false>, B, 256, 0, s, m.d_mesh_fptr.p, m.d_free_rows.p, (const double*)m.f64.g.p,
+               (const float*)nullptr, (const float*)nullptr, m.d_mesh_gsq.p);
 }
 
 void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStream_t s) {
-  k_split_df<<<grid_for(n), kBlock, 0, s>>>(x, n, hi, lo);
+  pdl_launch(k_split_df, grid_for(n), kBlock, 0, s, x, n, hi, lo);
 }
 
 void launch_inertial_target(const double* x, const double* v, int64_t n, double h, const double* grav, double* xt,

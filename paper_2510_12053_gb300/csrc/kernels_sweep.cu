@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
     const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, int64_t smap_max,
     HT* __restrict__ cpl) {
+  pdl_entry();
   using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* ptr = smem;
@@ -208,6 +209,139 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   cpl[(int64_t)blockIdx.x * 32 + tid] = tot;
 }
 
+// The same coupling products with one warp per vertex (kWarps vertices per
+// CTA, no CTA-wide barrier).  The warp stages U_i and its rows' starts in its
+// own slice of shared memory, then splits the support's flattened list of
+// upper blocks (rows of S in support order, then row i) evenly over its
+// lanes: lane L takes blocks [L c, (L+1) c) with c = ceil(total / 32), walking
+// the row boundaries as it goes, so every lane issues about the same number
+// of independent block loads.  b = U^T g_C takes the rows round-robin.  The
+// 27 sums are reduced by a fixed shuffle tree.
+template <typename HT, typename SlotT, bool kMixed, int kUpd, int kWarps>
+__global__ void __launch_bounds__(32 * kWarps) k_couple_warp(
+    const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
+    const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
+    const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
+    const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, HT* __restrict__ cpl) {
+  pdl_entry();
+  using Codes = SlotCodes<SlotT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * kWarps + warp;
+  if (k >= count) return;  // whole warp leaves together
+  const size_t per_warp = align16((size_t)sup_max * 9 * sizeof(HT)) + 2 * align16((size_t)(sup_max + 2) * 4);
+  unsigned char* ptr = smem + (size_t)warp * per_warp;
+  HT* Us = reinterpret_cast<HT*>(ptr);
+  ptr += align16((size_t)sup_max * 9 * sizeof(HT));
+  int* rstart = reinterpret_cast<int*>(ptr);  // [m + 1] first upper block of each row
+  ptr += align16((size_t)(sup_max + 2) * 4);
+  int* roff = reinterpret_cast<int*>(ptr);    // [m + 2] offset of each row in the flattened list
+
+  const int i = verts[k];
+  const int s0 = sup_ptr[i];
+  const int m = sup_ptr[i + 1] - s0;
+  const int64_t c0 = smap_ptr[i];
+  for (int q = lane; q < 9 * m; q += 32) Us[q] = U[(int64_t)s0 * 9 + q];
+  // row starts and the exclusive prefix of the row lengths (rows 0..m-1 = S, row m = i)
+  int carry = 0;
+  for (int base = 0; base <= m; base += 32) {
+    const int r = base + lane;
+    int len = 0;
+    if (r <= m) {
+      const int j = r < m ? sup_idx[s0 + r] : i;
+      const int a = up_ptr[j];
+      rstart[r] = a;
+      len = up_ptr[j + 1] - a;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (r <= m) roff[r] = carry + incl - len;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) roff[m + 1] = carry;
+  __syncwarp();
+  const int total = carry;
+
+  HT h00 = 0, h01 = 0, h02 = 0, h11 = 0, h12 = 0, h22 = 0;
+  HT A[9], Hii[9], b[3] = {0, 0, 0};
+  mat3_zero(A);
+  mat3_zero(Hii);
+  const int chunk = (total + 31) >> 5;
+  int q = lane * chunk;
+  const int qend = min(total, q + chunk);
+  if (q < qend) {
+    // row containing flattened block q: the last r with roff[r] <= q
+    int lo = 0, hi = m;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (roff[mid] <= q) lo = mid;
+      else hi = mid - 1;
+    }
+    int r = lo;
+    int rend = roff[r + 1];
+    for (; q < qend; ++q) {
+      while (q >= rend) {
+        ++r;
+        rend = roff[r + 1];
+      }
+      const unsigned code = smap[c0 + q];
+      if (code == Codes::kNone) continue;
+      HT H[9];
+      load_block(bsr, (int64_t)rstart[r] + (q - roff[r]), H);
+      if (r < m) {
+        const HT* Uj = Us + 9 * r;
+        if (code == Codes::kSelf) {
+          if (kUpd == CC_UPDATE_CC) mat3_tmul_acc(H, Uj, A);
+        } else {
+          const bool dg = code == Codes::kDiag;
+          const HT w = dg ? HT(0.5) : HT(1);
+          HT T[9], M[9];
+          mat3_zero(T);
+          mat3_mul_acc(H, Us + 9 * (dg ? r : (int)code), T);
+          mat3_zero(M);
+          mat3_tmul_acc(Uj, T, M);
+          h00 += 2 * w * M[0]; h11 += 2 * w * M[4]; h22 += 2 * w * M[8];
+          h01 += w * (M[1] + M[3]); h02 += w * (M[2] + M[6]); h12 += w * (M[5] + M[7]);
+        }
+      } else {
+        if (code == Codes::kDiag) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) Hii[c] = H[c];
+        } else if (kUpd == CC_UPDATE_CC) {
+          mat3_mul_acc(H, Us + 9 * code, A);
+        }
+      }
+    }
+  }
+  for (int r = lane; r < m; r += 32) {
+    const int j = sup_idx[s0 + r];
+    const HT* Uj = Us + 9 * r;
+    HT gj[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gj[a] = kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[c] += Uj[c] * gj[0] + Uj[3 + c] * gj[1] + Uj[6 + c] * gj[2];
+  }
+  HT vals27[27] = {h00, h01, h02, h11, h12, h22, A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], A[8],
+                   b[0], b[1], b[2], Hii[0], Hii[1], Hii[2], Hii[3], Hii[4], Hii[5], Hii[6], Hii[7], Hii[8]};
+  HT mine = 0;
+#pragma unroll
+  for (int v = 0; v < 27; ++v) {
+    const HT t = warp_sum(vals27[v]);
+    if (lane == v) mine = t;
+  }
+  if (lane < 27) cpl[k * 32 + lane] = mine;
+}
+
+template <typename HT>
+__host__ __device__ inline size_t warp_smem_bytes(int sup_max, int warps) {
+  return (size_t)warps * (align16((size_t)sup_max * 9 * sizeof(HT)) + 2 * align16((size_t)(sup_max + 2) * 4));
+}
+
 // Batched condensation (Eq. 9-12), one free vertex per thread: a warp
 // condenses 32 vertices at once, so the float64 or float-float 3x3 algebra
 // runs at full SIMD width instead of on one lane per vertex.  3x3 inverses
@@ -222,6 +356,7 @@ __global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, con
                            double* __restrict__ x, float4* __restrict__ x_hi, float4* __restrict__ x_lo,
                            AR rel, const int32_t* __restrict__ vert_mesh, const int32_t* __restrict__ active,
                            unsigned long long* __restrict__ fallback, unsigned long long* __restrict__ err) {
+  pdl_entry();
   using Ar = Arith<AR>;
   using V = typename Ar::V;
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -358,13 +493,39 @@ void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, co
   if (m.smap_wide) {
     auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-    kern<<<(unsigned)count, kThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
-                                                 m.d_smap_ptr.p, m.d_smap16.p, bsr, g64, g_hi, supm, smx, cpl);
+    pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, cpl);
   } else {
     auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-    kern<<<(unsigned)count, kThreads, smem, s>>>(verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, U, m.d_up_ptr.p,
-                                                 m.d_smap_ptr.p, m.d_smap8.p, bsr, g64, g_hi, supm, smx, cpl);
+    pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, cpl);
+  }
+  CCG_CUDA(cudaGetLastError());
+}
+
+template <typename HT, bool kMixed, int kUpd>
+void launch_couple_warp(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
+                        const float* g_hi, HT* cpl, cudaStream_t s) {
+  constexpr int kWarps = 4;
+  const int supm = m.sup_max > 0 ? m.sup_max : 1;
+  const size_t smem = warp_smem_bytes<HT>(supm, kWarps);
+  CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+  const unsigned grid = (unsigned)((count + kWarps - 1) / kWarps);
+  if (m.smap_wide) {
+    auto kern = k_couple_warp<HT, uint16_t, kMixed, kUpd, kWarps>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    pdl_launch(kern, grid, 32 * kWarps, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, cpl);
+  } else {
+    auto kern = k_couple_warp<HT, uint8_t, kMixed, kUpd, kWarps>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    pdl_launch(kern, grid, 32 * kWarps, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, cpl);
   }
   CCG_CUDA(cudaGetLastError());
 }
@@ -376,6 +537,7 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
   float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
   if (kUpd != CC_UPDATE_CD) {
     switch (m.tune_couple_threads) {
+      case 32: launch_couple_warp<HT, kMixed, kUpd>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
       case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
       case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
       default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, s);
@@ -384,13 +546,13 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
   const unsigned grid = (unsigned)((count + 127) / 128);
   if constexpr (kMixed) {
     const df rel{1e-12f, (float)(1e-12 - (double)1e-12f)};
-    k_condense<df, HT, kMixed, kUpd><<<grid, 128, 0, s>>>(verts, count, cpl, m.d_sup_ptr.p, m.d_up_ptr.p, bsr, g64,
-                                                         g_hi, g_lo, m.n, x, xh, xl, rel, m.d_vert_mesh.p,
-                                                         m.d_mesh_active.p, c.fallback, c.error);
+    pdl_launch(k_condense<df, HT, kMixed, kUpd>, grid, 128, 0, s, verts, count, (const HT*)cpl,
+               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl, rel,
+               (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
   } else {
-    k_condense<double, HT, kMixed, kUpd><<<grid, 128, 0, s>>>(verts, count, cpl, m.d_sup_ptr.p, m.d_up_ptr.p, bsr,
-                                                             g64, g_hi, g_lo, m.n, x, xh, xl, 1e-12,
-                                                             m.d_vert_mesh.p, m.d_mesh_active.p, c.fallback, c.error);
+    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, 128, 0, s, verts, count, (const HT*)cpl,
+               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
+               1e-12, (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
   }
   CCG_CUDA(cudaGetLastError());
 }

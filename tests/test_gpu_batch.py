@@ -93,9 +93,9 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     res_a = batch.solve_batch(x0.clone(), precision="mixed", tol=1e-6, max_iters=200, check_every=1)
     tune = batch.autotune(x0, precision="mixed", sweeps=2)
     assert torch.equal(x0, before)                      # x is not modified
-    assert tune["couple_threads"] in (64, 128, 256) and tune["gather_warps"] in (2, 4, 8)
+    assert tune["couple_threads"] in (32, 64, 128, 256) and tune["gather_warps"] in (2, 4, 8)
     assert all(v > 0 for v in tune["couple_ms"] + tune["gather_ms"])
-    assert tune["couple_ms"][(64, 128, 256).index(tune["couple_threads"])] == min(tune["couple_ms"])
+    assert tune["couple_ms"][(32, 64, 128, 256).index(tune["couple_threads"])] == min(tune["couple_ms"])
     assert tune["gather_ms"][(2, 4, 8).index(tune["gather_warps"])] == min(tune["gather_ms"])
     xb = x0.clone()
     res_b = batch.solve_batch(xb, precision="mixed", tol=1e-6, max_iters=200, check_every=1)

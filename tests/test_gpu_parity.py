@@ -123,6 +123,31 @@ def test_one_fp64_sweep_matches_oracle(update, schedule):
         (st_o.fallback_empty, st_o.fallback_reduced, st_o.fallback_schur)
 
 
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_coupling_launch_shape_matches_oracle(threads, precision):
+    """One CC sweep with each coupling-kernel shape (32 = one warp per vertex)."""
+    scene = _box(dims=(7, 6, 5), seed=9)
+    pb, topo, sup, U = _oracle(scene, 2)
+    x0 = _state(scene, 0.05, 6)
+    x_o = solvers.sweep(pb, topo, sup, U, x0, None, "cc", "colored")
+    m = _gpu(scene, 2)
+    m.set_launch_shape(couple_threads=threads)
+    xd = cc.to_soa(x0)
+    m.sweep(xd, update="cc", schedule="colored", precision=precision)
+    d_o, d_g = x_o - x0, cc.from_soa(xd) - x0
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert np.abs(d_g - d_o).max() <= tol * np.abs(d_o).max()
+
+
+def test_launch_shape_rejects_unknown_values():
+    m = _gpu(_box(dims=(3, 3, 3)), 2)
+    with pytest.raises(cc.CCError):
+        m.set_launch_shape(couple_threads=96)
+    with pytest.raises(cc.CCError):
+        m.set_launch_shape(gather_warps=3)
+
+
 def test_pinned_rows_untouched_and_colour_range():
     scene = _box()
     m = _gpu(scene, 2)
