@@ -359,10 +359,16 @@ cc_status cc_set_launch_shape(cc_mesh* mesh, int32_t couple_threads, int32_t gat
  * tcgen05 MMA with TMA-loaded, 128-byte-swizzled tiles and a float32
  * accumulator in tensor memory.  n_tile in {0 (automatic), 64, 128, 192,
  * 256}; k_splits >= 1 splits K over CTAs (partial products summed in a fixed
- * order afterwards), 0 = 1.  CC_ERR_TIMEOUT if a bounded device wait
- * expired. */
+ * order afterwards), 0 = 1; flags: 0 or CC_GEMM_ONE_TILE_PER_CTA.
+ * CC_ERR_TIMEOUT if a bounded device wait expired. */
 cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
-                          int32_t K, float* C, int64_t ldc, int32_t n_tile, int32_t k_splits, void* stream);
+                          int32_t K, float* C, int64_t ldc, int32_t n_tile, int32_t k_splits, int32_t flags,
+                          void* stream);
+/* cc_gemm_bf16_tn flags: the default kernel is persistent and warp-specialised
+ * (one CTA per SM looping over tiles: a TMA producer warp, an MMA warp, 16
+ * epilogue warps, two tensor-memory accumulators); this flag selects the
+ * simpler one-tile-per-CTA kernel instead. */
+#define CC_GEMM_ONE_TILE_PER_CTA 1
 
 /* Network inputs: 64 stencil slots x 4 channels + 2 material channels. */
 #define CC_LEARNED_D_IN 258
@@ -372,6 +378,12 @@ cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb
 #define CC_LEARNED_LDX 264
 
 typedef struct cc_mlp cc_mlp;
+
+/* The network's activation arithmetic, exposed for testing: for device
+ * float32 x [n], out [n][3] = (erf(x), GELU(x), GELU'(x)) exactly as the GEMM
+ * epilogues evaluate them (erf by Abramowitz and Stegun formula 7.1.26,
+ * |error| <= 1.5e-7; GELU in erf form). */
+cc_status cc_mlp_activation(const float* x, int32_t n, float* out, void* stream);
 
 typedef struct {
   int32_t d_in;       /* input width (CC_LEARNED_D_IN for bases) */

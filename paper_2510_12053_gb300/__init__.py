@@ -134,7 +134,9 @@ _SIGS = {
     "cc_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(BatchStats)]),
     "cc_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
     "cc_gemm_bf16_tn": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]),
+                                       ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, _P]),
+    "cc_mlp_activation": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "cc_mlp_create": (ctypes.c_int, [ctypes.POINTER(MlpConfig), _P, ctypes.POINTER(_P)]),
     "cc_mlp_destroy": (None, [_P]),
     "cc_mlp_param_count": (ctypes.c_int64, [_P]),
@@ -416,7 +418,7 @@ class Mesh:
                            st.sweeps.fallback_schur, hist)
 
 
-def gemm_bf16_tn(A, B, out=None, stream=None, n_tile: int = 0, k_splits: int = 0):
+def gemm_bf16_tn(A, B, out=None, stream=None, n_tile: int = 0, k_splits: int = 0, one_tile_per_cta: bool = False):
     """C = A . B^T on the tcgen05 kernel (A [M, K], B [N, K] bf16 CUDA tensors)."""
     import torch
     M, K = A.shape
@@ -424,8 +426,18 @@ def gemm_bf16_tn(A, B, out=None, stream=None, n_tile: int = 0, k_splits: int = 0
     C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().cc_gemm_bf16_tn(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), M, N, K, C.data_ptr(),
-                                 C.stride(0), int(n_tile), int(k_splits), _stream_ptr(st)))
+                                 C.stride(0), int(n_tile), int(k_splits), 1 if one_tile_per_cta else 0,
+                                 _stream_ptr(st)))
     return C
+
+
+def mlp_activation(x):
+    """(erf, GELU, GELU') of a float32 CUDA tensor as the network's epilogues compute them."""
+    import torch
+    out = torch.empty((x.numel(), 3), dtype=torch.float32, device=x.device)
+    _check(lib().cc_mlp_activation(x.data_ptr(), x.numel(), out.data_ptr(),
+                                   _stream_ptr(torch.cuda.current_stream())))
+    return out
 
 
 def _dev(t, dtype, name, cols=None):

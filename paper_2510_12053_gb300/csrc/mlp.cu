@@ -652,7 +652,7 @@ void read_err(DBuf<int>& err, cudaStream_t s, const char* msg) {
 extern "C" {
 
 cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N, int32_t K,
-                          float* C, int64_t ldc, int32_t n_tile, int32_t k_splits, void* stream) {
+                          float* C, int64_t ldc, int32_t n_tile, int32_t k_splits, int32_t flags, void* stream) {
   CC_API_BODY("cc_gemm_bf16_tn", {
     CCG_CHECK(A && B && C && ldc >= N, CC_ERR_INVALID_ARG, "bad GEMM arguments");
     CCG_CHECK(k_splits >= 0 && n_tile >= 0, CC_ERR_INVALID_ARG, "bad GEMM launch shape");
@@ -663,6 +663,7 @@ cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb
     GemmShape sh = gemm_pick_shape(M, N, K, false);
     if (n_tile) sh.bn = n_tile;
     sh.splits = std::max(1, (int)k_splits);
+    sh.persistent = (flags & CC_GEMM_ONE_TILE_PER_CTA) == 0;
     GemmEpilogue ep;
     if (sh.splits == 1) {
       ep.c32 = C;
@@ -685,6 +686,15 @@ cc_status cc_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb
     CCG_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CCG_CUDA(cudaStreamSynchronize(s));
     CCG_CHECK(h == 0, CC_ERR_TIMEOUT, "a bounded wait in the GEMM kernel expired");
+  })
+}
+
+cc_status cc_mlp_activation(const float* x, int32_t n, float* out, void* stream) {
+  CC_API_BODY("cc_mlp_activation", {
+    CCG_CHECK(x && out && n >= 0, CC_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return CC_OK;
+    gelu_check(x, n, out, (cudaStream_t)stream);
+    CCG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   })
 }
 

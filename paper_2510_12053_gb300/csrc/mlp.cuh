@@ -29,8 +29,9 @@ struct GemmEpilogue {
 };
 
 struct GemmShape {
-  int bn = 64;      // N tile (64, 128, 192 or 256)
-  int splits = 1;   // K splits (kEpiF32 only)
+  int bn = 64;             // N tile (64, 128, 192 or 256)
+  int splits = 1;          // K splits (kEpiF32 only)
+  bool persistent = true;  // persistent warp-specialised kernel; false: one tile per CTA
 };
 
 // C[M x N] = A[M x K] . B[N x K]^T, A and B row-major BF16 with leading
@@ -40,8 +41,10 @@ struct GemmShape {
 void gemm_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, int epi,
              const GemmEpilogue& ep, int* err, cudaStream_t s, GemmShape shape);
 // Launch shape for an M x N x K product: the widest N tile that still gives
-// about two CTAs per SM, and (when allow_split) enough K splits to fill the
+// at least one tile per SM, and (when allow_split) enough K splits to fill the
 // GPU with at least four K tiles per split.
 GemmShape gemm_pick_shape(int M, int N, int K, bool allow_split);
+// out[3k .. 3k+2] = (erf, GELU, GELU') of x[k] with the epilogues' arithmetic
+void gelu_check(const float* x, int n, float* out, cudaStream_t s);
 
 }  // namespace ccg

@@ -112,10 +112,147 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+}  // namespace
+
+// erf(x) from Abramowitz and Stegun, Handbook of Mathematical Functions
+// (1964), formula 7.1.26 (Hastings' rational approximation):
+//   erf(u) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-u^2),
+//   t = 1 / (1 + p u), u = |x|, odd in x, with |error| <= 1.5e-7.
+// Branch-free: one reciprocal, one exponential, five FMAs.  Its error is ~1e-4
+// of a BF16 rounding step, where the activations it feeds are stored.
+__device__ __forceinline__ float erf_as7126(float x) {
+  const float u = fabsf(x);
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
+  float q = fmaf(t, 1.061405429f, -1.453152027f);
+  q = fmaf(t, q, 1.421413741f);
+  q = fmaf(t, q, -0.284496736f);
+  q = fmaf(t, q, 0.254829592f);
+  const float y = fmaf(-q * t, __expf(-u * u), 1.0f);
+  return copysignf(y, x);
+}
+
+namespace {
+
+// GELU, erf form: z Phi(z) = z (1 + erf(z / sqrt 2)) / 2, and its derivative
+// Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as7126(z * 0.70710678118654752f)); }
 
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  return 0.5f * (1.0f + erf_as7126(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+__global__ void k_erf_check(const float* __restrict__ x, int n, float* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    out[3 * k] = erf_as7126(x[k]);
+    out[3 * k + 1] = gelu(x[k]);
+    out[3 * k + 2] = gelu_grad(x[k]);
+  }
+}
+
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+__device__ __forceinline__ void load16(const float* src, float (&d)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; k += 4) {
+    const float4 q = *reinterpret_cast<const float4*>(src + k);
+    d[k] = q.x; d[k + 1] = q.y; d[k + 2] = q.z; d[k + 3] = q.w;
+  }
+}
+
+__device__ __forceinline__ void store16(float* dst, const float (&v)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; k += 4) *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+}
+
+// 16 float32 values -> 16 BF16 (round to nearest even), two per conversion
+__device__ __forceinline__ void store16_bf16(__nv_bfloat16* dst, const float (&g)[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(g[2 * k], g[2 * k + 1]);
+    w[k] = *reinterpret_cast<const uint32_t*>(&p2);
+  }
+  reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Epilogue of 16 accumulator columns [col0, col0 + 16) of one row.  Full,
+// aligned chunks take vector loads and stores with no per-column checks.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(float (&v)[16], int row, int col0, int N, const GemmEpilogue& ep,
+                                               float* c32) {
+  const bool full = col0 + 16 <= N;
+  if (EPI == kEpiF32 || EPI == kEpiBiasF32) {
+    float* dst = c32 + (int64_t)row * ep.ldc + col0;
+    if (full && aligned16(dst) && (EPI == kEpiF32 || aligned16(ep.bias + col0))) {
+      if (EPI == kEpiBiasF32) {
+        float b[16];
+        load16(ep.bias + col0, b);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += b[k];
+      }
+      store16(dst, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (col0 + k < N) dst[k] = v[k] + (EPI == kEpiBiasF32 ? ep.bias[col0 + k] : 0.0f);
+    }
+    return;
+  }
+  float g[16];
+  __nv_bfloat16* hdst = ep.h16 + (int64_t)row * ep.ldh + col0;
+  if (EPI == kEpiBiasGelu) {
+    float* zdst = ep.z32 ? ep.z32 + (int64_t)row * ep.ldz + col0 : nullptr;
+    if (full && aligned16(ep.bias + col0) && aligned16(hdst) && (!zdst || aligned16(zdst))) {
+      float b[16];
+      load16(ep.bias + col0, b);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        v[k] += b[k];
+        g[k] = gelu(v[k]);
+      }
+      if (zdst) store16(zdst, v);  // pre-activations are kept for training only
+      store16_bf16(hdst, g);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (col0 + k < N) {
+          const float z = v[k] + ep.bias[col0 + k];
+          g[k] = gelu(z);
+          if (zdst) zdst[k] = z;
+          hdst[k] = __float2bfloat16_rn(g[k]);
+        } else {
+          g[k] = 0.0f;
+        }
+      }
+    }
+  } else {  // kEpiGeluGrad: dZ = C * gelu'(Z)
+    const float* zsrc = ep.z32 + (int64_t)row * ep.ldz + col0;
+    if (full && aligned16(zsrc) && aligned16(hdst)) {
+      float z[16];
+      load16(zsrc, z);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) g[k] = v[k] * gelu_grad(z[k]);
+      store16_bf16(hdst, g);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (col0 + k < N) {
+          g[k] = v[k] * gelu_grad(zsrc[k]);
+          hdst[k] = __float2bfloat16_rn(g[k]);
+        } else {
+          g[k] = 0.0f;
+        }
+      }
+    }
+  }
+  if (ep.ht16) {
+    // transposed copy: consecutive lanes write consecutive rows
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (col0 + k < N) ep.ht16[(int64_t)(col0 + k) * ep.ldt + row] = __float2bfloat16_rn(g[k]);
+  }
 }
 
 template <int BN, int EPI>
@@ -219,69 +356,187 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tmem_ld16(lane_base + c, v);
-      if (row >= M) continue;
-      const int col0 = n0 + c;
-      if (col0 >= N) continue;
-      const bool full = col0 + 16 <= N;
-      if (EPI == kEpiF32 || EPI == kEpiBiasF32) {
-        if (EPI == kEpiBiasF32) {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] += (col0 + k < N) ? ep.bias[col0 + k] : 0.0f;
-        }
-        float* dst = c32 + (int64_t)row * ep.ldc + col0;
-        if (full && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-#pragma unroll
-          for (int k = 0; k < 16; k += 4) *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-        } else {
-          for (int k = 0; k < 16 && col0 + k < N; ++k) dst[k] = v[k];
-        }
-        continue;
-      }
-      __nv_bfloat16 hb[16];
-      if (EPI == kEpiBiasGelu) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float z = v[k] + ((col0 + k < N) ? ep.bias[col0 + k] : 0.0f);
-          v[k] = z;
-          hb[k] = __float2bfloat16_rn(gelu(z));
-        }
-        if (ep.z32) {  // pre-activations are kept for training only
-          float* zdst = ep.z32 + (int64_t)row * ep.ldz + col0;
-          if (full && ((reinterpret_cast<uintptr_t>(zdst) & 15) == 0)) {
-#pragma unroll
-            for (int k = 0; k < 16; k += 4)
-              *reinterpret_cast<float4*>(zdst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-          } else {
-            for (int k = 0; k < 16 && col0 + k < N; ++k) zdst[k] = v[k];
-          }
-        }
-      } else {  // kEpiGeluGrad: dZ = C * gelu'(Z)
-        const float* zsrc = ep.z32 + (int64_t)row * ep.ldz + col0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float z = (col0 + k < N) ? zsrc[k] : 0.0f;
-          hb[k] = __float2bfloat16_rn(v[k] * gelu_grad(z));
-        }
-      }
-      __nv_bfloat16* hdst = ep.h16 + (int64_t)row * ep.ldh + col0;
-      if (full && ((reinterpret_cast<uintptr_t>(hdst) & 15) == 0)) {
-        uint4 w[2];
-        memcpy(w, hb, sizeof(w));
-        reinterpret_cast<uint4*>(hdst)[0] = w[0];
-        reinterpret_cast<uint4*>(hdst)[1] = w[1];
-      } else {
-        for (int k = 0; k < 16 && col0 + k < N; ++k) hdst[k] = hb[k];
-      }
-      if (ep.ht16) {
-        // transposed copy: consecutive lanes write consecutive rows
-        for (int k = 0; k < 16 && col0 + k < N; ++k) ep.ht16[(int64_t)(col0 + k) * ep.ldt + row] = hb[k];
-      }
+      if (row >= M || n0 + c >= N) continue;
+      epilogue_chunk<EPI>(v, row, n0 + c, N, ep, c32);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  }
+}
+
+// ---- persistent, warp-specialised version --------------------------------------
+// One CTA per SM loops over output tiles (and K splits).  Warp 0 (one thread)
+// is the TMA producer of a kWsStages-deep ring of A/B tiles; warp 1 (one
+// thread) issues the tcgen05 MMAs into one of two accumulators in tensor
+// memory (2 x 256 columns = the SM's 512); warps 2..17 are the epilogue, four
+// per tensor-memory lane quarter (warp w reads lanes 32 (w % 4) ..), each
+// owning a quarter of the tile's columns.  While the epilogue drains
+// accumulator a, the MMAs of the next tile fill accumulator a ^ 1.
+//   full[s]      producer -> MMA: stage s loaded (TMA transaction bytes)
+//   empty[s]     MMA -> producer: stage s read (tcgen05.commit)
+//   acc_full[a]  MMA -> epilogue: accumulator a complete (tcgen05.commit)
+//   acc_empty[a] epilogue -> MMA: accumulator a drained (one arrival per warp)
+// Every wait is bounded; a role that times out raises the CTA's failure flag,
+// the others stop at their next wait, in-flight copies and MMAs are waited
+// for (bounded) and tensor memory is freed before the CTA returns.
+constexpr int kWsEpiWarps = 16;
+constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
+constexpr int kWsAccCols = 256;
+
+__host__ __device__ constexpr int ws_stages(int bn) {
+  return (200 * 1024) / (kBM * kBK * 2 + bn * kBK * 2) > 8 ? 8 : (200 * 1024) / (kBM * kBK * 2 + bn * kBK * 2);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kWsThreads, 1) k_gemm_ws(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB, int M, int N,
+                                                           int K, int kt_per_split, int splits, GemmEpilogue ep,
+                                                           int* __restrict__ err) {
+  constexpr int S = ws_stages(BN);
+  constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int failed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
+  const int kt_all = (K + kBK - 1) / kBK;
+  const int tiles = mt * nt * splits;
+
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kWsEpiWarps);
+    }
+    mbar_init(&mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(2 * kWsAccCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer ----
+    int it = 0;
+    for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+      const int z = t % splits, tn = (t / splits) % nt, tm = t / (splits * nt);
+      const int kt0 = z * kt_per_split, nk = min(kt_all - kt0, kt_per_split);
+      for (int kk = 0; kk < nk; ++kk, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          failed = 1;
+          break;
+        }
+        uint8_t* a = smem + s * (kABytes + kBBytes);
+        mbar_expect_tx(&full[s], kABytes + kBBytes);
+        tma_load_2d(a, &mapA, &full[s], (kt0 + kk) * kBK, tm * kBM);
+        tma_load_2d(a + kABytes, &mapB, &full[s], (kt0 + kk) * kBK, tn * BN);
+      }
+    }
+    // copies still in flight complete before the CTA can exit: the last load
+    // of every stage is consumed by the MMA thread or waited for here
+    if (failed) {
+      for (int q = max(0, it - S); q < it; ++q) mbar_wait(&full[q % S], (uint32_t)(q / S) & 1u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    constexpr uint32_t idesc = instr_desc_bf16(BN);
+    int it = 0, tc = 0;
+    for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x, ++tc) {
+      const int z = t % splits;
+      const int kt0 = z * kt_per_split, nk = min(kt_all - kt0, kt_per_split);
+      const int a = tc & 1;
+      const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+      if (!mbar_wait(&acc_empty[a], aph ^ 1u)) {
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + (uint32_t)(a * kWsAccCols);
+      bool ok = true;
+      for (int kk = 0; kk < nk; ++kk, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!mbar_wait(&full[s], ph)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint8_t* sa = smem + s * (kABytes + kBBytes);
+        const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + kABytes);
+#pragma unroll
+        for (int k4 = 0; k4 < kBK / 16; ++k4)
+          mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc, (kk > 0 || k4 > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      if (!ok) {
+        failed = 1;
+        break;
+      }
+      mma_commit(&acc_full[a]);
+    }
+    // every MMA issued by this thread has completed before tensor memory is freed
+    mma_commit(&mma_done);
+    mbar_wait(&mma_done, 0u);
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    const int ew = warp - 2, quarter = warp & 3, cg = ew >> 2;
+    constexpr int kColsPerWarp = BN / 4;
+    int tc = 0;
+    for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x, ++tc) {
+      const int z = t % splits, tn = (t / splits) % nt, tm = t / (splits * nt);
+      const int a = tc & 1;
+      const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+      const bool ok = mbar_wait(&acc_full[a], aph);
+      if (!__all_sync(0xffffffffu, ok)) {
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = tm * kBM + 32 * quarter + lane;
+      const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * kWsAccCols);
+      float* c32 = ep.c32;
+      if (EPI == kEpiF32 && c32) c32 += (int64_t)z * ep.split_stride;
+#pragma unroll 1
+      for (int c = cg * kColsPerWarp; c < (cg + 1) * kColsPerWarp; c += 16) {
+        float v[16];
+        tmem_ld16(base + (uint32_t)c, v);
+        const int col0 = tn * BN + c;
+        if (row < M && col0 < N) epilogue_chunk<EPI>(v, row, col0, N, ep, c32);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+    }
+  }
+  __syncthreads();
+  if (failed && threadIdx.x == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWsAccCols)
+                 : "memory");
   }
 }
 
@@ -321,17 +576,35 @@ CUtensorMap make_map(const void* ptr, int64_t rows, int64_t cols, int64_t ld, in
   return map;
 }
 
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  CCG_CUDA(cudaGetDevice(&dev));
+  int& v = cached[dev & 63];
+  if (!v) CCG_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+  return v;
+}
+
 template <int BN, int EPI>
-void launch_bn(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int splits, const GemmEpilogue& ep,
-               int* err, cudaStream_t s) {
-  const size_t smem = (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
-  auto kern = k_gemm_tn<BN, EPI>;
-  set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+void launch_bn(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, const GemmShape& sh,
+               const GemmEpilogue& ep, int* err, cudaStream_t s) {
   const int kt_all = (K + kBK - 1) / kBK;
-  const int per = (kt_all + splits - 1) / splits;
+  const int per = (kt_all + sh.splits - 1) / sh.splits;
   const int z = (kt_all + per - 1) / per;  // every split gets at least one K tile
-  const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN), (unsigned)z);
-  kern<<<grid, 128, smem, s>>>(a, b, M, N, K, per, ep, err);
+  if (sh.persistent) {
+    const size_t smem = (size_t)ws_stages(BN) * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
+    auto kern = k_gemm_ws<BN, EPI>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    const int64_t tiles = (int64_t)((M + kBM - 1) / kBM) * ((N + BN - 1) / BN) * z;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms());
+    kern<<<grid, kWsThreads, smem, s>>>(a, b, M, N, K, per, z, ep, err);
+  } else {
+    const size_t smem = (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
+    auto kern = k_gemm_tn<BN, EPI>;
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN), (unsigned)z);
+    kern<<<grid, 128, smem, s>>>(a, b, M, N, K, per, ep, err);
+  }
   CCG_CUDA(cudaGetLastError());
 }
 
@@ -340,24 +613,30 @@ void launch_epi(const void* A, int64_t lda, const void* B, int64_t ldb, int M, i
                 const GemmEpilogue& ep, int* err, cudaStream_t s) {
   const CUtensorMap ma = make_map(A, M, K, lda, kBM);
   switch (sh.bn) {
-    case 64: launch_bn<64, EPI>(ma, make_map(B, N, K, ldb, 64), M, N, K, sh.splits, ep, err, s); break;
-    case 128: launch_bn<128, EPI>(ma, make_map(B, N, K, ldb, 128), M, N, K, sh.splits, ep, err, s); break;
-    case 192: launch_bn<192, EPI>(ma, make_map(B, N, K, ldb, 192), M, N, K, sh.splits, ep, err, s); break;
-    default: launch_bn<256, EPI>(ma, make_map(B, N, K, ldb, 256), M, N, K, sh.splits, ep, err, s); break;
+    case 64: launch_bn<64, EPI>(ma, make_map(B, N, K, ldb, 64), M, N, K, sh, ep, err, s); break;
+    case 128: launch_bn<128, EPI>(ma, make_map(B, N, K, ldb, 128), M, N, K, sh, ep, err, s); break;
+    case 192: launch_bn<192, EPI>(ma, make_map(B, N, K, ldb, 192), M, N, K, sh, ep, err, s); break;
+    default: launch_bn<256, EPI>(ma, make_map(B, N, K, ldb, 256), M, N, K, sh, ep, err, s); break;
   }
 }
 
 }  // namespace
 
+void gelu_check(const float* x, int n, float* out, cudaStream_t s) {
+  k_erf_check<<<(n + 255) / 256, 256, 0, s>>>(x, n, out);
+  CCG_CUDA(cudaGetLastError());
+}
+
 GemmShape gemm_pick_shape(int M, int N, int K, bool allow_split) {
-  constexpr int kSlots = 2 * 152;  // about two resident CTAs per SM
+  // the persistent kernel keeps one CTA per SM; aim for at least one tile per SM
+  const int slots = num_sms();
   GemmShape sh;
   const int mt = (M + kBM - 1) / kBM;
   const int cands[4] = {256, 192, 128, 64};
   sh.bn = 64;
   for (int bn : cands) {
     if (N % bn != 0 && bn != 64) continue;
-    if ((int64_t)mt * ((N + bn - 1) / bn) >= kSlots || allow_split) {
+    if ((int64_t)mt * ((N + bn - 1) / bn) >= slots || allow_split) {
       sh.bn = bn;
       break;
     }
@@ -365,7 +644,7 @@ GemmShape gemm_pick_shape(int M, int N, int K, bool allow_split) {
   if (allow_split) {
     const int tiles = mt * ((N + sh.bn - 1) / sh.bn);
     const int kt = (K + kBK - 1) / kBK;
-    const int want = (kSlots + tiles - 1) / tiles;
+    const int want = (slots + tiles - 1) / tiles;
     sh.splits = std::max(1, std::min(want, kt / 4));
   }
   return sh;

@@ -40,19 +40,42 @@ def _bf16(rows, cols, seed, ld=None, scale=1.0):
 
 
 # ---------------------------------------------------------------- GEMM
-@pytest.mark.parametrize("M,N,K,tile,splits", [
-    (128, 64, 64, 0, 0), (300, 256, 320, 0, 0), (1000, 576, 256, 0, 0), (257, 192, 200, 0, 0),
-    (8192, 256, 576, 0, 0), (64, 128, 1000, 0, 0), (300, 256, 320, 64, 0), (300, 256, 320, 128, 0),
-    (576, 256, 8192, 0, 16), (256, 258, 1000, 64, 5), (256, 256, 4096, 128, 64)])
-def test_gemm_bf16_matches_exact_product(M, N, K, tile, splits):
+GEMM_CASES = [(128, 64, 64, 0, 0), (300, 256, 320, 0, 0), (1000, 576, 256, 0, 0), (257, 192, 200, 0, 0),
+              (8192, 256, 576, 0, 0), (64, 128, 1000, 0, 0), (300, 256, 320, 64, 0), (300, 256, 320, 128, 0),
+              (576, 256, 8192, 0, 16), (256, 258, 1000, 64, 5), (256, 256, 4096, 128, 64),
+              (40000, 256, 258, 0, 0), (20000, 576, 256, 192, 0), (5000, 64, 64, 64, 0)]
+
+
+@pytest.mark.parametrize("one_tile", [False, True], ids=["persistent", "one-tile"])
+@pytest.mark.parametrize("M,N,K,tile,splits", GEMM_CASES)
+def test_gemm_bf16_matches_exact_product(M, N, K, tile, splits, one_tile):
     ld = (K + 7) // 8 * 8
     A, An = _bf16(M, K, 1 + M, ld)
     B, Bn = _bf16(N, K, 2 + N, ld)
-    C = cc.gemm_bf16_tn(A[:, :K], B[:, :K], n_tile=tile, k_splits=splits)
+    C = cc.gemm_bf16_tn(A[:, :K], B[:, :K], n_tile=tile, k_splits=splits, one_tile_per_cta=one_tile)
     torch.cuda.synchronize()
     ref = An @ Bn.T
     err = np.abs(C.cpu().double().numpy() - ref).max()
     assert err <= 1e-5 * np.abs(ref).max() + 1e-6, err
+
+
+# ---------------------------------------------------------------- activation
+def test_activation_matches_erf_within_its_published_bound():
+    """erf by Abramowitz-Stegun 7.1.26 (|error| <= 1.5e-7) against the oracle's
+    erf (scipy, float64) and CUDA's erff through torch; GELU and GELU' against
+    the oracle's erf-form formulas."""
+    from scipy.special import erf as erf64
+    x = np.concatenate([np.linspace(-9, 9, 20001), meshgen.normal(3, np.arange(20000)) * 2]).astype(np.float32)
+    out = cc.mlp_activation(torch.from_numpy(x).cuda()).cpu().double().numpy()
+    xd = x.astype(np.float64)
+    # 1.5e-7 (the formula) + float32 evaluation (approximate reciprocal and __expf,
+    # a few ulps each, amplified by the polynomial) < 1e-6, i.e. < 1/4000 of a BF16 step
+    assert np.max(np.abs(out[:, 0] - erf64(xd))) <= 1e-6
+    ref_cuda = torch.erf(torch.from_numpy(x).cuda()).cpu().double().numpy()
+    assert np.max(np.abs(out[:, 0] - ref_cuda)) <= 1e-6
+    g, gp = mlp.gelu(xd), mlp.gelu_grad(xd)
+    assert np.max(np.abs(out[:, 1] - g) / np.maximum(1.0, np.abs(xd))) <= 1e-6
+    assert np.max(np.abs(out[:, 2] - gp)) <= 2e-6
 
 
 # ---------------------------------------------------------------- network
