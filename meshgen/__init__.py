@@ -201,6 +201,32 @@ def cantilever(nx: int, ny: int, nz: int, *, cell: float, E: float = 1e7, nu: fl
                  v0=np.zeros_like(X), h=h, gravity=np.array([0.0, -g, 0.0]), dims=dims, cell=cell)
 
 
+def twist_box(nx: int, ny: int, nz: int, *, E: float = 1e5, nu: float = 0.3, rho: float = 1000.0,
+              angle: float = 1.5707963267948966, jitter_amount: float = 0.0, seed: int = 0,
+              name: str = "twist") -> Scene:
+    """Bar along z (``nz`` cells long, unit cell size scaled so the longest
+    side is 1), both end faces clamped, the z = L face turned by ``angle``
+    about the bar's axis.  Initial guess: every cross-section turned by
+    ``angle * z / L`` (a uniform twist), so elements start far from their rest
+    orientation."""
+    cell = 1.0 / max(nx, ny, nz)
+    X = grid_vertices(nx, ny, nz, cell)
+    if jitter_amount > 0.0:
+        X = jitter(X, (nx, ny, nz), cell, jitter_amount, seed)
+    tets = kuhn_tets(nx, ny, nz)
+    L = nz * cell
+    cx, cy = 0.5 * nx * cell, 0.5 * ny * cell
+    lo = np.isclose(X[:, 2], 0.0)
+    hi = np.isclose(X[:, 2], L)
+    pinned = (lo | hi).astype(np.uint8)
+    th = angle * X[:, 2] / L
+    c, s_ = np.cos(th), np.sin(th)
+    x0 = X.copy()
+    x0[:, 0] = cx + c * (X[:, 0] - cx) - s_ * (X[:, 1] - cy)
+    x0[:, 1] = cy + s_ * (X[:, 0] - cx) + c * (X[:, 1] - cy)
+    return Scene(name, X, tets, pinned, x0, Material(E, nu, rho), dims=(nx, ny, nz), cell=cell)
+
+
 def random_box(index: int, seed: int, *, side_lo: int = 4, side_hi: int = 24, E_lo: float = 1e4,
                E_hi: float = 1e7, nu_lo: float = 0.30, nu_hi: float = 0.49, f_lo: float = 1.1,
                f_hi: float = 1.8, jitter_amount: float = 0.0, init: str = "linear") -> Scene:

@@ -120,10 +120,50 @@ def local_update(kind: str, H, g, i: int, S, U, stats: Optional[Stats] = None) -
     return -np.linalg.solve(M, gt)
 
 
+def vertex_rotations(problem: Problem, topo: Topology, x: np.ndarray) -> np.ndarray:
+    """Per-vertex rotations R_j [n, 3, 3] for corotated bases (Sec. 3.1,
+    "Accounting for Large Deformations"; the paper estimates them from the
+    displacement of each vertex's neighbourhood without giving the formula).
+    Reading: fit the neighbourhood's deformation gradient by least squares,
+    F_j = A_j C_j^{-1} with A_j = sum over the 1-ring l of (x_l - x_j)(X_l - X_j)^T
+    and C_j = sum of (X_l - X_j)(X_l - X_j)^T, and take its orthogonal polar
+    factor (scipy.linalg.polar).  This is exact for every homogeneous
+    deformation (a rigid motion gives its rotation, a pure stretch the
+    identity).  R_j = I when det F_j <= 0 (an inverted neighbourhood has no
+    proper rotation to extract)."""
+    from scipy.linalg import polar
+    X = problem.X
+    R = np.zeros((problem.n, 3, 3))
+    for j in range(problem.n):
+        nb = topo.nbr_idx[topo.nbr_ptr[j]:topo.nbr_ptr[j + 1]]
+        A = np.zeros((3, 3))
+        C = np.zeros((3, 3))
+        for l in nb:
+            A += np.outer(x[l] - x[j], X[l] - X[j])
+            C += np.outer(X[l] - X[j], X[l] - X[j])
+        F = A @ np.linalg.inv(C) if len(nb) else np.eye(3)
+        if len(nb) == 0 or not np.linalg.det(F) > 0.0:
+            R[j] = np.eye(3)
+        else:
+            R[j] = polar(F)[0]
+    return R
+
+
+def rotate_bases(sup, bases, R) -> list:
+    """U_i^rot[j] = R_j U_i[j] for every support vertex j (the rotation formula of Sec. 3.1)."""
+    return [np.einsum("aij,ajk->aik", R[np.asarray(S, dtype=np.int64)], U) if len(S) else U
+            for S, U in zip(sup, bases)]
+
+
 def sweep(problem: Problem, topo: Topology, sup, bases, x: np.ndarray, xt=None, kind: str = "cc",
-          schedule: str = "colored", stats: Optional[Stats] = None) -> np.ndarray:
-    """One iteration: Jacobi (Algorithm 1) or coloured Gauss-Seidel.  Returns new x."""
+          schedule: str = "colored", stats: Optional[Stats] = None, corotated: bool = False) -> np.ndarray:
+    """One iteration: Jacobi (Algorithm 1) or coloured Gauss-Seidel.  Returns new x.
+
+    With ``corotated`` the bases are rotated once per iteration, at its start,
+    by the rotations of the current configuration (Sec. 3.1)."""
     x = np.array(x, dtype=np.float64, copy=True)
+    if corotated:
+        bases = rotate_bases(sup, bases, vertex_rotations(problem, topo, x))
     if schedule == "colored":
         groups = topo.color_classes(free_only=True)
     elif schedule == "jacobi":
@@ -181,11 +221,14 @@ class History:
 
 def solve(problem: Problem, topo: Topology, sup, bases, x0, xt=None, kind: str = "cc",
           schedule: str = "colored", tol: float = 1e-6, max_iters: int = 100,
-          line_search: bool = False, stats: Optional[Stats] = None, min_iters: int = 0):
+          line_search: bool = False, stats: Optional[Stats] = None, min_iters: int = 0,
+          corotated: bool = False):
     """Iterate sweeps until ||g_free|| / ||g_free(x0)|| <= tol or max_iters.
 
-    With ``line_search`` (Jacobi only) the sweep's updates form a global
-    direction d and x <- x + alpha d with alpha from backtracking (Sec. 4.4)."""
+    With ``line_search`` every iteration's updates form one global direction d
+    (Jacobi: the local updates of all free vertices from g, H at x, as in
+    Algorithm 1; coloured: d = sweep(x) - x) and x <- x + alpha d with alpha
+    from backtracking on the energy (Sec. 4.4, "Sensitivity to basis quality")."""
     x = np.array(x0, dtype=np.float64, copy=True)
     g = problem.gradient(x, xt)
     hist = History([problem.energy(x, xt)], [problem.free_gradient_norm(g)])
@@ -195,11 +238,15 @@ def solve(problem: Problem, topo: Topology, sup, bases, x0, xt=None, kind: str =
             hist.converged = True
             break
         if line_search:
-            d = jacobi_direction(problem, sup, bases, x, xt, kind, stats)
+            if schedule == "jacobi":
+                B = rotate_bases(sup, bases, vertex_rotations(problem, topo, x)) if corotated else bases
+                d = jacobi_direction(problem, sup, B, x, xt, kind, stats)
+            else:
+                d = sweep(problem, topo, sup, bases, x, xt, kind, schedule, stats, corotated) - x
             a = backtracking(problem, x, d, xt)
             x = x + a * d
         else:
-            x = sweep(problem, topo, sup, bases, x, xt, kind, schedule, stats)
+            x = sweep(problem, topo, sup, bases, x, xt, kind, schedule, stats, corotated)
         g = problem.gradient(x, xt)
         hist.energy.append(problem.energy(x, xt))
         hist.grad_norm.append(problem.free_gradient_norm(g))

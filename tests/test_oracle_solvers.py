@@ -200,3 +200,76 @@ def test_normalized_residual_definition():
     g = np.linalg.norm(pb.gradient(sc.x0)[pb.free])
     r = solvers.normalized_residual(pb, g)
     assert r == pytest.approx(g / (pb.total_volume() * pb.n * 1e5))
+
+
+# ---------------------------------------------------------------- corotated bases (Sec. 3.1)
+def _rot(axis, ang):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_rotvec(np.asarray(axis, dtype=float) / np.linalg.norm(axis) * ang).as_matrix()
+
+
+def test_vertex_rotations_closed_forms():
+    sc, pb, topo = _setup(n=3, jit=0.05)
+    Q = _rot([1.0, 2.0, -0.5], 0.7)
+    R = solvers.vertex_rotations(pb, topo, pb.X @ Q.T + np.array([0.3, -1.0, 2.0]))
+    np.testing.assert_allclose(R, np.broadcast_to(Q, R.shape), rtol=0, atol=1e-12)   # rigid motion -> Q
+    S = np.diag([1.5, 0.8, 1.1])
+    R = solvers.vertex_rotations(pb, topo, pb.X @ S)                                  # pure stretch -> I
+    np.testing.assert_allclose(R, np.broadcast_to(np.eye(3), R.shape), rtol=0, atol=1e-12)
+    R = solvers.vertex_rotations(pb, topo, _state(sc, 0.02, 5))
+    for Rj in R:
+        np.testing.assert_allclose(Rj @ Rj.T, np.eye(3), rtol=0, atol=1e-12)
+        assert np.linalg.det(Rj) == pytest.approx(1.0, abs=1e-12)
+    R = solvers.vertex_rotations(pb, topo, -pb.X)                                    # inverted: det A < 0 -> I
+    np.testing.assert_allclose(R, np.broadcast_to(np.eye(3), R.shape), rtol=0, atol=0)
+
+
+def test_corotated_sweep_is_equivariant_under_rigid_rotation():
+    """E(Qx) = E(x), g(Qx) = Q g, H(Qx) = Q H Q^T and R_j(Qx) = Q R_j(x), so the
+    rotated bases carry Q and the corotated sweep commutes with Q; the fixed
+    rest bases do not."""
+    sc, pb, topo = _setup(n=3, jit=0.05, factor=1.2)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    x = _state(sc, 0.02, 7)
+    Q = _rot([0.3, -1.0, 0.4], 1.1)
+    xr = solvers.sweep(pb, topo, sup, U, x, kind="cc", corotated=True)
+    xq = solvers.sweep(pb, topo, sup, U, x @ Q.T, kind="cc", corotated=True)
+    np.testing.assert_allclose(xq, xr @ Q.T, rtol=0, atol=1e-10 * np.abs(xr).max())
+    xf = solvers.sweep(pb, topo, sup, U, x, kind="cc")
+    xfq = solvers.sweep(pb, topo, sup, U, x @ Q.T, kind="cc")
+    assert np.abs(xfq - xf @ Q.T).max() > 1e-6 * np.abs(xf - x).max()
+
+
+def test_corotated_equals_fixed_when_nothing_rotates():
+    sc, pb, topo = _setup(n=3, jit=0.05, factor=1.2)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    x = pb.X @ np.diag([1.2, 1.0, 1.0])   # a pure stretch of the rest shape: every R_j = I
+    a = solvers.sweep(pb, topo, sup, U, x, kind="cc", corotated=True)
+    b = solvers.sweep(pb, topo, sup, U, x, kind="cc")
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(b).max())
+
+
+def test_corotated_bases_help_a_twisted_bar():
+    sc = meshgen.twist_box(2, 2, 6, angle=np.pi / 2, nu=0.3)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    _, hf = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-4, max_iters=80)
+    _, hr = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-4, max_iters=80, corotated=True)
+    assert hr.converged and hr.iterations < hf.iterations
+
+
+def test_global_line_search_never_increases_the_energy():
+    """Sec. 4.4: with backtracking on the accumulated direction the energy is
+    non-increasing, here on a nearly incompressible stretch where plain
+    coloured CC blows up within a few sweeps."""
+    sc = meshgen.stretch_box(4, 3, 3, E=1e5, nu=0.45, factor=1.5, jitter_amount=0.05, seed=2)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    for schedule in ("colored", "jacobi"):
+        _, h = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", schedule=schedule, tol=1e-12, max_iters=8,
+                             line_search=True)
+        assert all(b <= a for a, b in zip(h.energy, h.energy[1:])), schedule
+    _, hp = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-12, max_iters=8)
+    assert max(hp.energy) > hp.energy[0]
