@@ -91,6 +91,13 @@ typedef struct {
   cc_precision precision;
   int32_t color_begin; /* first colour to run (0 for a whole sweep) */
   int32_t color_end;   /* one past the last colour; -1 = all.  Ignored for Jacobi. */
+  int32_t corotated;   /* 1: corotated bases (Sec. 3.1): at the start of the sweep every
+                          vertex's rotation R_j is estimated from the current x and the
+                          bases become U_i^rot[j] = R_j U_i[j].  R_j is the orthogonal
+                          polar factor of the neighbourhood's least-squares deformation
+                          gradient F_j = A_j C_j^{-1}, A_j = sum over the 1-ring of
+                          (x_l - x_j)(X_l - X_j)^T, C_j = sum of (X_l - X_j)(X_l - X_j)^T
+                          (I when det F_j <= 0). */
 } cc_sweep_opts;
 
 typedef struct {
@@ -111,6 +118,12 @@ typedef struct {
   int32_t use_graph;   /* 1: replay the check_every sweeps as one captured CUDA graph */
   double* residual_history; /* host, max_iters + 1 entries (or NULL): ||g_free|| after
                                each checked sweep, entry 0 = start; unchecked entries = -1 */
+  int32_t corotated;   /* 1: corotated bases, rotations re-estimated every sweep (see cc_sweep_opts) */
+  int32_t line_search; /* 1: global backtracking line search (Sec. 4.4): every sweep's displacement
+                          d = x_sweep - x becomes a direction, x <- x + a d with the largest
+                          a in {1, 1/2, ..., 2^-29} for which E(x + a d) <= E(x) (float64
+                          energy), a = 0 if none.  Host-synchronous, no graph replay;
+                          cc_solve_step only (cc_solve_batch rejects it). */
 } cc_step_opts;
 
 typedef struct {

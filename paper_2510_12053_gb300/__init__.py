@@ -46,7 +46,7 @@ class Material(ctypes.Structure):
 
 class SweepOpts(ctypes.Structure):
     _fields_ = [("update", ctypes.c_int), ("schedule", ctypes.c_int), ("precision", ctypes.c_int),
-                ("color_begin", ctypes.c_int32), ("color_end", ctypes.c_int32)]
+                ("color_begin", ctypes.c_int32), ("color_end", ctypes.c_int32), ("corotated", ctypes.c_int32)]
 
 
 class SweepStats(ctypes.Structure):
@@ -58,7 +58,8 @@ class StepOpts(ctypes.Structure):
     _fields_ = [("update", ctypes.c_int), ("schedule", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("min_iters", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("residual_history", ctypes.POINTER(ctypes.c_double))]
+                ("residual_history", ctypes.POINTER(ctypes.c_double)), ("corotated", ctypes.c_int32),
+                ("line_search", ctypes.c_int32)]
 
 
 class StepStats(ctypes.Structure):
@@ -272,7 +273,7 @@ class Mesh:
 
     def solve_batch(self, x, v=None, *, update: str = "cc", schedule: str = "colored", precision: str = "mixed",
                     tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0, check_every: int = 1,
-                    use_graph: bool = False) -> dict:
+                    use_graph: bool = False, corotated: bool = False) -> dict:
         B = len(self.batch_offsets()) - 1
         it = np.zeros(B, dtype=np.int32)
         status = np.zeros(B, dtype=np.int32)
@@ -283,7 +284,7 @@ class Mesh:
                         g0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         gf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, SweepStats())
         o = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters, check_every,
-                     int(use_graph), None)
+                     int(use_graph), None, int(corotated))
         rc = lib().cc_solve_batch(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
                                   ctypes.byref(st))
         if rc not in (OK, ERR_NOT_CONVERGED):
@@ -394,8 +395,8 @@ class Mesh:
         return e.value, grad, gn.value
 
     def sweep(self, x, xtilde=None, update: str = "cc", schedule: str = "colored", precision: str = "fp64",
-              color_begin: int = 0, color_end: int = -1) -> SweepStats:
-        o = SweepOpts(UPDATE[update], SCHED[schedule], PREC[precision], color_begin, color_end)
+              color_begin: int = 0, color_end: int = -1, corotated: bool = False) -> SweepStats:
+        o = SweepOpts(UPDATE[update], SCHED[schedule], PREC[precision], color_begin, color_end, int(corotated))
         st = SweepStats()
         _check(lib().cc_sweep(self._h, _dev3n(x, self.n, "x"), _dev3n(xtilde, self.n, "xtilde"),
                               ctypes.byref(o), ctypes.byref(st)))
@@ -403,11 +404,13 @@ class Mesh:
 
     def solve_step(self, x, v=None, *, update: str = "cc", schedule: str = "colored", precision: str = "mixed",
                    tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0, check_every: int = 1,
-                   use_graph: bool = False, history: bool = False) -> SolveResult:
+                   use_graph: bool = False, history: bool = False, corotated: bool = False,
+                   line_search: bool = False) -> SolveResult:
         hist = np.full(max_iters + 1, -1.0) if history else None
         o = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters, check_every,
                      int(use_graph),
-                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None)
+                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
+                     int(corotated), int(line_search))
         st = StepStats()
         rc = lib().cc_solve_step(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
                                  ctypes.byref(st))

@@ -181,6 +181,13 @@ void solve_list(Mesh& m, const cc_sweep_opts& o, const int32_t* verts, int64_t c
 // One sweep over colours [cb, ce).  `fresh` means g and H already hold the
 // derivatives at x (no refresh needed before the first colour).
 void sweep_body(Mesh& m, double* x, const double* xt, const cc_sweep_opts& o, int cb, int ce, bool fresh) {
+  m.rot_active = o.corotated != 0 && o.update != CC_UPDATE_CD;
+  if (m.rot_active) {
+    // corotated bases: rotations of the configuration at the start of the sweep (Sec. 3.1)
+    const int e0 = prof_event(m);
+    launch_rotations(m, x, o.precision == CC_PREC_MIXED, m.stream);
+    prof_close(m, P_SOLVE, e0, 1);
+  }
   if (o.schedule == CC_SCHED_JACOBI) {
     if (!fresh) refresh_all(m, o.precision, x, xt);
     solve_list(m, o, m.d_free_rows.p, m.n_free, x);
@@ -515,7 +522,7 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
     CCG_CHECK(o->max_iters >= 0 && o->min_iters >= 0 && o->tol >= 0, CC_ERR_INVALID_ARG, "bad iteration limits");
     CCG_CHECK((m->h > 0.0) == (v != nullptr), CC_ERR_INVALID_ARG,
               "v must be given exactly for dynamic meshes (h > 0)");
-    cc_sweep_opts so{o->update, o->schedule, o->precision, 0, -1};
+    cc_sweep_opts so{o->update, o->schedule, o->precision, 0, -1, o->corotated};
     int cb, ce;
     check_sweep_opts(*m, so, &cb, &ce);
     ensure_state(*m, o->precision);
@@ -560,11 +567,11 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
     std::string key;
     if (graph) {
       char buf[256];
-      std::snprintf(buf, sizeof(buf), "step %p %p %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
-                    (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0);
+      std::snprintf(buf, sizeof(buf), "step %p %p %d %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
+                    (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0, (int)o->corotated);
       key = buf;
     }
-    while (!conv && it < o->max_iters) {
+    while (!conv && it < o->max_iters && !o->line_search) {
       const int chunk = std::min(every, o->max_iters - it);
       const bool replay = graph && chunk == every && it > 0;
       run_chunk(*m, x, xt, so, cb, ce, chunk, replay, key, false);
@@ -574,6 +581,46 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
       if (o->residual_history) o->residual_history[it] = gcur;
       CCG_CHECK(std::isfinite(gcur), CC_ERR_NUMERIC, "non-finite residual");
       if (it >= o->min_iters && gcur <= o->tol * g0) conv = true;
+    }
+    // Global backtracking line search (Sec. 4.4): the sweep's displacement is
+    // the direction, the step the largest 2^-k (k < 30) that does not raise E.
+    if (o->line_search && !conv && it < o->max_iters) {
+      if (!m->d_xls0.p) {
+        m->d_xls0.alloc(3 * n);
+        m->d_xls1.alloc(3 * n);
+      }
+      auto energy_at = [&](const double* xe) {
+        const int ee = prof_event(*m);
+        launch_energy(*m, xe, xt, m->d_scalars.p + 1, s);
+        prof_close(*m, P_RED, ee, dyn ? 3 : 2);
+        return read_scalar(*m, m->d_scalars.p + 1);
+      };
+      while (!conv && it < o->max_iters) {
+        CCG_CUDA(cudaMemcpyAsync(m->d_xls0.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        const double E0 = energy_at(x);
+        sweep_body(*m, x, xt, so, cb, ce, true);  // g, H are current at x (refreshed below)
+        CCG_CUDA(cudaMemcpyAsync(m->d_xls1.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        double a = 1.0;
+        bool found = false;
+        for (int k = 0; k < 30; ++k) {
+          if (k > 0) launch_line_point(m->d_xls0.p, m->d_xls1.p, n, a, x, s);
+          const double E1 = energy_at(x);
+          if (E1 <= E0) {
+            found = true;
+            break;
+          }
+          a *= 0.5;
+        }
+        if (!found) CCG_CUDA(cudaMemcpyAsync(x, m->d_xls0.p, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (o->precision == CC_PREC_MIXED) split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
+        refresh_all(*m, o->precision, x, xt);
+        gnorm(*m, o->precision, nullptr, m->d_scalars.p);
+        ++it;
+        gcur = std::sqrt(read_scalar(*m, m->d_scalars.p));
+        if (o->residual_history) o->residual_history[it] = gcur;
+        CCG_CHECK(std::isfinite(gcur), CC_ERR_NUMERIC, "non-finite residual");
+        if (it >= o->min_iters && gcur <= o->tol * g0) conv = true;
+      }
     }
     int e1 = prof_event(*m);
     launch_energy(*m, x, xt, m->d_scalars.p + 1, s);
@@ -707,12 +754,13 @@ cc_status cc_batch_offsets(const cc_mesh* m, int64_t* offsets, int32_t* count) {
 cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o, cc_batch_stats* st) {
   try {
     ccg::g_last_error.clear();
+    CCG_CHECK(!o || !o->line_search, CC_ERR_INVALID_ARG, "the line search runs in cc_solve_step only");
     CCG_CHECK(m && x && o && st && st->iterations && st->status && st->g0 && st->g_final, CC_ERR_INVALID_ARG,
               "NULL argument");
     CCG_CHECK(o->max_iters >= 0 && o->min_iters >= 0 && o->tol >= 0, CC_ERR_INVALID_ARG, "bad iteration limits");
     CCG_CHECK((m->h > 0.0) == (v != nullptr), CC_ERR_INVALID_ARG,
               "v must be given exactly for dynamic meshes (h > 0)");
-    cc_sweep_opts so{o->update, o->schedule, o->precision, 0, -1};
+    cc_sweep_opts so{o->update, o->schedule, o->precision, 0, -1, o->corotated};
     int cb, ce;
     check_sweep_opts(*m, so, &cb, &ce);
     ensure_state(*m, o->precision);
@@ -760,8 +808,8 @@ cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o
     std::string key;
     if (graph) {
       char buf[256];
-      std::snprintf(buf, sizeof(buf), "batch %p %p %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
-                    (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0);
+      std::snprintf(buf, sizeof(buf), "batch %p %p %d %d %d %d %d %d", (void*)x, (const void*)xt, (int)o->precision,
+                    (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0, (int)o->corotated);
       key = buf;
     }
     int it = 0;

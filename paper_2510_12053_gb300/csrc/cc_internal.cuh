@@ -94,6 +94,7 @@ struct StateF64 {
   DBuf<double> bsr;   // [nnz_up][12] upper Hessian blocks, rows padded to 4
   DBuf<double> U;     // [sup_total][9]
   DBuf<double> cpl;   // [n_free][32] coupling products of the vertices being solved
+  DBuf<double> rot;   // [n][9] per-vertex rotations of corotated bases
 };
 
 struct StateMixed {
@@ -104,6 +105,7 @@ struct StateMixed {
   DBuf<float> bsr;    // [nnz_up][12]
   DBuf<float> U;      // [sup_total][9]
   DBuf<float> cpl;    // [n_free][32]
+  DBuf<float> rot;    // [n][9] per-vertex rotations of corotated bases
   DBuf<float4> x_hi;  // [n] position mirror, float-float split
   DBuf<float4> x_lo;
   DBuf<float4> xt_hi; // inertial target mirror
@@ -219,6 +221,8 @@ struct Mesh {
   DBuf<uint8_t> d_smap8;
   DBuf<uint16_t> d_smap16;
   DBuf<int4> d_vt_ids;       // [4T] vertex ids of the tet at each (vertex, slot) entry
+  DBuf<double> d_Xrest;      // [3][n] rest positions (uploaded on first use)
+  bool rot_active = false;   // the current sweep uses corotated bases
 
   StateF64 f64;
   StateMixed mx;
@@ -229,6 +233,8 @@ struct Mesh {
   DBuf<unsigned long long> d_counters; // [4] fallback counters + [4] error flags
   DBuf<double> d_xtilde;     // [3][n] dynamic target (solve_step)
   DBuf<double> d_xold;       // [3][n]
+  DBuf<double> d_xls0;       // [3][n] line search: x before the sweep
+  DBuf<double> d_xls1;       // [3][n] line search: x after the sweep
   double* h_pinned_scalars = nullptr; // pinned host [8]
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key;
@@ -296,6 +302,8 @@ void launch_local_solve_f64(Mesh& m, cc_update upd, const int32_t* verts, int64_
                             double* x, SweepCounters c, cudaStream_t s);
 void launch_local_solve_mixed(Mesh& m, cc_update upd, const int32_t* verts, int64_t count,
                               double* x, SweepCounters c, cudaStream_t s);
+// per-vertex rotations of the corotated bases at x (float64 or float32 result)
+void launch_rotations(Mesh& m, const double* x, bool mixed, cudaStream_t s);
 // reductions
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out_scalar,
                    cudaStream_t s);
@@ -308,6 +316,8 @@ void launch_inertial_target(const double* x, const double* v, int64_t n, double 
                             const double* grav, double* xt, cudaStream_t s);
 void launch_velocity(const double* x, const double* xold, int64_t n, double h, double* v,
                      cudaStream_t s);
+// x = x0 + alpha (x1 - x0), all 3n entries (line search trial point)
+void launch_line_point(const double* x0, const double* x1, int64_t n, double alpha, double* x, cudaStream_t s);
 // colouring and subspace build
 void run_coloring(Mesh& m);
 void run_subspace_build(Mesh& m, int32_t k);

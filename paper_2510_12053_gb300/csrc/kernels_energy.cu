@@ -537,6 +537,14 @@ __global__ void k_velocity(const double* __restrict__ x, const double* __restric
   v[k] = (x[k] - xold[k]) / h;
 }
 
+__global__ void k_line_point(const double* __restrict__ x0, const double* __restrict__ x1, int64_t n, double alpha,
+                             double* __restrict__ x) {
+  pdl_entry();
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= 3 * n) return;
+  x[k] = x0[k] + alpha * (x1[k] - x0[k]);
+}
+
 constexpr int kRedBlocks = 1024;
 
 }  // namespace
@@ -628,6 +636,10 @@ void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStr
 void launch_inertial_target(const double* x, const double* v, int64_t n, double h, const double* grav, double* xt,
                             cudaStream_t s) {
   k_inertial_target<<<grid_for(n), kBlock, 0, s>>>(x, v, n, h, grav[0], grav[1], grav[2], xt);
+}
+
+void launch_line_point(const double* x0, const double* x1, int64_t n, double alpha, double* x, cudaStream_t s) {
+  pdl_launch(k_line_point, grid_for(3 * n), kBlock, 0, s, x0, x1, n, alpha, x);
 }
 
 void launch_velocity(const double* x, const double* xold, int64_t n, double h, double* v, cudaStream_t s) {

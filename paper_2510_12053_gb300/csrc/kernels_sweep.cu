@@ -14,6 +14,8 @@
 // gives, for every block it reads, the support slot of the block's column.
 // Same-coloured vertices share no tet, and this kernel reads only g, H and U,
 // so writing x in place is race-free for both schedules.
+#include <vector>
+
 #include "cc_internal.cuh"
 #include "dmath.cuh"
 
@@ -75,6 +77,31 @@ struct SlotCodes<uint16_t> {
   static constexpr unsigned kNone = 0xFFFF, kSelf = 0xFFFE, kDiag = 0xFFFD;
 };
 
+// Stages U_i in shared memory, rotated for corotated bases (Sec. 3.1):
+// U_i^rot[j] = R_j U_i[j] (rot: [n][9] row-major rotations, or nullptr).
+template <typename HT>
+__device__ __forceinline__ void stage_basis(HT* Us, const HT* __restrict__ U, const HT* __restrict__ rot,
+                                            const int32_t* __restrict__ sup_idx, int s0, int m, int t, int nt) {
+  if (!rot) {
+    for (int k = t; k < 9 * m; k += nt) Us[k] = U[(int64_t)s0 * 9 + k];
+    return;
+  }
+  for (int a = t; a < m; a += nt) {
+    const HT* R = rot + 9 * (int64_t)sup_idx[s0 + a];
+    const HT* Ua = U + (int64_t)(s0 + a) * 9;
+    HT r[9], u[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      r[q] = R[q];
+      u[q] = Ua[q];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Us[9 * a + 3 * i + d] = r[3 * i] * u[d] + r[3 * i + 1] * u[3 + d] + r[3 * i + 2] * u[6 + d];
+  }
+}
+
 // Coupling products, one CTA per free vertex i of the list.  Quarter-warps take
 // the block rows of the support S and of i itself; their lanes take the row's
 // upper blocks (H_jl, l >= j).  The vertex's slot map (one code per block,
@@ -90,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
     const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, int64_t smap_max,
-    HT* __restrict__ cpl) {
+    const HT* __restrict__ rot, HT* __restrict__ cpl) {
   pdl_entry();
   using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -116,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   const int64_t c0 = smap_ptr[i];
   const int ncodes = (int)(smap_ptr[i + 1] - c0);
 
-  for (int k = tid; k < 9 * m; k += kThreads) Us[k] = U[(int64_t)s0 * 9 + k];
+  stage_basis<HT>(Us, U, rot, sup_idx, s0, m, tid, kThreads);
   for (int k = tid; k < ncodes; k += kThreads) codes[k] = smap[c0 + k];
   for (int s = tid; s <= m; s += kThreads) {
     const int j = s < m ? sup_idx[s0 + s] : i;
@@ -222,7 +249,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_couple_warp(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
-    const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, HT* __restrict__ cpl) {
+    const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, const HT* __restrict__ rot,
+    HT* __restrict__ cpl) {
   pdl_entry();
   using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -241,7 +269,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_couple_warp(
   const int s0 = sup_ptr[i];
   const int m = sup_ptr[i + 1] - s0;
   const int64_t c0 = smap_ptr[i];
-  for (int q = lane; q < 9 * m; q += 32) Us[q] = U[(int64_t)s0 * 9 + q];
+  stage_basis<HT>(Us, U, rot, sup_idx, s0, m, lane, 32);
   // row starts and the exclusive prefix of the row lengths (rows 0..m-1 = S, row m = i)
   int carry = 0;
   for (int base = 0; base <= m; base += 32) {
@@ -485,7 +513,7 @@ __global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, con
 
 template <typename HT, bool kMixed, int kUpd, int kThreads>
 void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
-                   const float* g_hi, HT* cpl, cudaStream_t s) {
+                   const float* g_hi, HT* cpl, const HT* rot, cudaStream_t s) {
   const int supm = m.sup_max > 0 ? m.sup_max : 1;
   const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
   const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
@@ -495,20 +523,20 @@ void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, co
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, cpl);
+               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, cpl);
   } else {
     auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, cpl);
+               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, cpl);
   }
   CCG_CUDA(cudaGetLastError());
 }
 
 template <typename HT, bool kMixed, int kUpd>
 void launch_couple_warp(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
-                        const float* g_hi, HT* cpl, cudaStream_t s) {
+                        const float* g_hi, HT* cpl, const HT* rot, cudaStream_t s) {
   constexpr int kWarps = 4;
   const int supm = m.sup_max > 0 ? m.sup_max : 1;
   const size_t smem = warp_smem_bytes<HT>(supm, kWarps);
@@ -519,13 +547,13 @@ void launch_couple_warp(Mesh& m, const int32_t* verts, int64_t count, const HT* 
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, grid, 32 * kWarps, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, cpl);
+               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, rot, cpl);
   } else {
     auto kern = k_couple_warp<HT, uint8_t, kMixed, kUpd, kWarps>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, grid, 32 * kWarps, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, cpl);
+               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, rot, cpl);
   }
   CCG_CUDA(cudaGetLastError());
 }
@@ -536,11 +564,16 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
   float4* xh = kMixed ? m.mx.x_hi.p : nullptr;
   float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
   if (kUpd != CC_UPDATE_CD) {
+    const HT* rot = nullptr;
+    if (m.rot_active) {
+      if constexpr (kMixed) rot = reinterpret_cast<const HT*>(m.mx.rot.p);
+      else rot = reinterpret_cast<const HT*>(m.f64.rot.p);
+    }
     switch (m.tune_couple_threads) {
-      case 32: launch_couple_warp<HT, kMixed, kUpd>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
-      case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
-      case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, s); break;
-      default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, s);
+      case 32: launch_couple_warp<HT, kMixed, kUpd>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
+      case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
+      case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
+      default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s);
     }
   }
   const unsigned grid = (unsigned)((count + 127) / 128);
@@ -558,6 +591,114 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
 }
 
 }  // namespace
+
+namespace {
+
+// Per-vertex rotations of corotated bases (Sec. 3.1), one thread per vertex:
+// F_j = A_j C_j^{-1} with A_j = sum over the 1-ring (ascending) of
+// (x_l - x_j)(X_l - X_j)^T and C_j = sum of (X_l - X_j)(X_l - X_j)^T (the
+// neighbourhood's least-squares deformation gradient, exact for homogeneous
+// deformations); R_j = orthogonal polar factor of F_j by Newton's iteration
+// Y <- (g Y + (g Y)^{-T}) / 2 with Higham's scaling g = sqrt(|Y^{-1}|_F / |Y|_F),
+// stopped when the update is below 64 units of roundoff of T (at most 40
+// steps); R_j = I when det F_j <= 0.  The sums are float64; the iteration
+// runs in T (float64 for the plain path, float32 for the mixed one).
+template <typename T>
+__device__ __forceinline__ T inv3(const T* a, T* o) {  // o = a^{-1}, returns det a
+  const T c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const T det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  const T id = T(1) / det;
+  o[0] = c00 * id; o[3] = c01 * id; o[6] = c02 * id;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+  return det;
+}
+
+template <typename T>
+__global__ void k_rotations(int64_t n, const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                            const double* __restrict__ x, const double* __restrict__ X, T* __restrict__ R) {
+  pdl_entry();
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, C[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const double xj[3] = {x[j], x[n + j], x[2 * n + j]}, Xj[3] = {X[j], X[n + j], X[2 * n + j]};
+  const int p0 = nbr_ptr[j], p1 = nbr_ptr[j + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int l = nbr_idx[p];
+    const double dx[3] = {x[l] - xj[0], x[n + l] - xj[1], x[2 * n + l] - xj[2]};
+    const double dX[3] = {X[l] - Xj[0], X[n + l] - Xj[1], X[2 * n + l] - Xj[2]};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A[3 * r + c] = fma(dx[r], dX[c], A[3 * r + c]);
+        C[3 * r + c] = fma(dX[r], dX[c], C[3 * r + c]);
+      }
+  }
+  T out[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};
+  double Ci[9];
+  if (p1 > p0 && inv3(C, Ci) > 0.0) {
+    T Y[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Y[3 * r + c] = (T)(A[3 * r] * Ci[c] + A[3 * r + 1] * Ci[3 + c] + A[3 * r + 2] * Ci[6 + c]);
+    T Yi[9];
+    if (inv3(Y, Yi) > T(0)) {
+      const T tol = T(64) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08));
+      for (int it = 0; it < 40; ++it) {
+        T ny = 0, ni = 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          ny += Y[q] * Y[q];
+          ni += Yi[q] * Yi[q];
+        }
+        const T g = sqrt(sqrt(ni / ny));
+        T dn = 0, yn = 0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T v = T(0.5) * (g * Y[3 * r + c] + Yi[3 * c + r] / g);  // (g Y + (g Y)^{-T}) / 2
+            dn += (v - Y[3 * r + c]) * (v - Y[3 * r + c]);
+            yn += v * v;
+            Y[3 * r + c] = v;
+          }
+        if (dn <= tol * tol * yn) break;
+        inv3(Y, Yi);
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) out[q] = Y[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) R[9 * j + q] = out[q];
+}
+
+}  // namespace
+
+void launch_rotations(Mesh& m, const double* x, bool mixed, cudaStream_t s) {
+  if (!m.d_Xrest.p) {
+    std::vector<double> soa(3 * m.n);
+    for (int64_t j = 0; j < m.n; ++j)
+      for (int a = 0; a < 3; ++a) soa[a * m.n + j] = m.X[3 * j + a];
+    m.d_Xrest.upload(soa, s);
+  }
+  const unsigned grid = (unsigned)((m.n + 127) / 128);
+  if (mixed) {
+    if (!m.mx.rot.p) m.mx.rot.alloc(9 * m.n);
+    pdl_launch(k_rotations<float>, grid, 128, 0, s, m.n, (const int32_t*)m.d_nbr_ptr.p, (const int32_t*)m.d_nbr_idx.p,
+               x, (const double*)m.d_Xrest.p, m.mx.rot.p);
+  } else {
+    if (!m.f64.rot.p) m.f64.rot.alloc(9 * m.n);
+    pdl_launch(k_rotations<double>, grid, 128, 0, s, m.n, (const int32_t*)m.d_nbr_ptr.p,
+               (const int32_t*)m.d_nbr_idx.p, x, (const double*)m.d_Xrest.p, m.f64.rot.p);
+  }
+}
 
 void launch_local_solve_f64(Mesh& m, cc_update upd, const int32_t* verts, int64_t count, double* x,
                             SweepCounters c, cudaStream_t s) {

@@ -299,3 +299,80 @@ def test_errors_are_reported_not_raised_from_c():
     with pytest.raises(cc.CCError) as e:
         cc.Mesh(scene.X, scene.tets, scene.pinned, E=1e5, nu=0.5)
     assert e.value.status == cc.ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- corotated bases (Sec. 3.1)
+@pytest.mark.parametrize("schedule", ["colored", "jacobi"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_corotated_sweep_matches_oracle(schedule, precision):
+    scene = meshgen.twist_box(3, 3, 6, angle=np.pi / 2, nu=0.3, jitter_amount=0.05, seed=4)
+    pb, topo, sup, U = _oracle(scene, 2)
+    x0 = scene.x0
+    x_o = solvers.sweep(pb, topo, sup, U, x0, None, "cc", schedule, corotated=True)
+    x_f = solvers.sweep(pb, topo, sup, U, x0, None, "cc", schedule)
+    m = _gpu(scene, 2)
+    xd = cc.to_soa(x0)
+    m.sweep(xd, update="cc", schedule=schedule, precision=precision, corotated=True)
+    x_g = cc.from_soa(xd)
+    d_o, d_g = x_o - x0, x_g - x0
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert np.abs(d_g - d_o).max() <= tol * np.abs(d_o).max()
+    if precision == "fp64":
+        assert np.abs(x_g - x_o).max() <= 1e-12 * np.abs(x_o).max()
+    assert np.abs(x_f - x_o).max() > 1e-3 * np.abs(d_o).max()    # the rotation matters here
+
+
+def test_corotated_solve_follows_the_oracle_and_beats_fixed_bases():
+    scene = meshgen.twist_box(3, 3, 8, angle=np.pi / 2, nu=0.3)
+    pb, topo, sup, U = _oracle(scene, 2)
+    _, h_o = solvers.solve(pb, topo, sup, U, scene.x0, kind="cc", tol=1e-6, max_iters=200, corotated=True)
+    m = _gpu(scene, 2)
+    res = {}
+    for corot in (False, True):
+        xd = cc.to_soa(scene.x0)
+        res[corot] = m.solve_step(xd, precision="mixed", tol=1e-6, max_iters=200, corotated=corot,
+                                  use_graph=True, check_every=1)
+    assert h_o.converged and res[True].converged
+    assert abs(res[True].iterations - h_o.iterations) <= 2
+    assert res[True].iterations < res[False].iterations
+
+
+# ---------------------------------------------------------------- global line search (Sec. 4.4)
+def test_line_search_follows_the_oracle_where_plain_cc_blows_up():
+    scene = meshgen.stretch_box(4, 3, 3, E=1e5, nu=0.45, factor=1.5, jitter_amount=0.05, seed=2)
+    pb, topo, sup, U = _oracle(scene, 2)
+    iters = 8
+    _, h_o = solvers.solve(pb, topo, sup, U, scene.x0, kind="cc", tol=1e-12, max_iters=iters, line_search=True)
+    m = _gpu(scene, 2)
+    xd = cc.to_soa(scene.x0)
+    r = m.solve_step(xd, precision="fp64", tol=1e-12, max_iters=iters, line_search=True, history=True)
+    hist = r.residuals[:iters + 1]
+    np.testing.assert_allclose(hist, h_o.grad_norm, rtol=1e-8)
+    assert r.energy == pytest.approx(h_o.energy[-1], rel=1e-10)
+    assert h_o.energy[-1] <= h_o.energy[0]
+    # mixed precision: finite and energy-decreasing where the plain mixed solve is not
+    xm = cc.to_soa(scene.x0)
+    e0 = m.energy_grad(cc.to_soa(scene.x0), precision="fp64", want_grad=False)[0]
+    rm = m.solve_step(xm, precision="mixed", tol=1e-12, max_iters=iters, line_search=True)
+    assert np.isfinite(rm.g_final) and rm.energy <= e0
+    xp = cc.to_soa(scene.x0)
+    try:
+        rp = m.solve_step(xp, precision="mixed", tol=1e-12, max_iters=iters)
+        blew_up = rp.g_final > 10 * rp.g0
+    except cc.CCError:
+        blew_up = True
+    assert blew_up
+
+
+def test_batch_rejects_the_line_search():
+    scenes = [meshgen.stretch_box(3, 3, 3, E=1e5, nu=0.3)] * 2
+    b = cc.Mesh.from_scenes(scenes)
+    b.color()
+    b.build_subspace(2)
+    x = cc.to_soa(np.concatenate([sc.x0 for sc in scenes]))
+    with pytest.raises(cc.CCError):
+        lib_opts = dict(precision="mixed", tol=1e-6, max_iters=4)
+        o = cc.StepOpts(cc.UPDATE["cc"], cc.SCHED["colored"], cc.PREC["mixed"], 1e-6, 4, 0, 1, 0, None, 0, 1)
+        st = cc.BatchStats()
+        rc = cc.lib().cc_solve_batch(b._h, x.data_ptr(), None, cc.ctypes.byref(o), cc.ctypes.byref(st))
+        cc._check(rc)
