@@ -119,6 +119,8 @@ typedef struct {
   double* residual_history; /* host, max_iters + 1 entries (or NULL): ||g_free|| after
                                each checked sweep, entry 0 = start; unchecked entries = -1 */
   int32_t corotated;   /* 1: corotated bases, rotations re-estimated every sweep (see cc_sweep_opts) */
+  int32_t restart_every; /* > 0: restarted CC, the bases are rebuilt from the Hessian at the
+                            current x (cc_build_subspace_at) before sweeps r, 2r, ... */
   int32_t line_search; /* 1: global backtracking line search (Sec. 4.4): every sweep's displacement
                           d = x_sweep - x becomes a direction, x <- x + a d with the largest
                           a in {1, 1/2, ..., 2^-29} for which E(x + a d) <= E(x) (float64
@@ -193,6 +195,13 @@ cc_status cc_color(cc_mesh* mesh, int32_t* colors_out, int32_t* num_colors);
  * Dense float64 Cholesky per patch on the GPU.  k_ring in [1, 4].
  * Requires cc_color first (CC_ERR_STATE otherwise). */
 cc_status cc_build_subspace(cc_mesh* mesh, int32_t k_ring);
+
+/* Restarted bases (Sec. 4.4, "Subspace quality"): rebuilds every U_i on its
+ * current support from the Hessian at x_dev (device [3][n] float64) instead
+ * of the rest configuration, in place.  A patch whose H_PP is not positive
+ * definite (dense Cholesky) keeps its current basis; kept (host, may be NULL)
+ * receives their number.  Requires a subspace (cc_build_subspace). */
+cc_status cc_build_subspace_at(cc_mesh* mesh, const double* x_dev, int64_t* kept);
 
 /* Replaces the bases with caller-supplied ones (e.g. noisy or learned):
  * sup_ptr host [n+1] int64, sup_idx host [sup_ptr[n]] int32 (ascending,

@@ -222,13 +222,16 @@ class History:
 def solve(problem: Problem, topo: Topology, sup, bases, x0, xt=None, kind: str = "cc",
           schedule: str = "colored", tol: float = 1e-6, max_iters: int = 100,
           line_search: bool = False, stats: Optional[Stats] = None, min_iters: int = 0,
-          corotated: bool = False):
+          corotated: bool = False, restart_every: int = 0):
     """Iterate sweeps until ||g_free|| / ||g_free(x0)|| <= tol or max_iters.
 
     With ``line_search`` every iteration's updates form one global direction d
     (Jacobi: the local updates of all free vertices from g, H at x, as in
     Algorithm 1; coloured: d = sweep(x) - x) and x <- x + alpha d with alpha
-    from backtracking on the energy (Sec. 4.4, "Sensitivity to basis quality")."""
+    from backtracking on the energy (Sec. 4.4, "Sensitivity to basis quality").
+    With ``restart_every`` = r > 0 the bases are rebuilt from the Hessian at
+    the current x before iterations r, 2r, ... (restarted CC, Sec. 4.4)."""
+    from .subspace import rebuild_bases_at
     x = np.array(x0, dtype=np.float64, copy=True)
     g = problem.gradient(x, xt)
     hist = History([problem.energy(x, xt)], [problem.free_gradient_norm(g)])
@@ -237,6 +240,8 @@ def solve(problem: Problem, topo: Topology, sup, bases, x0, xt=None, kind: str =
         if it >= min_iters and (g0 == 0.0 or hist.grad_norm[-1] <= tol * g0):
             hist.converged = True
             break
+        if restart_every > 0 and it > 0 and it % restart_every == 0:
+            bases, _ = rebuild_bases_at(problem, sup, bases, x)
         if line_search:
             if schedule == "jacobi":
                 B = rotate_bases(sup, bases, vertex_rotations(problem, topo, x)) if corotated else bases

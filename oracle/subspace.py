@@ -57,6 +57,32 @@ def build_local_bases(problem: Problem, topo: Topology, k: int, x=None) -> Tuple
     return sup, bases
 
 
+def rebuild_bases_at(problem: Problem, sup, bases, x) -> Tuple[List[np.ndarray], int]:
+    """Restarted bases (Sec. 4.4, "Subspace quality"): Eq. 5 on the same
+    supports with the Hessian at the current configuration x.  Reading (the
+    paper is silent on indefinite patches): a patch whose H_PP is not
+    positive definite (plain Cholesky fails) keeps its current basis.
+    Returns (bases, number of patches kept)."""
+    H = problem.hessian(x)
+    out, kept = [], 0
+    for i in range(problem.n):
+        S = sup[i]
+        if not problem.free[i] or len(S) == 0:
+            out.append(bases[i])
+            continue
+        P = dofs(S)
+        Hr = H[P]
+        H_PP = Hr[:, P].toarray()
+        try:
+            np.linalg.cholesky(H_PP)
+        except np.linalg.LinAlgError:
+            out.append(bases[i])
+            kept += 1
+            continue
+        out.append((-np.linalg.solve(H_PP, Hr[:, dofs([i])].toarray())).reshape(len(S), 3, 3))
+    return out, kept
+
+
 def global_basis(problem: Problem, H, i: int) -> Tuple[np.ndarray, np.ndarray]:
     """Eq. 5 over all complementary free DOFs: (support, [|S|, 3, 3])."""
     S = np.array([j for j in range(problem.n) if problem.free[j] and j != i], dtype=np.int64)

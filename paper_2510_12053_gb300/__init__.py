@@ -59,7 +59,7 @@ class StepOpts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("min_iters", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("residual_history", ctypes.POINTER(ctypes.c_double)), ("corotated", ctypes.c_int32),
-                ("line_search", ctypes.c_int32)]
+                ("restart_every", ctypes.c_int32), ("line_search", ctypes.c_int32)]
 
 
 class StepStats(ctypes.Structure):
@@ -124,6 +124,7 @@ _SIGS = {
     "cc_color": (ctypes.c_int, [_P, _P, _P]),
     "cc_build_subspace": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_set_subspace": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cc_build_subspace_at": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
     "cc_energy_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "cc_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SweepOpts), ctypes.POINTER(SweepStats)]),
     "cc_solve_step": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(StepStats)]),
@@ -318,6 +319,12 @@ class Mesh:
     def build_subspace(self, k: int):
         _check(lib().cc_build_subspace(self._h, int(k)))
 
+    def build_subspace_at(self, x) -> int:
+        """Restarted bases from the Hessian at x; returns how many patches kept their basis."""
+        kept = ctypes.c_int64()
+        _check(lib().cc_build_subspace_at(self._h, _dev3n(x, self.n, "x"), ctypes.byref(kept)))
+        return kept.value
+
     def set_subspace(self, sup_ptr, sup_idx, U):
         sp = np.ascontiguousarray(sup_ptr, dtype=np.int64)
         si = np.ascontiguousarray(sup_idx, dtype=np.int32)
@@ -405,12 +412,12 @@ class Mesh:
     def solve_step(self, x, v=None, *, update: str = "cc", schedule: str = "colored", precision: str = "mixed",
                    tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0, check_every: int = 1,
                    use_graph: bool = False, history: bool = False, corotated: bool = False,
-                   line_search: bool = False) -> SolveResult:
+                   line_search: bool = False, restart_every: int = 0) -> SolveResult:
         hist = np.full(max_iters + 1, -1.0) if history else None
         o = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters, check_every,
                      int(use_graph),
                      hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
-                     int(corotated), int(line_search))
+                     int(corotated), int(restart_every), int(line_search))
         st = StepStats()
         rc = lib().cc_solve_step(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
                                  ctypes.byref(st))

@@ -429,6 +429,16 @@ cc_status cc_build_subspace(cc_mesh* m, int32_t k) {
   })
 }
 
+cc_status cc_build_subspace_at(cc_mesh* m, const double* x, int64_t* kept) {
+  CC_API_BODY("cc_build_subspace_at", {
+    CCG_CHECK(m && x, CC_ERR_INVALID_ARG, "NULL argument");
+    CCG_CHECK(m->k_ring != 0 && m->f64.U.p, CC_ERR_STATE, "cc_build_subspace must run first");
+    ensure_state(*m, CC_PREC_FP64);
+    const int64_t k = ccg::rebuild_bases_at(*m, x);
+    if (kept) *kept = k;
+  })
+}
+
 cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup_idx, const double* U) {
   CC_API_BODY("cc_set_subspace", {
     CCG_CHECK(m && sup_ptr && U, CC_ERR_INVALID_ARG, "NULL argument");
@@ -571,8 +581,20 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
                     (int)o->schedule, (int)o->update, every, m->prof.on ? 1 : 0, (int)o->corotated);
       key = buf;
     }
+    const int restart = std::max(0, o->restart_every);
+    auto maybe_restart = [&]() {
+      if (restart > 0 && it > 0 && it % restart == 0) {
+        // restarted CC: bases from the Hessian at the current x, then the
+        // solver state is brought back to x (the rebuild overwrote float64 rows)
+        ensure_state(*m, CC_PREC_FP64);
+        rebuild_bases_at(*m, x);
+        refresh_all(*m, o->precision, x, xt);
+      }
+    };
     while (!conv && it < o->max_iters && !o->line_search) {
-      const int chunk = std::min(every, o->max_iters - it);
+      maybe_restart();
+      int chunk = std::min(every, o->max_iters - it);
+      if (restart > 0) chunk = std::min(chunk, restart - it % restart);
       const bool replay = graph && chunk == every && it > 0;
       run_chunk(*m, x, xt, so, cb, ce, chunk, replay, key, false);
       it += chunk;
@@ -596,6 +618,7 @@ cc_status cc_solve_step(cc_mesh* m, double* x, double* v, const cc_step_opts* o,
         return read_scalar(*m, m->d_scalars.p + 1);
       };
       while (!conv && it < o->max_iters) {
+        maybe_restart();
         CCG_CUDA(cudaMemcpyAsync(m->d_xls0.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         const double E0 = energy_at(x);
         sweep_body(*m, x, xt, so, cb, ce, true);  // g, H are current at x (refreshed below)
@@ -754,7 +777,8 @@ cc_status cc_batch_offsets(const cc_mesh* m, int64_t* offsets, int32_t* count) {
 cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o, cc_batch_stats* st) {
   try {
     ccg::g_last_error.clear();
-    CCG_CHECK(!o || !o->line_search, CC_ERR_INVALID_ARG, "the line search runs in cc_solve_step only");
+    CCG_CHECK(!o || (!o->line_search && o->restart_every <= 0), CC_ERR_INVALID_ARG,
+              "the line search and restarts run in cc_solve_step only");
     CCG_CHECK(m && x && o && st && st->iterations && st->status && st->g0 && st->g_final, CC_ERR_INVALID_ARG,
               "NULL argument");
     CCG_CHECK(o->max_iters >= 0 && o->min_iters >= 0 && o->tol >= 0, CC_ERR_INVALID_ARG, "bad iteration limits");

@@ -323,7 +323,9 @@ void run_coloring(Mesh& m);
 void run_subspace_build(Mesh& m, int32_t k);
 void build_supports(Mesh& m, int32_t k);
 void rest_hessian_f64(Mesh& m);
-void patch_solves(Mesh& m, const int32_t* d_verts, int64_t count);
+void hessian_f64_at(Mesh& m, const double* x);
+int64_t patch_solves(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail);
+int64_t rebuild_bases_at(Mesh& m, const double* x);
 void bases_to_f32(Mesh& m);
 // solver state of one precision (allocated once, on first use)
 void ensure_state(Mesh& m, cc_precision p);

@@ -153,10 +153,12 @@ __global__ void k_patch_basis(const int32_t* __restrict__ verts, const int32_t* 
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < 9 * m; k += blockDim.x) {
-    const int a = k / 9, q = k % 9, r = q / 3, d = q % 3;
-    Uout[(int64_t)(s0 + a) * 9 + q] = R[d * N + 3 * a + r];
-  }
+  // a patch whose H_PP is not positive definite leaves its basis untouched
+  if (!bad)
+    for (int k = threadIdx.x; k < 9 * m; k += blockDim.x) {
+      const int a = k / 9, q = k % 9, r = q / 3, d = q % 3;
+      Uout[(int64_t)(s0 + a) * 9 + q] = R[d * N + 3 * a + r];
+    }
   if (threadIdx.x == 0 && bad) atomicAdd(fail, 1);
 }
 
@@ -269,27 +271,43 @@ void build_supports(Mesh& m, int32_t k) {
   m.mx.U.alloc(9 * std::max<int64_t>(total, 1));
 }
 
-// Rest Hessian of E in float64 into the float64 block rows (dynamic meshes:
-// M + h^2 K).  The float64 solver state must exist.
-void rest_hessian_f64(Mesh& m) {
+// Hessian of E at x (device float64 [3][n]) in float64 into the float64
+// block rows (dynamic meshes: M + h^2 K).  The float64 solver state must exist.
+void hessian_f64_at(Mesh& m, const double* x) {
   cudaStream_t s = m.stream;
+  const double w = m.h > 0.0 ? m.h * m.h : 1.0;
+  launch_tet_grad_f64(m, x, m.d_all_tets.p, m.n_active_tets, w, s);
+  launch_rows_f64(m, x, x, w, s);
+  CCG_CUDA(cudaStreamSynchronize(s));
+}
+
+// Rest Hessian (the bases' configuration, Sec. 3.1).
+void rest_hessian_f64(Mesh& m) {
   const int64_t n = m.n;
   DBuf<double> Xs;
   std::vector<double> soa(3 * n);
   for (int64_t j = 0; j < n; ++j)
     for (int a = 0; a < 3; ++a) soa[a * n + j] = m.X[3 * j + a];
-  Xs.upload(soa, s);
-  const double w = m.h > 0.0 ? m.h * m.h : 1.0;
-  launch_tet_grad_f64(m, Xs.p, m.d_all_tets.p, m.n_active_tets, w, s);
-  launch_rows_f64(m, Xs.p, Xs.p, w, s);
-  CCG_CUDA(cudaStreamSynchronize(s));
+  Xs.upload(soa, m.stream);
+  hessian_f64_at(m, Xs.p);
+}
+
+// Restarted bases: Eq. 5 on the current supports with the Hessian at x,
+// written over the current bases; patches whose H_PP is not positive
+// definite keep their basis.  Returns how many kept theirs.
+int64_t rebuild_bases_at(Mesh& m, const double* x) {
+  hessian_f64_at(m, x);
+  const int64_t kept = patch_solves(m, m.d_free_rows.p, m.n_free, false);
+  bases_to_f32(m);
+  CCG_CUDA(cudaStreamSynchronize(m.stream));
+  return kept;
 }
 
 // Dense patch solves (Eq. 5 on P = S_i) for a device list of free vertices,
 // written into the float64 bases.  Needs the rest Hessian in the block rows.
-void patch_solves(Mesh& m, const int32_t* d_verts, int64_t count) {
+int64_t patch_solves(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail) {
   cudaStream_t s = m.stream;
-  if (count <= 0) return;
+  if (count <= 0) return 0;
   const int Nmax = 3 * std::max(m.sup_max, 1);
   const size_t per = (size_t)Nmax * Nmax + 3 * (size_t)Nmax;
   int64_t batch = std::max<int64_t>(1, (int64_t)((size_t(1) << 30) / (per * sizeof(double))));
@@ -308,7 +326,8 @@ void patch_solves(Mesh& m, const int32_t* d_verts, int64_t count) {
   int32_t nfail = 0;
   CCG_CUDA(cudaMemcpyAsync(&nfail, fail.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CCG_CUDA(cudaStreamSynchronize(s));
-  CCG_CHECK(nfail == 0, CC_ERR_NUMERIC, "a patch Hessian was not positive definite");
+  CCG_CHECK(nfail == 0 || !throw_on_fail, CC_ERR_NUMERIC, "a patch Hessian was not positive definite");
+  return nfail;
 }
 
 namespace {
@@ -330,7 +349,7 @@ void bases_to_f32(Mesh& m) {
 void run_subspace_build(Mesh& m, int32_t k) {
   build_supports(m, k);
   rest_hessian_f64(m);
-  patch_solves(m, m.d_free_rows.p, m.n_free);
+  patch_solves(m, m.d_free_rows.p, m.n_free, true);
   bases_to_f32(m);
   CCG_CUDA(cudaStreamSynchronize(m.stream));
 }

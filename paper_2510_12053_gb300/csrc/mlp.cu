@@ -1024,7 +1024,7 @@ cc_status cc_build_learned_subspace(cc_mesh* m, cc_mlp* net, double tau, double*
     if (!fall.empty()) {
       DBuf<int32_t> fl;
       fl.upload(fall, s);
-      patch_solves(*m, fl.p, (int64_t)fall.size());
+      patch_solves(*m, fl.p, (int64_t)fall.size(), true);
       bases_to_f32(*m);
     }
     CCG_CUDA(cudaStreamSynchronize(s));

@@ -372,7 +372,33 @@ def test_batch_rejects_the_line_search():
     x = cc.to_soa(np.concatenate([sc.x0 for sc in scenes]))
     with pytest.raises(cc.CCError):
         lib_opts = dict(precision="mixed", tol=1e-6, max_iters=4)
-        o = cc.StepOpts(cc.UPDATE["cc"], cc.SCHED["colored"], cc.PREC["mixed"], 1e-6, 4, 0, 1, 0, None, 0, 1)
+        o = cc.StepOpts(cc.UPDATE["cc"], cc.SCHED["colored"], cc.PREC["mixed"], 1e-6, 4, 0, 1, 0, None, 0, 0, 1)
         st = cc.BatchStats()
         rc = cc.lib().cc_solve_batch(b._h, x.data_ptr(), None, cc.ctypes.byref(o), cc.ctypes.byref(st))
         cc._check(rc)
+
+
+
+# ---------------------------------------------------------------- restarted bases (Sec. 4.4)
+def test_bases_rebuilt_at_x_match_the_oracle():
+    scene = _box(dims=(5, 4, 4), seed=7, factor=1.3)
+    pb, topo, sup, U = _oracle(scene, 2)
+    x = _state(scene, 0.03, 9)
+    Ux, kept_o = subspace.rebuild_bases_at(pb, sup, U, x)
+    m = _gpu(scene, 2)
+    kept = m.build_subspace_at(cc.to_soa(x))
+    assert kept == kept_o == 0
+    sp, Ug = m.export("sup_ptr"), m.export("U").reshape(-1, 3, 3)
+    for v in np.flatnonzero(pb.free):
+        np.testing.assert_allclose(Ug[sp[v]:sp[v + 1]], Ux[v], rtol=0, atol=1e-10 * max(1.0, np.abs(Ux[v]).max()))
+
+
+def test_restarted_solve_follows_the_oracle():
+    scene = meshgen.twist_box(3, 3, 8, angle=np.pi / 2, nu=0.3)
+    pb, topo, sup, U = _oracle(scene, 2)
+    _, h_o = solvers.solve(pb, topo, sup, U, scene.x0, kind="cc", tol=1e-6, max_iters=200, restart_every=5)
+    _, h_f = solvers.solve(pb, topo, sup, U, scene.x0, kind="cc", tol=1e-6, max_iters=200)
+    m = _gpu(scene, 2)
+    r = m.solve_step(cc.to_soa(scene.x0), precision="fp64", tol=1e-6, max_iters=200, restart_every=5, check_every=1)
+    assert h_o.converged and r.converged
+    assert abs(r.iterations - h_o.iterations) <= 1 and h_o.iterations < h_f.iterations

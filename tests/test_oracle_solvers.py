@@ -273,3 +273,30 @@ def test_global_line_search_never_increases_the_energy():
         assert all(b <= a for a, b in zip(h.energy, h.energy[1:])), schedule
     _, hp = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-12, max_iters=8)
     assert max(hp.energy) > hp.energy[0]
+
+
+# ---------------------------------------------------------------- restarted bases (Sec. 4.4)
+def test_rebuilt_bases_at_rest_equal_the_rest_bases_and_solve_eq5_at_x():
+    sc, pb, topo = _setup(n=3, jit=0.05, factor=1.3)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    same, kept = subspace.rebuild_bases_at(pb, sup, [np.zeros_like(u) for u in U], pb.X)
+    assert kept == 0
+    for a, b in zip(same, U):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * max(1.0, np.abs(b).max() if b.size else 1.0))
+    x = _state(sc, 0.03, 9)
+    Ux, kept = subspace.rebuild_bases_at(pb, sup, U, x)
+    H = pb.hessian(x)
+    for i in np.flatnonzero(pb.free)[:6]:      # Eq. 5 at x: H_PP U + H_Pi = 0
+        P, I = subspace.dofs(sup[i]), subspace.dofs([int(i)])
+        R = H[P][:, P] @ Ux[i].reshape(-1, 3) + H[P][:, I].toarray()
+        assert np.abs(R).max() <= 1e-9 * np.abs(H[P][:, I].toarray()).max()
+
+
+def test_restarted_bases_help_the_twisted_bar():
+    sc = meshgen.twist_box(2, 2, 6, angle=np.pi / 2, nu=0.3)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    _, hf = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-4, max_iters=80)
+    _, hr = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-4, max_iters=80, restart_every=5)
+    assert hr.converged and hr.iterations < hf.iterations
