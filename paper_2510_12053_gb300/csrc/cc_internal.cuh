@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <new>
 #include <utility>
 #include <string>
@@ -281,6 +282,9 @@ void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
 void build_topology(Mesh& m);
 // Slot maps for the current supports (after cc_build_subspace / cc_set_subspace).
 void build_slot_maps(Mesh& m);
+// host worker threads for setup passes, and a parallel loop over vertex ranges
+int host_threads(int64_t items);
+void parallel_ranges(int64_t n, int nt, const std::function<void(int, int64_t, int64_t)>& f);
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels_*.cu)

@@ -226,12 +226,16 @@ void run_coloring(Mesh& m) {
 void build_supports(Mesh& m, int32_t k) {
   cudaStream_t s = m.stream;
   const int64_t n = m.n;
-  m.sup_ptr.assign(n + 1, 0);
-  m.sup_idx.clear();
-  std::vector<int32_t> stamp(n, -1), ring, frontier, next;
-  int32_t supmax = 0;
-  for (int64_t v = 0; v < n; ++v) {
-    if (!m.pinned[v]) {
+  // vertex ranges in parallel (each with its own visit stamps); concatenated in order
+  const int nt = host_threads(n);
+  std::vector<std::vector<int32_t>> idx_t(nt);
+  std::vector<int64_t> len(n, 0);
+  std::vector<int32_t> supmax_t(nt, 0);
+  parallel_ranges(n, nt, [&](int t, int64_t v0, int64_t v1) {
+    std::vector<int32_t> stamp(n, -1), ring, frontier, next;
+    std::vector<int32_t>& out = idx_t[t];
+    for (int64_t v = v0; v < v1; ++v) {
+      if (m.pinned[v]) continue;
       ring.clear();
       frontier.assign(1, (int32_t)v);
       stamp[v] = (int32_t)v;
@@ -249,11 +253,17 @@ void build_supports(Mesh& m, int32_t k) {
         frontier.swap(next);
       }
       std::sort(ring.begin(), ring.end());
-      m.sup_idx.insert(m.sup_idx.end(), ring.begin(), ring.end());
-      supmax = std::max<int32_t>(supmax, (int32_t)ring.size());
+      out.insert(out.end(), ring.begin(), ring.end());
+      len[v] = (int64_t)ring.size();
+      supmax_t[t] = std::max<int32_t>(supmax_t[t], (int32_t)ring.size());
     }
-    m.sup_ptr[v + 1] = (int64_t)m.sup_idx.size();
-  }
+  });
+  m.sup_ptr.assign(n + 1, 0);
+  for (int64_t v = 0; v < n; ++v) m.sup_ptr[v + 1] = m.sup_ptr[v] + len[v];
+  m.sup_idx.clear();
+  m.sup_idx.reserve(m.sup_ptr[n]);
+  for (int t = 0; t < nt; ++t) m.sup_idx.insert(m.sup_idx.end(), idx_t[t].begin(), idx_t[t].end());
+  const int32_t supmax = *std::max_element(supmax_t.begin(), supmax_t.end());
   CCG_CHECK(m.sup_idx.size() < (size_t(1) << 31), CC_ERR_INVALID_ARG, "support arrays exceed 2^31 entries");
   CCG_CHECK(supmax < 32768, CC_ERR_INVALID_ARG, "support larger than 32767 vertices");
   m.sup_max = supmax;

@@ -576,14 +576,17 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
       default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s);
     }
   }
-  const unsigned grid = (unsigned)((count + 127) / 128);
+  // one vertex per thread in 32-thread blocks: a colour holds a few thousand
+  // vertices, so small blocks spread the long per-vertex chains over every SM
+  constexpr int kCondenseThreads = 32;
+  const unsigned grid = (unsigned)((count + kCondenseThreads - 1) / kCondenseThreads);
   if constexpr (kMixed) {
     const df rel{1e-12f, (float)(1e-12 - (double)1e-12f)};
-    pdl_launch(k_condense<df, HT, kMixed, kUpd>, grid, 128, 0, s, verts, count, (const HT*)cpl,
+    pdl_launch(k_condense<df, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
                (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl, rel,
                (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
   } else {
-    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, 128, 0, s, verts, count, (const HT*)cpl,
+    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
                (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
                1e-12, (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
   }

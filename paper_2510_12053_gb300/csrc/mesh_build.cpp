@@ -3,12 +3,44 @@
 // index with.  Integer outputs follow fixed orders (ascending ids) so that
 // they can be compared bit for bit with an independent implementation.
 #include <algorithm>
+#include <exception>
+#include <thread>
+#include <functional>
 #include <cmath>
 #include <cstring>
 
 #include "cc_internal.cuh"
 
 namespace ccg {
+
+// Host worker threads for setup passes over vertex ranges (one per hardware
+// thread, at most 32; one for small inputs).
+int host_threads(int64_t items) {
+  if (items < 20000) return 1;
+  const unsigned hc = std::thread::hardware_concurrency();
+  return (int)std::max<unsigned>(1, std::min<unsigned>(hc ? hc : 1, 32));
+}
+
+void parallel_ranges(int64_t n, int nt, const std::function<void(int, int64_t, int64_t)>& f) {
+  if (nt <= 1) {
+    f(0, 0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::vector<std::exception_ptr> err(nt);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() {
+      try {
+        f(t, n * t / nt, n * (t + 1) / nt);
+      } catch (...) {
+        err[t] = std::current_exception();
+      }
+    });
+  for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
+}
+
 
 static void inverse3(const double* A, double* inv, double* det) {
   double c00 = A[4] * A[8] - A[5] * A[7];
@@ -272,12 +304,16 @@ void build_slot_maps(Mesh& m) {
   m.smap_wide = m.sup_max >= 250;
   const uint16_t kNone = m.smap_wide ? 0xFFFF : 0xFF, kSelf = m.smap_wide ? 0xFFFE : 0xFE,
                  kDiag = m.smap_wide ? 0xFFFD : 0xFD;
-  std::vector<int64_t> ptr(n + 1, 0);
-  std::vector<uint16_t> codes;
-  std::vector<int32_t> slot(n, -1);
-  int64_t longest = 0;
-  for (int64_t v = 0; v < n; ++v) {
-    if (!m.pinned[v]) {
+  // vertex ranges in parallel, each with its own slot scratch; concatenated in order
+  const int nt = host_threads(n);
+  std::vector<std::vector<uint16_t>> codes_t(nt);
+  std::vector<int64_t> len(n, 0);
+  std::vector<int64_t> longest_t(nt, 0);
+  parallel_ranges(n, nt, [&](int t, int64_t v0, int64_t v1) {
+    std::vector<int32_t> slot(n, -1);
+    std::vector<uint16_t>& codes = codes_t[t];
+    for (int64_t v = v0; v < v1; ++v) {
+      if (m.pinned[v]) continue;
       const int64_t s0 = m.sup_ptr[v], s1 = m.sup_ptr[v + 1];
       for (int64_t s = s0; s < s1; ++s) slot[m.sup_idx[s]] = (int32_t)(s - s0);
       const int64_t before = (int64_t)codes.size();
@@ -292,12 +328,17 @@ void build_slot_maps(Mesh& m) {
           codes.push_back(c);
         }
       }
-      longest = std::max<int64_t>(longest, (int64_t)codes.size() - before);
+      len[v] = (int64_t)codes.size() - before;
+      longest_t[t] = std::max<int64_t>(longest_t[t], len[v]);
       for (int64_t s = s0; s < s1; ++s) slot[m.sup_idx[s]] = -1;
     }
-    ptr[v + 1] = (int64_t)codes.size();
-  }
-  m.smap_max = longest;
+  });
+  std::vector<int64_t> ptr(n + 1, 0);
+  for (int64_t v = 0; v < n; ++v) ptr[v + 1] = ptr[v] + len[v];
+  std::vector<uint16_t> codes;
+  codes.reserve(ptr[n]);
+  for (int t = 0; t < nt; ++t) codes.insert(codes.end(), codes_t[t].begin(), codes_t[t].end());
+  m.smap_max = *std::max_element(longest_t.begin(), longest_t.end());
   m.d_smap_ptr.upload(ptr, m.stream);
   if (m.smap_wide) {
     m.d_smap16.upload(codes, m.stream);
