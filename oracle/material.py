@@ -17,6 +17,16 @@ Derivatives (C = cof F = dJ/dF):
 with d2J/dF_ab dF_cd = eps_ace eps_bdf F_ef.  Index convention: F_ab, a = row
 (spatial axis), b = column (material axis).
 
+``fcr`` is the paper's Fixed Corotational density (Sec. 4.1),
+
+    Psi(F) = mu ||F - R||_F^2 + lam/2 (J - 1)^2,  F = R S (polar decomposition),
+    P      = 2 mu (F - R) + lam (J - 1) C,
+    dP[dF] = 2 mu (dF - dR) + lam (C : dF) C + lam (J - 1) d2J/dF2 : dF,
+
+with dR = R [w]_x, (tr(S) I - S) w = axial(R^T dF - dF^T R) (differentiating
+F = R S: the skew part of R^T dF is (W S + S W)/2 with W = R^T dR).  Its
+linearisation at F = I is Hooke's law with (mu, lam).
+
 ``linear`` is the small-strain Hooke density Psi = mu eps:eps + lam/2 tr(eps)^2,
 eps = sym(F) - I, used only to build the quadratic problems on which the
 paper's single-iteration claim (Sec. 4.3) is exact.
@@ -82,6 +92,56 @@ def snh_dstress(F: np.ndarray, mu: float, lam_hat: float) -> np.ndarray:
     return out
 
 
+def polar_rotation(F: np.ndarray) -> np.ndarray:
+    """R of F = R S with R a proper rotation, from the SVD F = U diag(s) V^T:
+    R = U diag(1, 1, det(U V^T)) V^T (the closest rotation when det F > 0)."""
+    U, _, Vt = np.linalg.svd(F)
+    d = np.sign(np.linalg.det(U @ Vt))
+    D = np.zeros(F.shape[:-2] + (3, 3))
+    D[..., 0, 0] = 1.0
+    D[..., 1, 1] = 1.0
+    D[..., 2, 2] = d
+    return U @ D @ Vt
+
+
+def fcr_energy(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
+    R = polar_rotation(F)
+    J = det3(F)
+    return mu * np.einsum("...ab,...ab->...", F - R, F - R) + 0.5 * lam * (J - 1.0) ** 2
+
+
+def fcr_stress(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
+    R = polar_rotation(F)
+    J = det3(F)
+    return 2.0 * mu * (F - R) + (lam * (J - 1.0))[..., None, None] * cofactor(F)
+
+
+def fcr_dstress(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
+    """dP_ab/dF_cd, shape [..., 3, 3, 3, 3], one basis direction E_cd at a time."""
+    R = polar_rotation(F)
+    S = np.swapaxes(R, -1, -2) @ F
+    J = det3(F)
+    C = cofactor(F)
+    K = np.einsum("...aa->...", S)[..., None, None] * np.eye(3) - S
+    Kinv = np.linalg.inv(K)
+    d2J = det_hessian(F)
+    out = np.zeros(F.shape[:-2] + (3, 3, 3, 3))
+    for c in range(3):
+        for d in range(3):
+            E = np.zeros((3, 3))
+            E[c, d] = 1.0
+            G = np.swapaxes(R, -1, -2) @ E
+            A = G - np.swapaxes(G, -1, -2)
+            ax = np.stack([A[..., 2, 1], A[..., 0, 2], A[..., 1, 0]], axis=-1)
+            w = np.einsum("...ij,...j->...i", Kinv, ax)
+            W = np.einsum("ijk,...k->...ij", -EPS, w)      # [w]_x: W v = w x v
+            dR = R @ W
+            dP = 2.0 * mu * (E - dR) + (lam * C[..., c, d])[..., None, None] * C \
+                + (lam * (J - 1.0))[..., None, None] * d2J[..., :, :, c, d]
+            out[..., :, :, c, d] = dP
+    return out
+
+
 def linear_energy(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
     eps = 0.5 * (F + np.swapaxes(F, -1, -2)) - np.eye(3)
     tr = np.einsum("...aa->...", eps)
@@ -103,22 +163,22 @@ def linear_dstress(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
 
 
 class Model:
-    """Energy density with parameters bound: ``kind`` in {"snh", "linear"}."""
+    """Energy density with parameters bound: ``kind`` in {"snh", "fcr", "linear"}."""
 
     def __init__(self, kind: str, E: float, nu: float):
         self.kind, self.E, self.nu = kind, E, nu
         if kind == "snh":
             self.a, self.b = snh_params(E, nu)
-        elif kind == "linear":
+        elif kind in ("linear", "fcr"):
             self.a, self.b = lame(E, nu)
         else:
             raise ValueError(kind)
 
     def energy(self, F):
-        return snh_energy(F, self.a, self.b) if self.kind == "snh" else linear_energy(F, self.a, self.b)
+        return {"snh": snh_energy, "fcr": fcr_energy, "linear": linear_energy}[self.kind](F, self.a, self.b)
 
     def stress(self, F):
-        return snh_stress(F, self.a, self.b) if self.kind == "snh" else linear_stress(F, self.a, self.b)
+        return {"snh": snh_stress, "fcr": fcr_stress, "linear": linear_stress}[self.kind](F, self.a, self.b)
 
     def dstress(self, F):
-        return snh_dstress(F, self.a, self.b) if self.kind == "snh" else linear_dstress(F, self.a, self.b)
+        return {"snh": snh_dstress, "fcr": fcr_dstress, "linear": linear_dstress}[self.kind](F, self.a, self.b)

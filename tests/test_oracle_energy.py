@@ -27,7 +27,7 @@ def small():
     return meshgen.stretch_box(2, 2, 3, E=1e5, nu=0.45, factor=1.3, jitter_amount=0.05, seed=7)
 
 
-@pytest.mark.parametrize("kind", ["snh", "linear"])
+@pytest.mark.parametrize("kind", ["snh", "fcr", "linear"])
 @pytest.mark.parametrize("dynamic", [False, True])
 def test_gradient_matches_central_differences(small, kind, dynamic):
     pb = fem.problem_from_scene(small, kind)
@@ -50,7 +50,7 @@ def test_gradient_matches_central_differences(small, kind, dynamic):
     assert np.linalg.norm(gfd - g) <= 1e-6 * np.linalg.norm(g)
 
 
-@pytest.mark.parametrize("kind", ["snh", "linear"])
+@pytest.mark.parametrize("kind", ["snh", "fcr", "linear"])
 def test_hessian_matches_central_differences(small, kind):
     pb = fem.problem_from_scene(small, kind)
     x = _perturbed(small, 0.2, 4)
@@ -67,15 +67,17 @@ def test_hessian_matches_central_differences(small, kind):
     assert np.allclose(H, H.T, rtol=0, atol=1e-9 * np.abs(H).max())
 
 
-def test_zero_energy_and_gradient_at_rest(small):
-    pb = fem.problem_from_scene(small)
+@pytest.mark.parametrize("kind", ["snh", "fcr"])
+def test_zero_energy_and_gradient_at_rest(small, kind):
+    pb = fem.problem_from_scene(small, kind)
     assert abs(pb.energy(small.X)) <= 1e-12 * small.material.E * pb.total_volume()
     g = pb.gradient(small.X)
     assert np.abs(g).max() <= 1e-10 * small.material.E * small.cell ** 2
 
 
-def test_rotation_and_translation_invariance(small):
-    pb = fem.problem_from_scene(small)
+@pytest.mark.parametrize("kind", ["snh", "fcr"])
+def test_rotation_and_translation_invariance(small, kind):
+    pb = fem.problem_from_scene(small, kind)
     x = _perturbed(small, 0.3, 5)
     R = _rotation(9)
     t = np.array([0.3, -1.2, 2.0])
@@ -85,13 +87,15 @@ def test_rotation_and_translation_invariance(small):
                                atol=1e-9 * np.abs(pb.gradient(x)).max())
 
 
-def test_rest_hessian_is_textbook_linear_elastic_stiffness():
+@pytest.mark.parametrize("kind", ["snh", "fcr"])
+def test_rest_hessian_is_textbook_linear_elastic_stiffness(kind):
     """V B^T D B with B built from barycentric shape gradients (4x4 inverse)
-    and D the isotropic Voigt matrix of (E, nu): pins lam_hat = lam + mu."""
+    and D the isotropic Voigt matrix of (E, nu): pins lam_hat = lam + mu for
+    stable Neo-Hookean and (mu, lam) for Fixed Corotational."""
     E, nu = 3.7e5, 0.41
     X = np.array([[0.0, 0.0, 0.0], [1.1, 0.1, 0.0], [0.2, 0.9, 0.1], [0.1, 0.2, 1.3]])
     tets = np.array([[0, 1, 2, 3]])
-    pb = fem.Problem(X, tets, np.zeros(4), material.Model("snh", E, nu))
+    pb = fem.Problem(X, tets, np.zeros(4), material.Model(kind, E, nu))
     M = np.hstack([np.ones((4, 1)), X])
     C = np.linalg.inv(M)            # N_v(X) = sum_k C[k, v] [1, X]_k
     grads = C[1:, :].T              # [4, 3]
@@ -147,3 +151,26 @@ def test_mesh_counts_match_workload_definitions():
             assert X.shape[0] == nv and T.shape[0] == nt
         else:
             assert 6 * nx * ny * nz == nt
+
+
+def test_polar_rotation_matches_scipy_and_is_proper():
+    from scipy.linalg import polar
+    F = np.stack([np.eye(3) + 0.4 * meshgen.normal(20 + k, np.arange(9)).reshape(3, 3) for k in range(20)])
+    F = F[np.linalg.det(F) > 0]
+    R = material.polar_rotation(F)
+    for Fk, Rk in zip(F, R):
+        np.testing.assert_allclose(Rk, polar(Fk)[0], rtol=0, atol=1e-12)
+        assert np.linalg.det(Rk) == pytest.approx(1.0, abs=1e-12)
+    Q = _rotation(4)
+    S = np.array([[1.3, 0.1, 0.0], [0.1, 0.9, 0.2], [0.0, 0.2, 1.1]])
+    np.testing.assert_allclose(material.polar_rotation(Q @ S), Q, rtol=0, atol=1e-12)
+
+
+def test_fcr_energy_closed_forms():
+    """Psi(R S) = mu |S - I|^2 + lam/2 (det S - 1)^2, independent of R."""
+    mu, lam = material.lame(2e5, 0.35)
+    S = np.array([[1.2, 0.05, 0.0], [0.05, 0.8, 0.1], [0.0, 0.1, 1.05]])
+    Q = _rotation(6)
+    want = mu * np.sum((S - np.eye(3)) ** 2) + 0.5 * lam * (np.linalg.det(S) - 1.0) ** 2
+    assert material.fcr_energy(Q @ S, mu, lam) == pytest.approx(want, rel=1e-13)
+    assert material.fcr_energy(Q, mu, lam) == pytest.approx(0.0, abs=1e-20)
