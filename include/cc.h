@@ -51,10 +51,20 @@ typedef enum {
 
 typedef struct cc_mesh cc_mesh; /* opaque; owns device and host rest data */
 
+/* Energy density Psi(F) of a mesh (E, nu -> Lame mu, lam):
+ *   CC_MODEL_SNH  stable Neo-Hookean, rest-stable form without the log term,
+ *                 Psi = mu/2 (|F|^2 - 3) - mu (J - 1) + (lam + mu)/2 (J - 1)^2
+ *   CC_MODEL_FCR  Fixed Corotational (the paper's material, Sec. 4.1),
+ *                 Psi = mu |F - R|^2 + lam/2 (J - 1)^2, R the polar rotation of F;
+ *                 every tet must stay non-inverted (det F > 0): an inverted tet
+ *                 makes the update non-finite (CC_ERR_NUMERIC). */
+typedef enum { CC_MODEL_SNH = 0, CC_MODEL_FCR = 1 } cc_model;
+
 typedef struct {
-  double E;   /* Young's modulus [Pa], > 0 */
-  double nu;  /* Poisson ratio, in (-1, 0.5) */
-  double rho; /* density [kg/m^3], >= 0 (used by the mass matrix only) */
+  double E;      /* Young's modulus [Pa], > 0 */
+  double nu;     /* Poisson ratio, in (-1, 0.5) */
+  double rho;    /* density [kg/m^3], >= 0 (used by the mass matrix only) */
+  int32_t model; /* cc_model (0: stable Neo-Hookean) */
 } cc_material;
 
 /* Arithmetic of a sweep.
@@ -306,7 +316,8 @@ cc_status cc_build_bases_noalloc(const double* H_blocks, const int32_t* row_ptr,
  * of a sweep covers all meshes.  Colours, supports and bases of each mesh are
  * exactly those it would get on its own (components never interact, and the
  * greedy colouring of the union in ascending id is the per-mesh colouring).
- * Each mesh keeps its own material; the time step h and gravity are shared. */
+ * Each mesh keeps its own material (E, nu, rho); the energy model, the time
+ * step h and gravity are shared (meshes with different models are rejected). */
 typedef struct {
   const double* X;       /* host [n][3] */
   int64_t n;
@@ -343,17 +354,22 @@ cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_s
 
 /* Launch-configuration autotuner (no counterpart in the paper).  Times
  * `sweeps` coloured CC sweeps from x_dev for each candidate configuration of
- * the two kernels whose best shape depends on the mesh: threads per vertex of
- * the coupling kernel (32 = one warp per vertex, 64, 128, 256) and block rows per CTA of the row
- * gather (2, 4, 8 warps), and keeps the fastest for this mesh.  x_dev is not
- * modified (the sweeps run on a private copy).  Requires cc_color and a
- * subspace.  Results with different configurations agree to float32
- * rounding (the coupling kernel's partial sums are grouped differently). */
+ * the two kernels whose best shape depends on the mesh, one parameter at a
+ * time in this order: threads per vertex of the coupling kernel (32 = one
+ * warp per vertex, 64, 128, 256), then, unless one warp won, threads per
+ * block row of the coupling kernel (1, 2, 4, 8), then block rows per CTA of
+ * the row gather (2, 4, 8 warps); it keeps the fastest of each for this
+ * mesh.  x_dev is not modified (the sweeps run on a private copy).  Requires
+ * cc_color and a subspace.  Results with different configurations agree to
+ * the working precision's rounding (the coupling kernel's partial sums are
+ * grouped differently). */
 typedef struct {
   int32_t couple_threads;
+  int32_t couple_row_lanes;
   int32_t gather_warps;
-  double couple_ms[4]; /* ms per sweep with 32, 64, 128, 256 threads per vertex */
-  double gather_ms[3]; /* ms per sweep with 2, 4, 8 warps per block */
+  double couple_ms[4];    /* ms per sweep with 32, 64, 128, 256 threads per vertex */
+  double row_lanes_ms[4]; /* ms per sweep with 1, 2, 4, 8 threads per block row (0: not timed) */
+  double gather_ms[3];    /* ms per sweep with 2, 4, 8 warps per block */
 } cc_tune_result;
 
 cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev, cc_precision precision,
@@ -361,9 +377,11 @@ cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_d
 
 /* Sets the launch shapes cc_autotune chooses among (no counterpart in the
  * paper): couple_threads in {32 (one warp per vertex), 64, 128, 256},
- * gather_warps in {2, 4, 8}; 0 keeps the current value.  CC_ERR_INVALID_ARG
- * for any other value. */
-cc_status cc_set_launch_shape(cc_mesh* mesh, int32_t couple_threads, int32_t gather_warps);
+ * gather_warps in {2, 4, 8}, couple_row_lanes (threads sharing one block row
+ * of the support in the coupling kernel with 64 or more threads) in
+ * {1, 2, 4, 8}; 0 keeps the current value.  CC_ERR_INVALID_ARG for any other
+ * value. */
+cc_status cc_set_launch_shape(cc_mesh* mesh, int32_t couple_threads, int32_t gather_warps, int32_t couple_row_lanes);
 
 /* ======================================================================
  * Learned perturbation bases.  The paper builds every U_i by the patch

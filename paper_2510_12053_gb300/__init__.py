@@ -41,7 +41,10 @@ class CCError(RuntimeError):
 
 
 class Material(ctypes.Structure):
-    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double)]
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("model", ctypes.c_int32)]
+
+
+MODEL = {"snh": 0, "fcr": 1}
 
 
 class SweepOpts(ctypes.Structure):
@@ -86,8 +89,9 @@ class BatchStats(ctypes.Structure):
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("couple_threads", ctypes.c_int32), ("gather_warps", ctypes.c_int32),
-                ("couple_ms", ctypes.c_double * 4), ("gather_ms", ctypes.c_double * 3)]
+    _fields_ = [("couple_threads", ctypes.c_int32), ("couple_row_lanes", ctypes.c_int32),
+                ("gather_warps", ctypes.c_int32), ("couple_ms", ctypes.c_double * 4),
+                ("row_lanes_ms", ctypes.c_double * 4), ("gather_ms", ctypes.c_double * 3)]
 
 
 class Profile(ctypes.Structure):
@@ -153,7 +157,7 @@ _SIGS = {
     "cc_learned_inputs": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]),
     "cc_build_learned_subspace": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(LearnedStats)]),
-    "cc_set_launch_shape": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "cc_set_launch_shape": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -223,13 +227,13 @@ class Mesh:
     """A tet mesh on the GPU (owns the library's ``cc_mesh``)."""
 
     def __init__(self, X, tets, pinned=None, *, E: float, nu: float, rho: float = 1000.0, h: float = 0.0,
-                 gravity=None, stream=None):
+                 gravity=None, stream=None, model: str = "snh"):
         X = np.ascontiguousarray(X, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int32)
         self.n, self.T = int(X.shape[0]), int(tets.shape[0])
         pin = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)
         grav = None if gravity is None else np.ascontiguousarray(gravity, dtype=np.float64)
-        mat = Material(E, nu, rho)
+        mat = Material(E, nu, rho, MODEL[model])
         out = _P()
         self._h = None
         _check(lib().cc_build_mesh(X.ctypes.data, self.n, tets.ctypes.data, self.T,
@@ -240,7 +244,7 @@ class Mesh:
         self.dynamic = h > 0.0
 
     @classmethod
-    def from_scenes(cls, scenes, stream=None) -> "Mesh":
+    def from_scenes(cls, scenes, stream=None, model: str = "snh") -> "Mesh":
         """A batch: the disjoint union of several meshes, solved together
         (materials per mesh; time step and gravity of the first scene)."""
         keep = []
@@ -252,7 +256,7 @@ class Mesh:
             keep += [X, T, P]
             m = sc.material
             descs[k] = MeshDesc(X.ctypes.data, X.shape[0], T.ctypes.data, T.shape[0], P.ctypes.data,
-                                Material(m.E, m.nu, m.rho))
+                                Material(m.E, m.nu, m.rho, MODEL[model]))
         grav = np.ascontiguousarray(scenes[0].gravity, dtype=np.float64)
         obj = cls.__new__(cls)
         obj._h = None
@@ -294,10 +298,10 @@ class Mesh:
                 "updates": st.totals.updates}
 
     @classmethod
-    def from_scene(cls, scene, stream=None) -> "Mesh":
+    def from_scene(cls, scene, stream=None, model: str = "snh") -> "Mesh":
         m = scene.material
         return cls(scene.X, scene.tets, scene.pinned, E=m.E, nu=m.nu, rho=m.rho, h=scene.h,
-                   gravity=scene.gravity, stream=stream)
+                   gravity=scene.gravity, stream=stream, model=model)
 
     def close(self):
         if self._h is not None and self._h.value:
@@ -373,12 +377,14 @@ class Mesh:
         r = TuneResult()
         _check(lib().cc_autotune(self._h, _dev3n(x, self.n, "x"), _dev3n(xtilde, self.n, "xtilde"), PREC[precision],
                                  int(sweeps), ctypes.byref(r)))
-        return {"couple_threads": r.couple_threads, "gather_warps": r.gather_warps,
-                "couple_ms": list(r.couple_ms), "gather_ms": list(r.gather_ms)}
+        return {"couple_threads": r.couple_threads, "couple_row_lanes": r.couple_row_lanes,
+                "gather_warps": r.gather_warps, "couple_ms": list(r.couple_ms),
+                "row_lanes_ms": list(r.row_lanes_ms), "gather_ms": list(r.gather_ms)}
 
-    def set_launch_shape(self, couple_threads: int = 0, gather_warps: int = 0):
-        """Pins the coupling kernel's threads per vertex (32 = one warp) and the gather's warps per block."""
-        _check(lib().cc_set_launch_shape(self._h, int(couple_threads), int(gather_warps)))
+    def set_launch_shape(self, couple_threads: int = 0, gather_warps: int = 0, couple_row_lanes: int = 0):
+        """Pins the coupling kernel's threads per vertex (32 = one warp) and threads per block row,
+        and the gather's warps per block (0 keeps a value)."""
+        _check(lib().cc_set_launch_shape(self._h, int(couple_threads), int(gather_warps), int(couple_row_lanes)))
 
     def profile_enable(self, on: bool = True):
         _check(lib().cc_profile_enable(self._h, int(on)))

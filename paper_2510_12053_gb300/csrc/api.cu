@@ -342,6 +342,7 @@ cc_status cc_build_mesh(const double* X, int64_t n, const int32_t* tets, int64_t
               "n or T out of range");
     CCG_CHECK(mat->E > 0 && mat->nu > -1.0 && mat->nu < 0.5 && mat->rho >= 0 && std::isfinite(mat->E),
               CC_ERR_INVALID_ARG, "bad material");
+    CCG_CHECK(mat->model == CC_MODEL_SNH || mat->model == CC_MODEL_FCR, CC_ERR_INVALID_ARG, "unknown material model");
     CCG_CHECK(h >= 0 && std::isfinite(h), CC_ERR_INVALID_ARG, "bad time step");
     m = new cc_mesh();
     m->n = n;
@@ -351,7 +352,8 @@ cc_status cc_build_mesh(const double* X, int64_t n, const int32_t* tets, int64_t
     m->rho = mat->rho;
     m->mu = mat->E / (2.0 * (1.0 + mat->nu));
     const double lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
-    m->lam_hat = lam + m->mu;
+    m->model = mat->model;
+    m->lam_hat = m->model == CC_MODEL_FCR ? lam : lam + m->mu;  // the density's second parameter
     m->h = h;
     if (gravity && h > 0)
       for (int a = 0; a < 3; ++a) m->grav[a] = gravity[a];
@@ -692,6 +694,8 @@ cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, co
       CCG_CHECK(d.X && d.tets && d.n >= 4 && d.T >= 1, CC_ERR_INVALID_ARG, "bad mesh in batch");
       CCG_CHECK(d.mat.E > 0 && d.mat.nu > -1.0 && d.mat.nu < 0.5 && d.mat.rho >= 0 && std::isfinite(d.mat.E),
                 CC_ERR_INVALID_ARG, "bad material in batch");
+      CCG_CHECK(d.mat.model == meshes[0].mat.model && (d.mat.model == CC_MODEL_SNH || d.mat.model == CC_MODEL_FCR),
+                CC_ERR_INVALID_ARG, "the meshes of a batch must share one known material model");
       n += d.n;
       T += d.T;
     }
@@ -704,7 +708,8 @@ cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, co
     m->nu = m0.nu;
     m->rho = m0.rho;
     m->mu = m0.E / (2.0 * (1.0 + m0.nu));
-    m->lam_hat = m0.E * m0.nu / ((1.0 + m0.nu) * (1.0 - 2.0 * m0.nu)) + m->mu;
+    m->model = m0.model;
+    m->lam_hat = m0.E * m0.nu / ((1.0 + m0.nu) * (1.0 - 2.0 * m0.nu)) + (m->model == CC_MODEL_FCR ? 0.0 : m->mu);
     m->h = h;
     if (gravity && h > 0)
       for (int a = 0; a < 3; ++a) m->grav[a] = gravity[a];
@@ -733,7 +738,8 @@ cc_status cc_build_batch(const cc_mesh_desc* meshes, int32_t count, double h, co
       if (d.pinned)
         for (int64_t v = 0; v < d.n; ++v) m->pinned[vo + v] = d.pinned[v] ? 1 : 0;
       const double mu = d.mat.E / (2.0 * (1.0 + d.mat.nu));
-      const double lh = d.mat.E * d.mat.nu / ((1.0 + d.mat.nu) * (1.0 - 2.0 * d.mat.nu)) + mu;
+      const double lh = d.mat.E * d.mat.nu / ((1.0 + d.mat.nu) * (1.0 - 2.0 * d.mat.nu)) +
+                        (m->model == CC_MODEL_FCR ? 0.0 : mu);
       for (int64_t t = 0; t < d.T; ++t) {
         m->tet_mu[to + t] = mu;
         m->tet_lh[to + t] = lh;
@@ -937,6 +943,18 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
       for (int k = 1; k < 4; ++k)
         if (out->couple_ms[k] < out->couple_ms[best]) best = k;
       m->tune_couple_threads = ct[best];
+      const int rl[4] = {1, 2, 4, 8};
+      int best_rl = -1;
+      for (int k = 0; k < 4; ++k) out->row_lanes_ms[k] = 0.0;
+      if (m->tune_couple_threads != 32) {  // the one-warp kernel splits blocks, not rows
+        const int keep = m->tune_couple_row_lanes;
+        for (int k = 0; k < 4; ++k) {
+          m->tune_couple_row_lanes = rl[k];
+          out->row_lanes_ms[k] = time_sweeps();
+          if (best_rl < 0 || out->row_lanes_ms[k] < out->row_lanes_ms[best_rl]) best_rl = k;
+        }
+        m->tune_couple_row_lanes = best_rl >= 0 ? rl[best_rl] : keep;
+      }
       for (int k = 0; k < 3; ++k) {
         m->tune_gather_wpb = gw[k];
         out->gather_ms[k] = time_sweeps();
@@ -958,13 +976,17 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
     CCG_CUDA(cudaMemsetAsync(m->d_counters.p, 0, 8 * sizeof(unsigned long long), s));
     CCG_CUDA(cudaStreamSynchronize(s));
     out->couple_threads = m->tune_couple_threads;
+    out->couple_row_lanes = m->tune_couple_row_lanes;
     out->gather_warps = m->tune_gather_wpb;
   })
 }
 
-cc_status cc_set_launch_shape(cc_mesh* m, int32_t couple_threads, int32_t gather_warps) {
+cc_status cc_set_launch_shape(cc_mesh* m, int32_t couple_threads, int32_t gather_warps, int32_t couple_row_lanes) {
   CC_API_BODY("cc_set_launch_shape", {
     CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    CCG_CHECK(couple_row_lanes == 0 || couple_row_lanes == 1 || couple_row_lanes == 2 || couple_row_lanes == 4 ||
+                  couple_row_lanes == 8,
+              CC_ERR_INVALID_ARG, "couple_row_lanes must be 1, 2, 4 or 8");
     CCG_CHECK(couple_threads == 0 || couple_threads == 32 || couple_threads == 64 || couple_threads == 128 ||
                   couple_threads == 256,
               CC_ERR_INVALID_ARG, "couple_threads must be 32, 64, 128 or 256");
@@ -972,6 +994,7 @@ cc_status cc_set_launch_shape(cc_mesh* m, int32_t couple_threads, int32_t gather
               "gather_warps must be 2, 4 or 8");
     if (couple_threads) m->tune_couple_threads = couple_threads;
     if (gather_warps) m->tune_gather_wpb = gather_warps;
+    if (couple_row_lanes) m->tune_couple_row_lanes = couple_row_lanes;
     drop_graph(*m);
   })
 }

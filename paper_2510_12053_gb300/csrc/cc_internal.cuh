@@ -138,10 +138,12 @@ struct Mesh {
   Prof prof;
   // launch configurations chosen by cc_autotune (defaults before tuning)
   int tune_couple_threads = 64;   // threads per vertex in the coupling kernel (32: one warp)
+  int tune_couple_row_lanes = 2;  // threads per block row in the coupling kernel (1, 2, 4, 8)
   int tune_gather_wpb = 4;        // warps (rows) per block in the row gather
   int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
   int32_t max_valence = 0;
   double E = 0, nu = 0, rho = 0, mu = 0, lam_hat = 0, h = 0;
+  int model = CC_MODEL_SNH;   // energy density (per mesh; batches share it)
   double grav[3] = {0, 0, 0};
   cudaStream_t stream = nullptr;
 
@@ -159,7 +161,8 @@ struct Mesh {
   int32_t max_up = 0;          // longest upper block row
   int32_t max_rs = 0;          // most staged sources of one free row
   std::vector<double> mass;
-  std::vector<double> tet_mu, tet_lh, tet_rho;   // per-tet material (a batch mixes materials)
+  std::vector<double> tet_mu, tet_lh, tet_rho;   // per-tet material (a batch mixes materials);
+                                                 // tet_lh = lam + mu (stable Neo-Hookean) or lam (FCR)
   std::vector<double> tet_E, tet_nu;             // the same as given (Young's modulus, Poisson ratio)
   // batches: mesh b owns vertices [mesh_vptr[b], mesh_vptr[b+1]) and tets [mesh_tptr[b], mesh_tptr[b+1])
   std::vector<int64_t> mesh_vptr, mesh_tptr;

@@ -226,4 +226,210 @@ __device__ __forceinline__ bool sym3_adj(const typename Arith<T>::V* M, typename
   return true;
 }
 
+// o = a^{-1} (3x3 row-major, adjugate over determinant); returns det a.
+template <typename T>
+__device__ __forceinline__ T inv3t(const T* a, T* o) {
+  const T c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const T det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  const T id = T(1) / det;
+  o[0] = c00 * id; o[3] = c01 * id; o[6] = c02 * id;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+  return det;
+}
+
+// Orthogonal polar factor R of F (F = R S, S symmetric positive definite)
+// for det F > 0, by Newton's iteration Y <- (g Y + (g Y)^{-T}) / 2 with
+// Higham's scaling g = sqrt(|Y^{-1}|_F / |Y|_F), stopped when the update is
+// below 64 units of roundoff of T (at most 40 steps).  Returns false (R
+// untouched) when det F <= 0.
+template <typename T>
+__device__ __forceinline__ bool polar_newton(const T* F, T* R) {
+  T Y[9], Yi[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Y[q] = F[q];
+  if (!(inv3t(Y, Yi) > T(0))) return false;
+  const T tol = T(64) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08));
+  for (int it = 0; it < 40; ++it) {
+    T ny = 0, ni = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      ny += Y[q] * Y[q];
+      ni += Yi[q] * Yi[q];
+    }
+    const T g = sqrt(sqrt(ni / ny));
+    T dn = 0, yn = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T v = T(0.5) * (g * Y[3 * r + c] + Yi[3 * c + r] / g);
+        dn += (v - Y[3 * r + c]) * (v - Y[3 * r + c]);
+        yn += v * v;
+        Y[3 * r + c] = v;
+      }
+    if (dn <= tol * tol * yn) break;
+    inv3t(Y, Yi);
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) R[q] = Y[q];
+  return true;
+}
+
+// Refines a float32 polar factor R0 of F to float-float accuracy.  R0 is
+// near the polar factor R but neither exactly orthogonal nor exactly aligned:
+// write R = R0 (I + X).  To first order, R^T R = I fixes the symmetric part
+// of X at -D/2 with D = R0^T R0 - I, and R^T F symmetric fixes its skew part
+// [w]x by
+//   (tr(S) I - S) w = axial(S0 - S0^T) - axial(D S - S D) / 2,
+// S0 = R0^T F, S = sym(S0) (with the identity [w]x S + S [w]x =
+// [(tr(S) I - S) w]x for symmetric S).  D and the right side are float-float
+// sums (their leading terms cancel); w and X, about float32 roundoff in size,
+// are formed in float32, and R = R0 + R0 X in float-float: the error left is
+// second order in R0's, about 1e-13.
+__device__ __forceinline__ void polar_refine_df(const float* R32, const df* F, df* R) {
+  df S[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      S[3 * r + c] = df_fma(df{R32[6 + r], 0.0f}, F[6 + c],
+                            df_fma(df{R32[3 + r], 0.0f}, F[3 + c], df_mul(df{R32[r], 0.0f}, F[c])));
+  float D[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      df d = df_fma(df{R32[6 + r], 0.0f}, df{R32[6 + c], 0.0f},
+                    df_fma(df{R32[3 + r], 0.0f}, df{R32[3 + c], 0.0f}, df_mul(df{R32[r], 0.0f}, df{R32[c], 0.0f})));
+      if (r == c) d = df_add(d, df{-1.0f, 0.0f});
+      D[3 * r + c] = d.hi + d.lo;
+    }
+  float Ss[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Ss[3 * r + c] = 0.5f * (S[3 * r + c].hi + S[3 * c + r].hi);
+  // DS - SD is skew (D, S symmetric): its axial vector from the lower entries
+  float DS[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      DS[3 * r + c] = (D[3 * r] * Ss[c] + D[3 * r + 1] * Ss[3 + c] + D[3 * r + 2] * Ss[6 + c]) -
+                      (Ss[3 * r] * D[c] + Ss[3 * r + 1] * D[3 + c] + Ss[3 * r + 2] * D[6 + c]);
+  const df a0 = df_sub(S[7], S[5]), a1 = df_sub(S[2], S[6]), a2 = df_sub(S[3], S[1]);
+  const float rhs[3] = {(a0.hi + a0.lo) - 0.5f * DS[7], (a1.hi + a1.lo) - 0.5f * DS[2],
+                        (a2.hi + a2.lo) - 0.5f * DS[3]};
+  const float tr = Ss[0] + Ss[4] + Ss[8];
+  float K[9], Ki[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) K[q] = -Ss[q];
+  K[0] += tr;
+  K[4] += tr;
+  K[8] += tr;
+  inv3t(K, Ki);
+  float w[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) w[r] = Ki[3 * r] * rhs[0] + Ki[3 * r + 1] * rhs[1] + Ki[3 * r + 2] * rhs[2];
+  const float X[9] = {-0.5f * D[0], -0.5f * D[1] - w[2], -0.5f * D[2] + w[1],
+                      -0.5f * D[3] + w[2], -0.5f * D[4], -0.5f * D[5] - w[0],
+                      -0.5f * D[6] - w[1], -0.5f * D[7] + w[0], -0.5f * D[8]};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d = R32[3 * r] * X[c] + R32[3 * r + 1] * X[3 + c] + R32[3 * r + 2] * X[6 + c];
+      R[3 * r + c] = two_sum(R32[3 * r + c], d);
+    }
+}
+
+// Fixed Corotational Hessian blocks (Sec. 4.1 material):
+//   dP[dF] = 2 mu (dF - dR) + lam (C : dF) C + lam (J - 1) d2J/dF2 : dF,
+//   dR = R [w]_x,  (tr(S) I - S) w = axial(R^T dF - dF^T R),  S = R^T F,
+// evaluated for the nine unit directions E_cd and contracted with the shape
+// vectors: block (v, w)[a][c] = V sum_{b,d} dP(E_cd)[a][b] G_v[b] G_w[d];
+// the 10 upper blocks (pairs a <= b) into dst[9 pair + q].
+template <typename T>
+__device__ __forceinline__ void fcr_hess_blocks(const T* F, const T* R, const T* C, T J, T mu, T lam, T V,
+                                                const T (&G)[4][3], T* __restrict__ dst) {
+  T S[9], K[9], Ki[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S[3 * r + c] = R[r] * F[c] + R[3 + r] * F[3 + c] + R[6 + r] * F[6 + c];
+  const T tr = S[0] + S[4] + S[8];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) K[q] = -S[q];
+  K[0] += tr;
+  K[4] += tr;
+  K[8] += tr;
+  inv3t(K, Ki);
+#pragma unroll
+  for (int q = 0; q < 90; ++q) dst[q] = T(0);
+  const T s = lam * (J - T(1));
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // R^T E_cd has column d = row c of R; its skew part's axial vector
+      T ax[3];
+      ax[0] = (d == 1 ? R[3 * c + 2] : T(0)) - (d == 2 ? R[3 * c + 1] : T(0));
+      ax[1] = (d == 2 ? R[3 * c + 0] : T(0)) - (d == 0 ? R[3 * c + 2] : T(0));
+      ax[2] = (d == 0 ? R[3 * c + 1] : T(0)) - (d == 1 ? R[3 * c + 0] : T(0));
+      T w[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w[i] = Ki[3 * i] * ax[0] + Ki[3 * i + 1] * ax[1] + Ki[3 * i + 2] * ax[2];
+      // dR = R [w]_x, [w]_x = [[0, -w2, w1], [w2, 0, -w0], [-w1, w0, 0]]
+      T dP[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T r0 = R[3 * a], r1 = R[3 * a + 1], r2 = R[3 * a + 2];
+        const T dR0 = r1 * w[2] - r2 * w[1];
+        const T dR1 = r2 * w[0] - r0 * w[2];
+        const T dR2 = r0 * w[1] - r1 * w[0];
+        dP[3 * a + 0] = T(-2) * mu * dR0;
+        dP[3 * a + 1] = T(-2) * mu * dR1;
+        dP[3 * a + 2] = T(-2) * mu * dR2;
+      }
+      dP[3 * c + d] += T(2) * mu;
+      const T cc = lam * C[3 * c + d];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) dP[q] += cc * C[q];
+      // d2J/dF_ab dF_cd = eps_ace eps_bdf F_ef: nonzero for a != c, b != d
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a == c) continue;
+        const int e = 3 - a - c;
+        const T sa = ((c - a + 3) % 3 == 1) ? T(1) : T(-1);  // eps_ace
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (b == d) continue;
+          const int f = 3 - b - d;
+          const T sb = ((d - b + 3) % 3 == 1) ? T(1) : T(-1);  // eps_bdf
+          dP[3 * a + b] += s * sa * sb * F[3 * e + f];
+        }
+      }
+      T y[4][3];
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[v][a] = dP[3 * a] * G[v][0] + dP[3 * a + 1] * G[v][1] + dP[3 * a + 2] * G[v][2];
+      int pair = 0;
+#pragma unroll
+      for (int va = 0; va < 4; ++va)
+#pragma unroll
+        for (int vb = va; vb < 4; ++vb) {
+          const T gw = V * G[vb][d];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dst[9 * pair + 3 * a + c] += y[va][a] * gw;
+          ++pair;
+        }
+    }
+}
+
 }  // namespace ccg

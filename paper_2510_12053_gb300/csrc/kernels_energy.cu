@@ -9,6 +9,12 @@
 //                           + s [F (G_v x G_w)]_skew ]
 // where G_1..G_3 are the rows of D_m^{-1}, G_0 = -(G_1 + G_2 + G_3), and
 // [q]_skew[a][c] = sum_e eps_ace q_e (the contraction of d2J/dF2 with G_v, G_w).
+// Fixed Corotational (the paper's material, Sec. 4.1), with (mu, lam) in
+// place of (mu, lam_hat) and R the polar rotation of F:
+//   Psi = mu |F - R|^2 + lam/2 (J - 1)^2,  P = 2 mu (F - R) + lam (J - 1) C,
+// Hessian blocks from fcr_hess_blocks.  An inverted tet (det F <= 0) has no
+// rotation to extract here: its gradient entries become NaN, which the
+// condensation reports as a non-finite update.
 #include "cc_internal.cuh"
 #include "dmath.cuh"
 
@@ -108,7 +114,8 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
                                                   const double* __restrict__ Bm, const double* __restrict__ vol,
                                                   const uint8_t* __restrict__ pinned, const double* __restrict__ x,
                                                   int64_t n, int t, double mu, double lh, double weight,
-                                                  double* __restrict__ gcon, double* __restrict__ hdst) {
+                                                  double* __restrict__ gcon, double* __restrict__ hdst,
+                                                  bool fcr) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -124,9 +131,19 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
   tet_kinematics_f64(p, B, kin);
   const double s = lh * (kin.J - 1.0) - mu;
   const double V = vol[t] * weight;
-  double P[9];
+  double P[9], R[9];
+  if (fcr) {
+    // lh holds lam for this material
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (!polar_newton<double>(kin.F, R))
+      for (int q = 0; q < 9; ++q) R[q] = nan;
+    const double sl = lh * (kin.J - 1.0);
 #pragma unroll
-  for (int q = 0; q < 9; ++q) P[q] = mu * kin.F[q] + s * kin.C[q];
+    for (int q = 0; q < 9; ++q) P[q] = 2.0 * mu * (kin.F[q] - R[q]) + sl * kin.C[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) P[q] = mu * kin.F[q] + s * kin.C[q];
+  }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     if (pinned[vid[v]]) continue;
@@ -135,11 +152,19 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
     for (int r = 0; r < 3; ++r)
       gcon[3 * e + r] = V * (P[3 * r] * kin.G[v][0] + P[3 * r + 1] * kin.G[v][1] + P[3 * r + 2] * kin.G[v][2]);
   }
-  tet_hess_blocks<double>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
+  if (fcr) fcr_hess_blocks<double>(kin.F, R, kin.C, kin.J, mu, lh, V, kin.G, hdst);
+  else tet_hess_blocks<double>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
 }
 
+// Per-thread staging pitch (values) of the tets' Hessian blocks in shared
+// memory.  An odd pitch puts the 32 lanes' k-th values in distinct banks (a
+// pitch of 96 would put them all in one bank: 32-way conflicts on every
+// staging store).
+constexpr int kStagePitch = 97;
+
 // Staged like the mixed kernel: per-thread blocks in shared memory, then
-// coalesced 16-byte stores of each tet's 768-byte region.
+// coalesced stores of each tet's 768-byte region.
+template <bool kFCR>
 __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                const double* __restrict__ Bm, const double* __restrict__ vol,
                                const uint8_t* __restrict__ pinned, const double* __restrict__ x, int64_t n,
@@ -152,17 +177,17 @@ __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __rest
   const int t = live ? list[k] : -1;
   if (live) {
     const double2 ml = mat[t];
-    tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, t, ml.x, ml.y, weight, gcon, hstage64 + threadIdx.x * 96);
+    tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, t, ml.x, ml.y, weight, gcon,
+                      hstage64 + threadIdx.x * kStagePitch, kFCR);
   }
   __syncwarp();
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   for (int u = 0; u < 32; ++u) {
     const int tu = __shfl_sync(0xffffffffu, t, u);
     if (tu < 0) continue;
-    for (int q = lane; q < 48; q += 32) {
-      const double2 v = reinterpret_cast<const double2*>(hstage64 + (wbase + u) * 96)[q];
-      reinterpret_cast<double2*>(hten + (int64_t)tu * 96)[q] = v;
-    }
+    const double* src = hstage64 + (wbase + u) * kStagePitch;
+#pragma unroll
+    for (int e = lane; e < 90; e += 32) hten[(int64_t)tu * 96 + e] = src[e];
   }
 }
 
@@ -171,7 +196,7 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
                                                     const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
                                                     const float4* __restrict__ x_lo, int t, df mu_d, df lh_d,
                                                     float mu_f, float lh_f, const float* __restrict__ volw32,
-                                                    float2* __restrict__ gcon, float* __restrict__ hdst) {
+                                                    float2* __restrict__ gcon, float* __restrict__ hdst, bool fcr) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -210,8 +235,31 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
   const float2 vw = volw[t];
   const df V{vw.x, vw.y};
   df P[9];
+  float R32[9];
+  if (fcr) {
+    // lh holds lam for this material; R to float32 by Newton, then one
+    // float-float correction against the full F
+    float Fh[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) P[q] = df_mul(V, df_fma(mu_d, F[q], df_mul(s, C[q])));
+    for (int q = 0; q < 9; ++q) Fh[q] = F[q].hi;
+    df R[9];
+    if (polar_newton<float>(Fh, R32)) {
+      polar_refine_df(R32, F, R);
+    } else {
+      const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        R32[q] = nan;
+        R[q] = df{nan, 0.0f};
+      }
+    }
+    const df sl = df_mul(lh_d, Jm1), mu2 = df_scale(mu_d, 2.0f);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) P[q] = df_mul(V, df_fma(mu2, df_sub(F[q], R[q]), df_mul(sl, C[q])));
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) P[q] = df_mul(V, df_fma(mu_d, F[q], df_mul(s, C[q])));
+  }
   df g[4][3];
 #pragma unroll
   for (int v = 1; v < 4; ++v)
@@ -242,9 +290,11 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
     G[3][b] = B[6 + b].hi;
     G[0][b] = -(G[1][b] + G[2][b] + G[3][b]);
   }
-  tet_hess_blocks<float>(Ff, Cf, s.hi, mu_f, lh_f, volw32[t], G, hdst);
+  if (fcr) fcr_hess_blocks<float>(Ff, R32, Cf, J.hi, mu_f, lh_f, volw32[t], G, hdst);
+  else tet_hess_blocks<float>(Ff, Cf, s.hi, mu_f, lh_f, volw32[t], G, hdst);
 }
 
+template <bool kFCR>
 __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                  const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
                                  const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
@@ -252,8 +302,8 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
                                  const float4* __restrict__ matdf, const float* __restrict__ volw32,
                                  float2* __restrict__ gcon, float* __restrict__ hten) {
   pdl_entry();
-  // Each thread's 96 Hessian values are staged in shared memory, then every
-  // warp writes its 32 tets' 384-byte regions with coalesced 16-byte stores.
+  // Each thread's 90 Hessian values are staged in shared memory, then every
+  // warp writes its 32 tets' regions with coalesced 128-byte stores.
   extern __shared__ __align__(16) float hstage[];
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < count;
@@ -261,17 +311,16 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
   if (live) {
     const float4 ml = matdf[t];  // (mu hi, mu lo, lam_hat hi, lam_hat lo)
     tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, t, df{ml.x, ml.y}, df{ml.z, ml.w}, ml.x, ml.z,
-                        volw32, gcon, hstage + threadIdx.x * 96);
+                        volw32, gcon, hstage + threadIdx.x * kStagePitch, kFCR);
   }
   __syncwarp();
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   for (int u = 0; u < 32; ++u) {
     const int tu = __shfl_sync(0xffffffffu, t, u);
     if (tu < 0) continue;
-    if (lane < 24) {
-      const float4 v = reinterpret_cast<const float4*>(hstage + (wbase + u) * 96)[lane];
-      reinterpret_cast<float4*>(hten + (int64_t)tu * 96)[lane] = v;
-    }
+    const float* src = hstage + (wbase + u) * kStagePitch;
+#pragma unroll
+    for (int e = lane; e < 90; e += 32) hten[(int64_t)tu * 96 + e] = src[e];
   }
 }
 
@@ -428,6 +477,7 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t count, d
   if (threadIdx.x == 0) out[0] = v;
 }
 
+template <bool kFCR>
 __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __restrict__ Bm,
                               const double* __restrict__ vol, const double* __restrict__ x, int64_t n,
                               int64_t T, const double2* __restrict__ mat, double weight, double* __restrict__ part) {
@@ -446,12 +496,24 @@ __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __res
     for (int q = 0; q < 9; ++q) B[q] = Bm[9 * t + q];
     TetF64 kin;
     tet_kinematics_f64(p, B, kin);
-    double I = 0.0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) I += kin.F[q] * kin.F[q];
     const double Jm1 = kin.J - 1.0;
     const double mu = mat[t].x, lh = mat[t].y;
-    e += weight * vol[t] * (0.5 * mu * (I - 3.0) - mu * Jm1 + 0.5 * lh * Jm1 * Jm1);
+    if (kFCR) {
+      double R[9];
+      double d2 = 0.0;
+      if (polar_newton<double>(kin.F, R)) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d2 += (kin.F[q] - R[q]) * (kin.F[q] - R[q]);
+      } else {
+        d2 = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      e += weight * vol[t] * (mu * d2 + 0.5 * lh * Jm1 * Jm1);
+    } else {
+      double I = 0.0;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) I += kin.F[q] * kin.F[q];
+      e += weight * vol[t] * (0.5 * mu * (I - 3.0) - mu * Jm1 + 0.5 * lh * Jm1 * Jm1);
+    }
   }
   e = block_sum(e);
   if (threadIdx.x == 0) part[blockIdx.x] = e;
@@ -554,19 +616,25 @@ void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t 
                          cudaStream_t s) {
   if (count <= 0) return;
   constexpr int kThreads = 64;
-  const size_t smem = (size_t)kThreads * 96 * sizeof(double);
-  pdl_launch(k_tet_grad_f64, grid_for(count, kThreads), kThreads, smem, s, m.d_tets.p, m.d_tslot.p, m.d_Bm.p,
-             m.d_vol.p, m.d_pinned.p, x, m.n, list, count, m.d_mat64.p, weight, m.f64.gcon.p, m.f64.hten.p);
+  const size_t smem = (size_t)kThreads * kStagePitch * sizeof(double);
+  auto kern = m.model == CC_MODEL_FCR ? k_tet_grad_f64<true> : k_tet_grad_f64<false>;
+  set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+  pdl_launch(kern, grid_for(count, kThreads), kThreads, smem, s, (const int4*)m.d_tets.p, (const int4*)m.d_tslot.p,
+             (const double*)m.d_Bm.p, (const double*)m.d_vol.p, (const uint8_t*)m.d_pinned.p, x, m.n, list, count,
+             (const double2*)m.d_mat64.p, weight, m.f64.gcon.p, m.f64.hten.p);
 }
 
 void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double weight, cudaStream_t s) {
   if (count <= 0) return;
   (void)weight;
   constexpr int kThreads = 128;
-  const size_t smem = (size_t)kThreads * 96 * sizeof(float);
-  pdl_launch(k_tet_grad_mixed, grid_for(count, kThreads), kThreads, smem, s, m.d_tets.p, m.d_tslot.p, m.d_Bm_df.p,
-             m.d_volw_df.p, m.d_pinned.p, m.mx.x_hi.p, m.mx.x_lo.p, list, count, m.d_matdf.p, m.d_volw32.p,
-             m.mx.gcon.p, m.mx.hten.p);
+  const size_t smem = (size_t)kThreads * kStagePitch * sizeof(float);
+  auto kern = m.model == CC_MODEL_FCR ? k_tet_grad_mixed<true> : k_tet_grad_mixed<false>;
+  set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+  pdl_launch(kern, grid_for(count, kThreads), kThreads, smem, s, (const int4*)m.d_tets.p, (const int4*)m.d_tslot.p,
+             (const float2*)m.d_Bm_df.p, (const float2*)m.d_volw_df.p, (const uint8_t*)m.d_pinned.p,
+             (const float4*)m.mx.x_hi.p, (const float4*)m.mx.x_lo.p, list, count, (const float4*)m.d_matdf.p,
+             (const float*)m.d_volw32.p, m.mx.gcon.p, m.mx.hten.p);
 }
 
 template <typename HT, bool kMixed>
@@ -597,8 +665,9 @@ void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s) {
 
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {
   const double w = m.h > 0.0 ? m.h * m.h : 1.0;
-  pdl_launch(k_energy_tets, kRedBlocks, kBlock, 0, s, m.d_tets.p, m.d_Bm.p, m.d_vol.p, x, m.n, m.T, m.d_mat64.p, w,
-             m.d_red.p);
+  pdl_launch(m.model == CC_MODEL_FCR ? k_energy_tets<true> : k_energy_tets<false>, kRedBlocks, kBlock, 0, s,
+             (const int4*)m.d_tets.p, (const double*)m.d_Bm.p, (const double*)m.d_vol.p, x, m.n, m.T,
+             (const double2*)m.d_mat64.p, w, m.d_red.p);
   if (m.h > 0.0 && xt) {
     pdl_launch(k_energy_inertia, kRedBlocks, kBlock, 0, s, m.d_mass.p, x, xt, m.n, m.d_red.p + kRedBlocks);
     pdl_launch(k_reduce_final, 1, 1024, 0, s, m.d_red.p, (int64_t)(2 * kRedBlocks), out);

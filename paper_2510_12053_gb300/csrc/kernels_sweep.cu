@@ -62,7 +62,7 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
 
 template <typename HT>
 __host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps) {
-  return align16((size_t)sup_max * 9 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
+  return align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
          align16((size_t)smap_max * code_bytes) + (size_t)nwarps * 32 * sizeof(HT);
 }
 
@@ -79,11 +79,21 @@ struct SlotCodes<uint16_t> {
 
 // Stages U_i in shared memory, rotated for corotated bases (Sec. 3.1):
 // U_i^rot[j] = R_j U_i[j] (rot: [n][9] row-major rotations, or nullptr).
-template <typename HT>
+// Slot a's entry (row r, column d) goes to Us[kSlot a + kRow r + d]: (9, 3)
+// packs the blocks, (12, 4) pads each row to four values for vector loads
+// (the pads are zeroed).
+template <typename HT, int kSlot = 9, int kRow = 3>
 __device__ __forceinline__ void stage_basis(HT* Us, const HT* __restrict__ U, const HT* __restrict__ rot,
                                             const int32_t* __restrict__ sup_idx, int s0, int m, int t, int nt) {
   if (!rot) {
-    for (int k = t; k < 9 * m; k += nt) Us[k] = U[(int64_t)s0 * 9 + k];
+    if (kSlot == 9) {
+      for (int k = t; k < 9 * m; k += nt) Us[k] = U[(int64_t)s0 * 9 + k];
+    } else {
+      for (int k = t; k < kSlot * m; k += nt) {
+        const int a = k / kSlot, e = k - a * kSlot, r = e / kRow, d = e - r * kRow;
+        Us[k] = d < 3 ? U[(int64_t)(s0 + a) * 9 + 3 * r + d] : HT(0);
+      }
+    }
     return;
   }
   for (int a = t; a < m; a += nt) {
@@ -96,34 +106,61 @@ __device__ __forceinline__ void stage_basis(HT* Us, const HT* __restrict__ U, co
       u[q] = Ua[q];
     }
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) Us[9 * a + 3 * i + d] = r[3 * i] * u[d] + r[3 * i + 1] * u[3 + d] + r[3 * i + 2] * u[6 + d];
+      for (int d = 0; d < 3; ++d)
+        Us[kSlot * a + kRow * i + d] = r[3 * i] * u[d] + r[3 * i + 1] * u[3 + d] + r[3 * i + 2] * u[6 + d];
+      if (kRow == 4) Us[kSlot * a + kRow * i + 3] = HT(0);
+    }
   }
 }
 
-// Coupling products, one CTA per free vertex i of the list.  Quarter-warps take
-// the block rows of the support S and of i itself; their lanes take the row's
-// upper blocks (H_jl, l >= j).  The vertex's slot map (one code per block,
-// staged in shared memory) gives each block's role: for j, l in S every
-// unordered pair is visited once and contributes M + M^T with
-// M = U_j^T H_jl U_l (H is symmetric); a block (j, i) of a support row gives
-// A's term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
+// Loads the padded 3 x 4 slot at p (three 16-byte rows) into a packed 3 x 3.
+template <typename HT>
+__device__ __forceinline__ void load_slot(const HT* p, HT* u);
+template <>
+__device__ __forceinline__ void load_slot<float>(const float* p, float* u) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float4 v = q[r];
+    u[3 * r] = v.x; u[3 * r + 1] = v.y; u[3 * r + 2] = v.z;
+  }
+}
+template <>
+__device__ __forceinline__ void load_slot<double>(const double* p, double* u) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double2 a = q[2 * r], b = q[2 * r + 1];
+    u[3 * r] = a.x; u[3 * r + 1] = a.y; u[3 * r + 2] = b.x;
+  }
+}
+
+// Coupling products, one CTA per free vertex i of the list.  Groups of
+// 2^row_lanes_log2 threads take the block rows of the support S and of i
+// itself; a group's threads take the row's upper blocks (H_jl, l >= j)
+// round-robin.  The vertex's slot map (one code per block, staged in shared
+// memory) gives each block's role.  Because H is symmetric,
+//   Ht = sum_j (U_j^T Z_j + Z_j^T U_j),  Z_j = 1/2 H_jj U_j + sum_{l > j} H_jl U_l,
+// so a thread accumulates its share of Z_j (27 FMA per block) and folds it
+// with U_j once at the row's end; a block (j, i) of a support row gives A's
+// term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
 // l > i.  The CTA writes 27 values per vertex: Ht (6, symmetric), A (9),
-// b (3), H_ii (9).
+// b (3), H_ii (9, stored directly by the thread that reads it).
 template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads>
 __global__ void __launch_bounds__(kThreads) k_couple(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
     const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, int64_t smap_max,
-    const HT* __restrict__ rot, HT* __restrict__ cpl) {
+    const HT* __restrict__ rot, int row_lanes_log2, HT* __restrict__ cpl) {
   pdl_entry();
   using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* ptr = smem;
-  HT* Us = reinterpret_cast<HT*>(ptr);
-  ptr += align16((size_t)sup_max * 9 * sizeof(HT));
+  HT* Us = reinterpret_cast<HT*>(ptr);  // [m][3][4]
+  ptr += align16((size_t)sup_max * 12 * sizeof(HT));
   int* rstart = reinterpret_cast<int*>(ptr);
   ptr += align16((size_t)(sup_max + 1) * 4);
   int* rlen = reinterpret_cast<int*>(ptr);
@@ -143,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   const int64_t c0 = smap_ptr[i];
   const int ncodes = (int)(smap_ptr[i + 1] - c0);
 
-  stage_basis<HT>(Us, U, rot, sup_idx, s0, m, tid, kThreads);
+  stage_basis<HT, 12, 4>(Us, U, rot, sup_idx, s0, m, tid, kThreads);
   for (int k = tid; k < ncodes; k += kThreads) codes[k] = smap[c0 + k];
   for (int s = tid; s <= m; s += kThreads) {
     const int j = s < m ? sup_idx[s0 + s] : i;
@@ -172,63 +209,78 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   __syncthreads();
 
   HT h00 = 0, h01 = 0, h02 = 0, h11 = 0, h12 = 0, h22 = 0;
-  HT A[9], Hii[9], b[3] = {0, 0, 0};
+  HT A[9], b[3] = {0, 0, 0};
   mat3_zero(A);
-  mat3_zero(Hii);
-  const int qw = tid >> 3, l8 = tid & 7;
-  for (int r = qw; r <= m; r += kThreads / 8) {
+  const int nl = 1 << row_lanes_log2, rl = tid & (nl - 1);
+  for (int r = tid >> row_lanes_log2; r <= m; r += kThreads >> row_lanes_log2) {
     const int P = rstart[r], L = rlen[r], off = roff[r];
-    const HT* Uj = Us + 9 * r;
-    for (int q = l8; q < L; q += 8) {
-      const unsigned code = codes[off + q];
-      if (code == Codes::kNone) continue;
-      HT H[9];
-      load_block(bsr, (int64_t)P + q, H);
-      if (r < m) {
+    if (r < m) {
+      HT Uj[9], Z[9];
+      load_slot(Us + 12 * r, Uj);
+      mat3_zero(Z);
+      bool any = false;
+      for (int q = rl; q < L; q += nl) {
+        const unsigned code = codes[off + q];
+        if (code == Codes::kNone) continue;
+        HT H[9];
+        load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kSelf) {
           if (kUpd == CC_UPDATE_CC) mat3_tmul_acc(H, Uj, A);
+        } else if (code == Codes::kDiag) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) H[c] *= HT(0.5);
+          mat3_mul_acc(H, Uj, Z);
+          any = true;
         } else {
-          // pair (j, l) adds M + M^T; the diagonal block (l = j, M symmetric)
-          // takes the same path with weight 1/2
-          const bool dg = code == Codes::kDiag;
-          const HT w = dg ? HT(0.5) : HT(1);
-          HT T[9], M[9];
-          mat3_zero(T);
-          mat3_mul_acc(H, Us + 9 * (dg ? r : (int)code), T);
-          mat3_zero(M);
-          mat3_tmul_acc(Uj, T, M);
-          h00 += 2 * w * M[0]; h11 += 2 * w * M[4]; h22 += 2 * w * M[8];
-          h01 += w * (M[1] + M[3]); h02 += w * (M[2] + M[6]); h12 += w * (M[5] + M[7]);
+          HT Ul[9];
+          load_slot(Us + 12 * (int)code, Ul);
+          mat3_mul_acc(H, Ul, Z);
+          any = true;
         }
-      } else {
+      }
+      if (any) {
+        HT M[9];
+        mat3_zero(M);
+        mat3_tmul_acc(Uj, Z, M);
+        h00 += 2 * M[0]; h11 += 2 * M[4]; h22 += 2 * M[8];
+        h01 += M[1] + M[3]; h02 += M[2] + M[6]; h12 += M[5] + M[7];
+      }
+      if (rl == 0) {
+        const int j = rid[r];
+        HT gj[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gj[a] = kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) b[c] += Uj[c] * gj[0] + Uj[3 + c] * gj[1] + Uj[6 + c] * gj[2];
+      }
+    } else {
+      for (int q = rl; q < L; q += nl) {
+        const unsigned code = codes[off + q];
+        if (code == Codes::kNone) continue;
+        HT H[9];
+        load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kDiag) {
 #pragma unroll
-          for (int c = 0; c < 9; ++c) Hii[c] = H[c];
+          for (int c = 0; c < 9; ++c) cpl[(int64_t)blockIdx.x * 32 + 18 + c] = H[c];
         } else if (kUpd == CC_UPDATE_CC) {
-          mat3_mul_acc(H, Us + 9 * code, A);
+          HT Ul[9];
+          load_slot(Us + 12 * (int)code, Ul);
+          mat3_mul_acc(H, Ul, A);
         }
       }
     }
-    if (l8 == 0 && r < m) {
-      const int j = rid[r];
-      HT gj[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) gj[a] = kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) b[c] += Uj[c] * gj[0] + Uj[3 + c] * gj[1] + Uj[6 + c] * gj[2];
-    }
   }
 
-  // CTA reduction of 27 values in a fixed order
-  HT vals27[27] = {h00, h01, h02, h11, h12, h22, A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], A[8],
-                   b[0], b[1], b[2], Hii[0], Hii[1], Hii[2], Hii[3], Hii[4], Hii[5], Hii[6], Hii[7], Hii[8]};
+  // CTA reduction of 18 values in a fixed order
+  HT vals[18] = {h00, h01, h02, h11, h12, h22, A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], A[8],
+                 b[0], b[1], b[2]};
 #pragma unroll
-  for (int v = 0; v < 27; ++v) vals27[v] = warp_sum(vals27[v]);
+  for (int v = 0; v < 18; ++v) vals[v] = warp_sum(vals[v]);
   if (lane == 0)
 #pragma unroll
-    for (int v = 0; v < 27; ++v) red[warp * 32 + v] = vals27[v];
+    for (int v = 0; v < 18; ++v) red[warp * 32 + v] = vals[v];
   __syncthreads();
-  if (tid >= 27) return;
+  if (tid >= 18) return;
   // fixed-order sum of the warps' partials
   HT tot = red[tid];
 #pragma unroll
@@ -518,18 +570,21 @@ void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, co
   const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
   const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
   CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+  const int lanes = m.tune_couple_row_lanes;
+  CCG_CHECK(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8, CC_ERR_STATE, "bad coupling row lanes");
+  const int lanes_log2 = lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : 3;
   if (m.smap_wide) {
     auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, cpl);
+               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
   } else {
     auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, cpl);
+               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
   }
   CCG_CUDA(cudaGetLastError());
 }

@@ -97,6 +97,9 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     assert all(v > 0 for v in tune["couple_ms"] + tune["gather_ms"])
     assert tune["couple_ms"][(32, 64, 128, 256).index(tune["couple_threads"])] == min(tune["couple_ms"])
     assert tune["gather_ms"][(2, 4, 8).index(tune["gather_warps"])] == min(tune["gather_ms"])
+    if tune["couple_threads"] != 32:
+        assert all(v > 0 for v in tune["row_lanes_ms"])
+        assert tune["row_lanes_ms"][(1, 2, 4, 8).index(tune["couple_row_lanes"])] == min(tune["row_lanes_ms"])
     xb = x0.clone()
     res_b = batch.solve_batch(xb, precision="mixed", tol=1e-6, max_iters=200, check_every=1)
     assert np.all(res_b["status"] == 1)

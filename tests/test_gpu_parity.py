@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import meshgen
-from oracle import fem, solvers, subspace, topology
+from oracle import fem, material, solvers, subspace, topology
 
 torch = pytest.importorskip("torch")
 import paper_2510_12053_gb300 as cc  # noqa: E402
@@ -123,16 +123,17 @@ def test_one_fp64_sweep_matches_oracle(update, schedule):
         (st_o.fallback_empty, st_o.fallback_reduced, st_o.fallback_schur)
 
 
-@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+@pytest.mark.parametrize("threads,lanes", [(32, 0)] + [(t, r) for t in (64, 128, 256) for r in (1, 2, 4, 8)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_every_coupling_launch_shape_matches_oracle(threads, precision):
-    """One CC sweep with each coupling-kernel shape (32 = one warp per vertex)."""
+def test_every_coupling_launch_shape_matches_oracle(threads, lanes, precision):
+    """One CC sweep with each coupling-kernel shape (32 = one warp per vertex;
+    otherwise threads per vertex x threads per block row)."""
     scene = _box(dims=(7, 6, 5), seed=9)
     pb, topo, sup, U = _oracle(scene, 2)
     x0 = _state(scene, 0.05, 6)
     x_o = solvers.sweep(pb, topo, sup, U, x0, None, "cc", "colored")
     m = _gpu(scene, 2)
-    m.set_launch_shape(couple_threads=threads)
+    m.set_launch_shape(couple_threads=threads, couple_row_lanes=lanes)
     xd = cc.to_soa(x0)
     m.sweep(xd, update="cc", schedule="colored", precision=precision)
     d_o, d_g = x_o - x0, cc.from_soa(xd) - x0
@@ -146,6 +147,8 @@ def test_launch_shape_rejects_unknown_values():
         m.set_launch_shape(couple_threads=96)
     with pytest.raises(cc.CCError):
         m.set_launch_shape(gather_warps=3)
+    with pytest.raises(cc.CCError):
+        m.set_launch_shape(couple_row_lanes=3)
 
 
 def test_pinned_rows_untouched_and_colour_range():
@@ -402,3 +405,89 @@ def test_restarted_solve_follows_the_oracle():
     r = m.solve_step(cc.to_soa(scene.x0), precision="fp64", tol=1e-6, max_iters=200, restart_every=5, check_every=1)
     assert h_o.converged and r.converged
     assert abs(r.iterations - h_o.iterations) <= 1 and h_o.iterations < h_f.iterations
+
+
+# ---------------------------------------------------------------- Fixed Corotational material (Sec. 4.1)
+def _fcr_oracle(scene, k=None):
+    pb = fem.problem_from_scene(scene, "fcr")
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    if k is None:
+        return pb, topo, None, None
+    sup, U = subspace.build_local_bases(pb, topo, k)
+    return pb, topo, sup, U
+
+
+@pytest.mark.parametrize("dynamic", [False, True])
+def test_fcr_energy_and_gradient(dynamic):
+    if dynamic:
+        scene = meshgen.cantilever(3, 4, 7, cell=1 / 16, E=1e6, nu=0.45)
+    else:
+        scene = _box(dims=(5, 6, 4), factor=1.3)
+    pb, _, _, _ = _fcr_oracle(scene)
+    x = _state(scene, 0.08, 8)
+    assert np.all(material.det3(pb.deformation(x)) > 0)   # the GPU path needs non-inverted tets
+    xt = None
+    if dynamic:
+        v = meshgen.normal(9, np.arange(3 * scene.n)).reshape(-1, 3) * 0.1
+        xt = pb.inertial_target(scene.X, v)
+    E_o = pb.energy(x, xt)
+    g_o = pb.gradient(x, xt)
+    g_o[~pb.free] = 0.0
+    m = cc.Mesh.from_scene(scene, model="fcr")
+    xd = cc.to_soa(x)
+    xtd = cc.to_soa(xt) if dynamic else None
+    for prec, tol in [("fp64", 1e-12), ("mixed", 1e-10)]:
+        E, g, gn = m.energy_grad(xd, xtd, precision=prec)
+        assert E == pytest.approx(E_o, rel=1e-12)
+        assert np.abs(cc.from_soa(g) - g_o).max() <= tol * np.abs(g_o).max()
+    # an inverted tet has no rotation to extract on the GPU: the energy is NaN
+    xi = scene.X.copy()
+    xi[pb.free] *= -1.0
+    assert np.any(material.det3(pb.deformation(xi)) <= 0)
+    for prec in ("fp64", "mixed"):
+        assert np.isnan(m.energy_grad(cc.to_soa(xi), xtd, precision=prec, want_grad=False)[0])
+
+
+@pytest.mark.parametrize("update", ["cc", "cd"])
+def test_fcr_one_fp64_sweep_matches_oracle(update):
+    scene = _box()
+    pb, topo, sup, U = _fcr_oracle(scene, 2)
+    x0 = _state(scene, 0.05, 4)
+    x_o = solvers.sweep(pb, topo, sup, U, x0, None, update, "colored")
+    m = cc.Mesh.from_scene(scene, model="fcr")
+    m.color()
+    m.build_subspace(2)
+    xd = cc.to_soa(x0)
+    m.sweep(xd, update=update, precision="fp64")
+    x_g = cc.from_soa(xd)
+    assert np.abs(x_g - x_o).max() <= 1e-12 * np.abs(x_o).max()
+    assert np.abs((x_g - x0) - (x_o - x0)).max() <= 1e-9 * np.abs(x_o - x0).max()
+
+
+def test_fcr_mixed_solve_follows_the_oracle():
+    scene = meshgen.stretch_box(5, 4, 4, E=1e5, nu=0.3, factor=1.5, jitter_amount=0.05, seed=1)
+    pb, topo, sup, U = _fcr_oracle(scene, 2)
+    _, h_o = solvers.solve(pb, topo, sup, U, scene.x0, kind="cc", tol=1e-6, max_iters=150)
+    m = cc.Mesh.from_scene(scene, model="fcr")
+    m.color()
+    m.build_subspace(2)
+    r = m.solve_step(cc.to_soa(scene.x0), precision="mixed", tol=1e-6, max_iters=150, check_every=1)
+    assert h_o.converged and r.converged
+    assert abs(r.iterations - h_o.iterations) <= 2
+    assert r.energy == pytest.approx(h_o.energy[-1], rel=1e-8)
+
+
+def test_batch_rejects_mixed_material_models():
+    a = meshgen.stretch_box(3, 3, 3, E=1e5, nu=0.3)
+    descs = (cc.MeshDesc * 2)()
+    keep = []
+    for k, model in enumerate((0, 1)):
+        X = np.ascontiguousarray(a.X)
+        T = np.ascontiguousarray(a.tets, dtype=np.int32)
+        P = np.ascontiguousarray(a.pinned, dtype=np.uint8)
+        keep += [X, T, P]
+        descs[k] = cc.MeshDesc(X.ctypes.data, X.shape[0], T.ctypes.data, T.shape[0], P.ctypes.data,
+                               cc.Material(1e5, 0.3, 1000.0, model))
+    out = cc.ctypes.c_void_p()
+    rc = cc.lib().cc_build_batch(descs, 2, 0.0, None, None, cc.ctypes.byref(out))
+    assert rc == cc.ERR_INVALID_ARG
