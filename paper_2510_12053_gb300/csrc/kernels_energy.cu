@@ -85,10 +85,10 @@ __device__ __forceinline__ void hess_block(const T* F, const T (&a_v)[3], const 
   K[7] -= s * q0;
 }
 
-// The tet's 10 upper Hessian blocks V K_ab (corner pairs a <= b, order (0,0),
+// The tet's upper Hessian blocks V K_ab (corner pairs a <= b, order (0,0),
 // (0,1), (0,2), (0,3), (1,1), (1,2), (1,3), (2,2), (2,3), (3,3)), each 3x3
-// row-major, into dst[9 pair + q].
-template <typename T>
+// row-major: pairs P0 <= pair < P1 into dst[9 (pair - P0) + q].
+template <typename T, int P0 = 0, int P1 = 10>
 __device__ __forceinline__ void tet_hess_blocks(const T* F, const T* C, T s, T mu, T lh, T V, const T (&G)[4][3],
                                                 T* __restrict__ dst) {
   T a[4][3];
@@ -101,12 +101,44 @@ __device__ __forceinline__ void tet_hess_blocks(const T* F, const T* C, T s, T m
   for (int va = 0; va < 4; ++va)
 #pragma unroll
     for (int vb = va; vb < 4; ++vb) {
-      T K[9];
-      hess_block<T>(F, a[va], a[vb], G[va], G[vb], mu, lh, s, K);
+      if (pair >= P0 && pair < P1) {
+        T K[9];
+        hess_block<T>(F, a[va], a[vb], G[va], G[vb], mu, lh, s, K);
 #pragma unroll
-      for (int q = 0; q < 9; ++q) dst[9 * pair + q] = V * K[q];
+        for (int q = 0; q < 9; ++q) dst[9 * (pair - P0) + q] = V * K[q];
+      }
       ++pair;
     }
+}
+
+// Hessian staging.  Each thread stages its tet's blocks in shared memory at a
+// per-thread pitch, then the warp copies every live tet's staged values to
+// the per-tet store with coalesced stores (flush).  The SNH blocks are formed
+// and flushed in two halves of five pairs (45 values, half the shared memory
+// per thread, so more warps stay resident); FCR forms all ten at once (its
+// blocks accumulate over the nine directions of dF).  The pitches are odd so
+// that the 32 lanes' k-th values fall in distinct banks.
+template <bool kFCR>
+struct TetStage {
+  static constexpr int kVals = kFCR ? 90 : 45;
+  static constexpr int kPitch = kFCR ? 91 : 45;
+};
+
+// Copies the warp's staged values (part `part` of each tet's 90) to the
+// per-tet store; t is this lane's tet (-1: none).  Every lane of the warp
+// calls it.
+template <typename T, int kVals, int kPitch>
+__device__ __forceinline__ void flush_stage(const T* hstage, int t, int part, T* __restrict__ hten) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  for (int u = 0; u < 32; ++u) {
+    const int tu = __shfl_sync(0xffffffffu, t, u);
+    if (tu < 0) continue;
+    const T* src = hstage + (wbase + u) * kPitch;
+#pragma unroll
+    for (int e = lane; e < kVals; e += 32) hten[(int64_t)tu * 96 + part * kVals + e] = src[e];
+  }
+  __syncwarp();
 }
 
 // ---- phase A: per-tet gradients and Hessian blocks of the tets whose vertices moved
@@ -114,8 +146,8 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
                                                   const double* __restrict__ Bm, const double* __restrict__ vol,
                                                   const uint8_t* __restrict__ pinned, const double* __restrict__ x,
                                                   int64_t n, int t, double mu, double lh, double weight,
-                                                  double* __restrict__ gcon, double* __restrict__ hdst,
-                                                  bool fcr) {
+                                                  double* __restrict__ gcon, double* __restrict__ hstage,
+                                                  bool fcr, bool live, int t_store, double* __restrict__ hten) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -146,24 +178,27 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    if (pinned[vid[v]]) continue;
+    if (!live || pinned[vid[v]]) continue;
     const int64_t e = ent[v];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
       gcon[3 * e + r] = V * (P[3 * r] * kin.G[v][0] + P[3 * r + 1] * kin.G[v][1] + P[3 * r + 2] * kin.G[v][2]);
   }
-  if (fcr) fcr_hess_blocks<double>(kin.F, R, kin.C, kin.J, mu, lh, V, kin.G, hdst);
-  else tet_hess_blocks<double>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
+  double* hdst = hstage + threadIdx.x * (fcr ? TetStage<true>::kPitch : TetStage<false>::kPitch);
+  if (fcr) {
+    fcr_hess_blocks<double>(kin.F, R, kin.C, kin.J, mu, lh, V, kin.G, hdst);
+    flush_stage<double, TetStage<true>::kVals, TetStage<true>::kPitch>(hstage, t_store, 0, hten);
+  } else {
+    tet_hess_blocks<double, 0, 5>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
+    flush_stage<double, TetStage<false>::kVals, TetStage<false>::kPitch>(hstage, t_store, 0, hten);
+    tet_hess_blocks<double, 5, 10>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
+    flush_stage<double, TetStage<false>::kVals, TetStage<false>::kPitch>(hstage, t_store, 1, hten);
+  }
 }
 
-// Per-thread staging pitch (values) of the tets' Hessian blocks in shared
-// memory.  An odd pitch puts the 32 lanes' k-th values in distinct banks (a
-// pitch of 96 would put them all in one bank: 32-way conflicts on every
-// staging store).
-constexpr int kStagePitch = 97;
-
-// Staged like the mixed kernel: per-thread blocks in shared memory, then
-// coalesced stores of each tet's 768-byte region.
+// Float64 per-tet kernel; the Hessian blocks go through the shared-memory
+// staging above.  Lanes past the list evaluate the list's first tet and store
+// nothing (every lane takes part in the warp's flushes).
 template <bool kFCR>
 __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                const double* __restrict__ Bm, const double* __restrict__ vol,
@@ -175,20 +210,10 @@ __global__ void k_tet_grad_f64(const int4* __restrict__ tets, const int4* __rest
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < count;
   const int t = live ? list[k] : -1;
-  if (live) {
-    const double2 ml = mat[t];
-    tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, t, ml.x, ml.y, weight, gcon,
-                      hstage64 + threadIdx.x * kStagePitch, kFCR);
-  }
-  __syncwarp();
-  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-  for (int u = 0; u < 32; ++u) {
-    const int tu = __shfl_sync(0xffffffffu, t, u);
-    if (tu < 0) continue;
-    const double* src = hstage64 + (wbase + u) * kStagePitch;
-#pragma unroll
-    for (int e = lane; e < 90; e += 32) hten[(int64_t)tu * 96 + e] = src[e];
-  }
+  const int tc = live ? t : list[0];
+  const double2 ml = mat[tc];
+  tet_grad_f64_body(tets, tslot, Bm, vol, pinned, x, n, tc, ml.x, ml.y, weight, gcon, hstage64, kFCR, live, t,
+                    hten);
 }
 
 __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tets, const int4* __restrict__ tslot,
@@ -196,7 +221,8 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
                                                     const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
                                                     const float4* __restrict__ x_lo, int t, df mu_d, df lh_d,
                                                     float mu_f, float lh_f, const float* __restrict__ volw32,
-                                                    float2* __restrict__ gcon, float* __restrict__ hdst, bool fcr) {
+                                                    float2* __restrict__ gcon, float* __restrict__ hstage, bool fcr,
+                                                    bool live, int t_store, float* __restrict__ hten) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -271,7 +297,7 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
   for (int r = 0; r < 3; ++r) g[0][r] = df_neg(df_add(df_add(g[1][r], g[2][r]), g[3][r]));
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    if (pinned[vid[v]]) continue;
+    if (!live || pinned[vid[v]]) continue;
     const int64_t e = ent[v];
 #pragma unroll
     for (int r = 0; r < 3; ++r) gcon[3 * e + r] = make_float2(g[v][r].hi, g[v][r].lo);
@@ -290,10 +316,22 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
     G[3][b] = B[6 + b].hi;
     G[0][b] = -(G[1][b] + G[2][b] + G[3][b]);
   }
-  if (fcr) fcr_hess_blocks<float>(Ff, R32, Cf, J.hi, mu_f, lh_f, volw32[t], G, hdst);
-  else tet_hess_blocks<float>(Ff, Cf, s.hi, mu_f, lh_f, volw32[t], G, hdst);
+  float* hdst = hstage + threadIdx.x * (fcr ? TetStage<true>::kPitch : TetStage<false>::kPitch);
+  const float V32 = volw32[t];
+  if (fcr) {
+    fcr_hess_blocks<float>(Ff, R32, Cf, J.hi, mu_f, lh_f, V32, G, hdst);
+    flush_stage<float, TetStage<true>::kVals, TetStage<true>::kPitch>(hstage, t_store, 0, hten);
+  } else {
+    tet_hess_blocks<float, 0, 5>(Ff, Cf, s.hi, mu_f, lh_f, V32, G, hdst);
+    flush_stage<float, TetStage<false>::kVals, TetStage<false>::kPitch>(hstage, t_store, 0, hten);
+    tet_hess_blocks<float, 5, 10>(Ff, Cf, s.hi, mu_f, lh_f, V32, G, hdst);
+    flush_stage<float, TetStage<false>::kVals, TetStage<false>::kPitch>(hstage, t_store, 1, hten);
+  }
 }
 
+// Float-float per-tet kernel (gradient in float-float, Hessian blocks in
+// float32 through the shared-memory staging above).  Lanes past the list
+// evaluate the list's first tet and store nothing.
 template <bool kFCR>
 __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                  const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
@@ -302,26 +340,14 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
                                  const float4* __restrict__ matdf, const float* __restrict__ volw32,
                                  float2* __restrict__ gcon, float* __restrict__ hten) {
   pdl_entry();
-  // Each thread's 90 Hessian values are staged in shared memory, then every
-  // warp writes its 32 tets' regions with coalesced 128-byte stores.
   extern __shared__ __align__(16) float hstage[];
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < count;
   const int t = live ? list[k] : -1;
-  if (live) {
-    const float4 ml = matdf[t];  // (mu hi, mu lo, lam_hat hi, lam_hat lo)
-    tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, t, df{ml.x, ml.y}, df{ml.z, ml.w}, ml.x, ml.z,
-                        volw32, gcon, hstage + threadIdx.x * kStagePitch, kFCR);
-  }
-  __syncwarp();
-  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-  for (int u = 0; u < 32; ++u) {
-    const int tu = __shfl_sync(0xffffffffu, t, u);
-    if (tu < 0) continue;
-    const float* src = hstage + (wbase + u) * kStagePitch;
-#pragma unroll
-    for (int e = lane; e < 90; e += 32) hten[(int64_t)tu * 96 + e] = src[e];
-  }
+  const int tc = live ? t : list[0];
+  const float4 ml = matdf[tc];  // (mu hi, mu lo, lam_hat hi, lam_hat lo)
+  tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, tc, df{ml.x, ml.y}, df{ml.z, ml.w}, ml.x, ml.z,
+                      volw32, gcon, hstage, kFCR, live, t, hten);
 }
 
 // ---- phase B: one warp per free row j ---------------------------------------
@@ -616,8 +642,10 @@ void launch_tet_grad_f64(Mesh& m, const double* x, const int32_t* list, int64_t 
                          cudaStream_t s) {
   if (count <= 0) return;
   constexpr int kThreads = 64;
-  const size_t smem = (size_t)kThreads * kStagePitch * sizeof(double);
-  auto kern = m.model == CC_MODEL_FCR ? k_tet_grad_f64<true> : k_tet_grad_f64<false>;
+  const bool fcr = m.model == CC_MODEL_FCR;
+  const size_t smem =
+      (size_t)kThreads * (fcr ? TetStage<true>::kPitch : TetStage<false>::kPitch) * sizeof(double);
+  auto kern = fcr ? k_tet_grad_f64<true> : k_tet_grad_f64<false>;
   set_smem_limit(reinterpret_cast<const void*>(kern), smem);
   pdl_launch(kern, grid_for(count, kThreads), kThreads, smem, s, (const int4*)m.d_tets.p, (const int4*)m.d_tslot.p,
              (const double*)m.d_Bm.p, (const double*)m.d_vol.p, (const uint8_t*)m.d_pinned.p, x, m.n, list, count,
@@ -628,8 +656,9 @@ void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double w
   if (count <= 0) return;
   (void)weight;
   constexpr int kThreads = 128;
-  const size_t smem = (size_t)kThreads * kStagePitch * sizeof(float);
-  auto kern = m.model == CC_MODEL_FCR ? k_tet_grad_mixed<true> : k_tet_grad_mixed<false>;
+  const bool fcr = m.model == CC_MODEL_FCR;
+  const size_t smem = (size_t)kThreads * (fcr ? TetStage<true>::kPitch : TetStage<false>::kPitch) * sizeof(float);
+  auto kern = fcr ? k_tet_grad_mixed<true> : k_tet_grad_mixed<false>;
   set_smem_limit(reinterpret_cast<const void*>(kern), smem);
   pdl_launch(kern, grid_for(count, kThreads), kThreads, smem, s, (const int4*)m.d_tets.p, (const int4*)m.d_tslot.p,
              (const float2*)m.d_Bm_df.p, (const float2*)m.d_volw_df.p, (const uint8_t*)m.d_pinned.p,
