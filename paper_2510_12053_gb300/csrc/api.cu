@@ -399,7 +399,7 @@ void cc_destroy_mesh(cc_mesh* m) {
   rel(m->d_mesh_fptr); rel(m->d_mesh_active); rel(m->d_mesh_ones); rel(m->d_mesh_gsq); rel(m->d_volw); rel(m->d_volw32); rel(m->d_volw_df); rel(m->d_mass);
   rel(m->d_mass32); rel(m->d_mass_df);
   rel(m->d_pinned); rel(m->d_vt_ptr); rel(m->d_nbr_ptr); rel(m->d_nbr_idx); rel(m->d_vt_tet); rel(m->d_vt_corner);
-  rel(m->d_up_ptr); rel(m->d_up_col); rel(m->d_rs_ptr); rel(m->d_rs_src); rel(m->d_free_rows);
+  rel(m->d_up_ptr); rel(m->d_up_col); rel(m->d_rs_ptr); rel(m->d_rs_src); rel(m->d_free_rows); rel(m->d_row_hdr);
   rel(m->d_color); rel(m->d_cv_idx); rel(m->d_tl); rel(m->d_all_tets); rel(m->d_sup_ptr); rel(m->d_sup_idx); rel(m->d_smap_ptr);
   rel(m->d_smap8); rel(m->d_smap16); rel(m->d_vt_ids);
   rel(m->f64.gcon); rel(m->f64.hten); rel(m->f64.g); rel(m->f64.cpl); rel(m->f64.bsr); rel(m->f64.U);

@@ -138,7 +138,7 @@ struct Mesh {
   Prof prof;
   // launch configurations chosen by cc_autotune (defaults before tuning)
   int tune_couple_threads = 64;   // threads per vertex in the coupling kernel (32: one warp)
-  int tune_couple_row_lanes = 2;  // threads per block row in the coupling kernel (1, 2, 4, 8)
+  int tune_couple_row_lanes = 4;  // threads per block row in the coupling kernel (1, 2, 4, 8)
   int tune_gather_wpb = 4;        // warps (rows) per block in the row gather
   int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
   int32_t max_valence = 0;
@@ -208,6 +208,7 @@ struct Mesh {
   DBuf<int32_t> d_rs_ptr;    // [nnz_up+1] sources of each upper block (free rows)
   DBuf<int32_t> d_rs_src;    // per-tet store offset of each source, bit 31 = transpose
   DBuf<int32_t> d_free_rows; // free vertices, ascending
+  DBuf<int4> d_row_hdr;      // [2 n_free] row gather records: (j, p0, nup, rb), (rcount, e0, val, 0)
   DBuf<int32_t> d_color;     // [n]
   std::vector<int32_t> cv_ptr;  // [C+1] free vertices per colour
   DBuf<int32_t> d_cv_idx;

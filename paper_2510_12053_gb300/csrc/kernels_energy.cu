@@ -350,6 +350,58 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
                       volw32, gcon, hstage, kFCR, live, t, hten);
 }
 
+// Gradient of free row j from its per-(vertex, slot) entries e0 .. e0 + val - 1
+// (plus the inertial term of dynamic solves).
+template <bool kMixed>
+__device__ __forceinline__ void row_gradient(int j, int e0, int val, int lane, const double* __restrict__ gcon64,
+                                             const float2* __restrict__ gcon_df, const double* __restrict__ mass64,
+                                             const float2* __restrict__ mass_df, const double* __restrict__ x,
+                                             const float4* __restrict__ x_hi, const float4* __restrict__ x_lo,
+                                             const double* __restrict__ xt, const float4* __restrict__ xt_hi,
+                                             const float4* __restrict__ xt_lo, int64_t n, bool dynamic,
+                                             double* __restrict__ g64, float* __restrict__ g_hi,
+                                             float* __restrict__ g_lo) {
+  // gradient: lane 8a + p (component a < 3, p < 8) sums the entries p, p + 8,
+  // ... of component a in order, then a fixed butterfly over its eight lanes
+  // finishes the sum (lanes 24..31 carry zeros through the shuffles)
+  const int ga = lane >> 3, gp = lane & 7;
+  if (kMixed) {
+    df gd{0.0f, 0.0f};
+    if (ga < 3)
+      for (int k = gp; k < val; k += 8) {
+        const float2 cc = gcon_df[3 * (int64_t)(e0 + k) + ga];
+        gd = df_add(gd, df{cc.x, cc.y});
+      }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      const df other{__shfl_xor_sync(0xffffffffu, gd.hi, o), __shfl_xor_sync(0xffffffffu, gd.lo, o)};
+      gd = df_add(gd, other);
+    }
+    if (ga < 3 && gp == 0) {
+      if (dynamic) {
+        const df mj{mass_df[j].x, mass_df[j].y};
+        const float xh = reinterpret_cast<const float*>(x_hi + j)[ga];
+        const float xl = reinterpret_cast<const float*>(x_lo + j)[ga];
+        const float th = reinterpret_cast<const float*>(xt_hi + j)[ga];
+        const float tl = reinterpret_cast<const float*>(xt_lo + j)[ga];
+        gd = df_fma(mj, df_sub(df{xh, xl}, df{th, tl}), gd);
+      }
+      g_hi[3 * (int64_t)j + ga] = gd.hi;
+      g_lo[3 * (int64_t)j + ga] = gd.lo;
+    }
+  } else {
+    double gs = 0.0;
+    if (ga < 3)
+      for (int k = gp; k < val; k += 8) gs += gcon64[3 * (int64_t)(e0 + k) + ga];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
+    if (ga < 3 && gp == 0) {
+      if (dynamic) gs += mass64[j] * (x[ga * n + j] - xt[ga * n + j]);
+      g64[3 * (int64_t)j + ga] = gs;
+    }
+  }
+}
+
 // ---- phase B: one warp per free row j ---------------------------------------
 // Every upper block (j, l) of the row sums its sources -- the stored blocks of
 // the incident tets, transposed where the tet lists l before j -- in a fixed
@@ -357,9 +409,11 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
 // sources are split over three groups of nine lanes, the other blocks take
 // nine lanes each, three per round.  Blocks are written padded to 3 x 4.  The
 // row's gradient is the fixed-butterfly sum of its per-(vertex, slot) entries.
+// A row starts from its 32-byte record (row id, block and source ranges,
+// entry range), so the index chain before the stored blocks are read is two
+// loads deep; the gradient, which needs only the record, is summed first.
 template <typename HT, bool kMixed>
-__global__ void k_row_gather(const int32_t* __restrict__ rows, int64_t nrows, const int32_t* __restrict__ vt_ptr,
-                             const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ rs_ptr,
+__global__ void k_row_gather(const int4* __restrict__ row_hdr, int64_t nrows, const int32_t* __restrict__ rs_ptr,
                              const int32_t* __restrict__ rs_src, const HT* __restrict__ hten,
                              const HT* __restrict__ massh, const double* __restrict__ mass64,
                              const float2* __restrict__ mass_df, const double* __restrict__ gcon64,
@@ -374,16 +428,16 @@ __global__ void k_row_gather(const int32_t* __restrict__ rows, int64_t nrows, co
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * wpb + warp;
   if (wid >= nrows) return;
-  const int j = rows[wid];
-  const int p0 = up_ptr[j], nup = up_ptr[j + 1] - p0;
+  const int4 h0 = __ldg(row_hdr + 2 * wid), h1 = __ldg(row_hdr + 2 * wid + 1);
+  const int j = h0.x, p0 = h0.y, nup = h0.z, rb = h0.w, rcount = h1.x;
+  row_gradient<kMixed>(j, h1.y, h1.z, lane, gcon64, gcon_df, mass64, mass_df, x, x_hi, x_lo, xt, xt_hi, xt_lo, n,
+                       dynamic, g64, g_hi, g_lo);
   const int c = lane % 9, grp = lane / 9, r = c / 3, col = c % 3;
   const int tidx = 3 * col + r;
   // the row's source offsets and per-block ranges, one coalesced pass
   int* roff = rsh + warp * (max_rs + max_up + 1);
   int* rsrc = roff + max_up + 1;
-  const int rb = rs_ptr[p0];
   for (int q = lane; q <= nup; q += 32) roff[q] = rs_ptr[p0 + q] - rb;
-  const int rcount = rs_ptr[p0 + nup] - rb;
   for (int k = lane; k < rcount; k += 32) rsrc[k] = rs_src[rb + k];
   __syncwarp();
 
@@ -422,56 +476,6 @@ __global__ void k_row_gather(const int32_t* __restrict__ rows, int64_t nrows, co
       HT* dst = bsr + (int64_t)(p0 + q) * 12 + 4 * r;
       dst[col] = acc;
       if (col == 2) dst[3] = HT(0);
-    }
-  }
-  // gradient
-  const int e0 = vt_ptr[j], val = vt_ptr[j + 1] - e0;
-  if (kMixed) {
-    df gd[3] = {df{0, 0}, df{0, 0}, df{0, 0}};
-    for (int k = lane; k < val; k += 32)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float2 cc = gcon_df[3 * (int64_t)(e0 + k) + a];
-        gd[a] = df_add(gd[a], df{cc.x, cc.y});
-      }
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        df other{__shfl_xor_sync(0xffffffffu, gd[a].hi, o), __shfl_xor_sync(0xffffffffu, gd[a].lo, o)};
-        gd[a] = df_add(gd[a], other);
-      }
-    if (lane == 0) {
-      if (dynamic) {
-        const df mj{mass_df[j].x, mass_df[j].y};
-        const float4 xh = x_hi[j], xl = x_lo[j], th = xt_hi[j], tl = xt_lo[j];
-        gd[0] = df_fma(mj, df_sub(df{xh.x, xl.x}, df{th.x, tl.x}), gd[0]);
-        gd[1] = df_fma(mj, df_sub(df{xh.y, xl.y}, df{th.y, tl.y}), gd[1]);
-        gd[2] = df_fma(mj, df_sub(df{xh.z, xl.z}, df{th.z, tl.z}), gd[2]);
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        g_hi[3 * (int64_t)j + a] = gd[a].hi;
-        g_lo[3 * (int64_t)j + a] = gd[a].lo;
-      }
-    }
-  } else {
-    double gs[3] = {0.0, 0.0, 0.0};
-    for (int k = lane; k < val; k += 32)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) gs[a] += gcon64[3 * (int64_t)(e0 + k) + a];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) gs[a] += __shfl_xor_sync(0xffffffffu, gs[a], o);
-    if (lane == 0) {
-      if (dynamic) {
-        const double mj = mass64[j];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gs[a] += mj * (x[a * n + j] - xt[a * n + j]);
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) g64[3 * (int64_t)j + a] = gs[a];
     }
   }
 }
@@ -675,7 +679,7 @@ static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, con
   const size_t smem = (size_t)wpb * (m.max_rs + m.max_up + 1) * sizeof(int);
   set_smem_limit(reinterpret_cast<const void*>(k_row_gather<HT, kMixed>), smem);
   pdl_launch(k_row_gather<HT, kMixed>, (unsigned)blocks, 32 * wpb, smem, s,
-      m.d_free_rows.p, m.n_free, m.d_vt_ptr.p, m.d_up_ptr.p, m.d_rs_ptr.p, m.d_rs_src.p, hten, massh, m.d_mass.p,
+      (const int4*)m.d_row_hdr.p, m.n_free, m.d_rs_ptr.p, m.d_rs_src.p, hten, massh, m.d_mass.p,
       m.d_mass_df.p, kMixed ? nullptr : m.f64.gcon.p, kMixed ? m.mx.gcon.p : nullptr, x,
       kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr, dyn ? xt : nullptr,
       kMixed ? m.mx.xt_hi.p : nullptr, kMixed ? m.mx.xt_lo.p : nullptr, m.n, dyn, m.max_rs, m.max_up, bsr,

@@ -264,6 +264,26 @@ void build_topology(Mesh& m) {
   m.d_rs_ptr.upload(rs_ptr, s);
   m.d_rs_src.upload(rs_src, s);
   m.d_free_rows.upload(free_rows, s);
+  {
+    // per free row, what the row gather needs first, in one 32-byte record:
+    // (j, first upper block, upper blocks, first source), (sources, first
+    // vertex-tet entry, entries, 0)
+    std::vector<int32_t> hdr(8 * free_rows.size(), 0);
+    for (size_t w = 0; w < free_rows.size(); ++w) {
+      const int32_t j = free_rows[w];
+      const int32_t p0 = (int32_t)m.up_ptr[j], p1 = (int32_t)m.up_ptr[j + 1];
+      int32_t* h = &hdr[8 * w];
+      h[0] = j;
+      h[1] = p0;
+      h[2] = p1 - p0;
+      h[3] = rs_ptr[p0];
+      h[4] = rs_ptr[p1] - rs_ptr[p0];
+      h[5] = (int32_t)m.vt_ptr[j];
+      h[6] = (int32_t)(m.vt_ptr[j + 1] - m.vt_ptr[j]);
+    }
+    m.d_row_hdr.upload(reinterpret_cast<const int4*>(hdr.data()), 2 * (int64_t)free_rows.size(), s);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
   m.d_all_tets.upload(active, s);
   {
     if (m.mesh_vptr.empty()) {
