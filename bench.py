@@ -85,6 +85,9 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the 256-mesh batched solve")
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--no-learned", action="store_true", help="skip the learned-basis workload")
+    p.add_argument("--resolution-sweep", action="store_true",
+                   help="add the SNH / FCR mesh-resolution sweep (8^3 .. 48^3 cubes)")
+    p.add_argument("--resolution-max-iters", type=int, default=3000)
     p.add_argument("--train-meshes", type=int, default=2000)
     p.add_argument("--train-steps", type=int, default=4000)
     p.add_argument("--train-batch", type=int, default=8192)
@@ -338,6 +341,43 @@ def mlp_flops(dims, rows, backward=False):
     if backward:
         f += 2.0 * rows * sum(nk) + 2.0 * rows * sum(nk[1:])
     return f
+
+
+def run_resolution(args, stream, dev):
+    """Mesh-resolution sweep with both materials: jittered n^3 stretch cubes
+    (E = 1e5, nu = 0.3, 1.5x, seed 0) for n in 8..48, solved to 1e-6 with
+    mixed-precision coloured CC on 2-ring rest bases; SNH and FCR with fixed
+    bases, FCR with corotated bases.  Sweeps and time to tolerance per case."""
+    import torch
+    import meshgen
+    import paper_2510_12053_gb300 as cc
+    out = []
+    for side in (8, 16, 24, 32, 48):
+        sc = meshgen.stretch_box(side, side, side, E=1e5, nu=0.3, factor=1.5, jitter_amount=0.05, seed=0,
+                                 name=f"cube{side}")
+        n_free = int((sc.pinned == 0).sum())
+        x0 = cc.to_soa(sc.x0, device=dev)
+        for model, corot in (("snh", False), ("fcr", False), ("fcr", True)):
+            m = cc.Mesh.from_scene(sc, stream=stream, model=model)
+            m.color()
+            m.build_subspace(K_RING)
+            x = x0.clone()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rec = {"side": side, "n_free": n_free, "material": model, "corotated": corot}
+            try:
+                r = m.solve_step(x, precision="mixed", tol=1e-6, max_iters=args.resolution_max_iters,
+                                 check_every=args.check_every, use_graph=not args.no_graph, corotated=corot)
+                ev1.record(stream)
+                ev1.synchronize()
+                rec.update(sweeps=r.iterations, converged=r.converged, ms=ev0.elapsed_time(ev1),
+                           rel_residual=r.g_final / r.g0)
+            except cc.CCError as e:   # a diverging solve is reported, not fatal
+                torch.cuda.synchronize()
+                rec.update(sweeps=None, converged=False, error=str(e))
+            m.close()
+            out.append(rec)
+    return out
 
 
 def run_learned(args, stream, dev):
@@ -635,6 +675,7 @@ def run_ours(args, rank, world):
     learned_res = None
     if not args.no_learned:
         learned_res = run_learned(args, stream, dev)
+    resolution_res = run_resolution(args, stream, dev) if args.resolution_sweep else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -669,6 +710,8 @@ def run_ours(args, rank, world):
             "batch": batch_res,
             "learned": learned_res,
         }
+        if resolution_res is not None:
+            line["resolution"] = resolution_res
         print(json.dumps(line), flush=True)
     for m in meshes:
         m.close()
