@@ -88,6 +88,9 @@ def parse():
     p.add_argument("--resolution-sweep", action="store_true",
                    help="add the SNH / FCR mesh-resolution sweep (8^3 .. 48^3 cubes)")
     p.add_argument("--resolution-max-iters", type=int, default=3000)
+    p.add_argument("--large-beam", action="store_true",
+                   help="add the throughput run on the 64x64x256-cell beam (1.09 M vertices)")
+    p.add_argument("--large-sweeps", type=int, default=40)
     p.add_argument("--train-meshes", type=int, default=2000)
     p.add_argument("--train-steps", type=int, default=4000)
     p.add_argument("--train-batch", type=int, default=8192)
@@ -377,6 +380,76 @@ def run_resolution(args, stream, dev):
                 rec.update(sweeps=None, converged=False, error=str(e))
             m.close()
             out.append(rec)
+    return out
+
+
+def run_large(args, stream, dev):
+    """Throughput on a mesh far larger than L2: the 64 x 64 x 256-cell beam
+    (1 085 825 vertices, 6 291 456 tets) as a quasistatic 1.2x stretch along
+    its long axis (SNH, E = 1e5, nu = 0.3, jitter 5%, seed 0), 2-ring bases,
+    mixed-precision coloured CC for a fixed number of sweeps (the run measures
+    rates, not convergence).  Per-class kernel time from CUDA events and the
+    HBM rate of the gather and per-tet kernels on their algorithmic bytes."""
+    import torch
+    import meshgen
+    import paper_2510_12053_gb300 as cc
+    sc = meshgen.stretch_box(64, 64, 256, E=1e5, nu=0.3, factor=1.2, jitter_amount=0.05, seed=0, axis=2,
+                             size=4.0, name="beam64x64x256")
+    n_free = int((sc.pinned == 0).sum())
+    t0 = time.perf_counter()
+    m = cc.Mesh.from_scene(sc, stream=stream)
+    m.color()
+    m.build_subspace(K_RING)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    x0 = cc.to_soa(sc.x0, device=dev)
+    sweeps = args.large_sweeps
+    m.solve_step(x0.clone(), precision="mixed", tol=1e-30, max_iters=4, check_every=4,
+                 use_graph=not args.no_graph)   # warm-up (graph capture)
+    m.profile_enable(True)
+    x = x0.clone()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    r = m.solve_step(x, precision="mixed", tol=1e-30, max_iters=sweeps, check_every=sweeps,
+                     use_graph=not args.no_graph)
+    ev1.record(stream)
+    ev1.synchronize()
+    prof = m.profile_read()
+    m.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    ncol = int(m.info().num_colors)
+    # algorithmic bytes (vectorised forms of the per-unit figures used for the cube)
+    tets = np.asarray(sc.tets, dtype=np.int64)
+    ge = tets[:, None, :] >= tets[:, :, None]
+    src = np.zeros(sc.n)
+    np.add.at(src, tets.ravel(), ge.sum(axis=2).ravel())
+    val = np.bincount(tets.ravel(), minlength=sc.n)
+    nbp, nbi = m.export("nbr_ptr"), m.export("nbr_idx")
+    owner = np.repeat(np.arange(sc.n), np.diff(nbp))
+    nup = np.bincount(owner[nbi > owner], minlength=sc.n) + 1
+    free = sc.pinned == 0
+    gather_bytes = float((src * 36 + val * 24 + nup * 36 + 24)[free].sum())
+    free_corners = int((sc.pinned[sc.tets] == 0).sum())
+    active_tets = int((sc.pinned[sc.tets] == 0).any(axis=1).sum())
+    tet_refreshes = r.iterations * free_corners + active_tets
+    gathers = r.iterations * ncol + 1
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    ga, te = prof["gather"], prof["tet_eval"]
+    out = {"workload": f"beam 64x64x256 cells ({sc.n} vertices, {sc.T} tets), 1.2x stretch along z, SNH E=1e5 "
+                       f"nu=0.3, jitter 5%, 2-ring bases, mixed coloured CC, {sweeps} sweeps",
+           "n_free": n_free, "colors": ncol, "setup_s": setup_s, "sweeps": r.iterations, "ms": ms,
+           "ms_per_sweep": ms / max(r.iterations, 1),
+           "vertex_updates_per_s": n_free * r.iterations / (ms / 1e3),
+           "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+           "peak_hbm_gbs": hbm, "peak_source": peak_src}
+    if ga["ms"] > 0:
+        a = gather_bytes * gathers / (ga["ms"] / 1e3) / 1e9
+        out["gather_hbm"] = {"achieved_gbs": a, "frac": a / hbm, "bytes_per_launch": gather_bytes}
+    if te["ms"] > 0:
+        a = TET_BYTES * tet_refreshes / (te["ms"] / 1e3) / 1e9
+        out["tet_eval_hbm"] = {"achieved_gbs": a, "frac": a / hbm, "bytes_per_tet": TET_BYTES}
+    m.close()
     return out
 
 
@@ -676,6 +749,7 @@ def run_ours(args, rank, world):
     if not args.no_learned:
         learned_res = run_learned(args, stream, dev)
     resolution_res = run_resolution(args, stream, dev) if args.resolution_sweep else None
+    large_res = run_large(args, stream, dev) if args.large_beam else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -712,6 +786,8 @@ def run_ours(args, rank, world):
         }
         if resolution_res is not None:
             line["resolution"] = resolution_res
+        if large_res is not None:
+            line["large_beam"] = large_res
         print(json.dumps(line), flush=True)
     for m in meshes:
         m.close()
