@@ -216,6 +216,27 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+# ----------------------------------------------------------------------------- ranks
+def reduce_over_ranks(x: float, world: int, device, op: str) -> float:
+    """A host number reduced over all ranks ("max": the slowest rank's time;
+    "sum": the units every rank processed).  One rank: x itself."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units: float, ms: float, world: int, device) -> float:
+    """Units per second of the whole job: the units all ranks processed over
+    the slowest rank's time."""
+    total_units = reduce_over_ranks(units, world, device, "sum")
+    slowest_ms = reduce_over_ranks(ms, world, device, "max")
+    return total_units / (slowest_ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- GPU
 def local_solve_flops(mesh):
     """Algorithmic float32 FLOPs of the coupling products per free vertex:
@@ -654,12 +675,9 @@ def run_ours(args, rank, world):
     for m in meshes:
         m.profile_enable(False)
     total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     updates = n_free * sweeps_total
-    value = world * updates / (total_ms / 1e3)
+    value = whole_job_rate(updates, total_ms, world, dev)
+    total_ms = reduce_over_ranks(total_ms, world, dev, "max")
     sweeps_per_solve = sweeps_total / (args.steps * len(meshes))
 
     # per-class device time over the timed region
@@ -727,6 +745,8 @@ def run_ours(args, rank, world):
     x_host.copy_(torch.as_tensor(np.ascontiguousarray(scs[0].x0.T)))
     out_host = torch.empty_like(x_host, pin_memory=True)
     e2e_ms, e2e_sweeps = [], 0
+    torch.cuda.synchronize()
+    dist_barrier()
     for _ in range(args.steps):
         flush.zero_()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -740,7 +760,9 @@ def run_ours(args, rank, world):
         ev1.record(stream)
         ev1.synchronize()
         e2e_ms.append(ev0.elapsed_time(ev1))
-    e2e_value = world * n_free * e2e_sweeps / (sum(e2e_ms) / 1e3)
+    torch.cuda.synchronize()
+    dist_barrier()
+    e2e_value = whole_job_rate(n_free * e2e_sweeps, sum(e2e_ms), world, dev)
 
     batch_res = None
     if not args.no_batch:
