@@ -673,6 +673,7 @@ void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double w
 template <typename HT, bool kMixed>
 static void launch_rows(Mesh& m, const double* x, const double* xt, HT* bsr, const HT* hten, const HT* massh,
                         cudaStream_t s) {
+  if (m.n_free <= 0) return;  // every vertex pinned: no rows
   const bool dyn = m.h > 0.0;
   const int wpb = m.tune_gather_wpb > 0 ? m.tune_gather_wpb : 4;
   const int64_t blocks = (m.n_free + wpb - 1) / wpb;
