@@ -273,7 +273,7 @@ def random_boxes(count: int, seed: int, **kw) -> List[Scene]:
     return [random_box(i, seed, **kw) for i in range(count)]
 
 
-# Named workloads (sizes of the paper-shaped tests; see the design doc for the recipe)
+# Named workloads (the sizes of the paper-shaped tests)
 def cube8_stretch(E: float = 1e5, init: str = "linear") -> Scene:
     """8x8x8-cell unit cube (729 vertices, 3 072 tets), clamped at x=0, pulled to 1.5 at x=1."""
     return stretch_box(8, 8, 8, E=E, nu=0.45, init=init, name="cube8_stretch")

@@ -2,8 +2,9 @@
 
 Integer outputs (adjacency, colours, supports) must be bit-identical.  A
 float64 sweep must match the oracle to 1e-12 relative in x (and its update to
-1e-9 relative).  Mixed-precision results are checked against the tolerances
-derived from float32 Hessian arithmetic ("Tolerances").
+1e-9 relative).  Mixed-precision results are checked against tolerances
+derived from float32 Hessian arithmetic: float32 coupling products carry about
+1e-6 relative error, amplified by the condition of the 3x3 local systems.
 """
 import numpy as np
 import pytest
