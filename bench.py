@@ -475,7 +475,7 @@ def run_large(args, stream, dev):
 
 
 def run_learned(args, stream, dev):
-    """Learned bases (configuration 5): train the network on computed 2-ring
+    """Learned bases: train the network on computed 2-ring
     bases of jittered random boxes (sides U{4..12}, batch-family materials and
     boundary conditions, seed 0; the last 10% held out), then solve the
     48x48x48-cell stretch cube (E = 1e6, jitter 5%) with learned bases (with
