@@ -243,7 +243,8 @@ __device__ __forceinline__ void acc_hu(double* acc, const double* Hb, bool tr, c
 // (transposed).  Fixed summation order; fixed shuffle reduction.
 __global__ void k_basis_residual(int nrows, const int32_t* __restrict__ rows, const int32_t* __restrict__ sup_ptr,
                                  const int32_t* __restrict__ sup_idx, const int32_t* __restrict__ up_ptr,
-                                 const int32_t* __restrict__ up_col, const double* __restrict__ bsr,
+                                 const int32_t* __restrict__ up_col, const int32_t* __restrict__ nbr_ptr,
+                                 const int32_t* __restrict__ nbr_idx, const double* __restrict__ bsr,
                                  const double* __restrict__ U, double* __restrict__ rho) {
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -270,10 +271,13 @@ __global__ void k_basis_residual(int nrows, const int32_t* __restrict__ rows, co
         if (t >= 0) acc_hu(acc, Hb, false, U + (int64_t)(s0 + t) * 9);
       }
     }
-    // rows l < j of the patch (and of i): block (l, j) is H_lj = H_jl^T
-    for (int b = -1; b < m; ++b) {
-      const int l = b < 0 ? i : S[b];
-      if (l >= j) continue;
+    // neighbours l < j of j that lie in the patch (or are i), ascending:
+    // block (l, j), stored in row l, is H_jl^T
+    for (int e = nbr_ptr[j]; e < nbr_ptr[j + 1]; ++e) {
+      const int l = nbr_idx[e];
+      if (l >= j) break;
+      const int b = l == i ? -1 : find_sorted_i32(S, m, l);
+      if (l != i && b < 0) continue;
       const int q0 = up_ptr[l] + 1, q1 = up_ptr[l + 1];  // diagonal first, then ascending
       const int pos = find_sorted_i32(up_col + q0, q1 - q0, j);
       if (pos < 0) continue;
@@ -1000,7 +1004,8 @@ cc_status cc_build_learned_subspace(cc_mesh* m, cc_mlp* net, double tau, double*
     rho.alloc(nf);
     k_basis_residual<<<blocks_for((int64_t)nf * 32, 256), 256, 0, s>>>(nf, m->d_free_rows.p, m->d_sup_ptr.p,
                                                                        m->d_sup_idx.p, m->d_up_ptr.p, m->d_up_col.p,
-                                                                       m->f64.bsr.p, m->f64.U.p, rho.p);
+                                                                       m->d_nbr_ptr.p, m->d_nbr_idx.p, m->f64.bsr.p,
+                                                                       m->f64.U.p, rho.p);
     CCG_CUDA(cudaGetLastError());
     std::vector<double> hr(nf);
     CCG_CUDA(cudaMemcpyAsync(hr.data(), rho.p, nf * sizeof(double), cudaMemcpyDeviceToHost, s));
