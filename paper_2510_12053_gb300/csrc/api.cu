@@ -464,7 +464,6 @@ cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup
     m->sup_ptr.assign(sup_ptr, sup_ptr + n + 1);
     m->sup_idx.assign(sup_idx, sup_idx + total);
     m->sup_max = supmax;
-    ccg::build_slot_maps(*m);
     int hs = 32;
     while (hs < 2 * std::max(supmax, 1)) hs <<= 1;
     m->hash_size = hs;
@@ -473,6 +472,7 @@ cc_status cc_set_subspace(cc_mesh* m, const int64_t* sup_ptr, const int32_t* sup
     for (int64_t v = 0; v <= n; ++v) sp32[v] = (int32_t)sup_ptr[v];
     m->d_sup_ptr.upload(sp32, m->stream);
     m->d_sup_idx.upload(m->sup_idx, m->stream);
+    ccg::build_slot_maps(*m);
     m->f64.U.alloc(9 * std::max<int64_t>(total, 1));
     if (total) CCG_CUDA(cudaMemcpyAsync(m->f64.U.p, U, 9 * total * sizeof(double), cudaMemcpyHostToDevice, m->stream));
     m->mx.U.alloc(9 * std::max<int64_t>(total, 1));

@@ -284,7 +284,8 @@ void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
 // Host-side helpers implemented in mesh_build.cpp (topology, plain C++)
 // ---------------------------------------------------------------------------
 void build_topology(Mesh& m);
-// Slot maps for the current supports (after cc_build_subspace / cc_set_subspace).
+// Slot maps for the current supports (after cc_build_subspace / cc_set_subspace;
+// kernels_setup.cu, built on the device: d_sup_ptr / d_sup_idx must be uploaded).
 void build_slot_maps(Mesh& m);
 // host worker threads for setup passes, and a parallel loop over vertex ranges
 int host_threads(int64_t items);

@@ -223,6 +223,113 @@ void run_coloring(Mesh& m) {
 
 // k-ring supports on the host: breadth-first over the 1-ring CSR, free
 // vertices only, i excluded, ascending.  Uploads them and the slot maps.
+namespace {
+// Index of key in the ascending a[0..m), or -1.
+__device__ __forceinline__ int find_in_sorted(const int32_t* __restrict__ a, int m, int key) {
+  int lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int x = a[mid];
+    if (x == key) return mid;
+    if (x < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// Slot maps, one warp per free vertex v: for every upper block of the rows
+// of S_v (in support order) and then of v's own row, in row order, a code:
+// the diagonal block, the block whose column is v itself, the support slot
+// of the block's column, or none (column outside the support).  Lane r takes
+// row r of a 32-row chunk; a warp scan of the row lengths places the rows.
+template <typename SlotT>
+__global__ void k_slot_maps(const int32_t* __restrict__ rows, int64_t nrows, const int32_t* __restrict__ sup_ptr,
+                            const int32_t* __restrict__ sup_idx, const int32_t* __restrict__ up_ptr,
+                            const int32_t* __restrict__ up_col, const int64_t* __restrict__ smap_ptr,
+                            SlotT* __restrict__ codes) {
+  constexpr unsigned kNone = sizeof(SlotT) == 1 ? 0xFFu : 0xFFFFu, kSelf = kNone - 1, kDiag = kNone - 2;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;  // whole warps leave together
+  const int v = rows[w];
+  const int s0 = sup_ptr[v], m = sup_ptr[v + 1] - s0;
+  const int32_t* S = sup_idx + s0;
+  int64_t base = smap_ptr[v];
+  for (int r0 = 0; r0 <= m; r0 += 32) {
+    const int r = r0 + lane;
+    int len = 0, p0 = 0;
+    if (r <= m) {
+      const int j = r < m ? S[r] : v;
+      p0 = up_ptr[j];
+      len = up_ptr[j + 1] - p0;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    for (int q = 0; q < len; ++q) {
+      const int l = up_col[p0 + q];
+      unsigned code;
+      if (q == 0) code = kDiag;
+      else if (l == v) code = kSelf;
+      else {
+        const int t = find_in_sorted(S, m, l);
+        code = t >= 0 ? (unsigned)t : kNone;
+      }
+      codes[base + (incl - len) + q] = (SlotT)code;
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+}  // namespace
+
+// Slot maps of the current supports (cc_build_subspace / cc_set_subspace),
+// built on the device from the uploaded supports and upper block pattern.
+// The host only sums the row lengths per vertex for the offsets.
+void build_slot_maps(Mesh& m) {
+  const int64_t n = m.n;
+  cudaStream_t s = m.stream;
+  m.smap_wide = m.sup_max >= 250;
+  std::vector<int64_t> len(n, 0);
+  const int nt = host_threads(n);
+  std::vector<int64_t> longest_t(nt, 0);
+  parallel_ranges(n, nt, [&](int t, int64_t v0, int64_t v1) {
+    for (int64_t v = v0; v < v1; ++v) {
+      if (m.pinned[v]) continue;
+      int64_t c = m.up_ptr[v + 1] - m.up_ptr[v];
+      for (int64_t p = m.sup_ptr[v]; p < m.sup_ptr[v + 1]; ++p) {
+        const int32_t j = m.sup_idx[p];
+        c += m.up_ptr[j + 1] - m.up_ptr[j];
+      }
+      len[v] = c;
+      longest_t[t] = std::max(longest_t[t], c);
+    }
+  });
+  std::vector<int64_t> ptr(n + 1, 0);
+  for (int64_t v = 0; v < n; ++v) ptr[v + 1] = ptr[v] + len[v];
+  m.smap_max = *std::max_element(longest_t.begin(), longest_t.end());
+  m.d_smap_ptr.upload(ptr, s);
+  const int64_t total = std::max<int64_t>(ptr[n], 1);
+  const unsigned grid = (unsigned)((m.n_free * 32 + 255) / 256);
+  if (m.smap_wide) {
+    m.d_smap16.alloc(total);
+    m.d_smap8.release();
+    if (m.n_free > 0)
+      k_slot_maps<uint16_t><<<grid, 256, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_sup_ptr.p, m.d_sup_idx.p,
+                                                 m.d_up_ptr.p, m.d_up_col.p, m.d_smap_ptr.p, m.d_smap16.p);
+  } else {
+    m.d_smap8.alloc(total);
+    m.d_smap16.release();
+    if (m.n_free > 0)
+      k_slot_maps<uint8_t><<<grid, 256, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_sup_ptr.p, m.d_sup_idx.p,
+                                                m.d_up_ptr.p, m.d_up_col.p, m.d_smap_ptr.p, m.d_smap8.p);
+  }
+  CCG_CUDA(cudaGetLastError());
+  CCG_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_supports(Mesh& m, int32_t k) {
   cudaStream_t s = m.stream;
   const int64_t n = m.n;
@@ -267,7 +374,6 @@ void build_supports(Mesh& m, int32_t k) {
   CCG_CHECK(m.sup_idx.size() < (size_t(1) << 31), CC_ERR_INVALID_ARG, "support arrays exceed 2^31 entries");
   CCG_CHECK(supmax < 32768, CC_ERR_INVALID_ARG, "support larger than 32767 vertices");
   m.sup_max = supmax;
-  build_slot_maps(m);
   int hs = 32;
   while (hs < 2 * std::max(supmax, 1)) hs <<= 1;
   m.hash_size = hs;
@@ -276,6 +382,7 @@ void build_supports(Mesh& m, int32_t k) {
   for (int64_t v = 0; v <= n; ++v) sp32[v] = (int32_t)m.sup_ptr[v];
   m.d_sup_ptr.upload(sp32, s);
   m.d_sup_idx.upload(m.sup_idx, s);
+  build_slot_maps(m);  // on the device, from the uploaded supports
   const int64_t total = (int64_t)m.sup_idx.size();
   m.f64.U.alloc(9 * std::max<int64_t>(total, 1));
   m.mx.U.alloc(9 * std::max<int64_t>(total, 1));

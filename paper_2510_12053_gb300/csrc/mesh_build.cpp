@@ -319,56 +319,4 @@ void build_topology(Mesh& m) {
   CCG_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
 }
 
-void build_slot_maps(Mesh& m) {
-  const int64_t n = m.n;
-  m.smap_wide = m.sup_max >= 250;
-  const uint16_t kNone = m.smap_wide ? 0xFFFF : 0xFF, kSelf = m.smap_wide ? 0xFFFE : 0xFE,
-                 kDiag = m.smap_wide ? 0xFFFD : 0xFD;
-  // vertex ranges in parallel, each with its own slot scratch; concatenated in order
-  const int nt = host_threads(n);
-  std::vector<std::vector<uint16_t>> codes_t(nt);
-  std::vector<int64_t> len(n, 0);
-  std::vector<int64_t> longest_t(nt, 0);
-  parallel_ranges(n, nt, [&](int t, int64_t v0, int64_t v1) {
-    std::vector<int32_t> slot(n, -1);
-    std::vector<uint16_t>& codes = codes_t[t];
-    for (int64_t v = v0; v < v1; ++v) {
-      if (m.pinned[v]) continue;
-      const int64_t s0 = m.sup_ptr[v], s1 = m.sup_ptr[v + 1];
-      for (int64_t s = s0; s < s1; ++s) slot[m.sup_idx[s]] = (int32_t)(s - s0);
-      const int64_t before = (int64_t)codes.size();
-      for (int64_t r = s0; r <= s1; ++r) {
-        const int64_t j = r < s1 ? m.sup_idx[r] : v;
-        for (int64_t p = m.up_ptr[j]; p < m.up_ptr[j + 1]; ++p) {
-          const int32_t l = m.up_col[p];
-          uint16_t c;
-          if (p == m.up_ptr[j]) c = kDiag;
-          else if (l == v) c = kSelf;
-          else c = slot[l] >= 0 ? (uint16_t)slot[l] : kNone;
-          codes.push_back(c);
-        }
-      }
-      len[v] = (int64_t)codes.size() - before;
-      longest_t[t] = std::max<int64_t>(longest_t[t], len[v]);
-      for (int64_t s = s0; s < s1; ++s) slot[m.sup_idx[s]] = -1;
-    }
-  });
-  std::vector<int64_t> ptr(n + 1, 0);
-  for (int64_t v = 0; v < n; ++v) ptr[v + 1] = ptr[v] + len[v];
-  std::vector<uint16_t> codes;
-  codes.reserve(ptr[n]);
-  for (int t = 0; t < nt; ++t) codes.insert(codes.end(), codes_t[t].begin(), codes_t[t].end());
-  m.smap_max = *std::max_element(longest_t.begin(), longest_t.end());
-  m.d_smap_ptr.upload(ptr, m.stream);
-  if (m.smap_wide) {
-    m.d_smap16.upload(codes, m.stream);
-    m.d_smap8.release();
-  } else {
-    std::vector<uint8_t> c8(codes.begin(), codes.end());
-    m.d_smap8.upload(c8, m.stream);
-    m.d_smap16.release();
-  }
-  CCG_CUDA(cudaStreamSynchronize(m.stream));
-}
-
 }  // namespace ccg
