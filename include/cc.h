@@ -154,6 +154,9 @@ typedef struct {
   int64_t support_total; /* sum of |S_i| (0 until cc_build_subspace) */
   int32_t support_max;
   int32_t max_valence; /* tets per vertex, maximum */
+  int64_t patch_float64; /* patches of the last basis build that the float32-factor, float64-refined
+                            solve handed to the plain float64 solve (non-positive float32 pivot, or
+                            refinement not down to 1e-11); 0 when every patch settled */
 } cc_mesh_info;
 
 /* Arrays cc_export can copy to the host (element type in brackets). */
@@ -202,7 +205,12 @@ cc_status cc_color(cc_mesh* mesh, int32_t* colors_out, int32_t* num_colors);
  * (Eq. 5, Sec. 3.1), one per free vertex i, on the patch P = S_i: the free
  * vertices within k_ring 1-ring hops of i, i excluded, every DOF outside P
  * held fixed.  H is the rest Hessian of E (dynamic meshes: M + h^2 K).
- * Dense float64 Cholesky per patch on the GPU.  k_ring in [1, 4].
+ * Patches of at most 192 unknowns (every 2-ring of a Kuhn grid): float32
+ * Cholesky in shared memory with float64 iterative refinement of U to
+ * float64 accuracy; larger patches, and those the refinement declines
+ * (cc_mesh_info.patch_float64), by dense float64 Cholesky.  A patch whose
+ * H_PP is not positive definite keeps its previous basis and fails the call
+ * with CC_ERR_NUMERIC.  k_ring in [1, 4].
  * Requires cc_color first (CC_ERR_STATE otherwise). */
 cc_status cc_build_subspace(cc_mesh* mesh, int32_t k_ring);
 

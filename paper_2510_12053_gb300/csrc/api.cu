@@ -1011,6 +1011,7 @@ cc_status cc_get_info(const cc_mesh* m, cc_mesh_info* info) {
     info->support_total = (int64_t)m->sup_idx.size();
     info->support_max = m->sup_max;
     info->max_valence = m->max_valence;
+    info->patch_float64 = m->last_patch_redo;
   })
 }
 

@@ -160,6 +160,7 @@ struct Mesh {
   int64_t nnz_up = 0;
   int32_t max_up = 0;          // longest upper block row
   int32_t max_rs = 0;          // most staged sources of one free row
+  int64_t last_patch_redo = 0; // patches the last mixed patch solve handed to the float64 kernel
   std::vector<double> mass;
   std::vector<double> tet_mu, tet_lh, tet_rho;   // per-tet material (a batch mixes materials);
                                                  // tet_lh = lam + mu (stable Neo-Hookean) or lam (FCR)

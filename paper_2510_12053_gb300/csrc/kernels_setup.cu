@@ -422,9 +422,241 @@ int64_t rebuild_bases_at(Mesh& m, const double* x) {
 
 // Dense patch solves (Eq. 5 on P = S_i) for a device list of free vertices,
 // written into the float64 bases.  Needs the rest Hessian in the block rows.
+namespace {
+// ---- patch solves in float32 with float64 iterative refinement --------------
+// For patches of at most kPmMaxN = 192 unknowns (every 2-ring of a Kuhn grid):
+// H_PP is assembled in float32 into shared memory (packed lower triangle,
+// column-major) and factored by Cholesky there; U = -H_PP^{-1} H_Pi is then
+// reached by iterative refinement -- z += L^{-T} L^{-1} (B - H_PP z), B = -H_Pi,
+// with the residual in float64 from the float64 block rows -- until the
+// correction is below 1e-13 of z or stops shrinking (it then sits at the
+// rounding level of the float64 residual).  A patch whose float32
+// factorization meets a non-positive pivot, or whose last correction is above
+// 1e-11 of z, is queued for the float64 kernel (which also decides positive
+// definiteness).
+constexpr int kPmMaxN = 192;
+constexpr int kPmMaxIt = 12;
+constexpr int kPmThreads = 256;
+
+__host__ __device__ constexpr size_t pm_smem_bytes() {
+  return (size_t)kPmMaxN * (kPmMaxN + 1) / 2 * sizeof(float) + 3 * (3 * (size_t)kPmMaxN * sizeof(double)) +
+         3 * (size_t)kPmMaxN * sizeof(float) + 64;
+}
+
+__device__ __forceinline__ int pm_idx(int N, int c, int r) {  // lower (r >= c), column c
+  return c * N - (c * (c - 1)) / 2 + (r - c);
+}
+
+// y_a = sum_t H_{S[a] S[t]} z_t (float64, 3 columns) for row block a of the
+// patch, from the upper block rows: blocks (j, l >= j) of row j = S[a], and
+// blocks (l, j) of the rows of j's lower neighbours l (stored transposed).
+__device__ void pm_apply_row(int a, int i, const int32_t* __restrict__ S, int m, int N,
+                             const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ up_col,
+                             const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                             const double* __restrict__ bsr, const double* Z, double* y /*[3][3] rows x cols*/) {
+  const int j = S[a];
+  for (int q = 0; q < 9; ++q) y[q] = 0.0;
+  for (int p = up_ptr[j]; p < up_ptr[j + 1]; ++p) {
+    const int l = up_col[p];
+    const int t = l == j ? a : (l == i ? -1 : find_sorted(S, m, l));
+    if (t < 0) continue;
+    const double* Hb = bsr + (int64_t)p * 12;  // H_jl, row r at Hb[4 r]
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) {
+        double acc = y[3 * r + d];
+        for (int c = 0; c < 3; ++c) acc = fma(Hb[4 * r + c], Z[d * N + 3 * t + c], acc);
+        y[3 * r + d] = acc;
+      }
+  }
+  for (int e = nbr_ptr[j]; e < nbr_ptr[j + 1]; ++e) {
+    const int l = nbr_idx[e];
+    if (l >= j) break;
+    if (l == i) continue;
+    const int t = find_sorted(S, m, l);
+    if (t < 0) continue;
+    const int q0 = up_ptr[l] + 1, q1 = up_ptr[l + 1];
+    const int pos = find_sorted(up_col + q0, q1 - q0, j);
+    if (pos < 0) continue;
+    const double* Hb = bsr + (int64_t)(q0 + pos) * 12;  // H_lj; H_jl = H_lj^T
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) {
+        double acc = y[3 * r + d];
+        for (int c = 0; c < 3; ++c) acc = fma(Hb[4 * c + r], Z[d * N + 3 * t + c], acc);
+        y[3 * r + d] = acc;
+      }
+  }
+}
+
+__global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
+    const int32_t* __restrict__ verts, const int32_t* __restrict__ sup_ptr, const int32_t* __restrict__ sup_idx,
+    const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ up_col, const int32_t* __restrict__ nbr_ptr,
+    const int32_t* __restrict__ nbr_idx, const double* __restrict__ bsr, double* __restrict__ Uout,
+    int32_t* __restrict__ redo, int32_t* __restrict__ n_redo) {
+  extern __shared__ __align__(16) unsigned char pm_smem[];
+  float* L = reinterpret_cast<float*>(pm_smem);
+  double* B = reinterpret_cast<double*>(pm_smem + (size_t)kPmMaxN * (kPmMaxN + 1) / 2 * sizeof(float));
+  double* Z = B + 3 * kPmMaxN;
+  double* R = Z + 3 * kPmMaxN;
+  float* D = reinterpret_cast<float*>(R + 3 * kPmMaxN);
+  __shared__ int bad;
+  __shared__ double dmax, zmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = verts[blockIdx.x];
+  const int s0 = sup_ptr[i], m = sup_ptr[i + 1] - s0;
+  const int N = 3 * m;
+  if (m == 0) return;  // the whole CTA leaves
+  const int32_t* S = sup_idx + s0;
+  const int nL = N * (N + 1) / 2;
+  for (int k = tid; k < nL; k += kPmThreads) L[k] = 0.0f;
+  for (int k = tid; k < 3 * N; k += kPmThreads) {
+    B[k] = 0.0;
+    Z[k] = 0.0;
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  // assembly: lower triangle of H_PP (float32) and B = -H_Pi (float64)
+  for (int a = tid; a <= m; a += kPmThreads) {
+    const int j = a < m ? S[a] : i;
+    for (int p = up_ptr[j]; p < up_ptr[j + 1]; ++p) {
+      const int l = up_col[p];
+      const double* Hb = bsr + (int64_t)p * 12;  // H_jl, row r at Hb[4 r]
+      if (a < m) {
+        if (l == j) {
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c <= r; ++c) L[pm_idx(N, 3 * a + c, 3 * a + r)] = (float)Hb[4 * r + c];
+        } else if (l == i) {
+          for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) B[d * N + 3 * a + r] = -Hb[4 * r + d];
+        } else {
+          const int t = find_sorted(S, m, l);  // l > j, so t > a: the block sits below the diagonal
+          if (t >= 0)
+            for (int r = 0; r < 3; ++r)
+              for (int c = 0; c < 3; ++c) L[pm_idx(N, 3 * a + r, 3 * t + c)] = (float)Hb[4 * r + c];
+        }
+      } else if (l != i) {
+        const int t = find_sorted(S, m, l);  // row i: H_li = H_il^T
+        if (t >= 0)
+          for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) B[d * N + 3 * t + r] = -Hb[4 * d + r];
+      }
+    }
+  }
+  __syncthreads();
+  // right-looking Cholesky in shared memory
+  for (int c = 0; c < N; ++c) {
+    if (tid == 0) {
+      const float d = L[pm_idx(N, c, c)];
+      if (!(d > 0.0f)) bad = 1;
+      L[pm_idx(N, c, c)] = sqrtf(fmaxf(d, 1e-30f));
+    }
+    __syncthreads();
+    const float piv = L[pm_idx(N, c, c)];
+    for (int r = c + 1 + tid; r < N; r += kPmThreads) L[pm_idx(N, c, r)] /= piv;
+    __syncthreads();
+    for (int r = c + 1 + tid; r < N; r += kPmThreads) {
+      const float lrc = L[pm_idx(N, c, r)];
+      for (int s = c + 1; s <= r; ++s) L[pm_idx(N, s, r)] -= lrc * L[pm_idx(N, c, s)];
+    }
+    __syncthreads();
+  }
+  bool ok = bad == 0;
+  // iterative refinement: R = B - H_PP Z (float64), D = (L L^T)^{-1} R (float32), Z += D
+  bool settled = false;
+  double prev = 1e300, ratio = 1e300;
+  for (int it = 0; ok && it < kPmMaxIt && !settled; ++it) {
+    for (int a = tid; a < m; a += kPmThreads) {
+      double y[9];
+      pm_apply_row(a, i, S, m, N, up_ptr, up_col, nbr_ptr, nbr_idx, bsr, Z, y);
+      for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) {
+          R[d * N + 3 * a + r] = B[d * N + 3 * a + r] - y[3 * r + d];
+          D[d * N + 3 * a + r] = (float)R[d * N + 3 * a + r];
+        }
+    }
+    if (tid == 0) {
+      dmax = 0.0;
+      zmax = 0.0;
+    }
+    __syncthreads();
+    // triangular solves, warp w < 3 for right-hand side w
+    if (warp < 3) {
+      float* y = D + warp * N;
+      for (int c = 0; c < N; ++c) {
+        if (lane == 0) y[c] /= L[pm_idx(N, c, c)];
+        __syncwarp();
+        const float yc = y[c];
+        for (int r = c + 1 + lane; r < N; r += 32) y[r] -= L[pm_idx(N, c, r)] * yc;
+        __syncwarp();
+      }
+      for (int c = N - 1; c >= 0; --c) {
+        if (lane == 0) y[c] /= L[pm_idx(N, c, c)];
+        __syncwarp();
+        const float yc = y[c];
+        for (int r = lane; r < c; r += 32) y[r] -= L[pm_idx(N, r, c)] * yc;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    double dl = 0.0, zl = 0.0;
+    for (int k = tid; k < 3 * N; k += kPmThreads) {
+      const double d = (double)D[k];
+      Z[k] += d;
+      dl = fmax(dl, fabs(d));
+      zl = fmax(zl, fabs(Z[k]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dl = fmax(dl, __shfl_xor_sync(0xffffffffu, dl, o));
+      zl = fmax(zl, __shfl_xor_sync(0xffffffffu, zl, o));
+    }
+    if (lane == 0) {
+      atomicMax(reinterpret_cast<unsigned long long*>(&dmax), __double_as_longlong(dl));
+      atomicMax(reinterpret_cast<unsigned long long*>(&zmax), __double_as_longlong(zl));
+    }
+    __syncthreads();
+    const double dm = dmax, zm = zmax;
+    __syncthreads();
+    settled = dm <= 1e-13 * zm;
+    ratio = zm > 0.0 ? dm / zm : 0.0;
+    if (dm > 0.5 * prev) break;  // corrections at the float64 rounding level of the residual
+    prev = dm;
+  }
+  // accepted when the last correction is at most 1e-11 of z (the float64
+  // solve's own rounding is about cond(H_PP) * 1e-16)
+  if (!(ok && (settled || ratio <= 1e-11))) {
+    if (tid == 0) redo[atomicAdd(n_redo, 1)] = i;
+    return;
+  }
+  for (int k = tid; k < 9 * m; k += kPmThreads) {
+    const int a = k / 9, q = k % 9, r = q / 3, d = q % 3;
+    Uout[(int64_t)(s0 + a) * 9 + q] = Z[d * N + 3 * a + r];
+  }
+}
+}  // namespace
+
 int64_t patch_solves(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail) {
   cudaStream_t s = m.stream;
   if (count <= 0) return 0;
+  DBuf<int32_t> redo;
+  m.last_patch_redo = count;
+  if (3 * m.sup_max <= kPmMaxN) {
+    // float32 factor + float64 refinement; the patches it hands back go to
+    // the float64 kernel below
+    redo.alloc(count + 1);
+    CCG_CUDA(cudaMemsetAsync(redo.p + count, 0, sizeof(int32_t), s));
+    const size_t smem = pm_smem_bytes();
+    set_smem_limit(reinterpret_cast<const void*>(k_patch_basis_mixed), smem);
+    k_patch_basis_mixed<<<(unsigned)count, kPmThreads, smem, s>>>(
+        d_verts, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_up_ptr.p, m.d_up_col.p, m.d_nbr_ptr.p, m.d_nbr_idx.p,
+        m.f64.bsr.p, m.f64.U.p, redo.p, redo.p + count);
+    CCG_CUDA(cudaGetLastError());
+    int32_t nr = 0;
+    CCG_CUDA(cudaMemcpyAsync(&nr, redo.p + count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    m.last_patch_redo = nr;
+    if (nr == 0) return 0;
+    d_verts = redo.p;
+    count = nr;
+  }
   const int Nmax = 3 * std::max(m.sup_max, 1);
   const size_t per = (size_t)Nmax * Nmax + 3 * (size_t)Nmax;
   int64_t batch = std::max<int64_t>(1, (int64_t)((size_t(1) << 30) / (per * sizeof(double))));
