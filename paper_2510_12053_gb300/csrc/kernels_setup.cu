@@ -440,7 +440,7 @@ constexpr int kPmThreads = 256;
 
 __host__ __device__ constexpr size_t pm_smem_bytes() {
   return (size_t)kPmMaxN * (kPmMaxN + 1) / 2 * sizeof(float) + 3 * (3 * (size_t)kPmMaxN * sizeof(double)) +
-         3 * (size_t)kPmMaxN * sizeof(float) + 64;
+         3 * (size_t)kPmMaxN * sizeof(float) + (size_t)kPmMaxN * (kPmMaxN + 1) / 2 + 64;
 }
 
 __device__ __forceinline__ int pm_idx(int N, int c, int r) {  // lower (r >= c), column c
@@ -498,6 +498,8 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
   double* Z = B + 3 * kPmMaxN;
   double* R = Z + 3 * kPmMaxN;
   float* D = reinterpret_cast<float*>(R + 3 * kPmMaxN);
+  uint8_t* colof = reinterpret_cast<uint8_t*>(D + 3 * kPmMaxN);  // packed index -> its column
+  __shared__ int cstart[kPmMaxN + 1];                              // packed start of each column
   __shared__ int bad;
   __shared__ double dmax, zmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -513,6 +515,11 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     Z[k] = 0.0;
   }
   if (tid == 0) bad = 0;
+  for (int c = tid; c <= N; c += kPmThreads) cstart[c] = c * N - (c * (c - 1)) / 2;
+  for (int c = tid; c < N; c += kPmThreads) {
+    const int e0 = c * N - (c * (c - 1)) / 2;
+    for (int e = e0; e < e0 + N - c; ++e) colof[e] = (uint8_t)c;
+  }
   __syncthreads();
   // assembly: lower triangle of H_PP (float32) and B = -H_Pi (float64)
   for (int a = tid; a <= m; a += kPmThreads) {
@@ -553,9 +560,14 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     const float piv = L[pm_idx(N, c, c)];
     for (int r = c + 1 + tid; r < N; r += kPmThreads) L[pm_idx(N, c, r)] /= piv;
     __syncthreads();
-    for (int r = c + 1 + tid; r < N; r += kPmThreads) {
-      const float lrc = L[pm_idx(N, c, r)];
-      for (int s = c + 1; s <= r; ++s) L[pm_idx(N, s, r)] -= lrc * L[pm_idx(N, c, s)];
+    // trailing update L(s, r) -= L(r, c) L(s, c), s > c, r >= s: the trailing
+    // columns are contiguous in the packed layout, so the threads stride over
+    // their elements evenly
+    const float* Lc = L + cstart[c] - c;  // Lc[r] = L(r, c)
+    for (int e = cstart[c + 1] + tid; e < nL; e += kPmThreads) {
+      const int sc = colof[e];
+      const int r = sc + (e - cstart[sc]);
+      L[e] -= Lc[r] * Lc[sc];
     }
     __syncthreads();
   }
