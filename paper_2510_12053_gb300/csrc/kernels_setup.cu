@@ -435,7 +435,7 @@ namespace {
 // 1e-11 of z, is queued for the float64 kernel (which also decides positive
 // definiteness).
 constexpr int kPmMaxN = 192;
-constexpr int kPmMaxIt = 12;
+constexpr int kPmMaxIt = 4;
 constexpr int kPmThreads = 256;
 
 __host__ __device__ constexpr size_t pm_smem_bytes() {
@@ -600,11 +600,15 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
         for (int r = c + 1 + lane; r < N; r += 32) y[r] -= L[pm_idx(N, c, r)] * yc;
         __syncwarp();
       }
+      // L^T x = y as dot products down the columns of L (contiguous in the
+      // packed layout): x_c = (y_c - sum_{r > c} L(r, c) x_r) / L(c, c)
       for (int c = N - 1; c >= 0; --c) {
-        if (lane == 0) y[c] /= L[pm_idx(N, c, c)];
-        __syncwarp();
-        const float yc = y[c];
-        for (int r = lane; r < c; r += 32) y[r] -= L[pm_idx(N, r, c)] * yc;
+        const float* Lc = L + cstart[c] - c;  // Lc[r] = L(r, c)
+        float acc = 0.0f;
+        for (int r = c + 1 + lane; r < N; r += 32) acc += Lc[r] * y[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[c] = (y[c] - acc) / Lc[c];
         __syncwarp();
       }
     }
