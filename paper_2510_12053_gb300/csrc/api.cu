@@ -175,9 +175,7 @@ void solve_list(Mesh& m, const cc_sweep_opts& o, const int32_t* verts, int64_t c
     launch_local_solve_f64(m, o.update, verts, count, x, counters(m), m.stream);
   else
     launch_local_solve_mixed(m, o.update, verts, count, x, counters(m), m.stream);
-  // CD: the condensation kernel alone; CC / JGS2: the coupling kernel, which
-  // condenses in the same launch unless it is the one-warp variant
-  prof_close(m, P_SOLVE, e0, (o.update == CC_UPDATE_CD || m.tune_couple_threads != 32) ? 1 : 2);
+  prof_close(m, P_SOLVE, e0, o.update == CC_UPDATE_CD ? 1 : 2);
 }
 
 // One sweep over colours [cb, ce).  `fresh` means g and H already hold the

@@ -14,7 +14,6 @@
 // gives, for every block it reads, the support slot of the block's column.
 // Same-coloured vertices share no tet, and this kernel reads only g, H and U,
 // so writing x in place is race-free for both schedules.
-#include <type_traits>
 #include <vector>
 
 #include "cc_internal.cuh"
@@ -76,31 +75,6 @@ struct SlotCodes<uint8_t> {
 template <>
 struct SlotCodes<uint16_t> {
   static constexpr unsigned kNone = 0xFFFF, kSelf = 0xFFFE, kDiag = 0xFFFD;
-};
-
-template <typename AR, typename HT, bool kMixed, int kUpd>
-__device__ __forceinline__ void condense_one(int i, const HT* cv, const int32_t* __restrict__ sup_ptr,
-                                             const int32_t* __restrict__ up_ptr, const HT* __restrict__ bsr,
-                                             const double* __restrict__ g64, const float* __restrict__ g_hi,
-                                             const float* __restrict__ g_lo, int64_t n, double* __restrict__ x,
-                                             float4* __restrict__ x_hi, float4* __restrict__ x_lo, AR rel,
-                                             unsigned long long* __restrict__ fallback,
-                                             unsigned long long* __restrict__ err);
-
-// What the condensation of a vertex needs besides its coupling values.
-template <typename AR>
-struct CondenseArgs {
-  const double* g64;
-  const float* g_lo;
-  int64_t n;
-  double* x;
-  float4* x_hi;
-  float4* x_lo;
-  AR rel;
-  const int32_t* vert_mesh;
-  const int32_t* active;
-  unsigned long long* fallback;
-  unsigned long long* err;
 };
 
 // Stages U_i in shared memory, rotated for corotated bases (Sec. 3.1):
@@ -174,19 +148,16 @@ __device__ __forceinline__ void load_slot<double>(const double* p, double* u) {
 // term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
 // l > i.  The CTA writes 27 values per vertex: Ht (6, symmetric), A (9),
 // b (3), H_ii (9, stored directly by the thread that reads it).
-// With kFused the CTA's thread 0 then condenses the vertex itself (the
-// condensation below, on the values kept in shared memory) and cpl is unused.
-template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads, typename AR, bool kFused>
-__global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 1024 / kThreads : 1) k_couple(
+template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_couple(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
     const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, int64_t smap_max,
-    const HT* __restrict__ rot, int row_lanes_log2, HT* __restrict__ cpl, CondenseArgs<AR> ca) {
+    const HT* __restrict__ rot, int row_lanes_log2, HT* __restrict__ cpl) {
   pdl_entry();
   using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ HT fin[32];  // the vertex's 27 coupling values (fused mode)
   unsigned char* ptr = smem;
   HT* Us = reinterpret_cast<HT*>(ptr);  // [m][3][4]
   ptr += align16((size_t)sup_max * 12 * sizeof(HT));
@@ -290,10 +261,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 1024 / kThreads : 
         load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kDiag) {
 #pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            if (kFused) fin[18 + c] = H[c];
-            else cpl[(int64_t)blockIdx.x * 32 + 18 + c] = H[c];
-          }
+          for (int c = 0; c < 9; ++c) cpl[(int64_t)blockIdx.x * 32 + 18 + c] = H[c];
         } else if (kUpd == CC_UPDATE_CC) {
           HT Ul[9];
           load_slot(Us + 12 * (int)code, Ul);
@@ -312,19 +280,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(HT) == 4 ? 1024 / kThreads : 
 #pragma unroll
     for (int v = 0; v < 18; ++v) red[warp * 32 + v] = vals[v];
   __syncthreads();
-  if (kFused) {
-    if (tid < 18) {
-      HT tot = red[tid];
-#pragma unroll
-      for (int w = 1; w < kThreads / 32; ++w) tot += red[32 * w + tid];
-      fin[tid] = tot;
-    }
-    __syncthreads();
-    if (tid == 0 && ca.active[ca.vert_mesh[i]] != 0)
-      condense_one<AR, HT, kMixed, kUpd>(i, fin, sup_ptr, up_ptr, bsr, ca.g64, g_hi, ca.g_lo, ca.n, ca.x, ca.x_hi,
-                                         ca.x_lo, ca.rel, ca.fallback, ca.err);
-    return;
-  }
   if (tid >= 18) return;
   // fixed-order sum of the warps' partials
   HT tot = red[tid];
@@ -473,19 +428,21 @@ __host__ __device__ inline size_t warp_smem_bytes(int sup_max, int warps) {
 // use the adjugate; the SPD guard is the Cholesky pivot test written with
 // leading minors.  `AR` is the arithmetic: double (float64 path) or df
 // (float-float, mixed path).
-// The condensation of one vertex i (Eq. 9-12) from its 27 coupling values
-// cv[0..26] = Ht (6, symmetric), A (9), b (3), H_ii (9); the CD update reads
-// H_ii from the block rows instead.  Updates x (and its float-float split).
 template <typename AR, typename HT, bool kMixed, int kUpd>
-__device__ __forceinline__ void condense_one(int i, const HT* cv, const int32_t* __restrict__ sup_ptr,
-                                             const int32_t* __restrict__ up_ptr, const HT* __restrict__ bsr,
-                                             const double* __restrict__ g64, const float* __restrict__ g_hi,
-                                             const float* __restrict__ g_lo, int64_t n, double* __restrict__ x,
-                                             float4* __restrict__ x_hi, float4* __restrict__ x_lo, AR rel,
-                                             unsigned long long* __restrict__ fallback,
-                                             unsigned long long* __restrict__ err) {
+__global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, const HT* __restrict__ cpl,
+                           const int32_t* __restrict__ sup_ptr, const int32_t* __restrict__ up_ptr,
+                           const HT* __restrict__ bsr, const double* __restrict__ g64,
+                           const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
+                           double* __restrict__ x, float4* __restrict__ x_hi, float4* __restrict__ x_lo,
+                           AR rel, const int32_t* __restrict__ vert_mesh, const int32_t* __restrict__ active,
+                           unsigned long long* __restrict__ fallback, unsigned long long* __restrict__ err) {
+  pdl_entry();
   using Ar = Arith<AR>;
   using V = typename Ar::V;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int i = verts[k];
+  if (active[vert_mesh[i]] == 0) return;  // this mesh of the batch has stopped
   auto ld = [](HT v) -> V {
     if constexpr (sizeof(HT) == 4) return Ar::mkf((float)v);
     else return Ar::mk((double)v);
@@ -498,7 +455,7 @@ __device__ __forceinline__ void condense_one(int i, const HT* cv, const int32_t*
     for (int c = 0; c < 9; ++c) H[c] = ld(Hb[c]);
   } else {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) H[c] = ld(cv[18 + c]);
+    for (int c = 0; c < 9; ++c) H[c] = ld(cpl[k * 32 + 18 + c]);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -513,12 +470,12 @@ __device__ __forceinline__ void condense_one(int i, const HT* cv, const int32_t*
     if (m == 0) {
       fb = 0;
     } else {
-      const V t0 = ld(cv[0]), t1 = ld(cv[1]), t2 = ld(cv[2]);
-      const V t3 = ld(cv[3]), t4 = ld(cv[4]), t5 = ld(cv[5]);
+      const V t0 = ld(cpl[k * 32 + 0]), t1 = ld(cpl[k * 32 + 1]), t2 = ld(cpl[k * 32 + 2]);
+      const V t3 = ld(cpl[k * 32 + 3]), t4 = ld(cpl[k * 32 + 4]), t5 = ld(cpl[k * 32 + 5]);
       const V Ht[9] = {t0, t1, t2, t1, t3, t4, t2, t4, t5};
       V b[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) b[c] = ld(cv[15 + c]);
+      for (int c = 0; c < 3; ++c) b[c] = ld(cpl[k * 32 + 15 + c]);
       if (kUpd == CC_UPDATE_JGS2) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) M[c] = Ar::add(H[c], Ht[c]);
@@ -530,7 +487,7 @@ __device__ __forceinline__ void condense_one(int i, const HT* cv, const int32_t*
         if (sym3_adj<AR>(Ht, rel, adj, &det)) {
           V A[9];
 #pragma unroll
-          for (int c = 0; c < 9; ++c) A[c] = ld(cv[6 + c]);
+          for (int c = 0; c < 9; ++c) A[c] = ld(cpl[k * 32 + 6 + c]);
           const V inv = Ar::div(Ar::mkf(1.0f), det);
           V Hi[9] = {adj[0], adj[1], adj[2], adj[1], adj[3], adj[4], adj[2], adj[4], adj[5]};
 #pragma unroll
@@ -606,26 +563,9 @@ __device__ __forceinline__ void condense_one(int i, const HT* cv, const int32_t*
   }
 }
 
-template <typename AR, typename HT, bool kMixed, int kUpd>
-__global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, const HT* __restrict__ cpl,
-                           const int32_t* __restrict__ sup_ptr, const int32_t* __restrict__ up_ptr,
-                           const HT* __restrict__ bsr, const double* __restrict__ g64,
-                           const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
-                           double* __restrict__ x, float4* __restrict__ x_hi, float4* __restrict__ x_lo,
-                           AR rel, const int32_t* __restrict__ vert_mesh, const int32_t* __restrict__ active,
-                           unsigned long long* __restrict__ fallback, unsigned long long* __restrict__ err) {
-  pdl_entry();
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  const int i = verts[k];
-  if (active[vert_mesh[i]] == 0) return;  // this mesh of the batch has stopped
-  condense_one<AR, HT, kMixed, kUpd>(i, cpl + k * 32, sup_ptr, up_ptr, bsr, g64, g_hi, g_lo, n, x, x_hi, x_lo, rel,
-                                     fallback, err);
-}
-
-template <typename HT, bool kMixed, int kUpd, int kThreads, typename AR, bool kFused>
+template <typename HT, bool kMixed, int kUpd, int kThreads>
 void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
-                   const float* g_hi, HT* cpl, const HT* rot, const CondenseArgs<AR>& ca, cudaStream_t s) {
+                   const float* g_hi, HT* cpl, const HT* rot, cudaStream_t s) {
   const int supm = m.sup_max > 0 ? m.sup_max : 1;
   const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
   const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
@@ -634,17 +574,17 @@ void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, co
   CCG_CHECK(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8, CC_ERR_STATE, "bad coupling row lanes");
   const int lanes_log2 = lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : 3;
   if (m.smap_wide) {
-    auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads, AR, kFused>;
+    auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl, ca);
+               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
   } else {
-    auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads, AR, kFused>;
+    auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);
     pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
                (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl, ca);
+               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
   }
   CCG_CUDA(cudaGetLastError());
 }
@@ -678,45 +618,33 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
                 const float* g_hi, const float* g_lo, HT* cpl, double* x, SweepCounters c, cudaStream_t s) {
   float4* xh = kMixed ? m.mx.x_hi.p : nullptr;
   float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
-  using AR = typename std::conditional<kMixed, df, double>::type;
-  CondenseArgs<AR> ca;
-  ca.g64 = g64;
-  ca.g_lo = g_lo;
-  ca.n = m.n;
-  ca.x = x;
-  ca.x_hi = xh;
-  ca.x_lo = xl;
-  if constexpr (kMixed) ca.rel = df{1e-12f, (float)(1e-12 - (double)1e-12f)};
-  else ca.rel = kPivotRel;
-  ca.vert_mesh = (const int32_t*)m.d_vert_mesh.p;
-  ca.active = (const int32_t*)m.d_mesh_active.p;
-  ca.fallback = c.fallback;
-  ca.err = c.error;
-  // the CTA coupling kernels condense their vertex themselves (fused); the
-  // one-warp kernel and the CD update leave it to the batched kernel below
-  bool fused = false;
   if (kUpd != CC_UPDATE_CD) {
     const HT* rot = nullptr;
     if (m.rot_active) {
       if constexpr (kMixed) rot = reinterpret_cast<const HT*>(m.mx.rot.p);
       else rot = reinterpret_cast<const HT*>(m.f64.rot.p);
     }
-    fused = m.tune_couple_threads != 32;
     switch (m.tune_couple_threads) {
       case 32: launch_couple_warp<HT, kMixed, kUpd>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
-      case 64: launch_couple<HT, kMixed, kUpd, 64, AR, true>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, ca, s); break;
-      case 256: launch_couple<HT, kMixed, kUpd, 256, AR, true>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, ca, s); break;
-      default: launch_couple<HT, kMixed, kUpd, 128, AR, true>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, ca, s);
+      case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
+      case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
+      default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s);
     }
   }
-  if (fused) return;
   // one vertex per thread in 32-thread blocks: a colour holds a few thousand
   // vertices, so small blocks spread the long per-vertex chains over every SM
   constexpr int kCondenseThreads = 32;
   const unsigned grid = (unsigned)((count + kCondenseThreads - 1) / kCondenseThreads);
-  pdl_launch(k_condense<AR, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
-             (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl, ca.rel,
-             (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
+  if constexpr (kMixed) {
+    const df rel{1e-12f, (float)(1e-12 - (double)1e-12f)};
+    pdl_launch(k_condense<df, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
+               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl, rel,
+               (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
+  } else {
+    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
+               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
+               1e-12, (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
+  }
   CCG_CUDA(cudaGetLastError());
 }
 
