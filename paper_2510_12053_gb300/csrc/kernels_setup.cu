@@ -429,7 +429,7 @@ namespace {
 // column-major) and factored by Cholesky there; U = -H_PP^{-1} H_Pi is then
 // reached by iterative refinement -- z += L^{-T} L^{-1} (B - H_PP z), B = -H_Pi,
 // with the residual in float64 from the float64 block rows -- until the
-// correction is below 1e-13 of z or stops shrinking (it then sits at the
+// correction is below 1e-12 of z or stops shrinking (it then sits at the
 // rounding level of the float64 residual).  A patch whose float32
 // factorization meets a non-positive pivot, or whose last correction is above
 // 1e-11 of z, is queued for the float64 kernel (which also decides positive
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     __syncthreads();
     const double dm = dmax, zm = zmax;
     __syncthreads();
-    settled = dm <= 1e-13 * zm;
+    settled = dm <= 1e-12 * zm;
     ratio = zm > 0.0 ? dm / zm : 0.0;
     if (dm > 0.5 * prev) break;  // corrections at the float64 rounding level of the residual
     prev = dm;
