@@ -334,6 +334,10 @@ void run_subspace_build(Mesh& m, int32_t k);
 void build_supports(Mesh& m, int32_t k);
 void rest_hessian_f64(Mesh& m);
 void hessian_f64_at(Mesh& m, const double* x);
+// U_i = -H_PP^{-1} H_Pi for the listed vertices from the float64 block rows:
+// float32 factor + float64 refinement where the patch fits (<= 192 unknowns),
+// float64 Cholesky otherwise; returns the patches that were not positive
+// definite (their bases untouched), or throws when throw_on_fail.
 int64_t patch_solves(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail);
 int64_t rebuild_bases_at(Mesh& m, const double* x);
 void bases_to_f32(Mesh& m);

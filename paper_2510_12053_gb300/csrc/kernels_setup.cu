@@ -63,9 +63,10 @@ __device__ __forceinline__ int find_sorted(const int32_t* a, int m, int key) {
   return -1;
 }
 
-// One CTA per free vertex of the batch.  A (column-major, N x N, N = 3m) and
-// the right-hand sides R (column-major N x 3) live in the CTA's slice of
-// scratch.  H is read from its upper 3x3 blocks (padded to 3 x 4): a block
+// Plain float64 patch solve (patches above 192 unknowns, and those the mixed
+// kernel below declines): one CTA per free vertex of the batch.  A
+// (column-major, N x N, N = 3m) and the right-hand sides R (column-major
+// N x 3) live in the CTA's slice of scratch.  H is read from its upper 3x3 blocks (padded to 3 x 4): a block
 // (j, l) of a support row j fills both (a, t) and (t, a); block (j, i) and
 // blocks (i, l) of row i fill -H_Pi.  Writes
 // U[(s0 + a) * 9 + 3 r + d] = z[3a + r][d] with H_PP z = -H_Pi.
