@@ -550,15 +550,17 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     }
   }
   __syncthreads();
-  // right-looking Cholesky in shared memory
+  // right-looking Cholesky in shared memory, two barriers per column: every
+  // thread takes the pivot from the (final) diagonal entry itself; the
+  // factor's diagonal is kept aside in dg and written back at the end
+  __shared__ float dg[kPmMaxN];
   for (int c = 0; c < N; ++c) {
+    const float d = L[pm_idx(N, c, c)];
+    const float piv = sqrtf(fmaxf(d, 1e-30f));
     if (tid == 0) {
-      const float d = L[pm_idx(N, c, c)];
       if (!(d > 0.0f)) bad = 1;
-      L[pm_idx(N, c, c)] = sqrtf(fmaxf(d, 1e-30f));
+      dg[c] = piv;
     }
-    __syncthreads();
-    const float piv = L[pm_idx(N, c, c)];
     for (int r = c + 1 + tid; r < N; r += kPmThreads) L[pm_idx(N, c, r)] /= piv;
     __syncthreads();
     // trailing update L(s, r) -= L(r, c) L(s, c), s > c, r >= s: the trailing
@@ -572,6 +574,8 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     }
     __syncthreads();
   }
+  for (int c = tid; c < N; c += kPmThreads) L[pm_idx(N, c, c)] = dg[c];
+  __syncthreads();
   bool ok = bad == 0;
   // iterative refinement: R = B - H_PP Z (float64), D = (L L^T)^{-1} R (float32), Z += D
   bool settled = false;
