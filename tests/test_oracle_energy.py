@@ -144,13 +144,10 @@ def test_mesh_counts_match_workload_definitions():
     rows = [list(map(int, l.split())) for l in open(
         __file__.replace("test_oracle_energy.py", "golden/mesh_counts.txt")) if l.strip() and l[0] != "#"]
     for nx, ny, nz, nv, nt in rows:
-        assert (nx + 1) * (ny + 1) * (nz + 1) == nv
-        if nv < 50000:
-            X = meshgen.grid_vertices(nx, ny, nz)
-            T = meshgen.kuhn_tets(nx, ny, nz)
-            assert X.shape[0] == nv and T.shape[0] == nt
-        else:
-            assert 6 * nx * ny * nz == nt
+        X = meshgen.grid_vertices(nx, ny, nz)
+        T = meshgen.kuhn_tets(nx, ny, nz)
+        assert X.shape[0] == nv and T.shape[0] == nt
+        assert T.min() == 0 and T.max() == nv - 1      # every vertex is a corner of some tet
 
 
 def test_polar_rotation_matches_scipy_and_is_proper():

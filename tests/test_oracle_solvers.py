@@ -195,11 +195,53 @@ def test_backtracking_line_search_decreases_energy():
     assert pb.energy(sc.x0 + a * d) < pb.energy(sc.x0)
 
 
-def test_normalized_residual_definition():
-    sc, pb, topo = _setup(n=2)
-    g = np.linalg.norm(pb.gradient(sc.x0)[pb.free])
-    r = solvers.normalized_residual(pb, g)
-    assert r == pytest.approx(g / (pb.total_volume() * pb.n * 1e5))
+def test_normalized_residual_of_a_uniformly_stretched_tet_in_closed_form():
+    """Sec. 4.1's termination value ||g|| / (V n E) (divided by h for dynamics)
+    on the unit corner tet (D_m = I, V = 1/6, n = 4) stretched to F = diag(s, 1, 1).
+    By hand: cof F = diag(1, s, s), J = s, so the stable Neo-Hookean stress is
+    P = diag((mu + lam_hat)(s - 1), (s - 1)(lam_hat s - mu), (s - 1)(lam_hat s - mu));
+    the corner gradients are V P e_1, V P e_2, V P e_3 and minus their sum, hence
+    ||g||^2 = 2 V^2 (P_00^2 + 2 P_11^2)."""
+    E, nu, s = 1e5, 0.3, 1.2
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float)
+    mu = E / (2 * (1 + nu))
+    lam_hat = E * nu / ((1 + nu) * (1 - 2 * nu)) + mu
+    P00, P11 = (mu + lam_hat) * (s - 1), (s - 1) * (lam_hat * s - mu)
+    g_closed = np.sqrt(2 * (P00 ** 2 + 2 * P11 ** 2)) / 6
+    expect = g_closed / ((1 / 6) * 4 * E)
+    x = X * np.array([s, 1.0, 1.0])
+    pb = fem.Problem(X, np.array([[0, 1, 2, 3]]), np.zeros(4, np.uint8), material.Model("snh", E, nu))
+    g = pb.free_gradient_norm(pb.gradient(x))
+    assert g == pytest.approx(g_closed, rel=1e-13)
+    assert solvers.normalized_residual(pb, g) == pytest.approx(expect, rel=1e-13)
+    h = 0.01
+    pbd = fem.Problem(X, np.array([[0, 1, 2, 3]]), np.zeros(4, np.uint8), material.Model("snh", E, nu), h=h)
+    assert solvers.normalized_residual(pbd, g) == pytest.approx(expect / h, rel=1e-13)
+
+
+def test_backward_euler_step_of_a_free_body_is_ballistic():
+    """Eq. 2 and its footnote on a body with no pinned vertex, starting at a
+    translate of its rest shape with one velocity v0 everywhere, under gravity
+    g: the elastic energy vanishes on every translate of the rest shape, so the
+    minimiser of Eq. 2 is the inertial target itself and one backward Euler
+    step must give exactly x1 = x0 + h v0 + h^2 g and v1 = v0 + h g (free fall).
+    A target with h instead of h^2, a flipped gravity or a velocity divided by
+    h^2 all fail here."""
+    X = meshgen.grid_vertices(2, 2, 2, 0.5)
+    tets = meshgen.kuhn_tets(2, 2, 2)
+    n = X.shape[0]
+    h, g = 1.0 / 60.0, np.array([0.0, -9.8, 0.0])
+    v0 = np.broadcast_to([0.3, -0.2, 0.1], (n, 3)).copy()
+    x0 = X + np.array([0.1, 0.2, -0.05])
+    pb = fem.Problem(X, tets, np.zeros(n, np.uint8), material.Model("snh", 1e5, 0.3), rho=1000.0, h=h, gravity=g)
+    np.testing.assert_allclose(pb.inertial_target(x0, v0), x0 + h * v0 + h * h * g, rtol=0, atol=1e-15)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    for kind in ("cc", "cd"):
+        x1, v1, hist = solvers.time_step(pb, topo, sup, U, x0, v0, kind=kind, tol=1e-13, max_iters=400)
+        assert hist.converged, kind
+        np.testing.assert_allclose(x1, x0 + h * v0 + h * h * g, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(v1, v0 + h * g, rtol=0, atol=1e-11)
 
 
 # ---------------------------------------------------------------- corotated bases (Sec. 3.1)
