@@ -303,11 +303,15 @@ cc_status cc_profile_read(cc_mesh* mesh, cc_profile* out);
  *             supports are written)
  *   max_support  largest |S_i| over verts (host int); values whose dense
  *             patch does not fit the array (above CC_NOALLOC_MAX_SUPPORT)
- *             are rejected with CC_ERR_INVALID_ARG before any GPU work
+ *             are rejected with CC_ERR_INVALID_ARG before any GPU work, and
+ *             so is a listed vertex whose support is larger than max_support
+ *             (a small device pass reads the supports first; no patch is
+ *             solved and U_out is untouched)
  *   stream    cudaStream_t (NULL: default stream); the call synchronises it
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls on a device share the array and it keeps the last
+ * device, with that device current, under a lock, so concurrent first calls
+ * from several host threads are safe); make that first call before any
+ * stream capture.  All calls on a device share the array and it keeps the last
  * call's contents; the kernel clears what must start at zero.  Calls that
  * overlap on the GPU (e.g. on two streams at once) race on the array: keep
  * them ordered.  CC_ERR_NUMERIC if a patch matrix is not positive definite. */

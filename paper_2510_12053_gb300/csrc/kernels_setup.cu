@@ -619,12 +619,15 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     }
     __syncthreads();
     double dl = 0.0, zl = 0.0;
+    bool nonfinite = false;
     for (int k = tid; k < 3 * N; k += kPmThreads) {
       const double d = (double)D[k];
       Z[k] += d;
+      nonfinite |= !isfinite(d) || !isfinite(Z[k]);  // fmax below would drop a NaN
       dl = fmax(dl, fabs(d));
       zl = fmax(zl, fabs(Z[k]));
     }
+    if (nonfinite) bad = 1;  // float32 overflow in the triangular solves: the float64 kernel redoes the patch
     for (int o = 16; o > 0; o >>= 1) {
       dl = fmax(dl, __shfl_xor_sync(0xffffffffu, dl, o));
       zl = fmax(zl, __shfl_xor_sync(0xffffffffu, zl, o));
@@ -635,7 +638,9 @@ __global__ void __launch_bounds__(kPmThreads) k_patch_basis_mixed(
     }
     __syncthreads();
     const double dm = dmax, zm = zmax;
+    ok = bad == 0;
     __syncthreads();
+    if (!ok) break;
     settled = dm <= 1e-12 * zm;
     ratio = zm > 0.0 ? dm / zm : 0.0;
     if (dm > 0.5 * prev) break;  // corrections at the float64 rounding level of the residual

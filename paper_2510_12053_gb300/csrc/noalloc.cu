@@ -10,6 +10,8 @@
 // loads this library and keeps until the process exits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "cc_internal.cuh"
@@ -20,11 +22,29 @@ namespace {
 // 16 MiB of float64 workspace (2 Mi doubles), shared by every call on a device.
 constexpr size_t kNoallocScratchDoubles = size_t(2) << 20;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+// Status words: [0] patches that were not positive definite, [1] the largest
+// support among the listed vertices, [2] patches larger than the slice.
 static __device__ __align__(256) int g_noalloc_fail[64];
 
 constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;  // guards the per-device address cache below
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 int* g_fail_ptr[kMaxDevices] = {nullptr};
+
+// Largest support |S_i| over the listed vertices, into *out (atomicMax; *out
+// starts at zero).  Runs before the patch kernel so that an understated
+// max_support is refused before any workspace slice is touched.
+__global__ void k_noalloc_max_support(const int32_t* __restrict__ verts, int64_t count,
+                                      const int32_t* __restrict__ sup_ptr, int* __restrict__ out) {
+  int best = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+    const int i = verts[k];
+    best = max(best, sup_ptr[i + 1] - sup_ptr[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
 
 __device__ __forceinline__ int find_sorted_na(const int32_t* a, int m, int key) {
   int lo = 0, hi = m - 1;
@@ -50,6 +70,10 @@ __global__ void k_patch_basis_noalloc(const int32_t* __restrict__ verts, const i
   const int s0 = sup_ptr[i], m = sup_ptr[i + 1] - s0;
   const int N = 3 * m;
   if (m == 0) return;
+  if (N > Nmax) {  // never true after the host's support check; refuse rather than overrun the slice
+    if (threadIdx.x == 0) atomicAdd(fail + 2, 1);
+    return;
+  }
   double* A = scratch + (size_t)blockIdx.x * ((size_t)Nmax * Nmax + 3 * (size_t)Nmax);
   double* R = A + (size_t)Nmax * Nmax;
   const int32_t* S = sup_idx + s0;
@@ -124,6 +148,7 @@ void noalloc_setup(double** scratch, int** fail) {
   int dev = 0;
   CCG_CUDA(cudaGetDevice(&dev));
   CCG_CHECK(dev >= 0 && dev < kMaxDevices, CC_ERR_INVALID_ARG, "device index beyond 63");
+  std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     void* q = nullptr;
@@ -160,7 +185,17 @@ extern "C" cc_status cc_build_bases_noalloc(const double* H_blocks, const int32_
     int* fail = nullptr;
     ccg::noalloc_setup(&scratch, &fail);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CCG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
+    CCG_CUDA(cudaMemsetAsync(fail, 0, 3 * sizeof(int), s));
+    // every listed support must fit the slice that max_support sizes
+    ccg::k_noalloc_max_support<<<(unsigned)std::min<int64_t>((count + 255) / 256, 1024), 256, 0, s>>>(
+        verts, count, sup_ptr, fail + 1);
+    CCG_CUDA(cudaGetLastError());
+    int hmax = 0;
+    CCG_CUDA(cudaMemcpyAsync(&hmax, fail + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CCG_CUDA(cudaStreamSynchronize(s));
+    CCG_CHECK(hmax <= max_support, CC_ERR_INVALID_ARG,
+              "cc_build_bases_noalloc: a listed vertex has " + std::to_string(hmax) +
+                  " support vertices, more than max_support = " + std::to_string(max_support));
     const int64_t batch = (int64_t)(ccg::kNoallocScratchDoubles / per);
     for (int64_t b0 = 0; b0 < count; b0 += batch) {
       const int64_t cnt = count - b0 < batch ? count - b0 : batch;
@@ -168,10 +203,11 @@ extern "C" cc_status cc_build_bases_noalloc(const double* H_blocks, const int32_
                                                                H_blocks, (int)Nmax, scratch, U_out, fail);
       CCG_CUDA(cudaGetLastError());
     }
-    int nfail = 0;
-    CCG_CUDA(cudaMemcpyAsync(&nfail, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hf[3] = {0, 0, 0};
+    CCG_CUDA(cudaMemcpyAsync(hf, fail, sizeof(hf), cudaMemcpyDeviceToHost, s));
     CCG_CUDA(cudaStreamSynchronize(s));
-    CCG_CHECK(nfail == 0, CC_ERR_NUMERIC, "cc_build_bases_noalloc: a patch Hessian was not positive definite");
+    CCG_CHECK(hf[2] == 0, CC_ERR_INVALID_ARG, "cc_build_bases_noalloc: a support grew beyond max_support");
+    CCG_CHECK(hf[0] == 0, CC_ERR_NUMERIC, "cc_build_bases_noalloc: a patch Hessian was not positive definite");
     return CC_OK;
   } catch (const ccg::Fail& f) {
     return f.st;

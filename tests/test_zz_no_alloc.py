@@ -6,7 +6,8 @@ cannot absorb cudaMalloc's implicit synchronisation); it works in a static
 16 MiB device array instead.  These tests call it through the C ABI and check
 that two calls in a row reproduce the bases of cc_build_subspace (which uses
 a cudaMalloc'ed workspace) within the tolerance the other basis tests use,
-and that a support too large for the static array is rejected.
+and that a support too large for the static array, or a max_support smaller
+than a listed vertex's support, is rejected before any patch is solved.
 """
 import ctypes
 
@@ -79,3 +80,21 @@ def test_noalloc_rejects_supports_larger_than_its_static_workspace():
     assert rc == cc.ERR_INVALID_ARG
     assert "16 MiB" in cc.lib().cc_last_error().decode()
     assert float(U_out.abs().max()) == 0.0
+
+
+def test_noalloc_rejects_an_understated_max_support_before_solving():
+    """max_support sizes each vertex's slice of the shared array; a caller
+    that understates it (here by one) gets CC_ERR_INVALID_ARG from the support
+    check that runs before the patch kernel, so U_out stays untouched."""
+    assert torch.cuda.is_available()
+    d, U_ref, max_support = _inputs()
+    U_out = torch.zeros(U_ref.size, dtype=torch.float64, device="cuda")
+    rc = _call(d, max_support - 1, U_out)
+    assert rc == cc.ERR_INVALID_ARG
+    assert "more than max_support" in cc.lib().cc_last_error().decode()
+    torch.cuda.synchronize()
+    assert float(U_out.abs().max()) == 0.0
+    # the entry point stays usable: the next call with the true maximum succeeds
+    rc = _call(d, max_support, U_out)
+    assert rc == cc.OK, cc.lib().cc_last_error().decode()
+    assert np.abs(U_out.cpu().numpy() - U_ref).max() <= 1e-10 * max(1.0, float(np.abs(U_ref).max()))
