@@ -25,6 +25,11 @@ import sys
 import tempfile
 import time
 
+# one BLAS thread per process: the oracle baseline below sets its own process
+# count, and threaded BLAS inside each of its workers oversubscribes the cores
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -95,6 +100,11 @@ def parse():
     p.add_argument("--train-steps", type=int, default=4000)
     p.add_argument("--train-batch", type=int, default=8192)
     p.add_argument("--learned-max-iters", type=int, default=2000, help="sweep cap of the 48^3 solves")
+    p.add_argument("--no-nu045", action="store_true", help="skip the nu = 0.45 solves of the named configuration")
+    p.add_argument("--cfg1-oracle", action="store_true",
+                   help="add the oracle's CD / CC / JGS2 / Newton timings on the 8^3 cube (100 iterations each)")
+    p.add_argument("--cpu-full-sweep", action="store_true",
+                   help="add one whole coloured CC sweep of the oracle on the 32^3 cube, single-threaded")
     return p.parse_args()
 
 
@@ -109,7 +119,9 @@ def workload_config(nu, n, T, n_free):
                         f"jitter 5% seed 0, x=0 clamped, x=1 pulled to 1.5, SNH nu={nu}, E in {E_SWEEP}, "
                         f"{K_RING}-ring bases, coloured CC, tol 1e-6 rel grad-norm",
             "n_free": n_free, "k_ring": K_RING, "schedule": "colored", "update": "cc",
-            "nu_note": "nu=0.45 of the named configuration diverges with 2-ring rest bases (oracle and GPU agree)",
+            "nu": nu, "E_values": E_SWEEP, "cells": list(DIMS), "tol": 1e-6,
+            "nu_note": "the named configuration's nu=0.45 diverges with 2-ring rest bases (oracle and GPU agree); "
+                       "its outcome is reported under cfg_nu045",
             "l2": "flushed between steps (256 MiB write)", "inputs": "resident in HBM"}
 
 
@@ -161,57 +173,234 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)
-def oracle_rate(scene, n_updates, seed=5):
-    """Vertex-updates/s of the FP64 oracle's coloured CC sweep, from one timed
-    gradient+Hessian assembly and ``n_updates`` timed local updates, scaled to
-    a full sweep (C assemblies + n_free updates)."""
-    from oracle import fem, solvers, subspace, topology
+# The float64 oracle timed on the host cores: one colour of a coloured CC
+# sweep of the 32^3 cube, exactly as the oracle's sweep does it (gradient and
+# Hessian assembly at the current x, then the local CC update of every free
+# vertex of the colour, applied).  Bases (Eq. 5 on the 2-ring patch at rest)
+# are built by the oracle beforehand and are not timed.  With several cores
+# the local updates of the colour are split over worker processes (spawned;
+# same-coloured vertices are independent), the assembly stays serial.
+_OW = {}
+
+
+def _ow_scene(nu):
     import meshgen
-    pb = fem.problem_from_scene(scene)
-    nb_ptr, nb_idx = topology.vertex_neighbors(pb.n, pb.tets)
-    color = topology.greedy_coloring(pb.n, nb_ptr, nb_idx)
-    C = int(color.max()) + 1
-    free = np.flatnonzero(pb.free)
-    pick = free[(meshgen.uniform01(seed, np.arange(n_updates)) * len(free)).astype(int)]
-    H0 = pb.hessian(pb.X)
-    sup = {}
-    bases = {}
-    for i in pick:
-        S = np.array([j for j in topology.k_ring(int(i), K_RING, nb_ptr, nb_idx) if j != i and pb.free[j]])
-        sup[int(i)] = S
-        bases[int(i)] = subspace.local_basis(H0, int(i), S)
+    return meshgen.stretch_box(*DIMS, E=E_SWEEP[1], nu=nu, factor=1.5, jitter_amount=0.05, seed=0)
+
+
+def _ow_init(nu, bases=True):
+    from oracle import fem, topology
+    sc = _ow_scene(nu)
+    pb = fem.problem_from_scene(sc)
+    _OW["pb"] = pb
+    if bases:
+        _OW["nb"] = topology.vertex_neighbors(pb.n, pb.tets)
+        _OW["H0"] = pb.hessian(pb.X)
+
+
+def _ow_bases(verts):
+    from oracle import subspace, topology
+    pb, (nb_ptr, nb_idx), H0 = _OW["pb"], _OW["nb"], _OW["H0"]
+    out = []
+    for i in verts:
+        S = np.array([j for j in topology.k_ring(int(i), K_RING, nb_ptr, nb_idx) if j != i and pb.free[j]],
+                     dtype=np.int64)
+        out.append((S, subspace.local_basis(H0, int(i), S)))
+    return out
+
+
+def _ow_updates(args):
+    """Local CC updates of a chunk of the colour's vertices from g, H (and
+    the bases) that the parent placed in shared memory."""
+    import scipy.sparse as sps
+    from multiprocessing import shared_memory
+    from oracle import solvers
+    verts, specs, shape = args
+    handles = [shared_memory.SharedMemory(name=name) for name, _, _ in specs]
+    try:
+        views = [np.ndarray(shp, dtype=dt, buffer=h.buf) for h, (_, shp, dt) in zip(handles, specs)]
+        data, indices, indptr, g, sptr, sidx, U = views
+        H = sps.csr_matrix((data, indices, indptr), shape=shape, copy=False)
+        d = np.empty((len(verts), 3))
+        for k, (i, pos) in enumerate(verts):
+            d[k] = solvers.local_update("cc", H, g, int(i), sidx[sptr[pos]:sptr[pos + 1]], U[sptr[pos]:sptr[pos + 1]])
+        del H, data, indices, indptr, g, sptr, sidx, U, views
+    finally:
+        for h in handles:
+            h.close()
+    return d
+
+
+class OracleColour:
+    """Times the oracle on colour ``c`` of the 32^3 cube with ``cores``
+    processes (1: in this process, no pool)."""
+
+    def __init__(self, nu, cores, colour=0):
+        from oracle import topology
+        self.cores = max(1, int(cores))
+        _ow_init(nu, bases=self.cores == 1)
+        self.pb = _OW["pb"]
+        self.x0 = _ow_scene(nu).x0
+        topo = topology.Topology(self.pb.n, self.pb.tets, self.pb.free)
+        self.verts = np.asarray(topo.color_classes(free_only=True)[colour], dtype=np.int64)
+        self.pool = None
+        self.shm = []
+        chunks = np.array_split(self.verts, self.cores * 4)
+        if self.cores > 1:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_ow_init, initargs=(nu,))
+            parts = self.pool.map(_ow_bases, chunks)
+        else:
+            parts = [_ow_bases(c) for c in chunks]
+        sb = [sb for part in parts for sb in part]
+        self.sptr = np.zeros(len(sb) + 1, dtype=np.int64)
+        self.sptr[1:] = np.cumsum([len(S) for S, _ in sb])
+        self.sidx = np.concatenate([S for S, _ in sb]) if sb else np.zeros(0, np.int64)
+        self.U = np.concatenate([U.reshape(-1, 3, 3) for _, U in sb]) if sb else np.zeros((0, 3, 3))
+        self.chunks = [list(zip(c.tolist(), range(o, o + len(c))))
+                       for c, o in zip(chunks, np.cumsum([0] + [len(c) for c in chunks[:-1]]))]
+
+    def _put(self, name, a):
+        from multiprocessing import shared_memory
+        a = np.ascontiguousarray(a)
+        h = shared_memory.SharedMemory(create=True, size=max(a.nbytes, 1))
+        self.shm.append(h)
+        np.ndarray(a.shape, dtype=a.dtype, buffer=h.buf)[...] = a
+        return (h.name, a.shape, a.dtype.str)
+
+    def step(self, x=None, serial=False):
+        """One timed colour from x (default x0), its updates over the worker
+        processes or (serial) in this process: returns (updates, seconds)."""
+        from oracle import solvers
+        x = np.array(self.x0 if x is None else x, dtype=np.float64, copy=True)
+        t0 = time.perf_counter()
+        g = self.pb.gradient(x)
+        H = self.pb.hessian(x)
+        if self.pool is None or serial:
+            d = np.empty((len(self.verts), 3))
+            for k, i in enumerate(self.verts):
+                S = self.sidx[self.sptr[k]:self.sptr[k + 1]]
+                d[k] = solvers.local_update("cc", H, g, int(i), S, self.U[self.sptr[k]:self.sptr[k + 1]])
+        else:
+            specs = [self._put("d", H.data), self._put("i", H.indices), self._put("p", H.indptr), self._put("g", g),
+                     self._put("sp", self.sptr), self._put("si", self.sidx), self._put("U", self.U)]
+            d = np.concatenate(self.pool.map(_ow_updates, [(c, specs, H.shape) for c in self.chunks]))
+        x[self.verts] += d
+        dt = time.perf_counter() - t0
+        for h in self.shm:
+            h.close()
+            h.unlink()
+        self.shm = []
+        return len(self.verts), dt
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+
+def host_info():
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model") and model is None:
+                model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def oracle_baseline(nu, cores=None, serial=True):
+    """Measured oracle rate (vertex-updates/s) on colour 0 of the 32^3 cube:
+    one timed colour with its updates over ``cores`` processes (default:
+    every host core) and, with ``serial``, one timed colour in one process."""
+    cores = os.cpu_count() if cores is None else cores
+    oc = OracleColour(nu, cores)
+    try:
+        u, t = oc.step()
+        out = {"value": u / t, "cores": oc.cores, "s": t, "updates": u}
+        if serial:
+            u1, t1 = oc.step(serial=True)
+            out["single_thread"] = {"value": u1 / t1, "cores": 1, "s": t1, "updates": u1}
+    finally:
+        oc.close()
+    return out
+
+
+def cfg1_oracle_timings(max_iters=100):
+    """The 8^3 cube (729 vertices, 3 072 tets; E = 1e5, nu = 0.45, 1.5x stretch,
+    2-ring bases, float64) solved by the oracle with CD, CC and JGS2 sweeps
+    (coloured) and Newton, ``max_iters`` iterations each: seconds, iterations
+    run and the final relative residual (a divergence ends the run early)."""
+    import meshgen
+    from oracle import fem, solvers, subspace, topology
+    sc = meshgen.cube8_stretch(E=1e5)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
     t0 = time.perf_counter()
-    g = pb.gradient(scene.x0)
-    H = pb.hessian(scene.x0)
-    t_asm = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for i in pick:
-        solvers.local_update("cc", H, g, int(i), sup[int(i)], bases[int(i)])
-    t_upd = (time.perf_counter() - t0) / len(pick)
-    sweep_s = C * t_asm + len(free) * t_upd
-    return len(free) / sweep_s, {"t_assembly_s": t_asm, "t_update_s": t_upd, "colors": C,
-                                 "sweep_s": sweep_s}
+    sup, U = subspace.build_local_bases(pb, topo, K_RING)
+    out = {"workload": f"cube8_stretch: 8x8x8 cells ({pb.n} vertices, {pb.T} tets), E=1e5, "
+                       f"nu={sc.material.nu}, 1.5x, 2-ring bases, float64 oracle",
+           "basis_build_s": time.perf_counter() - t0}
+    for kind in ("cd", "cc", "jgs2", "newton"):
+        t0 = time.perf_counter()
+        try:
+            with np.errstate(all="ignore"):
+                if kind == "newton":
+                    _, h = solvers.newton(pb, sc.x0, tol=1e-30, max_iters=max_iters)
+                else:
+                    _, h = solvers.solve(pb, topo, sup, U, sc.x0, kind=kind, tol=1e-30, max_iters=max_iters)
+            g = np.asarray(h.grad_norm)
+            rec = {"iterations": h.iterations, "rel_residual": float(g[-1] / g[0]),
+                   "min_rel_residual": float(np.nanmin(g / g[0]))}
+        except Exception as e:   # a diverged iteration (singular local solve) ends the run
+            rec = {"iterations": None, "error": f"{type(e).__name__}: {e}"}
+        rec["s"] = time.perf_counter() - t0
+        out[kind] = rec
+    return out
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    sc = scenes(args.nu)[1]
-    vals = []
-    for k in range(args.warmup + args.steps):
-        v, info = oracle_rate(sc, 60, seed=11 + k)
-        if k >= args.warmup:
-            vals.append(v)
-    value = statistics.mean(vals)
+    sc = _ow_scene(args.nu)
     n_free = int((sc.pinned == 0).sum())
-    sample = (f"per step: one float64 gradient+Hessian assembly of the full cube and 60 local CC updates, "
-              f"scaled to one {info['colors']}-colour sweep ({n_free} updates)")
+    cores = os.cpu_count()
+    oc = OracleColour(args.nu, cores)
+    try:
+        for _ in range(args.warmup):
+            oc.step()
+        ups, secs, per = 0, 0.0, []
+        for _ in range(args.steps):
+            u, t = oc.step()
+            ups += u
+            secs += t
+            per.append(t)
+    finally:
+        oc.close()
+    value = ups / secs
+    sample = (f"per step: colour 0 of one coloured CC sweep of the full 32^3 cube ({len(oc.verts)} of {n_free} "
+              f"free vertices): float64 gradient + Hessian assembly at x0 (serial), then every local CC update of "
+              f"the colour over {cores} processes; 2-ring oracle bases built beforehand (untimed)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "vertex-updates/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_free / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.nu, sc.n, sc.T, n_free),
-        "cpu_baseline": {"value": value, "unit": "vertex-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "vertex-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "host": host_info(), "s_per_step": per},
         "e2e": {"value": value, "unit": "vertex-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -609,6 +798,107 @@ def run_learned(args, stream, dev):
     return out
 
 
+SWEEP_KERNELS = ("k_tet_grad_mixed", "k_row_gather", "k_couple", "k_condense")
+
+
+def sweep_ncu_traffic(ncol):
+    """DRAM bytes of one sweep from the committed ncu summary (one launch of
+    each sweep kernel per colour), or None when a kernel changed since."""
+    t = [ncu_traffic(k) for k in SWEEP_KERNELS]
+    return None if None in t else ncol * float(sum(t))
+
+
+def per_class_rooflines(cls, meshes, scs, sweeps, tet_refreshes, row_gathers, flops_per_sweep, hbm, peak_src):
+    """Every kernel class of the profiled step against its own bound."""
+    roof = {}
+    ls = cls["local_solve"]
+    if ls["ms"] > 0:
+        ach = flops_per_sweep * sweeps / (ls["ms"] / 1e3) / 1e12
+        tr = [ncu_traffic("k_couple"), ncu_traffic("k_condense")]
+        roof["local_solve"] = {"kernel": "k_couple + k_condense (coupling products + batched Schur solve)",
+                               "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": ach / FP32_PEAK_TFLOPS,
+                               "traffic": (tr[0] + tr[1]) if None not in tr else None,
+                               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                               "algorithmic": f"{flops_per_sweep / meshes[0].info().n_free:.0f} FP32 flop per vertex per sweep",
+                               "avg_launch_ms": ls["ms"] / max(ls["launches"] // 2, 1)}
+    ga = cls["gather"]
+    if ga["ms"] > 0:
+        gb = gather_bytes_per_refresh(scs[0])
+        ach = gb * row_gathers / (ga["ms"] / 1e3) / 1e9
+        roof["gather"] = {"kernel": "k_row_gather (gradient + upper block rows of every free vertex)",
+                          "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                          "traffic": ncu_traffic("k_row_gather"), "peak_source": peak_src,
+                          "algorithmic": f"{gb / 1e6:.1f} MB per launch (counts the per-tet Hessian store, "
+                                         f"which the sweep roofline treats as overhead)",
+                          "avg_launch_ms": ga["ms"] / max(ga["launches"], 1)}
+    te = cls["tet_eval"]
+    if te["ms"] > 0:
+        ach = TET_BYTES * tet_refreshes / (te["ms"] / 1e3) / 1e9
+        roof["tet_eval"] = {"kernel": "k_tet_grad_mixed (float-float gradient + float32 Hessian blocks per tet)",
+                            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                            "traffic": ncu_traffic("k_tet_grad_mixed"), "peak_source": peak_src,
+                            "algorithmic": f"{TET_BYTES} B per refreshed tet",
+                            "avg_launch_ms": te["ms"] / max(te["launches"], 1)}
+    return roof
+
+
+def run_nu045(args, stream, dev):
+    """The named configuration as written: the 32^3 cube at nu = 0.45, the
+    same four E values, mixed coloured CC to 1e-6 (at most max_iters sweeps).
+    Reports each solve's outcome: converged, stopped at the cap (with its
+    residual) or ended by a non-finite update (with the sweeps run before)."""
+    import torch
+    import paper_2510_12053_gb300 as cc
+    out = []
+    for sc in scenes(0.45):
+        m = cc.Mesh.from_scene(sc, stream=stream)
+        m.color()
+        m.build_subspace(K_RING)
+        x = cc.to_soa(sc.x0, device=dev)
+        rec = {"E": sc.material.E, "nu": 0.45}
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        hist = None
+        try:
+            r = m.solve_step(x, precision="mixed", tol=1e-6, max_iters=args.max_iters, check_every=args.check_every,
+                             use_graph=not args.no_graph, history=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            hist = r.residuals
+            rec.update(outcome="converged" if r.converged else "cap", sweeps=r.iterations,
+                       rel_residual=r.g_final / r.g0, ms=ev0.elapsed_time(ev1))
+        except cc.CCError as e:
+            torch.cuda.synchronize()
+            rec.update(outcome="diverged", error=str(e))
+        if hist is not None:
+            h = hist[hist >= 0]
+            rec["max_rel_residual"] = float(h.max() / h[0]) if h.size else None
+        m.close()
+        out.append(rec)
+    return out
+
+
+def oracle_full_sweep(nu):
+    """One whole coloured CC sweep of the oracle (its own ``solvers.sweep``) on
+    the 32^3 cube from x0, single-threaded; the 2-ring bases of every free
+    vertex are built by the oracle first (timed separately)."""
+    from oracle import fem, solvers, subspace, topology
+    sc = _ow_scene(nu)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    t0 = time.perf_counter()
+    sup, U = subspace.build_local_bases(pb, topo, K_RING)
+    t_b = time.perf_counter() - t0
+    st = solvers.Stats()
+    t0 = time.perf_counter()
+    solvers.sweep(pb, topo, sup, U, sc.x0, None, "cc", "colored", st)
+    t_s = time.perf_counter() - t0
+    n_free = int(pb.free.sum())
+    return {"basis_build_s": t_b, "sweep_s": t_s, "updates": st.updates, "vertex_updates_per_s": st.updates / t_s,
+            "cores": 1, "n_free": n_free, "host": host_info()}
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2510_12053_gb300 as cc
@@ -650,7 +940,7 @@ def run_ours(args, rank, world):
         one_step("mixed")
     torch.cuda.synchronize()
     for m in meshes:
-        m.profile_enable(True)
+        m.profile_enable(False)   # resets the launch counters; no event timing inside the timed region
     clocks = Clocks(dev.index)
     dist_barrier()
     torch.cuda.synchronize()
@@ -671,61 +961,56 @@ def run_ours(args, rank, world):
     dist_barrier()
     wall_ms = 1e3 * (time.perf_counter() - t_wall)
     clk = clocks.stop()
-    prof = [m.profile_read() for m in meshes]
-    for m in meshes:
-        m.profile_enable(False)
+    launches = sum(m.profile_read()["total_launches"] for m in meshes)
     total_ms = sum(times)
     updates = n_free * sweeps_total
     value = whole_job_rate(updates, total_ms, world, dev)
     total_ms = reduce_over_ranks(total_ms, world, dev, "max")
     sweeps_per_solve = sweeps_total / (args.steps * len(meshes))
+    ms_per_sweep = total_ms / max(sweeps_total, 1)
 
-    # per-class device time over the timed region
+    # per-class device time: one more step with event timing on, outside the timed region
+    for m in meshes:
+        m.profile_enable(True)
+    flush.zero_()
+    sweeps_prof, _ = one_step("mixed")
+    torch.cuda.synchronize()
+    prof = [m.profile_read() for m in meshes]
+    for m in meshes:
+        m.profile_enable(False)
     cls = {k: {"ms": sum(p[k]["ms"] for p in prof), "launches": sum(p[k]["launches"] for p in prof)}
            for k in cc.PROFILE_CLASSES}
-    launches = sum(p["total_launches"] for p in prof)
     dominant = max(cc.PROFILE_CLASSES, key=lambda k: cls[k]["ms"])
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    solves = args.steps * len(meshes)
     ncol = int(meshes[0].info().num_colors)
-    # units processed in the timed region
+    # units processed in the profiling step
     free_corners = int((scs[0].pinned[scs[0].tets] == 0).sum())
     active_tets = int((scs[0].pinned[scs[0].tets] == 0).any(axis=1).sum())
-    tet_refreshes = sweeps_total * free_corners + solves * active_tets
-    row_gathers = sweeps_total * ncol + solves
+    tet_refreshes = sweeps_prof * free_corners + len(meshes) * active_tets
+    row_gathers = sweeps_prof * ncol + len(meshes)
     fl = local_solve_flops(meshes[0])
     flops_per_sweep = float(fl.sum())
-    roof = {}
-    ls = cls["local_solve"]
-    if ls["ms"] > 0:
-        ach = flops_per_sweep * sweeps_total / (ls["ms"] / 1e3) / 1e12
-        tr = [ncu_traffic("k_couple"), ncu_traffic("k_condense")]
-        roof["local_solve"] = {"kernel": "k_couple + k_condense (coupling products + batched Schur solve)",
-                               "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": ach / FP32_PEAK_TFLOPS,
-                               "traffic": (tr[0] + tr[1]) if None not in tr else None,
-                               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                               "algorithmic": f"{flops_per_sweep / meshes[0].info().n_free:.0f} FP32 flop per vertex per sweep",
-                               "avg_launch_ms": ls["ms"] / max(ls["launches"] // 2, 1)}
-    ga = cls["gather"]
-    if ga["ms"] > 0:
-        gb = gather_bytes_per_refresh(scs[0])
-        ach = gb * row_gathers / (ga["ms"] / 1e3) / 1e9
-        roof["gather"] = {"kernel": "k_row_gather (gradient + upper block rows of every free vertex)",
-                          "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                          "traffic": ncu_traffic("k_row_gather"), "peak_source": peak_src,
-                          "algorithmic": f"{gb / 1e6:.1f} MB per launch",
-                          "avg_launch_ms": ga["ms"] / max(ga["launches"], 1)}
-    te = cls["tet_eval"]
-    if te["ms"] > 0:
-        ach = TET_BYTES * tet_refreshes / (te["ms"] / 1e3) / 1e9
-        roof["tet_eval"] = {"kernel": "k_tet_grad_mixed (float-float gradient + float32 Hessian blocks per tet)",
-                            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                            "traffic": ncu_traffic("k_tet_grad_mixed"), "peak_source": peak_src,
-                            "algorithmic": f"{TET_BYTES} B per refreshed tet",
-                            "avg_launch_ms": te["ms"] / max(te["launches"], 1)}
-    roofline = roof.get(dominant) or next(iter(roof.values()), None)
+
+    # the sweep against the HBM roofline on its algorithmic bytes: bases and
+    # support ids read once, tet ids / D_m^-1 / V_t for the four refreshes of
+    # every tet, positions read once per colour and written once
+    sup_total = int(meshes[0].info().support_total)
+    b_u, b_d = 4, 4   # float32 bases and D_m^-1 on the mixed path
+    sweep_bytes = sup_total * (9 * b_u + 4) + 4 * T * (16 + 9 * b_d + 4) + (ncol + 1) * n * 24
+    sweep_ach = sweep_bytes / (ms_per_sweep / 1e3) / 1e9
+    sweep_traffic = sweep_ncu_traffic(ncol)
+    sweep_flops_rate = flops_per_sweep / (ms_per_sweep / 1e3) / 1e12
+    roofline = {"kernel": "sweep", "bound": "hbm", "achieved": sweep_ach, "peak": hbm, "unit": "GB/s",
+                "frac": sweep_ach / hbm, "traffic": sweep_traffic, "peak_source": peak_src + " (HBM copy)",
+                "algorithmic": f"{sweep_bytes / 1e6:.1f} MB per {ncol}-colour sweep (bases {sup_total} blocks x 40 B, "
+                               f"{T} tets x 4 refreshes x 56 B, positions {ncol + 1} x {n} x 24 B)",
+                "ms_per_sweep": ms_per_sweep, "units": "one coloured sweep (every free vertex updated once)",
+                "fp32_alu": {"achieved_tflops": sweep_flops_rate, "peak": FP32_PEAK_TFLOPS,
+                             "frac": sweep_flops_rate / FP32_PEAK_TFLOPS,
+                             "note": "coupling products only; peak derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}}
+    roof = per_class_rooflines(cls, meshes, scs, sweeps_prof, tet_refreshes, row_gathers, flops_per_sweep,
+                               hbm, peak_src)
 
     # plain float64 CC on the same solves
     fp64 = None
@@ -763,7 +1048,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     dist_barrier()
     e2e_value = whole_job_rate(n_free * e2e_sweeps, sum(e2e_ms), world, dev)
+    for m in meshes:
+        m.close()
 
+    nu045 = None if args.no_nu045 else run_nu045(args, stream, dev)
     batch_res = None
     if not args.no_batch:
         batch_res = run_batch(args, stream, dev)
@@ -775,11 +1063,15 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, info = oracle_rate(scs[1], 300)
-        cpu = {"value": v, "unit": "vertex-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"one float64 gradient+Hessian assembly of the full cube ({info['t_assembly_s']:.2f} s) "
-                         f"and 300 local CC updates ({1e3 * info['t_update_s']:.2f} ms each), scaled to one "
-                         f"{info['colors']}-colour sweep"}
+        ob = oracle_baseline(args.nu)
+        cpu = {"value": ob["value"], "unit": "vertex-updates/s", "cores": ob["cores"], "kind": "oracle",
+               "sample": f"colour 0 of one coloured CC sweep of the full 32^3 cube ({ob['updates']} of {n_free} free "
+                         f"vertices, E=1e5): float64 gradient + Hessian assembly at x0 (serial) and every local CC "
+                         f"update of the colour over {ob['cores']} processes, {ob['s']:.1f} s; 2-ring oracle bases "
+                         f"built beforehand (untimed)",
+               "single_thread": ob.get("single_thread"), "host": host_info()}
+    cfg1 = cfg1_oracle_timings() if (rank == 0 and args.cfg1_oracle) else None
+    full_cpu = oracle_full_sweep(args.nu) if (rank == 0 and args.cpu_full_sweep) else None
 
     if rank == 0:
         line = {
@@ -796,13 +1088,15 @@ def run_ours(args, rank, world):
             "wall_ms_timed": wall_ms,
             "roofline": roofline,
             "roofline_all": roof,
-            "kernel_ms": {k: round(v["ms"], 3) for k, v in cls.items()},
+            "kernel_ms_profiled_step": {k: round(v["ms"], 3) for k, v in cls.items()},
+            "kernel_launches_profiled_step": {k: v["launches"] for k, v in cls.items()},
             "dominant_kernel_class": dominant,
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "vertex-updates/s", "h2d_bytes_per_step": 24 * n * len(meshes),
                     "d2h_bytes_per_step": 24 * n * len(meshes)},
             "cpu_baseline": cpu,
+            "cfg_nu045": nu045,
             "batch": batch_res,
             "learned": learned_res,
         }
@@ -810,9 +1104,11 @@ def run_ours(args, rank, world):
             line["resolution"] = resolution_res
         if large_res is not None:
             line["large_beam"] = large_res
+        if cfg1 is not None:
+            line["cfg1_oracle"] = cfg1
+        if full_cpu is not None:
+            line["cpu_full_sweep"] = full_cpu
         print(json.dumps(line), flush=True)
-    for m in meshes:
-        m.close()
 
 
 def main():

@@ -423,11 +423,10 @@ __host__ __device__ inline size_t warp_smem_bytes(int sup_max, int warps) {
 }
 
 // Batched condensation (Eq. 9-12), one free vertex per thread: a warp
-// condenses 32 vertices at once, so the float64 or float-float 3x3 algebra
-// runs at full SIMD width instead of on one lane per vertex.  3x3 inverses
-// use the adjugate; the SPD guard is the Cholesky pivot test written with
-// leading minors.  `AR` is the arithmetic: double (float64 path) or df
-// (float-float, mixed path).
+// condenses 32 vertices at once, so the float64 3x3 algebra runs at full
+// SIMD width instead of on one lane per vertex.  3x3 inverses use the
+// adjugate; the SPD guard is the Cholesky pivot test written with leading
+// minors.  `AR` is the arithmetic type (double on both paths).
 template <typename AR, typename HT, bool kMixed, int kUpd>
 __global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, const HT* __restrict__ cpl,
                            const int32_t* __restrict__ sup_ptr, const int32_t* __restrict__ up_ptr,
@@ -459,8 +458,9 @@ __global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, con
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if constexpr (kMixed) gi[a] = V{g_hi[3 * (int64_t)i + a], g_lo[3 * (int64_t)i + a]};
-    else gi[a] = Ar::mk(g64[3 * (int64_t)i + a]);
+    if constexpr (!kMixed) gi[a] = Ar::mk(g64[3 * (int64_t)i + a]);
+    else if constexpr (sizeof(V) == sizeof(double)) gi[a] = (double)g_hi[3 * (int64_t)i + a] + (double)g_lo[3 * (int64_t)i + a];
+    else gi[a] = V{g_hi[3 * (int64_t)i + a], g_lo[3 * (int64_t)i + a]};
   }
   V M[9], rhs[3];
   int fb = -1;
@@ -636,10 +636,11 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
   constexpr int kCondenseThreads = 32;
   const unsigned grid = (unsigned)((count + kCondenseThreads - 1) / kCondenseThreads);
   if constexpr (kMixed) {
-    const df rel{1e-12f, (float)(1e-12 - (double)1e-12f)};
-    pdl_launch(k_condense<df, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
-               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl, rel,
-               (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
+    // float64 condensation of the float32 coupling products (the 3x3 Schur
+    // solves of Eq. 11-12 stay in float64 in both precisions)
+    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
+               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
+               1e-12, (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
   } else {
     pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
                (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
