@@ -870,9 +870,12 @@ def run_nu045(args, stream, dev):
                        rel_residual=r.g_final / r.g0, ms=ev0.elapsed_time(ev1))
         except cc.CCError as e:
             torch.cuda.synchronize()
-            rec.update(outcome="diverged", error=str(e))
+            hist = getattr(e, "residuals", None)
+            done = np.flatnonzero(hist >= 0) if hist is not None else np.zeros(0, int)
+            rec.update(outcome="diverged", error=str(e),
+                       sweeps_before_failure=int(done.max()) if done.size else None)
         if hist is not None:
-            h = hist[hist >= 0]
+            h = hist[np.isfinite(hist) & (hist >= 0)]
             rec["max_rel_residual"] = float(h.max() / h[0]) if h.size else None
         m.close()
         out.append(rec)

@@ -395,6 +395,20 @@ cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_d
  * value. */
 cc_status cc_set_launch_shape(cc_mesh* mesh, int32_t couple_threads, int32_t gather_warps, int32_t couple_row_lanes);
 
+/* Selects between equivalent kernel variants of the mixed-precision sweep
+ * (no counterpart in the paper; both compute Eq. 9-12 on the same data):
+ *   rows_from_positions  1: the stable Neo-Hookean float32 block rows are
+ *                        formed per row from the positions (no per-tet
+ *                        Hessian store); 0: per-tet Hessian store + gather.
+ *                        Fixed Corotational always uses the store.
+ *   couple_staged        1: the coupling kernel copies all blocks it reads
+ *                        to shared memory first (cp.async); 0: it loads them
+ *                        as it goes.
+ * 1 sets, 0 clears, -1 keeps a switch; anything else is CC_ERR_INVALID_ARG.
+ * The defaults are 0 and 0 (measured faster on the 32^3 cube); cc_autotune
+ * tries both.  Results agree within float32 rounding. */
+cc_status cc_set_sweep_variant(cc_mesh* mesh, int32_t rows_from_positions, int32_t couple_staged);
+
 /* ======================================================================
  * Learned perturbation bases.  The paper builds every U_i by the patch
  * solve of Eq. 5 (Sec. 3.1) and has no learned component: everything below

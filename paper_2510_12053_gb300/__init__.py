@@ -158,6 +158,7 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int64)]),
     "cc_build_learned_subspace": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(LearnedStats)]),
     "cc_set_launch_shape": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "cc_set_sweep_variant": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "cc_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "cc_build_bases_noalloc": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -386,6 +387,10 @@ class Mesh:
         and the gather's warps per block (0 keeps a value)."""
         _check(lib().cc_set_launch_shape(self._h, int(couple_threads), int(gather_warps), int(couple_row_lanes)))
 
+    def set_sweep_variant(self, rows_from_positions: int = -1, couple_staged: int = -1):
+        """Chooses the mixed sweep's kernel variants (1 on, 0 off, -1 keep)."""
+        _check(lib().cc_set_sweep_variant(self._h, int(rows_from_positions), int(couple_staged)))
+
     def profile_enable(self, on: bool = True):
         _check(lib().cc_profile_enable(self._h, int(on)))
 
@@ -428,7 +433,9 @@ class Mesh:
         rc = lib().cc_solve_step(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
                                  ctypes.byref(st))
         if rc not in (OK, ERR_NOT_CONVERGED):
-            _check(rc)
+            err = CCError(rc, lib().cc_last_error().decode())
+            err.residuals = hist   # the residuals checked before the failure (-1 past it)
+            raise err
         return SolveResult(st.iterations, bool(st.converged), st.g0, st.g_final, st.energy_final,
                            st.sweeps.updates, st.sweeps.fallback_empty, st.sweeps.fallback_reduced,
                            st.sweeps.fallback_schur, hist)

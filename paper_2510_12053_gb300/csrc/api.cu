@@ -67,7 +67,6 @@ void ensure_state(Mesh& m, cc_precision p) {
   } else {
     if (!m.mx.gcon.p) {
       m.mx.gcon.alloc(3 * ne);
-      m.mx.hten.alloc(96 * (size_t)m.T);
       m.mx.g_hi.alloc(3 * m.n);
       m.mx.g_lo.alloc(3 * m.n);
       m.mx.bsr.alloc(12 * m.nnz_up);
@@ -81,6 +80,8 @@ void ensure_state(Mesh& m, cc_precision p) {
       CCG_CUDA(cudaMemsetAsync(m.mx.xt_hi.p, 0, m.n * sizeof(float4), s));
       CCG_CUDA(cudaMemsetAsync(m.mx.xt_lo.p, 0, m.n * sizeof(float4), s));
     }
+    // the per-tet Hessian store exists only for the gather path
+    if (!rows_from_positions(m) && !m.mx.hten.p) m.mx.hten.alloc(96 * (size_t)m.T);
   }
 }
 
@@ -996,6 +997,18 @@ cc_status cc_set_launch_shape(cc_mesh* m, int32_t couple_threads, int32_t gather
     if (gather_warps) m->tune_gather_wpb = gather_warps;
     if (couple_row_lanes) m->tune_couple_row_lanes = couple_row_lanes;
     drop_graph(*m);
+  })
+}
+
+cc_status cc_set_sweep_variant(cc_mesh* m, int32_t rows_from_positions, int32_t couple_staged) {
+  CC_API_BODY("cc_set_sweep_variant", {
+    CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
+    CCG_CHECK(rows_from_positions >= -1 && rows_from_positions <= 1 && couple_staged >= -1 && couple_staged <= 1,
+              CC_ERR_INVALID_ARG, "variant switches are 1 (on), 0 (off) or -1 (keep)");
+    if (rows_from_positions >= 0) m->rows_build = rows_from_positions != 0;
+    if (couple_staged >= 0) m->couple_staged = couple_staged != 0;
+    drop_graph(*m);
+    if (m->mx.gcon.p) ensure_state(*m, CC_PREC_MIXED);  // allocates the per-tet store if the gather path is back
   })
 }
 

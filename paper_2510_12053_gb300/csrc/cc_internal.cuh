@@ -140,6 +140,8 @@ struct Mesh {
   int tune_couple_threads = 64;   // threads per vertex in the coupling kernel (32: one warp)
   int tune_couple_row_lanes = 4;  // threads per block row in the coupling kernel (1, 2, 4, 8)
   int tune_gather_wpb = 4;        // warps (rows) per block in the row gather
+  bool couple_staged = false;     // coupling kernel copies its blocks to shared memory first (cp.async)
+  bool rows_build = false;        // mixed stable Neo-Hookean rows formed from the positions (k_row_build)
   int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
   int32_t max_valence = 0;
   double E = 0, nu = 0, rho = 0, mu = 0, lam_hat = 0, h = 0;
@@ -189,6 +191,7 @@ struct Mesh {
   DBuf<double> d_Bm;         // [T][9] D_m^{-1}, row-major (row c = shape vector of corner c+1)
   DBuf<float2> d_Bm_df;      // [T][9] float-float copy
   DBuf<float> d_Bm32;        // [T][9]
+  DBuf<float> d_Bm32p;       // [T][3][4] rows padded to four (row build)
   DBuf<double> d_vol;        // [T]
   DBuf<double2> d_mat64;     // [T] (mu, lam_hat) of the tet's material
   DBuf<float4> d_matdf;      // [T] (mu hi, mu lo, lam_hat hi, lam_hat lo)
@@ -208,6 +211,7 @@ struct Mesh {
   DBuf<int32_t> d_up_col;    // [nnz_up]
   DBuf<int32_t> d_rs_ptr;    // [nnz_up+1] sources of each upper block (free rows)
   DBuf<int32_t> d_rs_src;    // per-tet store offset of each source, bit 31 = transpose
+  DBuf<uint16_t> d_rs_loc;   // the same sources as row-local codes k * 4 + w (row build)
   DBuf<int32_t> d_free_rows; // free vertices, ascending
   DBuf<int4> d_row_hdr;      // [2 n_free] row gather records: (j, p0, nup, rb), (rcount, e0, val, 0)
   DBuf<int32_t> d_color;     // [n]
@@ -265,6 +269,14 @@ __device__ __forceinline__ void pdl_entry() {
 #endif
 
 bool pdl_enabled();  // true when CC_GB300_PDL is set in the environment (default: ordinary launches)
+
+// The mixed path of the stable Neo-Hookean material forms its float32 block
+// rows from the positions (k_row_build) instead of a per-tet Hessian store;
+// the float64 path and Fixed Corotational keep the store (FCR's blocks need
+// the polar rotation, too costly to form four times per tet).
+inline bool rows_from_positions(const Mesh& m) {
+  return m.rows_build && m.model == CC_MODEL_SNH && m.max_valence <= 64;
+}
 
 template <typename... KArgs, typename... Args>
 void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {

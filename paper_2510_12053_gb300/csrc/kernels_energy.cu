@@ -222,7 +222,8 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
                                                     const float4* __restrict__ x_lo, int t, df mu_d, df lh_d,
                                                     float mu_f, float lh_f, const float* __restrict__ volw32,
                                                     float2* __restrict__ gcon, float* __restrict__ hstage, bool fcr,
-                                                    bool live, int t_store, float* __restrict__ hten) {
+                                                    bool live, int t_store, float* __restrict__ hten,
+                                                    bool hess = true) {
   const int4 tv = tets[t], ts = tslot[t];
   const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
   const int ent[4] = {ts.x, ts.y, ts.z, ts.w};
@@ -302,6 +303,7 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
 #pragma unroll
     for (int r = 0; r < 3; ++r) gcon[3 * e + r] = make_float2(g[v][r].hi, g[v][r].lo);
   }
+  if (!hess) return;  // the rows are built from the positions (k_row_build)
   // float32 Hessian blocks from the high parts
   float Ff[9], Cf[9], G[4][3];
 #pragma unroll
@@ -332,7 +334,7 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
 // Float-float per-tet kernel (gradient in float-float, Hessian blocks in
 // float32 through the shared-memory staging above).  Lanes past the list
 // evaluate the list's first tet and store nothing.
-template <bool kFCR>
+template <bool kFCR, bool kHess = true>
 __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __restrict__ tslot,
                                  const float2* __restrict__ Bm_df, const float2* __restrict__ volw,
                                  const uint8_t* __restrict__ pinned, const float4* __restrict__ x_hi,
@@ -347,7 +349,7 @@ __global__ void k_tet_grad_mixed(const int4* __restrict__ tets, const int4* __re
   const int tc = live ? t : list[0];
   const float4 ml = matdf[tc];  // (mu hi, mu lo, lam_hat hi, lam_hat lo)
   tet_grad_mixed_body(tets, tslot, Bm_df, volw, pinned, x_hi, x_lo, tc, df{ml.x, ml.y}, df{ml.z, ml.w}, ml.x, ml.z,
-                      volw32, gcon, hstage, kFCR, live, t, hten);
+                      volw32, gcon, hstage, kFCR, live, t, hten, kHess);
 }
 
 // Gradient of free row j from its per-(vertex, slot) entries e0 .. e0 + val - 1
@@ -476,6 +478,142 @@ __global__ void k_row_gather(const int4* __restrict__ row_hdr, int64_t nrows, co
       HT* dst = bsr + (int64_t)(p0 + q) * 12 + 4 * r;
       dst[col] = acc;
       if (col == 2) dst[3] = HT(0);
+    }
+  }
+}
+
+// ---- phase B without the per-tet store (mixed path, stable Neo-Hookean) ----
+// One warp per free row j.  The gradient is summed from the per-(vertex,
+// slot) entries exactly as in k_row_gather.  The upper block row is formed
+// from the positions instead of a stored Hessian: lane k takes the row's k-th
+// incident tet (ascending tet id), forms F = D_s D_m^{-1} in float32 (edge
+// vectors from the float-float position mirror, so they carry full float32
+// accuracy), cof F and J, and the blocks K_{cj,w} = d2E_t/dx_j dx_w of every
+// corner w whose vertex id is >= j (float32, the formula of hess_block),
+// staged in shared memory.  Lanes (block, component) then sum each block's
+// sources -- the row-local codes k * 4 + w of the upper blocks, ascending --
+// in the same fixed order as the gather.  Each tet's kinematics are formed
+// by its four rows, but no Hessian value goes through global memory.
+template <int kMaxVal>
+__global__ void __launch_bounds__(128) k_row_build(
+    const int4* __restrict__ row_hdr, int64_t nrows, const int32_t* __restrict__ rs_ptr,
+    const uint16_t* __restrict__ rs_loc, const int32_t* __restrict__ vt_tet, const uint8_t* __restrict__ vt_corner,
+    const int4* __restrict__ vt_ids, const float4* __restrict__ Bm32p, const float* __restrict__ volw32,
+    const float4* __restrict__ matdf, const float4* __restrict__ x_hi, const float4* __restrict__ x_lo,
+    const float* __restrict__ mass32, const float2* __restrict__ mass_df, const float2* __restrict__ gcon_df,
+    const float4* __restrict__ xt_hi, const float4* __restrict__ xt_lo, bool dynamic, int max_rs, int max_up,
+    float* __restrict__ bsr, float* __restrict__ g_hi, float* __restrict__ g_lo) {
+  pdl_entry();
+  constexpr int kPitch = 37;  // odd: the lanes' staged blocks start in distinct banks
+  extern __shared__ __align__(16) float rb_smem[];
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int64_t wid = (int64_t)blockIdx.x * wpb + warp;
+  if (wid >= nrows) return;
+  float* stage = rb_smem + warp * (kMaxVal * kPitch);
+  int* roff = reinterpret_cast<int*>(rb_smem + wpb * (kMaxVal * kPitch)) + warp * (max_up + 1 + (max_rs + 1) / 2);
+  uint16_t* rloc = reinterpret_cast<uint16_t*>(roff + max_up + 1);
+  const int4 h0 = __ldg(row_hdr + 2 * wid), h1 = __ldg(row_hdr + 2 * wid + 1);
+  const int j = h0.x, p0 = h0.y, nup = h0.z, rb = h0.w, rcount = h1.x, e0 = h1.y, val = h1.z;
+  row_gradient<true>(j, e0, val, lane, nullptr, gcon_df, nullptr, mass_df, nullptr, x_hi, x_lo, nullptr, xt_hi,
+                     xt_lo, 0, dynamic, nullptr, g_hi, g_lo);
+  for (int q = lane; q <= nup; q += 32) roff[q] = rs_ptr[p0 + q] - rb;
+  for (int k = lane; k < rcount; k += 32) rloc[k] = rs_loc[rb + k];
+  for (int k = lane; k < val; k += 32) {
+    const int t = vt_tet[e0 + k];
+    const int cj = vt_corner[e0 + k];
+    const int4 tv = vt_ids[e0 + k];  // the tet's vertex ids, stored per entry: no load waits for t
+    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+    float4 ph[4], pl[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      ph[v] = x_hi[vid[v]];
+      pl[v] = x_lo[vid[v]];
+    }
+    const float4 b0 = Bm32p[3 * (int64_t)t], b1 = Bm32p[3 * (int64_t)t + 1], b2 = Bm32p[3 * (int64_t)t + 2];
+    float G[4][3] = {{-(b0.x + b1.x + b2.x), -(b0.y + b1.y + b2.y), -(b0.z + b1.z + b2.z)},
+                     {b0.x, b0.y, b0.z}, {b1.x, b1.y, b1.z}, {b2.x, b2.y, b2.z}};
+    float F[9];
+    {
+      float e[3][3];  // e[v - 1][a]: edge x_v - x_0
+#pragma unroll
+      for (int v = 1; v < 4; ++v) {
+        e[v - 1][0] = (ph[v].x - ph[0].x) + (pl[v].x - pl[0].x);
+        e[v - 1][1] = (ph[v].y - ph[0].y) + (pl[v].y - pl[0].y);
+        e[v - 1][2] = (ph[v].z - ph[0].z) + (pl[v].z - pl[0].z);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) F[3 * a + b] = fmaf(e[2][a], G[3][b], fmaf(e[1][a], G[2][b], e[0][a] * G[1][b]));
+    }
+    float C[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int b1i = (b + 1) % 3, b2i = (b + 2) % 3;
+      C[0 + b] = F[3 + b1i] * F[6 + b2i] - F[6 + b1i] * F[3 + b2i];
+      C[3 + b] = F[6 + b1i] * F[0 + b2i] - F[0 + b1i] * F[6 + b2i];
+      C[6 + b] = F[0 + b1i] * F[3 + b2i] - F[3 + b1i] * F[0 + b2i];
+    }
+    const float J = F[0] * C[0] + F[3] * C[3] + F[6] * C[6];
+    const float4 ml = matdf[t];  // (mu hi, mu lo, lam_hat hi, lam_hat lo)
+    const float mu = ml.x, lh = ml.z, V = volw32[t];
+    const float sJ = lh * (J - 1.0f) - mu;
+    float a[4][3];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) a[v][r] = C[3 * r] * G[v][0] + C[3 * r + 1] * G[v][1] + C[3 * r + 2] * G[v][2];
+    float aj[3], Gj[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      aj[r] = cj == 0 ? a[0][r] : cj == 1 ? a[1][r] : cj == 2 ? a[2][r] : a[3][r];
+      Gj[r] = cj == 0 ? G[0][r] : cj == 1 ? G[1][r] : cj == 2 ? G[2][r] : G[3][r];
+    }
+    float* dst = stage + k * kPitch;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (vid[w] < j) continue;
+      float K[9];
+      hess_block<float>(F, aj, a[w], Gj, G[w], mu, lh, sJ, K);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) dst[9 * w + q] = V * K[q];
+    }
+  }
+  __syncwarp();
+  const int c = lane % 9, grp = lane / 9, r = c / 3, col = c % 3;
+  // diagonal block: one source per incident tet, three interleaved partial sums
+  {
+    float acc = 0.0f;
+    if (grp < 3) {
+      const int s1 = roff[1];
+      for (int s = grp; s < s1; s += 3) {
+        const int code = rloc[s];
+        acc += stage[(code >> 2) * kPitch + 9 * (code & 3) + c];
+      }
+    }
+    const float a1 = __shfl_down_sync(0xffffffffu, acc, 9);
+    const float a2 = __shfl_down_sync(0xffffffffu, acc, 18);
+    if (lane < 9) {
+      float d = (acc + a1) + a2;
+      if (dynamic && r == col) d += mass32[j];
+      float* dst = bsr + (int64_t)p0 * 12 + 4 * r;
+      dst[col] = d;
+      if (col == 2) dst[3] = 0.0f;
+    }
+  }
+  // off-diagonal upper blocks, three per round
+  for (int base = 1; base < nup; base += 3) {
+    const int q = base + grp;
+    if (grp < 3 && q < nup) {
+      float acc = 0.0f;
+      const int s1 = roff[q + 1];
+      for (int s = roff[q]; s < s1; ++s) {
+        const int code = rloc[s];
+        acc += stage[(code >> 2) * kPitch + 9 * (code & 3) + c];
+      }
+      float* dst = bsr + (int64_t)(p0 + q) * 12 + 4 * r;
+      dst[col] = acc;
+      if (col == 2) dst[3] = 0.0f;
     }
   }
 }
@@ -661,6 +799,13 @@ void launch_tet_grad_mixed(Mesh& m, const int32_t* list, int64_t count, double w
   (void)weight;
   constexpr int kThreads = 128;
   const bool fcr = m.model == CC_MODEL_FCR;
+  if (rows_from_positions(m)) {
+    pdl_launch(k_tet_grad_mixed<false, false>, grid_for(count, kThreads), kThreads, 0, s, (const int4*)m.d_tets.p,
+               (const int4*)m.d_tslot.p, (const float2*)m.d_Bm_df.p, (const float2*)m.d_volw_df.p,
+               (const uint8_t*)m.d_pinned.p, (const float4*)m.mx.x_hi.p, (const float4*)m.mx.x_lo.p, list, count,
+               (const float4*)m.d_matdf.p, (const float*)m.d_volw32.p, m.mx.gcon.p, (float*)nullptr);
+    return;
+  }
   const size_t smem = (size_t)kThreads * (fcr ? TetStage<true>::kPitch : TetStage<false>::kPitch) * sizeof(float);
   auto kern = fcr ? k_tet_grad_mixed<true> : k_tet_grad_mixed<false>;
   set_smem_limit(reinterpret_cast<const void*>(kern), smem);
@@ -694,7 +839,26 @@ void launch_rows_f64(Mesh& m, const double* x, const double* xt, double weight, 
 
 void launch_rows_mixed(Mesh& m, double weight, cudaStream_t s) {
   (void)weight;
-  launch_rows<float, true>(m, nullptr, nullptr, m.mx.bsr.p, m.mx.hten.p, m.d_mass32.p, s);
+  if (!rows_from_positions(m)) {
+    launch_rows<float, true>(m, nullptr, nullptr, m.mx.bsr.p, m.mx.hten.p, m.d_mass32.p, s);
+    return;
+  }
+  if (m.n_free <= 0) return;
+  const bool dyn = m.h > 0.0;
+  constexpr int kWpb = 4;
+  const int64_t blocks = (m.n_free + kWpb - 1) / kWpb;
+  const int maxval = m.max_valence <= 32 ? 32 : 64;
+  const size_t smem = (size_t)kWpb * ((size_t)maxval * 37 * sizeof(float) +
+                                      (size_t)(m.max_up + 1 + (m.max_rs + 1) / 2) * sizeof(int));
+  auto kern = maxval == 32 ? k_row_build<32> : k_row_build<64>;
+  set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+  pdl_launch(kern, (unsigned)blocks, 32 * kWpb, smem, s, (const int4*)m.d_row_hdr.p, m.n_free,
+             (const int32_t*)m.d_rs_ptr.p, (const uint16_t*)m.d_rs_loc.p, (const int32_t*)m.d_vt_tet.p,
+             (const uint8_t*)m.d_vt_corner.p, (const int4*)m.d_vt_ids.p, (const float4*)m.d_Bm32p.p,
+             (const float*)m.d_volw32.p, (const float4*)m.d_matdf.p, (const float4*)m.mx.x_hi.p,
+             (const float4*)m.mx.x_lo.p, (const float*)m.d_mass32.p, (const float2*)m.d_mass_df.p,
+             (const float2*)m.mx.gcon.p, (const float4*)m.mx.xt_hi.p, (const float4*)m.mx.xt_lo.p, dyn, m.max_rs,
+             m.max_up, m.mx.bsr.p, m.mx.g_hi.p, m.mx.g_lo.p);
 }
 
 void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {

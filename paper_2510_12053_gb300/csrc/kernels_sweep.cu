@@ -61,10 +61,21 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
 
 
 template <typename HT>
-__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps) {
-  return align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
-         align16((size_t)smap_max * code_bytes) + (size_t)nwarps * 32 * sizeof(HT);
+__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps,
+                                                 bool staged = false) {
+  size_t b = align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
+             align16((size_t)smap_max * code_bytes) + align16((size_t)nwarps * 32 * sizeof(HT));
+  if (staged) b += align16((size_t)(sup_max + 1) * 3 * sizeof(HT)) + (size_t)smap_max * 12 * sizeof(HT);
+  return b;
 }
+
+// 16-byte global -> shared copy that bypasses the registers (cp.async, L2
+// only) and the wait for all of the thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename SlotT>
 struct SlotCodes;
@@ -148,7 +159,11 @@ __device__ __forceinline__ void load_slot<double>(const double* p, double* u) {
 // term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
 // l > i.  The CTA writes 27 values per vertex: Ht (6, symmetric), A (9),
 // b (3), H_ii (9, stored directly by the thread that reads it).
-template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads>
+// kStaged: before any arithmetic every thread issues cp.async copies of all
+// the blocks it will use (and the support's gradients are staged with the
+// basis), so a thread waits for the L2 once instead of once per block; the
+// blocks sit in shared memory at their position in the slot map.
+template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads, bool kStaged = false>
 __global__ void __launch_bounds__(kThreads) k_couple(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
@@ -172,6 +187,10 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   SlotT* codes = reinterpret_cast<SlotT*>(ptr);
   ptr += align16((size_t)smap_max * sizeof(SlotT));
   HT* red = reinterpret_cast<HT*>(ptr);  // [warps][32]
+  ptr += align16((size_t)(kThreads / 32) * 32 * sizeof(HT));
+  HT* gsm = reinterpret_cast<HT*>(ptr);  // [m + 1][3] gradients of the rows (kStaged)
+  ptr += kStaged ? align16((size_t)(sup_max + 1) * 3 * sizeof(HT)) : 0;
+  HT* blk = reinterpret_cast<HT*>(ptr);  // [ncodes][12] staged blocks (kStaged)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = verts[blockIdx.x];
@@ -188,6 +207,9 @@ __global__ void __launch_bounds__(kThreads) k_couple(
     rstart[s] = a;
     rlen[s] = up_ptr[j + 1] - a;
     rid[s] = j;
+    if (kStaged && s < m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gsm[3 * s + c] = kMixed ? (HT)g_hi[3 * (int64_t)j + c] : (HT)g64[3 * (int64_t)j + c];
   }
   __syncthreads();
   // exclusive prefix of the row lengths (offsets into the slot map), warp 0
@@ -208,10 +230,25 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   }
   __syncthreads();
 
+  const int nl = 1 << row_lanes_log2, rl = tid & (nl - 1);
+  if (kStaged) {
+    // every block this thread reads below, copied ahead (same row/block walk)
+    constexpr int kChunks = 12 * sizeof(HT) / 16;
+    for (int r = tid >> row_lanes_log2; r <= m; r += kThreads >> row_lanes_log2) {
+      const int P = rstart[r], L = rlen[r], off = roff[r];
+      for (int q = rl; q < L; q += nl) {
+        if (codes[off + q] == Codes::kNone) continue;
+        const HT* src = bsr + (int64_t)(P + q) * 12;
+        HT* dst = blk + (size_t)(off + q) * 12;
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) cp_async16(dst + c * (16 / sizeof(HT)), src + c * (16 / sizeof(HT)));
+      }
+    }
+    cp_async_wait_all();
+  }
   HT h00 = 0, h01 = 0, h02 = 0, h11 = 0, h12 = 0, h22 = 0;
   HT A[9], b[3] = {0, 0, 0};
   mat3_zero(A);
-  const int nl = 1 << row_lanes_log2, rl = tid & (nl - 1);
   for (int r = tid >> row_lanes_log2; r <= m; r += kThreads >> row_lanes_log2) {
     const int P = rstart[r], L = rlen[r], off = roff[r];
     if (r < m) {
@@ -223,7 +260,8 @@ __global__ void __launch_bounds__(kThreads) k_couple(
         const unsigned code = codes[off + q];
         if (code == Codes::kNone) continue;
         HT H[9];
-        load_block(bsr, (int64_t)P + q, H);
+        if (kStaged) load_slot(blk + (size_t)(off + q) * 12, H);
+        else load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kSelf) {
           if (kUpd == CC_UPDATE_CC) mat3_tmul_acc(H, Uj, A);
         } else if (code == Codes::kDiag) {
@@ -249,7 +287,8 @@ __global__ void __launch_bounds__(kThreads) k_couple(
         const int j = rid[r];
         HT gj[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) gj[a] = kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
+        for (int a = 0; a < 3; ++a)
+          gj[a] = kStaged ? gsm[3 * r + a] : kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
 #pragma unroll
         for (int c = 0; c < 3; ++c) b[c] += Uj[c] * gj[0] + Uj[3 + c] * gj[1] + Uj[6 + c] * gj[2];
       }
@@ -258,7 +297,8 @@ __global__ void __launch_bounds__(kThreads) k_couple(
         const unsigned code = codes[off + q];
         if (code == Codes::kNone) continue;
         HT H[9];
-        load_block(bsr, (int64_t)P + q, H);
+        if (kStaged) load_slot(blk + (size_t)(off + q) * 12, H);
+        else load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kDiag) {
 #pragma unroll
           for (int c = 0; c < 9; ++c) cpl[(int64_t)blockIdx.x * 32 + 18 + c] = H[c];
@@ -568,11 +608,31 @@ void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, co
                    const float* g_hi, HT* cpl, const HT* rot, cudaStream_t s) {
   const int supm = m.sup_max > 0 ? m.sup_max : 1;
   const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
-  const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
-  CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
   const int lanes = m.tune_couple_row_lanes;
   CCG_CHECK(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8, CC_ERR_STATE, "bad coupling row lanes");
   const int lanes_log2 = lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : 3;
+  // blocks staged by cp.async where they fit next to the basis (float32 rows
+  // of the usual 2-ring supports: about 30 KB per vertex)
+  const size_t smem_st = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32, true);
+  if (m.couple_staged && smem_st <= 64 * 1024) {
+    if (m.smap_wide) {
+      auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads, true>;
+      set_smem_limit(reinterpret_cast<const void*>(kern), smem_st);
+      pdl_launch(kern, (unsigned)count, kThreads, smem_st, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+                 (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+                 (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
+    } else {
+      auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads, true>;
+      set_smem_limit(reinterpret_cast<const void*>(kern), smem_st);
+      pdl_launch(kern, (unsigned)count, kThreads, smem_st, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+                 (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+                 (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
+    }
+    CCG_CUDA(cudaGetLastError());
+    return;
+  }
+  const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
+  CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
   if (m.smap_wide) {
     auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads>;
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);

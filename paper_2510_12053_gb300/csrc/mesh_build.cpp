@@ -150,9 +150,13 @@ void build_topology(Mesh& m) {
   //      the tet's stored upper block pair (min(cj,w), max(cj,w)) in the
   //      per-tet Hessian store (96 values per tet), bit 31 set when the
   //      stored block must be transposed (cj > w).  Ascending slot order.
+  //      The same sources also get a row-local code k * 4 + w (k = the
+  //      tet's position in the row's vertex-tet list, w = the corner of l in
+  //      it) for the row build, which forms K_{cj,w} itself.
   static const int kPair[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
   std::vector<int32_t> rs_ptr(m.nnz_up + 1, 0);
   std::vector<int32_t> rs_src;
+  std::vector<uint16_t> rs_loc;
   for (int64_t v = 0; v < n; ++v) {
     const int64_t p0 = m.up_ptr[v], p1 = m.up_ptr[v + 1];
     if (m.pinned[v]) {
@@ -169,6 +173,7 @@ void build_topology(Mesh& m) {
           if (tv[w] == col) {
             const uint32_t off = (uint32_t)(t * 96 + 9 * kPair[cj][w]);
             rs_src.push_back((int32_t)(off | (cj > w ? 0x80000000u : 0u)));
+            rs_loc.push_back((uint16_t)(((e - m.vt_ptr[v]) << 2) | w));
           }
       }
       rs_ptr[p + 1] = (int32_t)rs_src.size();
@@ -197,11 +202,12 @@ void build_topology(Mesh& m) {
 
   // ---- upload
   std::vector<float2> Bm_df(9 * T);
-  std::vector<float> Bm32(9 * T);
+  std::vector<float> Bm32(9 * T), Bm32p(12 * T, 0.0f);
   for (int64_t k = 0; k < 9 * T; ++k) {
     float hi = (float)Bm[k];
     Bm_df[k] = make_float2(hi, (float)(Bm[k] - (double)hi));
     Bm32[k] = hi;
+    Bm32p[12 * (k / 9) + 4 * ((k % 9) / 3) + k % 3] = hi;  // rows padded to four for 16-byte loads
   }
   auto to32 = [&](const std::vector<int64_t>& a) {
     std::vector<int32_t> r(a.size());
@@ -213,6 +219,7 @@ void build_topology(Mesh& m) {
   m.d_Bm.upload(Bm, s);
   m.d_Bm_df.upload(Bm_df, s);
   m.d_Bm32.upload(Bm32, s);
+  m.d_Bm32p.upload(Bm32p, s);
   m.d_vol.upload(vol, s);
   {
     std::vector<double2> m64(T);
@@ -263,6 +270,7 @@ void build_topology(Mesh& m) {
   m.d_up_col.upload(m.up_col, s);
   m.d_rs_ptr.upload(rs_ptr, s);
   m.d_rs_src.upload(rs_src, s);
+  m.d_rs_loc.upload(rs_loc, s);
   m.d_free_rows.upload(free_rows, s);
   {
     // per free row, what the row gather needs first, in one 32-byte record:
