@@ -342,3 +342,28 @@ def test_restarted_bases_help_the_twisted_bar():
     _, hf = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-4, max_iters=80)
     _, hr = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=1e-4, max_iters=80, restart_every=5)
     assert hr.converged and hr.iterations < hf.iterations
+
+
+def test_stored_cube16_trajectory_is_the_oracles():
+    """The fixture the GPU trajectory test compares against
+    (tests/golden/cube16_trajectory.txt, written by make_cube16_trajectory.py)
+    starts where the oracle starts: its first sweep's energy and gradient norm
+    are recomputed here from the oracle."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cube16_trajectory.txt")
+    rows = {}
+    E = None
+    for line in open(path):
+        key, _, rest = line.partition(" ")
+        if key == "E":
+            E = float(rest)
+        elif key in ("energy", "gnorm") and E == 1e4:
+            rows[key] = np.array([float(v) for v in rest.split()])
+    sc = meshgen.stretch_box(16, 16, 16, E=1e4, nu=0.3, factor=1.5, jitter_amount=0.05, seed=0)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, U = subspace.build_local_bases(pb, topo, 2)
+    x, hist = solvers.solve(pb, topo, sup, U, sc.x0, kind="cc", tol=0.0, max_iters=1)
+    assert len(rows["energy"]) == 51 and len(rows["gnorm"]) == 51
+    np.testing.assert_allclose(hist.energy, rows["energy"][:2], rtol=1e-13)
+    np.testing.assert_allclose(hist.grad_norm, rows["gnorm"][:2], rtol=1e-12)
