@@ -382,8 +382,15 @@ typedef struct {
   double couple_ms[4];    /* ms per sweep with 32, 64, 128, 256 threads per vertex */
   double row_lanes_ms[4]; /* ms per sweep with 1, 2, 4, 8 threads per block row (0: not timed) */
   double gather_ms[3];    /* ms per sweep with 2, 4, 8 warps per block */
+  int32_t rows_from_positions;  /* chosen sweep variant (cc_set_sweep_variant) */
+  int32_t fused_condense;
+  double variant_ms[4];   /* ms per sweep with (rows_from_positions, fused_condense) = (0,0), (0,1), (1,0),
+                             (1,1), at the default launch shapes; variants a mesh cannot use stay 0 */
 } cc_tune_result;
 
+/* Tunes in this order: the sweep variant, the coupling kernel's threads per
+ * vertex, its threads per block row, the gather's warps per block; each
+ * choice is timed over `sweeps` sweeps from x (x itself is not modified). */
 cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev, cc_precision precision,
                       int32_t sweeps, cc_tune_result* out);
 
@@ -395,19 +402,24 @@ cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_d
  * value. */
 cc_status cc_set_launch_shape(cc_mesh* mesh, int32_t couple_threads, int32_t gather_warps, int32_t couple_row_lanes);
 
-/* Selects between equivalent kernel variants of the mixed-precision sweep
- * (no counterpart in the paper; both compute Eq. 9-12 on the same data):
- *   rows_from_positions  1: the stable Neo-Hookean float32 block rows are
- *                        formed per row from the positions (no per-tet
- *                        Hessian store); 0: per-tet Hessian store + gather.
- *                        Fixed Corotational always uses the store.
- *   couple_staged        1: the coupling kernel copies all blocks it reads
- *                        to shared memory first (cp.async); 0: it loads them
- *                        as it goes.
+/* Selects between equivalent kernel variants of the sweep (no counterpart in
+ * the paper; both settings compute Eq. 9-12 on the same data):
+ *   rows_from_positions  1: the mixed path's stable Neo-Hookean float32 block
+ *                        rows are formed per row from the positions (no
+ *                        per-tet Hessian store); 0: per-tet Hessian store +
+ *                        gather.  Fixed Corotational and the float64 path
+ *                        always use the store.
+ *   fused_condense       1: the coupling kernel condenses its vertices itself
+ *                        (the last CTA of every 32 list entries runs the
+ *                        float64 3x3 solves of the group, one vertex per
+ *                        lane); 0: a separate condensation launch.  The
+ *                        one-warp coupling shape always launches it apart.
  * 1 sets, 0 clears, -1 keeps a switch; anything else is CC_ERR_INVALID_ARG.
- * The defaults are 0 and 0 (measured faster on the 32^3 cube); cc_autotune
- * tries both.  Results agree within float32 rounding. */
-cc_status cc_set_sweep_variant(cc_mesh* mesh, int32_t rows_from_positions, int32_t couple_staged);
+ * Defaults: both 0 (measured fastest on the 32^3 cube); cc_autotune tries
+ * every applicable combination.  The fused and separate
+ * condensations give identical results; the two row builds agree within
+ * float32 rounding. */
+cc_status cc_set_sweep_variant(cc_mesh* mesh, int32_t rows_from_positions, int32_t fused_condense);
 
 /* ======================================================================
  * Learned perturbation bases.  The paper builds every U_i by the patch

@@ -91,7 +91,9 @@ class BatchStats(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("couple_threads", ctypes.c_int32), ("couple_row_lanes", ctypes.c_int32),
                 ("gather_warps", ctypes.c_int32), ("couple_ms", ctypes.c_double * 4),
-                ("row_lanes_ms", ctypes.c_double * 4), ("gather_ms", ctypes.c_double * 3)]
+                ("row_lanes_ms", ctypes.c_double * 4), ("gather_ms", ctypes.c_double * 3),
+                ("rows_from_positions", ctypes.c_int32), ("fused_condense", ctypes.c_int32),
+                ("variant_ms", ctypes.c_double * 4)]
 
 
 class Profile(ctypes.Structure):
@@ -380,16 +382,18 @@ class Mesh:
                                  int(sweeps), ctypes.byref(r)))
         return {"couple_threads": r.couple_threads, "couple_row_lanes": r.couple_row_lanes,
                 "gather_warps": r.gather_warps, "couple_ms": list(r.couple_ms),
-                "row_lanes_ms": list(r.row_lanes_ms), "gather_ms": list(r.gather_ms)}
+                "row_lanes_ms": list(r.row_lanes_ms), "gather_ms": list(r.gather_ms),
+                "rows_from_positions": r.rows_from_positions, "fused_condense": r.fused_condense,
+                "variant_ms": list(r.variant_ms)}
 
     def set_launch_shape(self, couple_threads: int = 0, gather_warps: int = 0, couple_row_lanes: int = 0):
         """Pins the coupling kernel's threads per vertex (32 = one warp) and threads per block row,
         and the gather's warps per block (0 keeps a value)."""
         _check(lib().cc_set_launch_shape(self._h, int(couple_threads), int(gather_warps), int(couple_row_lanes)))
 
-    def set_sweep_variant(self, rows_from_positions: int = -1, couple_staged: int = -1):
-        """Chooses the mixed sweep's kernel variants (1 on, 0 off, -1 keep)."""
-        _check(lib().cc_set_sweep_variant(self._h, int(rows_from_positions), int(couple_staged)))
+    def set_sweep_variant(self, rows_from_positions: int = -1, fused_condense: int = -1):
+        """Chooses the sweep's kernel variants (1 on, 0 off, -1 keep)."""
+        _check(lib().cc_set_sweep_variant(self._h, int(rows_from_positions), int(fused_condense)))
 
     def profile_enable(self, on: bool = True):
         _check(lib().cc_profile_enable(self._h, int(on)))

@@ -55,6 +55,10 @@ void drop_graph(Mesh& m) {
 void ensure_state(Mesh& m, cc_precision p) {
   cudaStream_t s = m.stream;
   const size_t ne = 4 * (size_t)m.T;
+  if (!m.d_grp_cnt.p) {  // arrival counters of the fused local solves (they reset themselves)
+    m.d_grp_cnt.alloc((size_t)(m.n_free + 31) / 32 + 1);
+    CCG_CUDA(cudaMemsetAsync(m.d_grp_cnt.p, 0, m.d_grp_cnt.count * sizeof(int32_t), s));
+  }
   if (p == CC_PREC_FP64) {
     if (!m.f64.gcon.p) {
       m.f64.gcon.alloc(3 * ne);
@@ -176,7 +180,7 @@ void solve_list(Mesh& m, const cc_sweep_opts& o, const int32_t* verts, int64_t c
     launch_local_solve_f64(m, o.update, verts, count, x, counters(m), m.stream);
   else
     launch_local_solve_mixed(m, o.update, verts, count, x, counters(m), m.stream);
-  prof_close(m, P_SOLVE, e0, o.update == CC_UPDATE_CD ? 1 : 2);
+  prof_close(m, P_SOLVE, e0, o.update == CC_UPDATE_CD || fused_local_solve(m, o.update) ? 1 : 2);
 }
 
 // One sweep over colours [cb, ce).  `fresh` means g and H already hold the
@@ -935,6 +939,24 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
       return ms / sweeps;
     };
     try {
+      // sweep variant first, at the current launch shapes
+      {
+        const bool rb0 = m->rows_build, fc0 = m->fused_condense;
+        int best_v = -1;
+        for (int v = 0; v < 4; ++v) {
+          out->variant_ms[v] = 0.0;
+          m->rows_build = (v >> 1) != 0;
+          m->fused_condense = (v & 1) != 0;
+          if (m->rows_build && !(p == CC_PREC_MIXED && rows_from_positions(*m))) continue;  // not applicable
+          ensure_state(*m, p);
+          drop_graph(*m);
+          out->variant_ms[v] = time_sweeps();
+          if (best_v < 0 || out->variant_ms[v] < out->variant_ms[best_v]) best_v = v;
+        }
+        m->rows_build = best_v >= 0 ? (best_v >> 1) != 0 : rb0;
+        m->fused_condense = best_v >= 0 ? (best_v & 1) != 0 : fc0;
+        ensure_state(*m, p);
+      }
       const int ct[4] = {32, 64, 128, 256}, gw[3] = {2, 4, 8};
       for (int k = 0; k < 4; ++k) {
         m->tune_couple_threads = ct[k];
@@ -979,6 +1001,8 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
     out->couple_threads = m->tune_couple_threads;
     out->couple_row_lanes = m->tune_couple_row_lanes;
     out->gather_warps = m->tune_gather_wpb;
+    out->rows_from_positions = m->rows_build ? 1 : 0;
+    out->fused_condense = m->fused_condense ? 1 : 0;
   })
 }
 
@@ -1000,13 +1024,13 @@ cc_status cc_set_launch_shape(cc_mesh* m, int32_t couple_threads, int32_t gather
   })
 }
 
-cc_status cc_set_sweep_variant(cc_mesh* m, int32_t rows_from_positions, int32_t couple_staged) {
+cc_status cc_set_sweep_variant(cc_mesh* m, int32_t rows_from_positions, int32_t fused_condense) {
   CC_API_BODY("cc_set_sweep_variant", {
     CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");
-    CCG_CHECK(rows_from_positions >= -1 && rows_from_positions <= 1 && couple_staged >= -1 && couple_staged <= 1,
+    CCG_CHECK(rows_from_positions >= -1 && rows_from_positions <= 1 && fused_condense >= -1 && fused_condense <= 1,
               CC_ERR_INVALID_ARG, "variant switches are 1 (on), 0 (off) or -1 (keep)");
     if (rows_from_positions >= 0) m->rows_build = rows_from_positions != 0;
-    if (couple_staged >= 0) m->couple_staged = couple_staged != 0;
+    if (fused_condense >= 0) m->fused_condense = fused_condense != 0;
     drop_graph(*m);
     if (m->mx.gcon.p) ensure_state(*m, CC_PREC_MIXED);  // allocates the per-tet store if the gather path is back
   })

@@ -140,7 +140,7 @@ struct Mesh {
   int tune_couple_threads = 64;   // threads per vertex in the coupling kernel (32: one warp)
   int tune_couple_row_lanes = 4;  // threads per block row in the coupling kernel (1, 2, 4, 8)
   int tune_gather_wpb = 4;        // warps (rows) per block in the row gather
-  bool couple_staged = false;     // coupling kernel copies its blocks to shared memory first (cp.async)
+  bool fused_condense = false;    // the coupling kernel's last CTA of every 32 vertices condenses them
   bool rows_build = false;        // mixed stable Neo-Hookean rows formed from the positions (k_row_build)
   int64_t n = 0, T = 0, n_free = 0, nnzb = 0;
   int32_t max_valence = 0;
@@ -241,6 +241,7 @@ struct Mesh {
   DBuf<double> d_red;        // reduction partials
   DBuf<double> d_scalars;    // [8]
   DBuf<unsigned long long> d_counters; // [4] fallback counters + [4] error flags
+  DBuf<int32_t> d_grp_cnt;   // arrivals per 32-vertex group of the fused coupling + condensation (self-resetting)
   DBuf<double> d_xtilde;     // [3][n] dynamic target (solve_step)
   DBuf<double> d_xold;       // [3][n]
   DBuf<double> d_xls0;       // [3][n] line search: x before the sweep
@@ -274,6 +275,12 @@ bool pdl_enabled();  // true when CC_GB300_PDL is set in the environment (defaul
 // rows from the positions (k_row_build) instead of a per-tet Hessian store;
 // the float64 path and Fixed Corotational keep the store (FCR's blocks need
 // the polar rotation, too costly to form four times per tet).
+// The coupling kernel condenses its vertices itself (one launch per colour
+// for the local solves) unless switched off or with the one-warp coupling kernel.
+inline bool fused_local_solve(const Mesh& m, cc_update upd) {
+  return upd != CC_UPDATE_CD && m.fused_condense && m.tune_couple_threads != 32;
+}
+
 inline bool rows_from_positions(const Mesh& m) {
   return m.rows_build && m.model == CC_MODEL_SNH && m.max_valence <= 64;
 }

@@ -312,6 +312,7 @@ void build_slot_maps(Mesh& m) {
   for (int64_t v = 0; v < n; ++v) ptr[v + 1] = ptr[v] + len[v];
   m.smap_max = *std::max_element(longest_t.begin(), longest_t.end());
   m.d_smap_ptr.upload(ptr, s);
+
   const int64_t total = std::max<int64_t>(ptr[n], 1);
   const unsigned grid = (unsigned)((m.n_free * 32 + 255) / 256);
   if (m.smap_wide) {

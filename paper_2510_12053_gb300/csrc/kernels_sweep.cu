@@ -61,21 +61,10 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
 
 
 template <typename HT>
-__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps,
-                                                 bool staged = false) {
-  size_t b = align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
-             align16((size_t)smap_max * code_bytes) + align16((size_t)nwarps * 32 * sizeof(HT));
-  if (staged) b += align16((size_t)(sup_max + 1) * 3 * sizeof(HT)) + (size_t)smap_max * 12 * sizeof(HT);
-  return b;
+__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps) {
+  return align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
+         align16((size_t)smap_max * code_bytes) + (size_t)nwarps * 32 * sizeof(HT);
 }
-
-// 16-byte global -> shared copy that bypasses the registers (cp.async, L2
-// only) and the wait for all of the thread's outstanding copies.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename SlotT>
 struct SlotCodes;
@@ -148,6 +137,198 @@ __device__ __forceinline__ void load_slot<double>(const double* p, double* u) {
   }
 }
 
+// What the condensation of a colour's vertices reads and writes.
+template <typename HT>
+struct CondenseArgs {
+  const int32_t* verts;
+  int64_t count;
+  const HT* cpl;  // [count][32]: Ht (6), A (9), b (3), H_ii (9) per vertex
+  const int32_t* sup_ptr;
+  const int32_t* up_ptr;
+  const HT* bsr;
+  const double* g64;
+  const float* g_hi;
+  const float* g_lo;
+  int64_t n;
+  double* x;
+  float4* x_hi;
+  float4* x_lo;
+  const int32_t* vert_mesh;
+  const int32_t* active;
+  unsigned long long* fallback;
+  unsigned long long* err;
+  int32_t* grp_cnt;  // arrivals per group of 32 list entries (fused kernel only)
+};
+
+// Condensation (Eq. 9-12) of list entry k.  3x3 inverses use the adjugate;
+// the SPD guard is the Cholesky pivot test written with leading minors.  `AR`
+// is the arithmetic type (double on both paths).  cpl is read through L2
+// (__ldcg): in the fused kernel other CTAs wrote it during this launch.
+template <typename AR, typename HT, bool kMixed, int kUpd>
+__device__ __forceinline__ void condense_vertex(const CondenseArgs<HT>& c, int64_t k, AR rel) {
+  using Ar = Arith<AR>;
+  using V = typename Ar::V;
+  const int i = c.verts[k];
+  if (c.active[c.vert_mesh[i]] == 0) return;  // this mesh of the batch has stopped
+  auto ld = [](HT v) -> V {
+    if constexpr (sizeof(HT) == 4) return Ar::mkf((float)v);
+    else return Ar::mk((double)v);
+  };
+  const HT* cp = c.cpl + k * 32;
+  V H[9], gi[3];
+  if (kUpd == CC_UPDATE_CD) {
+    HT Hb[9];
+    load_block(c.bsr, c.up_ptr[i], Hb);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) H[q] = ld(Hb[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) H[q] = ld(__ldcg(cp + 18 + q));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if constexpr (!kMixed) gi[a] = Ar::mk(c.g64[3 * (int64_t)i + a]);
+    else if constexpr (sizeof(V) == sizeof(double))
+      gi[a] = (double)c.g_hi[3 * (int64_t)i + a] + (double)c.g_lo[3 * (int64_t)i + a];
+    else gi[a] = V{c.g_hi[3 * (int64_t)i + a], c.g_lo[3 * (int64_t)i + a]};
+  }
+  V M[9], rhs[3];
+  int fb = -1;
+  bool done = false;
+  if (kUpd != CC_UPDATE_CD) {
+    const int m = c.sup_ptr[i + 1] - c.sup_ptr[i];
+    if (m == 0) {
+      fb = 0;
+    } else {
+      const V t0 = ld(__ldcg(cp + 0)), t1 = ld(__ldcg(cp + 1)), t2 = ld(__ldcg(cp + 2));
+      const V t3 = ld(__ldcg(cp + 3)), t4 = ld(__ldcg(cp + 4)), t5 = ld(__ldcg(cp + 5));
+      const V Ht[9] = {t0, t1, t2, t1, t3, t4, t2, t4, t5};
+      V b[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) b[q] = ld(__ldcg(cp + 15 + q));
+      if (kUpd == CC_UPDATE_JGS2) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) M[q] = Ar::add(H[q], Ht[q]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) rhs[q] = Ar::add(gi[q], b[q]);
+        done = true;
+      } else {
+        V adj[6], det;
+        if (sym3_adj<AR>(Ht, rel, adj, &det)) {
+          V A[9];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) A[q] = ld(__ldcg(cp + 6 + q));
+          const V inv = Ar::div(Ar::mkf(1.0f), det);
+          V Hi[9] = {adj[0], adj[1], adj[2], adj[1], adj[3], adj[4], adj[2], adj[4], adj[5]};
+#pragma unroll
+          for (int q = 0; q < 9; ++q) Hi[q] = Ar::mul(Hi[q], inv);
+          // W = A Ht^{-1};  S = W A^T;  gt = g_i - W b
+          V W[9];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              W[3 * r + q] = Ar::fma(A[3 * r + 2], Hi[6 + q], Ar::fma(A[3 * r + 1], Hi[3 + q], Ar::mul(A[3 * r], Hi[q])));
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const V Src = Ar::fma(W[3 * r + 2], A[3 * q + 2], Ar::fma(W[3 * r + 1], A[3 * q + 1], Ar::mul(W[3 * r], A[3 * q])));
+              M[3 * r + q] = Ar::sub(H[3 * r + q], Src);
+            }
+            rhs[r] = Ar::sub(gi[r], Ar::fma(W[3 * r + 2], b[2], Ar::fma(W[3 * r + 1], b[1], Ar::mul(W[3 * r], b[0]))));
+          }
+          done = true;
+        } else {
+          fb = 1;
+        }
+      }
+    }
+  }
+  V dx[3];
+  bool ok = false;
+  if (done) {
+    V adj[6], det;
+    if (sym3_adj<AR>(M, rel, adj, &det)) {
+      const V inv = Ar::neg(Ar::div(Ar::mkf(1.0f), det));
+      dx[0] = Ar::mul(inv, Ar::fma(adj[0], rhs[0], Ar::fma(adj[1], rhs[1], Ar::mul(adj[2], rhs[2]))));
+      dx[1] = Ar::mul(inv, Ar::fma(adj[1], rhs[0], Ar::fma(adj[3], rhs[1], Ar::mul(adj[4], rhs[2]))));
+      dx[2] = Ar::mul(inv, Ar::fma(adj[2], rhs[0], Ar::fma(adj[4], rhs[1], Ar::mul(adj[5], rhs[2]))));
+      ok = true;
+    } else {
+      fb = kUpd == CC_UPDATE_JGS2 ? 1 : 2;
+    }
+  }
+  if (!ok) {
+    // coordinate descent step: one Newton step on vertex i
+    V adj[6], det;
+    if (sym3_adj<AR>(H, Ar::mkf(0.0f), adj, &det)) {
+      const V inv = Ar::neg(Ar::div(Ar::mkf(1.0f), det));
+      dx[0] = Ar::mul(inv, Ar::fma(adj[0], gi[0], Ar::fma(adj[1], gi[1], Ar::mul(adj[2], gi[2]))));
+      dx[1] = Ar::mul(inv, Ar::fma(adj[1], gi[0], Ar::fma(adj[3], gi[1], Ar::mul(adj[4], gi[2]))));
+      dx[2] = Ar::mul(inv, Ar::fma(adj[2], gi[0], Ar::fma(adj[4], gi[1], Ar::mul(adj[5], gi[2]))));
+    } else {
+      atomicOr(c.err, 1ull);
+      return;
+    }
+  }
+  if (fb >= 0) atomicAdd(&c.fallback[fb], 1ull);
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = Ar::to_double(dx[a]);
+  if (!(isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]))) {
+    atomicOr(c.err, 1ull);
+    return;
+  }
+  double xn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xn[a] = c.x[a * c.n + i] + d[a];
+    c.x[a * c.n + i] = xn[a];
+  }
+  if (kMixed) {
+    df a0 = df_from_double(xn[0]), a1 = df_from_double(xn[1]), a2 = df_from_double(xn[2]);
+    c.x_hi[i] = make_float4(a0.hi, a1.hi, a2.hi, 0.f);
+    c.x_lo[i] = make_float4(a0.lo, a1.lo, a2.lo, 0.f);
+  }
+}
+
+// Batched condensation, one list entry per thread: a warp condenses 32
+// vertices at once, so the float64 3x3 algebra runs at full SIMD width
+// instead of on one lane per vertex.
+template <typename AR, typename HT, bool kMixed, int kUpd>
+__global__ void k_condense(CondenseArgs<HT> c, AR rel) {
+  pdl_entry();
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= c.count) return;
+  condense_vertex<AR, HT, kMixed, kUpd>(c, k, rel);
+}
+
+// Tail of the fused coupling kernel: after its CTA has written the products
+// of list entry blockIdx.x, the last CTA to finish in each group of 32
+// entries condenses the whole group, one vertex per lane of its first warp
+// (the float64 condensation at full warp width, no separate launch).  Every
+// thread that wrote cpl fences before the CTA's arrival is counted; the
+// counter is reset by the group's last CTA for the next launch.  Which CTA
+// condenses does not change any result.
+template <typename AR, typename HT, bool kMixed, int kUpd>
+__device__ __forceinline__ void condense_group_tail(const CondenseArgs<HT>& c, AR rel) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  const int64_t grp = blockIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    const int need = (int)min((int64_t)32, c.count - grp * 32);
+    last = atomicAdd(c.grp_cnt + grp, 1) == need - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
+  if (threadIdx.x == 0) c.grp_cnt[grp] = 0;
+  const int64_t k = grp * 32 + threadIdx.x;
+  if (k < c.count) condense_vertex<AR, HT, kMixed, kUpd>(c, k, rel);
+}
+
 // Coupling products, one CTA per free vertex i of the list.  Groups of
 // 2^row_lanes_log2 threads take the block rows of the support S and of i
 // itself; a group's threads take the row's upper blocks (H_jl, l >= j)
@@ -159,17 +340,14 @@ __device__ __forceinline__ void load_slot<double>(const double* p, double* u) {
 // term H_ij U_j = H_ji^T U_j; row i gives H_ii and the terms H_il U_l with
 // l > i.  The CTA writes 27 values per vertex: Ht (6, symmetric), A (9),
 // b (3), H_ii (9, stored directly by the thread that reads it).
-// kStaged: before any arithmetic every thread issues cp.async copies of all
-// the blocks it will use (and the support's gradients are staged with the
-// basis), so a thread waits for the L2 once instead of once per block; the
-// blocks sit in shared memory at their position in the slot map.
-template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads, bool kStaged = false>
+// kFuse: the CTA then takes part in the group condensation (condense_group_tail).
+template <typename HT, typename SlotT, bool kMixed, int kUpd, int kThreads, bool kFuse = false>
 __global__ void __launch_bounds__(kThreads) k_couple(
     const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
     const int32_t* __restrict__ sup_idx, const HT* __restrict__ U, const int32_t* __restrict__ up_ptr,
     const int64_t* __restrict__ smap_ptr, const SlotT* __restrict__ smap, const HT* __restrict__ bsr,
     const double* __restrict__ g64, const float* __restrict__ g_hi, int sup_max, int64_t smap_max,
-    const HT* __restrict__ rot, int row_lanes_log2, HT* __restrict__ cpl) {
+    const HT* __restrict__ rot, int row_lanes_log2, HT* __restrict__ cpl, CondenseArgs<HT> ca) {
   pdl_entry();
   using Codes = SlotCodes<SlotT>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -187,10 +365,6 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   SlotT* codes = reinterpret_cast<SlotT*>(ptr);
   ptr += align16((size_t)smap_max * sizeof(SlotT));
   HT* red = reinterpret_cast<HT*>(ptr);  // [warps][32]
-  ptr += align16((size_t)(kThreads / 32) * 32 * sizeof(HT));
-  HT* gsm = reinterpret_cast<HT*>(ptr);  // [m + 1][3] gradients of the rows (kStaged)
-  ptr += kStaged ? align16((size_t)(sup_max + 1) * 3 * sizeof(HT)) : 0;
-  HT* blk = reinterpret_cast<HT*>(ptr);  // [ncodes][12] staged blocks (kStaged)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = verts[blockIdx.x];
@@ -207,9 +381,6 @@ __global__ void __launch_bounds__(kThreads) k_couple(
     rstart[s] = a;
     rlen[s] = up_ptr[j + 1] - a;
     rid[s] = j;
-    if (kStaged && s < m)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) gsm[3 * s + c] = kMixed ? (HT)g_hi[3 * (int64_t)j + c] : (HT)g64[3 * (int64_t)j + c];
   }
   __syncthreads();
   // exclusive prefix of the row lengths (offsets into the slot map), warp 0
@@ -230,25 +401,10 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   }
   __syncthreads();
 
-  const int nl = 1 << row_lanes_log2, rl = tid & (nl - 1);
-  if (kStaged) {
-    // every block this thread reads below, copied ahead (same row/block walk)
-    constexpr int kChunks = 12 * sizeof(HT) / 16;
-    for (int r = tid >> row_lanes_log2; r <= m; r += kThreads >> row_lanes_log2) {
-      const int P = rstart[r], L = rlen[r], off = roff[r];
-      for (int q = rl; q < L; q += nl) {
-        if (codes[off + q] == Codes::kNone) continue;
-        const HT* src = bsr + (int64_t)(P + q) * 12;
-        HT* dst = blk + (size_t)(off + q) * 12;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c) cp_async16(dst + c * (16 / sizeof(HT)), src + c * (16 / sizeof(HT)));
-      }
-    }
-    cp_async_wait_all();
-  }
   HT h00 = 0, h01 = 0, h02 = 0, h11 = 0, h12 = 0, h22 = 0;
   HT A[9], b[3] = {0, 0, 0};
   mat3_zero(A);
+  const int nl = 1 << row_lanes_log2, rl = tid & (nl - 1);
   for (int r = tid >> row_lanes_log2; r <= m; r += kThreads >> row_lanes_log2) {
     const int P = rstart[r], L = rlen[r], off = roff[r];
     if (r < m) {
@@ -260,8 +416,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
         const unsigned code = codes[off + q];
         if (code == Codes::kNone) continue;
         HT H[9];
-        if (kStaged) load_slot(blk + (size_t)(off + q) * 12, H);
-        else load_block(bsr, (int64_t)P + q, H);
+        load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kSelf) {
           if (kUpd == CC_UPDATE_CC) mat3_tmul_acc(H, Uj, A);
         } else if (code == Codes::kDiag) {
@@ -287,8 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
         const int j = rid[r];
         HT gj[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          gj[a] = kStaged ? gsm[3 * r + a] : kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
+        for (int a = 0; a < 3; ++a) gj[a] = kMixed ? (HT)g_hi[3 * (int64_t)j + a] : (HT)g64[3 * (int64_t)j + a];
 #pragma unroll
         for (int c = 0; c < 3; ++c) b[c] += Uj[c] * gj[0] + Uj[3 + c] * gj[1] + Uj[6 + c] * gj[2];
       }
@@ -297,8 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
         const unsigned code = codes[off + q];
         if (code == Codes::kNone) continue;
         HT H[9];
-        if (kStaged) load_slot(blk + (size_t)(off + q) * 12, H);
-        else load_block(bsr, (int64_t)P + q, H);
+        load_block(bsr, (int64_t)P + q, H);
         if (code == Codes::kDiag) {
 #pragma unroll
           for (int c = 0; c < 9; ++c) cpl[(int64_t)blockIdx.x * 32 + 18 + c] = H[c];
@@ -320,12 +473,14 @@ __global__ void __launch_bounds__(kThreads) k_couple(
 #pragma unroll
     for (int v = 0; v < 18; ++v) red[warp * 32 + v] = vals[v];
   __syncthreads();
-  if (tid >= 18) return;
-  // fixed-order sum of the warps' partials
-  HT tot = red[tid];
+  if (tid < 18) {
+    // fixed-order sum of the warps' partials
+    HT tot = red[tid];
 #pragma unroll
-  for (int w = 1; w < kThreads / 32; ++w) tot += red[32 * w + tid];
-  cpl[(int64_t)blockIdx.x * 32 + tid] = tot;
+    for (int w = 1; w < kThreads / 32; ++w) tot += red[32 * w + tid];
+    cpl[(int64_t)blockIdx.x * 32 + tid] = tot;
+  }
+  if constexpr (kFuse) condense_group_tail<double, HT, kMixed, kUpd>(ca, 1e-12);
 }
 
 // The same coupling products with one warp per vertex (kWarps vertices per
@@ -462,189 +617,29 @@ __host__ __device__ inline size_t warp_smem_bytes(int sup_max, int warps) {
   return (size_t)warps * (align16((size_t)sup_max * 9 * sizeof(HT)) + 2 * align16((size_t)(sup_max + 2) * 4));
 }
 
-// Batched condensation (Eq. 9-12), one free vertex per thread: a warp
-// condenses 32 vertices at once, so the float64 3x3 algebra runs at full
-// SIMD width instead of on one lane per vertex.  3x3 inverses use the
-// adjugate; the SPD guard is the Cholesky pivot test written with leading
-// minors.  `AR` is the arithmetic type (double on both paths).
-template <typename AR, typename HT, bool kMixed, int kUpd>
-__global__ void k_condense(const int32_t* __restrict__ verts, int64_t count, const HT* __restrict__ cpl,
-                           const int32_t* __restrict__ sup_ptr, const int32_t* __restrict__ up_ptr,
-                           const HT* __restrict__ bsr, const double* __restrict__ g64,
-                           const float* __restrict__ g_hi, const float* __restrict__ g_lo, int64_t n,
-                           double* __restrict__ x, float4* __restrict__ x_hi, float4* __restrict__ x_lo,
-                           AR rel, const int32_t* __restrict__ vert_mesh, const int32_t* __restrict__ active,
-                           unsigned long long* __restrict__ fallback, unsigned long long* __restrict__ err) {
-  pdl_entry();
-  using Ar = Arith<AR>;
-  using V = typename Ar::V;
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= count) return;
-  const int i = verts[k];
-  if (active[vert_mesh[i]] == 0) return;  // this mesh of the batch has stopped
-  auto ld = [](HT v) -> V {
-    if constexpr (sizeof(HT) == 4) return Ar::mkf((float)v);
-    else return Ar::mk((double)v);
-  };
-  V H[9], gi[3];
-  if (kUpd == CC_UPDATE_CD) {
-    HT Hb[9];
-    load_block(bsr, up_ptr[i], Hb);
-#pragma unroll
-    for (int c = 0; c < 9; ++c) H[c] = ld(Hb[c]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 9; ++c) H[c] = ld(cpl[k * 32 + 18 + c]);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if constexpr (!kMixed) gi[a] = Ar::mk(g64[3 * (int64_t)i + a]);
-    else if constexpr (sizeof(V) == sizeof(double)) gi[a] = (double)g_hi[3 * (int64_t)i + a] + (double)g_lo[3 * (int64_t)i + a];
-    else gi[a] = V{g_hi[3 * (int64_t)i + a], g_lo[3 * (int64_t)i + a]};
-  }
-  V M[9], rhs[3];
-  int fb = -1;
-  bool done = false;
-  if (kUpd != CC_UPDATE_CD) {
-    const int m = sup_ptr[i + 1] - sup_ptr[i];
-    if (m == 0) {
-      fb = 0;
-    } else {
-      const V t0 = ld(cpl[k * 32 + 0]), t1 = ld(cpl[k * 32 + 1]), t2 = ld(cpl[k * 32 + 2]);
-      const V t3 = ld(cpl[k * 32 + 3]), t4 = ld(cpl[k * 32 + 4]), t5 = ld(cpl[k * 32 + 5]);
-      const V Ht[9] = {t0, t1, t2, t1, t3, t4, t2, t4, t5};
-      V b[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) b[c] = ld(cpl[k * 32 + 15 + c]);
-      if (kUpd == CC_UPDATE_JGS2) {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) M[c] = Ar::add(H[c], Ht[c]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) rhs[c] = Ar::add(gi[c], b[c]);
-        done = true;
-      } else {
-        V adj[6], det;
-        if (sym3_adj<AR>(Ht, rel, adj, &det)) {
-          V A[9];
-#pragma unroll
-          for (int c = 0; c < 9; ++c) A[c] = ld(cpl[k * 32 + 6 + c]);
-          const V inv = Ar::div(Ar::mkf(1.0f), det);
-          V Hi[9] = {adj[0], adj[1], adj[2], adj[1], adj[3], adj[4], adj[2], adj[4], adj[5]};
-#pragma unroll
-          for (int c = 0; c < 9; ++c) Hi[c] = Ar::mul(Hi[c], inv);
-          // W = A Ht^{-1};  S = W A^T;  gt = g_i - W b
-          V W[9];
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              W[3 * r + c] = Ar::fma(A[3 * r + 2], Hi[6 + c], Ar::fma(A[3 * r + 1], Hi[3 + c], Ar::mul(A[3 * r], Hi[c])));
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const V Src = Ar::fma(W[3 * r + 2], A[3 * c + 2], Ar::fma(W[3 * r + 1], A[3 * c + 1], Ar::mul(W[3 * r], A[3 * c])));
-              M[3 * r + c] = Ar::sub(H[3 * r + c], Src);
-            }
-            rhs[r] = Ar::sub(gi[r], Ar::fma(W[3 * r + 2], b[2], Ar::fma(W[3 * r + 1], b[1], Ar::mul(W[3 * r], b[0]))));
-          }
-          done = true;
-        } else {
-          fb = 1;
-        }
-      }
-    }
-  }
-  V dx[3];
-  bool ok = false;
-  if (done) {
-    V adj[6], det;
-    if (sym3_adj<AR>(M, rel, adj, &det)) {
-      const V inv = Ar::neg(Ar::div(Ar::mkf(1.0f), det));
-      dx[0] = Ar::mul(inv, Ar::fma(adj[0], rhs[0], Ar::fma(adj[1], rhs[1], Ar::mul(adj[2], rhs[2]))));
-      dx[1] = Ar::mul(inv, Ar::fma(adj[1], rhs[0], Ar::fma(adj[3], rhs[1], Ar::mul(adj[4], rhs[2]))));
-      dx[2] = Ar::mul(inv, Ar::fma(adj[2], rhs[0], Ar::fma(adj[4], rhs[1], Ar::mul(adj[5], rhs[2]))));
-      ok = true;
-    } else {
-      fb = kUpd == CC_UPDATE_JGS2 ? 1 : 2;
-    }
-  }
-  if (!ok) {
-    // coordinate descent step: one Newton step on vertex i
-    V adj[6], det;
-    if (sym3_adj<AR>(H, Ar::mkf(0.0f), adj, &det)) {
-      const V inv = Ar::neg(Ar::div(Ar::mkf(1.0f), det));
-      dx[0] = Ar::mul(inv, Ar::fma(adj[0], gi[0], Ar::fma(adj[1], gi[1], Ar::mul(adj[2], gi[2]))));
-      dx[1] = Ar::mul(inv, Ar::fma(adj[1], gi[0], Ar::fma(adj[3], gi[1], Ar::mul(adj[4], gi[2]))));
-      dx[2] = Ar::mul(inv, Ar::fma(adj[2], gi[0], Ar::fma(adj[4], gi[1], Ar::mul(adj[5], gi[2]))));
-    } else {
-      atomicOr(err, 1ull);
-      return;
-    }
-  }
-  if (fb >= 0) atomicAdd(&fallback[fb], 1ull);
-  double d[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) d[a] = Ar::to_double(dx[a]);
-  if (!(isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]))) {
-    atomicOr(err, 1ull);
-    return;
-  }
-  double xn[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    xn[a] = x[a * n + i] + d[a];
-    x[a * n + i] = xn[a];
-  }
-  if (kMixed) {
-    df a0 = df_from_double(xn[0]), a1 = df_from_double(xn[1]), a2 = df_from_double(xn[2]);
-    x_hi[i] = make_float4(a0.hi, a1.hi, a2.hi, 0.f);
-    x_lo[i] = make_float4(a0.lo, a1.lo, a2.lo, 0.f);
-  }
-}
-
 template <typename HT, bool kMixed, int kUpd, int kThreads>
 void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
-                   const float* g_hi, HT* cpl, const HT* rot, cudaStream_t s) {
+                   const float* g_hi, HT* cpl, const HT* rot, const CondenseArgs<HT>& ca, bool fuse,
+                   cudaStream_t s) {
   const int supm = m.sup_max > 0 ? m.sup_max : 1;
   const int64_t smx = m.smap_max > 0 ? m.smap_max : 1;
   const int lanes = m.tune_couple_row_lanes;
   CCG_CHECK(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8, CC_ERR_STATE, "bad coupling row lanes");
   const int lanes_log2 = lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : 3;
-  // blocks staged by cp.async where they fit next to the basis (float32 rows
-  // of the usual 2-ring supports: about 30 KB per vertex)
-  const size_t smem_st = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32, true);
-  if (m.couple_staged && smem_st <= 64 * 1024) {
-    if (m.smap_wide) {
-      auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads, true>;
-      set_smem_limit(reinterpret_cast<const void*>(kern), smem_st);
-      pdl_launch(kern, (unsigned)count, kThreads, smem_st, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
-                 (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-                 (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
-    } else {
-      auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads, true>;
-      set_smem_limit(reinterpret_cast<const void*>(kern), smem_st);
-      pdl_launch(kern, (unsigned)count, kThreads, smem_st, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
-                 (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-                 (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
-    }
-    CCG_CUDA(cudaGetLastError());
-    return;
-  }
   const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
   CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
+  auto go = [&](auto kern, const auto* smap) {
+    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
+    pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
+               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
+               smap, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl, ca);
+  };
   if (m.smap_wide) {
-    auto kern = k_couple<HT, uint16_t, kMixed, kUpd, kThreads>;
-    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-    pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
-               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint16_t*)m.d_smap16.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
+    if (fuse) go(k_couple<HT, uint16_t, kMixed, kUpd, kThreads, true>, (const uint16_t*)m.d_smap16.p);
+    else go(k_couple<HT, uint16_t, kMixed, kUpd, kThreads, false>, (const uint16_t*)m.d_smap16.p);
   } else {
-    auto kern = k_couple<HT, uint8_t, kMixed, kUpd, kThreads>;
-    set_smem_limit(reinterpret_cast<const void*>(kern), smem);
-    pdl_launch(kern, (unsigned)count, kThreads, smem, s, verts, count, (const int32_t*)m.d_sup_ptr.p,
-               (const int32_t*)m.d_sup_idx.p, U, (const int32_t*)m.d_up_ptr.p, (const int64_t*)m.d_smap_ptr.p,
-               (const uint8_t*)m.d_smap8.p, bsr, g64, g_hi, supm, smx, rot, lanes_log2, cpl);
+    if (fuse) go(k_couple<HT, uint8_t, kMixed, kUpd, kThreads, true>, (const uint8_t*)m.d_smap8.p);
+    else go(k_couple<HT, uint8_t, kMixed, kUpd, kThreads, false>, (const uint8_t*)m.d_smap8.p);
   }
   CCG_CUDA(cudaGetLastError());
 }
@@ -676,8 +671,15 @@ void launch_couple_warp(Mesh& m, const int32_t* verts, int64_t count, const HT* 
 template <typename HT, bool kMixed, int kUpd>
 void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const HT* bsr, const double* g64,
                 const float* g_hi, const float* g_lo, HT* cpl, double* x, SweepCounters c, cudaStream_t s) {
-  float4* xh = kMixed ? m.mx.x_hi.p : nullptr;
-  float4* xl = kMixed ? m.mx.x_lo.p : nullptr;
+  const CondenseArgs<HT> ca{verts, count, cpl, (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr,
+                            g64, g_hi, g_lo, m.n, x, kMixed ? m.mx.x_hi.p : nullptr, kMixed ? m.mx.x_lo.p : nullptr,
+                            (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error,
+                            m.d_grp_cnt.p};
+  // the coupling CTAs condense their vertices themselves (last of every 32),
+  // except with the one-warp coupling kernel or when switched off
+  const bool fuse = fused_local_solve(m, (cc_update)kUpd);
+  CCG_CHECK(!fuse || (int64_t)m.d_grp_cnt.count >= (count + 31) / 32, CC_ERR_STATE, "group counters missing");
+  const CondenseArgs<HT>& cf = ca;
   if (kUpd != CC_UPDATE_CD) {
     const HT* rot = nullptr;
     if (m.rot_active) {
@@ -686,26 +688,19 @@ void launch_one(Mesh& m, const int32_t* verts, int64_t count, const HT* U, const
     }
     switch (m.tune_couple_threads) {
       case 32: launch_couple_warp<HT, kMixed, kUpd>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
-      case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
-      case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s); break;
-      default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, s);
+      case 64: launch_couple<HT, kMixed, kUpd, 64>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, cf, fuse, s); break;
+      case 256: launch_couple<HT, kMixed, kUpd, 256>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, cf, fuse, s); break;
+      default: launch_couple<HT, kMixed, kUpd, 128>(m, verts, count, U, bsr, g64, g_hi, cpl, rot, cf, fuse, s);
     }
   }
-  // one vertex per thread in 32-thread blocks: a colour holds a few thousand
-  // vertices, so small blocks spread the long per-vertex chains over every SM
+  if (fuse) return;
+  // float64 condensation of the coupling products (the 3x3 Schur solves of
+  // Eq. 11-12 stay in float64 in both precisions), one vertex per thread in
+  // 32-thread blocks: a colour holds a few thousand vertices, so small blocks
+  // spread the long per-vertex chains over every SM
   constexpr int kCondenseThreads = 32;
   const unsigned grid = (unsigned)((count + kCondenseThreads - 1) / kCondenseThreads);
-  if constexpr (kMixed) {
-    // float64 condensation of the float32 coupling products (the 3x3 Schur
-    // solves of Eq. 11-12 stay in float64 in both precisions)
-    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
-               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
-               1e-12, (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
-  } else {
-    pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, verts, count, (const HT*)cpl,
-               (const int32_t*)m.d_sup_ptr.p, (const int32_t*)m.d_up_ptr.p, bsr, g64, g_hi, g_lo, m.n, x, xh, xl,
-               1e-12, (const int32_t*)m.d_vert_mesh.p, (const int32_t*)m.d_mesh_active.p, c.fallback, c.error);
-  }
+  pdl_launch(k_condense<double, HT, kMixed, kUpd>, grid, kCondenseThreads, 0, s, ca, 1e-12);
   CCG_CUDA(cudaGetLastError());
 }
 
