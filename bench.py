@@ -512,6 +512,46 @@ def run_batch(args, stream, dev):
     ms = ev0.elapsed_time(ev1)
     nfree = np.array([int((sc.pinned == 0).sum()) for sc in scenes])
     applied = int((nfree * res["iterations"]).sum())
+    nus = np.array([sc.material.nu for sc in scenes])
+
+    def buckets(r):
+        out = {}
+        for name, sel in (("nu<0.35", nus < 0.35), ("nu>=0.35", nus >= 0.35)):
+            st = r["status"][sel]
+            out[name] = {"meshes": int(sel.sum()), "converged": int((st == 1).sum()),
+                         "diverged": int((st == -1).sum()), "not_reached": int((st == 0).sum())}
+        return out
+
+    # the same batch with the per-mesh global line search (Sec. 4.4): meshes
+    # that plain CC blows up take damped steps instead of diverging
+    x.copy_(x0)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    res_ls = batch.solve_batch(x, precision="mixed", tol=1e-6, max_iters=args.max_iters // 2, check_every=8,
+                               line_search=True)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_ls = ev0.elapsed_time(ev1)
+    # launch gaps of the graph replay: 16 sweeps timed plain, then the same 16
+    # sweeps with every kernel class timed by events; sum of kernel time vs wall
+    x.copy_(x0)
+    batch.solve_batch(x, precision="mixed", tol=0.0, max_iters=16, check_every=16, use_graph=True)
+    x.copy_(x0)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    batch.solve_batch(x, precision="mixed", tol=0.0, max_iters=16, check_every=16, use_graph=True)
+    ev1.record(stream)
+    ev1.synchronize()
+    wall16 = ev0.elapsed_time(ev1)
+    batch.profile_enable(True)
+    x.copy_(x0)
+    batch.solve_batch(x, precision="mixed", tol=0.0, max_iters=16, check_every=16, use_graph=True)
+    x.copy_(x0)
+    batch.solve_batch(x, precision="mixed", tol=0.0, max_iters=16, check_every=16, use_graph=True)
+    torch.cuda.synchronize()
+    prof = batch.profile_read()
+    batch.profile_enable(False)
+    kern16 = sum(prof[k]["ms"] for k in cc.PROFILE_CLASSES) / 2.0
     # the same meshes solved one after another (first 16, warm, launch by launch)
     loop_ms, loop_upd = 0.0, 0
     for sc in scenes[:16]:
@@ -535,12 +575,20 @@ def run_batch(args, stream, dev):
            "tets": int(sum(sc.T for sc in scenes)), "setup_ms": setup_ms, "autotune": tune,
            "ms_until_all_stopped": ms, "sweeps_launched": int(res["sweeps"]),
            "converged": int((res["status"] == 1).sum()), "diverged": int((res["status"] == -1).sum()),
-           "not_reached": int((res["status"] == 0).sum()),
+           "not_reached": int((res["status"] == 0).sum()), "by_nu": buckets(res),
            "applied_vertex_updates_per_s": applied / (ms / 1e3),
+           "line_search": {"ms_until_all_stopped": ms_ls, "sweeps_launched": int(res_ls["sweeps"]),
+                           "converged": int((res_ls["status"] == 1).sum()),
+                           "diverged": int((res_ls["status"] == -1).sum()),
+                           "not_reached": int((res_ls["status"] == 0).sum()), "by_nu": buckets(res_ls),
+                           "max_sweeps": args.max_iters // 2},
+           "graph_replay_16_sweeps": {"wall_ms": wall16, "sum_of_kernel_ms": kern16,
+                                      "note": "kernel time summed over classes from event-timed replays; "
+                                              "wall minus that sum bounds what a persistent kernel could save"},
            "looped_single_mesh_solves": {"meshes": 16, "ms": loop_ms,
                                          "vertex_updates_per_s": loop_upd / (loop_ms / 1e3)},
            "note": "nu >= 0.35 diverges with 2-ring rest bases; such meshes are frozen when their residual "
-                   "exceeds 1e6 x its start"}
+                   "exceeds 1e6 x its start; with the line search they stall instead (not reached)"}
     batch.close()
     return out
 
@@ -733,6 +781,21 @@ def run_learned(args, stream, dev):
         m.color()
         return m
 
+    free = sc.pinned == 0
+
+    def literal_fallbacks(mesh):
+        """The workload text's fallback rule read literally: after one Jacobi
+        sweep from x0 with the mesh's bases and one coordinate-descent sweep,
+        count the free vertices whose gradient norm after the former exceeds
+        the latter (evaluation only)."""
+        norms = []
+        for upd in ("cc", "cd"):
+            xs = x0.clone()
+            mesh.sweep(xs, update=upd, schedule="jacobi", precision="mixed")
+            _, g, _ = mesh.energy_grad(xs, precision="fp64", want_grad=True)
+            norms.append(torch.linalg.vector_norm(g, dim=0).cpu().numpy()[free])
+        return int((norms[0] > norms[1]).sum())
+
     res = {}
     # computed bases (mixed), warm once then timed
     m = fresh()
@@ -743,7 +806,8 @@ def run_learned(args, stream, dev):
     m.build_subspace(K_RING)
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
-    res["computed_mixed"] = dict(solve(m, "mixed"), acquisition_ms=build_ms)
+    res["computed_mixed"] = dict(solve(m, "mixed"), acquisition_ms=build_ms,
+                                 literal_rule_fallbacks=literal_fallbacks(m))
     res["plain_fp64"] = dict(solve(m, "fp64"), acquisition_ms=build_ms)
     m.close()
     # learned bases (mixed)
@@ -756,7 +820,9 @@ def run_learned(args, stream, dev):
     torch.cuda.synchronize()
     acq_ms = 1e3 * (time.perf_counter() - t0)
     rq = np.quantile(rho.cpu().numpy(), [0.5, 0.9, 0.99, 1.0])
+    lit = literal_fallbacks(m)
     res["learned_mixed"] = dict(solve(m, "mixed"), acquisition_ms=acq_ms,
+                                literal_rule_fallbacks=lit, literal_rule_fallback_frac=lit / max(n_free, 1),
                                 fallback=int(st["n_fallback"]), fallback_frac=st["n_fallback"] / max(st["n_free"], 1),
                                 rho_mean=st["rho_mean"], rho_max_kept=st["rho_max"],
                                 rho_quantiles={"p50": rq[0], "p90": rq[1], "p99": rq[2], "max": rq[3]},

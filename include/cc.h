@@ -359,15 +359,19 @@ typedef struct {
  * residual of each mesh is reduced separately at every check, and a mesh that
  * converged or diverged stops moving (its vertices are skipped by the
  * condensation kernel) while the others continue.  x_dev, v_dev: device
- * [3][n_total] (v_dev NULL for quasistatics).  Returns CC_OK when every mesh
+ * [3][n_total] (v_dev NULL for quasistatics).  opts->line_search: every mesh
+ * takes its own backtracking step on its own energy after each sweep (one
+ * launch per trial for all meshes; a mesh without a decreasing step stays
+ * put).  opts->restart_every: the bases of the whole batch are rebuilt at the
+ * current x every that many sweeps.  Returns CC_OK when every mesh
  * converged, CC_ERR_NOT_CONVERGED otherwise (stats valid). */
 cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_step_opts* opts,
                          cc_batch_stats* stats);
 
 /* Launch-configuration autotuner (no counterpart in the paper).  Times
- * `sweeps` coloured CC sweeps from x_dev for each candidate configuration of
- * the two kernels whose best shape depends on the mesh, one parameter at a
- * time in this order: threads per vertex of the coupling kernel (32 = one
+ * `sweeps` coloured CC sweeps from x_dev for each candidate configuration,
+ * one parameter at a time in this order: the sweep variant
+ * (cc_set_sweep_variant), threads per vertex of the coupling kernel (32 = one
  * warp per vertex, 64, 128, 256), then, unless one warp won, threads per
  * block row of the coupling kernel (1, 2, 4, 8), then block rows per CTA of
  * the row gather (2, 4, 8 warps); it keeps the fastest of each for this
@@ -388,9 +392,6 @@ typedef struct {
                              (1,1), at the default launch shapes; variants a mesh cannot use stay 0 */
 } cc_tune_result;
 
-/* Tunes in this order: the sweep variant, the coupling kernel's threads per
- * vertex, its threads per block row, the gather's warps per block; each
- * choice is timed over `sweeps` sweeps from x (x itself is not modified). */
 cc_status cc_autotune(cc_mesh* mesh, const double* x_dev, const double* xtilde_dev, cc_precision precision,
                       int32_t sweeps, cc_tune_result* out);
 

@@ -281,7 +281,8 @@ class Mesh:
 
     def solve_batch(self, x, v=None, *, update: str = "cc", schedule: str = "colored", precision: str = "mixed",
                     tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0, check_every: int = 1,
-                    use_graph: bool = False, corotated: bool = False) -> dict:
+                    use_graph: bool = False, corotated: bool = False, line_search: bool = False,
+                    restart_every: int = 0) -> dict:
         B = len(self.batch_offsets()) - 1
         it = np.zeros(B, dtype=np.int32)
         status = np.zeros(B, dtype=np.int32)
@@ -292,7 +293,7 @@ class Mesh:
                         g0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         gf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, SweepStats())
         o = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters, check_every,
-                     int(use_graph), None, int(corotated))
+                     int(use_graph), None, int(corotated), int(restart_every), int(line_search))
         rc = lib().cc_solve_batch(self._h, _dev3n(x, self.n, "x"), _dev3n(v, self.n, "v"), ctypes.byref(o),
                                   ctypes.byref(st))
         if rc not in (OK, ERR_NOT_CONVERGED):

@@ -788,8 +788,6 @@ cc_status cc_batch_offsets(const cc_mesh* m, int64_t* offsets, int32_t* count) {
 cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o, cc_batch_stats* st) {
   try {
     ccg::g_last_error.clear();
-    CCG_CHECK(!o || (!o->line_search && o->restart_every <= 0), CC_ERR_INVALID_ARG,
-              "the line search and restarts run in cc_solve_step only");
     CCG_CHECK(m && x && o && st && st->iterations && st->status && st->g0 && st->g_final, CC_ERR_INVALID_ARG,
               "NULL argument");
     CCG_CHECK(o->max_iters >= 0 && o->min_iters >= 0 && o->tol >= 0, CC_ERR_INVALID_ARG, "bad iteration limits");
@@ -848,15 +846,11 @@ cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o
       key = buf;
     }
     int it = 0;
-    while (live > 0 && it < o->max_iters) {
-      CCG_CUDA(cudaMemcpyAsync(m->d_mesh_active.p, active.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      const int chunk = std::min(every, o->max_iters - it);
-      const bool replay = graph && chunk == every && it > 0;
-      run_chunk(*m, x, xt, so, cb, ce, chunk, replay, key, true);
-      it += chunk;
+    // per-mesh bookkeeping after every residual check: converged, diverged
+    // (non-finite or above 1e6 x its start) or still running
+    auto check_meshes = [&]() {
       CCG_CUDA(cudaMemcpyAsync(gsq.data(), m->d_mesh_gsq.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
       CCG_CUDA(cudaStreamSynchronize(s));
-      if (replay) prof_after_replay(*m);
       for (int32_t b = 0; b < B; ++b) {
         if (!active[b]) continue;
         const double g = std::sqrt(gsq[b]);
@@ -871,6 +865,84 @@ cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o
         }
         active[b] = 0;
         --live;
+      }
+    };
+    const int restart = std::max(0, o->restart_every);
+    auto maybe_restart = [&]() {
+      if (restart > 0 && it > 0 && it % restart == 0) {
+        // restarted CC on the whole union: bases from the Hessian at the current x
+        ensure_state(*m, CC_PREC_FP64);
+        rebuild_bases_at(*m, x);
+        refresh_all(*m, o->precision, x, xt);
+      }
+    };
+    auto upload_active = [&]() {
+      CCG_CUDA(cudaMemcpyAsync(m->d_mesh_active.p, active.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    };
+    while (!o->line_search && live > 0 && it < o->max_iters) {
+      maybe_restart();
+      upload_active();
+      int chunk = std::min(every, o->max_iters - it);
+      if (restart > 0) chunk = std::min(chunk, restart - it % restart);
+      const bool replay = graph && chunk == every && it > 0;
+      run_chunk(*m, x, xt, so, cb, ce, chunk, replay, key, true);
+      it += chunk;
+      if (replay) prof_after_replay(*m);
+      check_meshes();
+    }
+    // Global backtracking line search per mesh (Sec. 4.4): each mesh takes
+    // the largest 2^-k (k < 30) of its own sweep displacement that does not
+    // raise its own energy, 0 if none; every trial is one launch for all.
+    if (o->line_search && live > 0 && it < o->max_iters) {
+      if (!m->d_xls0.p) {
+        m->d_xls0.alloc(3 * n);
+        m->d_xls1.alloc(3 * n);
+      }
+      std::vector<double> E0(B), E1(B), alpha(B);
+      std::vector<char> searching(B);
+      auto energies = [&](const double* xe, std::vector<double>& out) {
+        launch_energy_mesh(*m, xe, xt, m->d_mesh_energy.p, s);
+        CCG_CUDA(cudaMemcpyAsync(out.data(), m->d_mesh_energy.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CCG_CUDA(cudaStreamSynchronize(s));
+      };
+      auto set_alpha = [&]() {
+        CCG_CUDA(cudaMemcpyAsync(m->d_mesh_alpha.p, alpha.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_line_point_mesh(*m, m->d_xls0.p, m->d_xls1.p, m->d_mesh_alpha.p, x, s);
+      };
+      while (live > 0 && it < o->max_iters) {
+        maybe_restart();
+        upload_active();
+        CCG_CUDA(cudaMemcpyAsync(m->d_xls0.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        energies(x, E0);
+        sweep_body(*m, x, xt, so, cb, ce, true);  // g, H are current at x (refreshed below); stopped meshes stay
+        CCG_CUDA(cudaMemcpyAsync(m->d_xls1.p, x, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int32_t b = 0; b < B; ++b) {
+          alpha[b] = active[b] ? 1.0 : 0.0;
+          searching[b] = active[b] ? 1 : 0;
+        }
+        for (int k = 0; k < 30; ++k) {
+          if (k > 0) set_alpha();
+          energies(x, E1);
+          bool any = false;
+          for (int32_t b = 0; b < B; ++b) {
+            if (!searching[b]) continue;
+            if (E1[b] <= E0[b]) {
+              searching[b] = 0;
+            } else {
+              alpha[b] *= 0.5;
+              any = true;
+            }
+          }
+          if (!any) break;
+        }
+        for (int32_t b = 0; b < B; ++b)
+          if (searching[b]) alpha[b] = 0.0;  // no decrease found: the mesh stays at x
+        set_alpha();
+        if (o->precision == CC_PREC_MIXED) split(*m, x, m->mx.x_hi.p, m->mx.x_lo.p);
+        refresh_all(*m, o->precision, x, xt);
+        launch_gnorm_mesh(*m, o->precision == CC_PREC_MIXED, s);
+        ++it;
+        check_meshes();
       }
     }
     activate_all(*m);

@@ -175,6 +175,9 @@ struct Mesh {
   DBuf<int32_t> d_mesh_active;                   // [B] 1 while the mesh is still being solved
   DBuf<int32_t> d_mesh_ones;                     // [B] all ones (resets d_mesh_active)
   DBuf<double> d_mesh_gsq;                       // [B] squared free gradient norm per mesh
+  DBuf<int64_t> d_mesh_vptr, d_mesh_tptr;        // [B+1] vertex and tet ranges (per-mesh energy)
+  DBuf<double> d_mesh_energy;                    // [B] per-mesh energy (batched line search)
+  DBuf<double> d_mesh_alpha;                     // [B] per-mesh line search step
   std::vector<int32_t> color;
   int32_t num_colors = 0;
   std::vector<int64_t> sup_ptr;
@@ -339,6 +342,10 @@ void launch_energy(Mesh& m, const double* x, const double* xt, double* out_scala
 void launch_gnorm_f64(Mesh& m, double* grad_out, double* out_scalar, cudaStream_t s);
 void launch_gnorm_mixed(Mesh& m, double* grad_out, double* out_scalar, cudaStream_t s);
 void launch_gnorm_mesh(Mesh& m, bool mixed, cudaStream_t s);  // per-mesh squared norms -> d_mesh_gsq
+// per-mesh energies of a batch -> out[B]; per-mesh line points x = x0 + alpha_b (x1 - x0)
+void launch_energy_mesh(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s);
+void launch_line_point_mesh(Mesh& m, const double* x0, const double* x1, const double* alpha, double* x,
+                            cudaStream_t s);
 // mirrors and small vector ops
 void launch_split_df(const double* x, int64_t n, float4* hi, float4* lo, cudaStream_t s);
 void launch_inertial_target(const double* x, const double* v, int64_t n, double h,

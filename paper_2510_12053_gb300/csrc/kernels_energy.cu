@@ -687,6 +687,69 @@ __global__ void k_energy_tets(const int4* __restrict__ tets, const double* __res
   if (threadIdx.x == 0) part[blockIdx.x] = e;
 }
 
+// Energy of every mesh of a batch (Eq. 2 per mesh): one CTA per mesh over its
+// tets [tptr[b], tptr[b+1]) and, when dynamic, its vertices, in a fixed order.
+template <bool kFCR>
+__global__ void k_energy_mesh(const int64_t* __restrict__ tptr, const int64_t* __restrict__ vptr,
+                              const int4* __restrict__ tets, const double* __restrict__ Bm,
+                              const double* __restrict__ vol, const double* __restrict__ x, int64_t n,
+                              const double2* __restrict__ mat, double weight, const double* __restrict__ mass,
+                              const double* __restrict__ xt, double* __restrict__ out) {
+  pdl_entry();
+  const int b = blockIdx.x;
+  double e = 0.0;
+  for (int64_t t = tptr[b] + threadIdx.x; t < tptr[b + 1]; t += blockDim.x) {
+    const int4 tv = tets[t];
+    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+    double p[4][3];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p[v][a] = x[a * n + vid[v]];
+    double B[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) B[q] = Bm[9 * t + q];
+    TetF64 kin;
+    tet_kinematics_f64(p, B, kin);
+    const double Jm1 = kin.J - 1.0;
+    const double mu = mat[t].x, lh = mat[t].y;
+    if (kFCR) {
+      double R[9];
+      double d2 = 0.0;
+      if (polar_newton<double>(kin.F, R)) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d2 += (kin.F[q] - R[q]) * (kin.F[q] - R[q]);
+      } else {
+        d2 = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      e += weight * vol[t] * (mu * d2 + 0.5 * lh * Jm1 * Jm1);
+    } else {
+      double I = 0.0;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) I += kin.F[q] * kin.F[q];
+      e += weight * vol[t] * (0.5 * mu * (I - 3.0) - mu * Jm1 + 0.5 * lh * Jm1 * Jm1);
+    }
+  }
+  if (xt)
+    for (int64_t j = vptr[b] + threadIdx.x; j < vptr[b + 1]; j += blockDim.x) {
+      const double d0 = x[j] - xt[j], d1 = x[n + j] - xt[n + j], d2 = x[2 * n + j] - xt[2 * n + j];
+      e += 0.5 * mass[j] * (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+  e = block_sum(e);
+  if (threadIdx.x == 0) out[b] = e;
+}
+
+// x = x0 + alpha[mesh of the vertex] (x1 - x0), all 3n entries.
+__global__ void k_line_point_mesh(const double* __restrict__ x0, const double* __restrict__ x1, int64_t n,
+                                  const int32_t* __restrict__ vert_mesh, const double* __restrict__ alpha,
+                                  double* __restrict__ x) {
+  pdl_entry();
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= 3 * n) return;
+  const double a = alpha[vert_mesh[k % n]];
+  x[k] = x0[k] + a * (x1[k] - x0[k]);
+}
+
 __global__ void k_energy_inertia(const double* __restrict__ mass, const double* __restrict__ x,
                                  const double* __restrict__ xt, int64_t n, double* __restrict__ part) {
   pdl_entry();
@@ -872,6 +935,21 @@ void launch_energy(Mesh& m, const double* x, const double* xt, double* out, cuda
   } else {
     pdl_launch(k_reduce_final, 1, 1024, 0, s, m.d_red.p, (int64_t)kRedBlocks, out);
   }
+}
+
+void launch_energy_mesh(Mesh& m, const double* x, const double* xt, double* out, cudaStream_t s) {
+  const double w = m.h > 0.0 ? m.h * m.h : 1.0;
+  const unsigned B = (unsigned)(m.mesh_vptr.size() - 1);
+  pdl_launch(m.model == CC_MODEL_FCR ? k_energy_mesh<true> : k_energy_mesh<false>, B, kBlock, 0, s,
+             (const int64_t*)m.d_mesh_tptr.p, (const int64_t*)m.d_mesh_vptr.p, (const int4*)m.d_tets.p,
+             (const double*)m.d_Bm.p, (const double*)m.d_vol.p, x, m.n, (const double2*)m.d_mat64.p, w,
+             (const double*)m.d_mass.p, m.h > 0.0 ? xt : nullptr, out);
+}
+
+void launch_line_point_mesh(Mesh& m, const double* x0, const double* x1, const double* alpha, double* x,
+                            cudaStream_t s) {
+  pdl_launch(k_line_point_mesh, grid_for(3 * m.n), kBlock, 0, s, x0, x1, m.n, (const int32_t*)m.d_vert_mesh.p, alpha,
+             x);
 }
 
 void launch_gnorm_f64(Mesh& m, double* grad_out, double* out, cudaStream_t s) {

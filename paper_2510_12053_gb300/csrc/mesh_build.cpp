@@ -315,6 +315,10 @@ void build_topology(Mesh& m) {
     m.d_mesh_active.upload(ones, s);
     m.d_mesh_ones.upload(ones, s);
     m.d_mesh_gsq.alloc(B);
+    m.d_mesh_vptr.upload(m.mesh_vptr, s);
+    m.d_mesh_tptr.upload(m.mesh_tptr, s);
+    m.d_mesh_energy.alloc(B);
+    m.d_mesh_alpha.alloc(B);
     CCG_CUDA(cudaStreamSynchronize(s));
   }
   {

@@ -368,18 +368,29 @@ def test_line_search_follows_the_oracle_where_plain_cc_blows_up():
     assert blew_up
 
 
-def test_batch_rejects_the_line_search():
-    scenes = [meshgen.stretch_box(3, 3, 3, E=1e5, nu=0.3)] * 2
+def test_batch_line_search_equals_each_mesh_line_search():
+    """Sec. 4.4's line search inside a batch: every mesh backtracks on its own
+    energy, so each follows its own single-mesh line-search solve (here one
+    mesh that plain CC blows up and one that converges)."""
+    scenes = [meshgen.stretch_box(4, 3, 3, E=1e5, nu=0.45, factor=1.5, jitter_amount=0.05, seed=2),
+              meshgen.stretch_box(3, 3, 4, E=2e5, nu=0.3, factor=1.2, seed=3)]
     b = cc.Mesh.from_scenes(scenes)
     b.color()
     b.build_subspace(2)
-    x = cc.to_soa(np.concatenate([sc.x0 for sc in scenes]))
-    with pytest.raises(cc.CCError):
-        lib_opts = dict(precision="mixed", tol=1e-6, max_iters=4)
-        o = cc.StepOpts(cc.UPDATE["cc"], cc.SCHED["colored"], cc.PREC["mixed"], 1e-6, 4, 0, 1, 0, None, 0, 0, 1)
-        st = cc.BatchStats()
-        rc = cc.lib().cc_solve_batch(b._h, x.data_ptr(), None, cc.ctypes.byref(o), cc.ctypes.byref(st))
-        cc._check(rc)
+    off = b.batch_offsets()
+    xd = cc.to_soa(np.concatenate([sc.x0 for sc in scenes]))
+    iters = 8
+    res = b.solve_batch(xd, precision="fp64", tol=1e-12, max_iters=iters, line_search=True)
+    xb = cc.from_soa(xd)
+    for k, sc in enumerate(scenes):
+        m = _gpu(sc, 2)
+        xk = cc.to_soa(sc.x0)
+        r = m.solve_step(xk, precision="fp64", tol=1e-12, max_iters=iters, line_search=True)
+        assert res["iterations"][k] == r.iterations
+        assert res["status"][k] != -1
+        np.testing.assert_allclose(xb[off[k]:off[k + 1]], cc.from_soa(xk), rtol=0,
+                                   atol=1e-10 * np.abs(cc.from_soa(xk)).max())
+        m.close()
 
 
 
