@@ -105,6 +105,11 @@ def parse():
                    help="add the oracle's CD / CC / JGS2 / Newton timings on the 8^3 cube (100 iterations each)")
     p.add_argument("--cpu-full-sweep", action="store_true",
                    help="add one whole coloured CC sweep of the oracle on the 32^3 cube, single-threaded")
+    p.add_argument("--cfg3", action="store_true",
+                   help="add the dynamic cantilever: 64x64x256 cells, 3-ring bases, backward Euler, 20 steps")
+    p.add_argument("--cfg3-cells", type=str, default="64,64,256", help="beam cells nx,ny,nz")
+    p.add_argument("--cfg3-steps", type=int, default=20)
+    p.add_argument("--cfg3-sweeps", type=int, default=20, help="sweep cap per time step")
     return p.parse_args()
 
 
@@ -527,7 +532,7 @@ def run_batch(args, stream, dev):
     x.copy_(x0)
     torch.cuda.synchronize()
     ev0.record(stream)
-    res_ls = batch.solve_batch(x, precision="mixed", tol=1e-6, max_iters=args.max_iters // 2, check_every=8,
+    res_ls = batch.solve_batch(x, precision="mixed", tol=1e-6, max_iters=args.max_iters // 4, check_every=8,
                                line_search=True)
     ev1.record(stream)
     ev1.synchronize()
@@ -581,7 +586,7 @@ def run_batch(args, stream, dev):
                            "converged": int((res_ls["status"] == 1).sum()),
                            "diverged": int((res_ls["status"] == -1).sum()),
                            "not_reached": int((res_ls["status"] == 0).sum()), "by_nu": buckets(res_ls),
-                           "max_sweeps": args.max_iters // 2},
+                           "max_sweeps": args.max_iters // 4},
            "graph_replay_16_sweeps": {"wall_ms": wall16, "sum_of_kernel_ms": kern16,
                                       "note": "kernel time summed over classes from event-timed replays; "
                                               "wall minus that sum bounds what a persistent kernel could save"},
@@ -709,6 +714,78 @@ def run_large(args, stream, dev):
         out["tet_eval_hbm"] = {"achieved_gbs": a, "frac": a / hbm, "bytes_per_tet": TET_BYTES}
     m.close()
     return out
+
+
+def run_cfg3(args, stream, dev):
+    """The dynamic cantilever as specified: 64 x 64 x 256 cells of 1/64 m
+    (1 085 825 vertices, 6 291 456 tets), z = 0 face clamped, gravity -y 9.8,
+    backward Euler dt = 1/60, SNH E = 1e7, nu = 0.45, rho = 1000, 3-ring rest
+    bases, mixed-precision coloured CC, 20 steps with a fixed sweep cap per
+    step (tolerance 1e-6 of each step's first residual).  Reports per step the
+    sweeps, the residual reduction and the time; the sweep rate; and the sweep
+    against the HBM roofline on its algorithmic bytes."""
+    import torch
+    import meshgen
+    import paper_2510_12053_gb300 as cc
+    nx, ny, nz = (int(v) for v in args.cfg3_cells.split(","))
+    sc = meshgen.beam_dynamic(nx, ny, nz)
+    n_free = int((sc.pinned == 0).sum())
+    t0 = time.perf_counter()
+    m = cc.Mesh.from_scene(sc, stream=stream)
+    t_mesh = time.perf_counter() - t0
+    m.color()
+    t_col = time.perf_counter() - t0 - t_mesh
+    m.build_subspace(3)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = m.info()
+    ncol = int(info.num_colors)
+    t_sub = setup_s - t_mesh - t_col
+
+    def run_steps(corotated):
+        x = cc.to_soa(sc.X, device=dev)
+        v = torch.zeros_like(x)
+        steps = []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total_ms, total_sweeps = 0.0, 0
+        for k in range(args.cfg3_steps):
+            ev0.record(stream)
+            try:
+                r = m.solve_step(x, v, precision="mixed", tol=1e-6, max_iters=args.cfg3_sweeps,
+                                 check_every=args.cfg3_sweeps, use_graph=not args.no_graph, corotated=corotated)
+            except cc.CCError as e:
+                torch.cuda.synchronize()
+                steps.append({"step": k, "error": str(e)})
+                break
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            total_ms += ms
+            total_sweeps += r.iterations
+            steps.append({"step": k, "sweeps": r.iterations, "rel_residual": r.g_final / r.g0, "ms": ms,
+                          "converged": r.converged})
+        return steps, total_ms, total_sweeps
+
+    plain_steps, total_ms, total_sweeps = run_steps(False)
+    corot_steps, corot_ms, corot_sweeps = run_steps(True)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    sweep_bytes = int(info.support_total) * 40 + 4 * sc.T * 56 + (ncol + 1) * sc.n * 24
+    ms_sweep = total_ms / max(total_sweeps, 1)
+    ach = sweep_bytes / (ms_sweep / 1e3) / 1e9 if total_sweeps else None
+    m.close()
+    return {"workload": f"cantilever {nx}x{ny}x{nz} cells of 1/64 m ({sc.n} vertices, {sc.T} tets), z=0 clamped, "
+                        f"gravity -y, backward Euler dt=1/60, SNH E=1e7 nu=0.45 rho=1000, 3-ring rest bases, "
+                        f"mixed coloured CC, {args.cfg3_steps} steps, at most {args.cfg3_sweeps} sweeps per step",
+            "n_free": n_free, "colors": ncol, "support_mean": info.support_total / max(n_free, 1),
+            "support_max": int(info.support_max), "setup_s": setup_s, "mesh_s": t_mesh, "color_s": t_col,
+            "subspace_s": t_sub, "patches_solved": int(info.patch_solved), "patches_shared": int(info.patch_shared),
+            "steps": plain_steps, "sweeps": total_sweeps, "ms": total_ms, "ms_per_sweep": ms_sweep,
+            "corotated": {"steps": corot_steps, "sweeps": corot_sweeps, "ms": corot_ms,
+                          "ms_per_sweep": corot_ms / max(corot_sweeps, 1)},
+            "vertex_updates_per_s": n_free * total_sweeps / (total_ms / 1e3) if total_ms else None,
+            "sweep_roofline": {"bound": "hbm", "algorithmic_bytes_per_sweep": sweep_bytes, "achieved_gbs": ach,
+                               "peak": hbm, "frac": ach / hbm if ach else None, "peak_source": peak_src}}
 
 
 def run_learned(args, stream, dev):
@@ -1129,6 +1206,7 @@ def run_ours(args, rank, world):
         learned_res = run_learned(args, stream, dev)
     resolution_res = run_resolution(args, stream, dev) if args.resolution_sweep else None
     large_res = run_large(args, stream, dev) if args.large_beam else None
+    cfg3_res = run_cfg3(args, stream, dev) if args.cfg3 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -1173,6 +1251,8 @@ def run_ours(args, rank, world):
             line["resolution"] = resolution_res
         if large_res is not None:
             line["large_beam"] = large_res
+        if cfg3_res is not None:
+            line["large_beam_k3_dynamic"] = cfg3_res
         if cfg1 is not None:
             line["cfg1_oracle"] = cfg1
         if full_cpu is not None:

@@ -157,6 +157,8 @@ typedef struct {
   int64_t patch_float64; /* patches of the last basis build that the float32-factor, float64-refined
                             solve handed to the plain float64 solve (non-positive float32 pivot, or
                             refinement not down to 1e-11); 0 when every patch settled */
+  int64_t patch_solved;  /* patches the last cc_build_subspace solved */
+  int64_t patch_shared;  /* bases it copied from a vertex with an identical patch instead */
 } cc_mesh_info;
 
 /* Arrays cc_export can copy to the host (element type in brackets). */
@@ -208,9 +210,15 @@ cc_status cc_color(cc_mesh* mesh, int32_t* colors_out, int32_t* num_colors);
  * Patches of at most 192 unknowns (every 2-ring of a Kuhn grid): float32
  * Cholesky in shared memory with float64 iterative refinement of U to
  * float64 accuracy; larger patches, and those the refinement declines
- * (cc_mesh_info.patch_float64), by dense float64 Cholesky.  A patch whose
- * H_PP is not positive definite keeps its previous basis and fails the call
- * with CC_ERR_NUMERIC.  k_ring in [1, 4].
+ * (cc_mesh_info.patch_float64), by dense float64 Cholesky.  Vertices whose
+ * patches are translated copies of one another (regular grids: equal support
+ * offsets, 1-ring geometry and material) share one solve: the others copy
+ * its basis, and every copy is kept only if it satisfies its own patch's
+ * Eq. 5 (||H_PP U_i + H_Pi|| / ||H_Pi||) to within 4x the residual of the
+ * patch it was computed on (or 1e-10), else it is solved on its own
+ * (cc_mesh_info.patch_solved / patch_shared).  A patch
+ * whose H_PP is not positive definite keeps its previous basis and fails the
+ * call with CC_ERR_NUMERIC.  k_ring in [1, 4].
  * Requires cc_color first (CC_ERR_STATE otherwise). */
 cc_status cc_build_subspace(cc_mesh* mesh, int32_t k_ring);
 

@@ -74,7 +74,8 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("T", ctypes.c_int64), ("n_free", ctypes.c_int64),
                 ("nnz_blocks", ctypes.c_int64), ("num_colors", ctypes.c_int32), ("k_ring", ctypes.c_int32),
                 ("support_total", ctypes.c_int64), ("support_max", ctypes.c_int32),
-                ("max_valence", ctypes.c_int32), ("patch_float64", ctypes.c_int64)]
+                ("max_valence", ctypes.c_int32), ("patch_float64", ctypes.c_int64),
+                ("patch_solved", ctypes.c_int64), ("patch_shared", ctypes.c_int64)]
 
 
 class MeshDesc(ctypes.Structure):

@@ -1121,6 +1121,8 @@ cc_status cc_get_info(const cc_mesh* m, cc_mesh_info* info) {
     info->support_max = m->sup_max;
     info->max_valence = m->max_valence;
     info->patch_float64 = m->last_patch_redo;
+    info->patch_solved = m->last_patch_solved;
+    info->patch_shared = m->last_patch_shared;
   })
 }
 

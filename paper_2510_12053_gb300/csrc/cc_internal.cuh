@@ -163,6 +163,8 @@ struct Mesh {
   int32_t max_up = 0;          // longest upper block row
   int32_t max_rs = 0;          // most staged sources of one free row
   int64_t last_patch_redo = 0; // patches the last mixed patch solve handed to the float64 kernel
+  int64_t last_patch_shared = 0; // bases the last build copied from an identical patch (no solve of their own)
+  int64_t last_patch_solved = 0; // patches the last build solved
   std::vector<double> mass;
   std::vector<double> tet_mu, tet_lh, tet_rho;   // per-tet material (a batch mixes materials);
                                                  // tet_lh = lam + mu (stable Neo-Hookean) or lam (FCR)
@@ -366,6 +368,12 @@ void hessian_f64_at(Mesh& m, const double* x);
 // definite (their bases untouched), or throws when throw_on_fail.
 int64_t patch_solves(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail);
 int64_t rebuild_bases_at(Mesh& m, const double* x);
+// Eq. 5 residuals of the float64 bases of a device vertex list (mlp.cu)
+void basis_residuals(Mesh& m, const int32_t* d_rows, int64_t count, double* rho, cudaStream_t s);
+// Patch solves of a vertex list that share one solve between vertices with
+// identical patches (translated copies on regular grids); every shared basis
+// is checked against its own Eq. 5 and re-solved on its own if it fails.
+int64_t patch_solves_shared(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail);
 void bases_to_f32(Mesh& m);
 // solver state of one precision (allocated once, on first use)
 void ensure_state(Mesh& m, cc_precision p);

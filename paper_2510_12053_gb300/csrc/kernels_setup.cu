@@ -722,10 +722,165 @@ void bases_to_f32(Mesh& m) {
   CCG_CUDA(cudaGetLastError());
 }
 
+namespace {
+
+__device__ __forceinline__ uint64_t sig_mix(uint64_t tag, uint64_t idx, uint64_t v) {
+  // SplitMix64's output function (Steele, Lea and Flood 2014) on a keyed word
+  uint64_t z = v + 0x9E3779B97F4A7C15ull * (tag * 0x100000001B3ull + idx + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Signature of vertex i's patch, one warp per listed vertex: the support as
+// offsets from i with each support vertex's tet count, i's 1-ring (offsets,
+// rest positions relative to X_i as bit patterns, pinned flags) and the
+// material of i's first tet, summed as keyed
+// 64-bit mixes (order-free, so the warp's partial sums combine exactly).
+// Equal signatures only propose that two patches are translated copies.
+__global__ void k_patch_signature(const int32_t* __restrict__ verts, int64_t count, const int32_t* __restrict__ sup_ptr,
+                                  const int32_t* __restrict__ sup_idx, const int32_t* __restrict__ nbr_ptr,
+                                  const int32_t* __restrict__ nbr_idx, const double* __restrict__ Xr, int64_t n,
+                                  const uint8_t* __restrict__ pinned, const int32_t* __restrict__ vt_ptr,
+                                  const int32_t* __restrict__ vt_tet, const double2* __restrict__ mat,
+                                  unsigned long long* __restrict__ sig) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= count) return;
+  const int i = verts[k];
+  const int s0 = sup_ptr[i], m = sup_ptr[i + 1] - s0;
+  const int e0 = nbr_ptr[i], ne = nbr_ptr[i + 1] - e0;
+  uint64_t h = 0;
+  for (int a = lane; a < m; a += 32) {
+    // the support vertex's offset and tet count (a support vertex on the
+    // mesh surface has a different block row than one inside)
+    const int j = sup_idx[s0 + a];
+    h += sig_mix(1, a, (uint64_t)(uint32_t)(j - i));
+    h += sig_mix(9, a, (uint64_t)(vt_ptr[j + 1] - vt_ptr[j]));
+  }
+  for (int e = lane; e < ne; e += 32) {
+    const int l = nbr_idx[e0 + e];
+    h += sig_mix(2, e, (uint64_t)(uint32_t)(l - i));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      h += sig_mix(3 + c, e, (uint64_t)__double_as_longlong(Xr[c * n + l] - Xr[c * n + i]));
+    h += sig_mix(6, e, pinned[l]);
+  }
+  if (lane == 0) {
+    h += sig_mix(7, (uint64_t)m, (uint64_t)ne);
+    const double2 mt = mat[vt_tet[vt_ptr[i]]];
+    h += sig_mix(8, 0, (uint64_t)__double_as_longlong(mt.x)) + sig_mix(8, 1, (uint64_t)__double_as_longlong(mt.y));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  if (lane == 0) sig[k] = h;
+}
+
+// U_v = U_rep (block for block) for the pairs (v, rep) of equal support size;
+// a pair whose sizes differ is flagged in bad[] and copies nothing.
+__global__ void k_copy_bases(const int32_t* __restrict__ dst_v, const int32_t* __restrict__ src_v, int64_t count,
+                             const int32_t* __restrict__ sup_ptr, double* __restrict__ U, int32_t* __restrict__ bad) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= count) return;
+  const int v = dst_v[k], r = src_v[k];
+  const int m = sup_ptr[v + 1] - sup_ptr[v];
+  if (m != sup_ptr[r + 1] - sup_ptr[r]) {
+    if (lane == 0) bad[k] = 1;
+    return;
+  }
+  const double* src = U + 9 * (int64_t)sup_ptr[r];
+  double* dst = U + 9 * (int64_t)sup_ptr[v];
+  for (int q = lane; q < 9 * m; q += 32) dst[q] = src[q];
+}
+
+}  // namespace
+
+int64_t patch_solves_shared(Mesh& m, const int32_t* d_verts, int64_t count, bool throw_on_fail) {
+  cudaStream_t s = m.stream;
+  m.last_patch_shared = 0;
+  m.last_patch_solved = count;
+  if (count < 1024) return patch_solves(m, d_verts, count, throw_on_fail);
+  if (!m.d_Xrest.p) {
+    std::vector<double> soa(3 * m.n);
+    for (int64_t j = 0; j < m.n; ++j)
+      for (int a = 0; a < 3; ++a) soa[a * m.n + j] = m.X[3 * j + a];
+    m.d_Xrest.upload(soa, s);
+    CCG_CUDA(cudaStreamSynchronize(s));
+  }
+  DBuf<unsigned long long> sig;
+  sig.alloc(count);
+  k_patch_signature<<<(unsigned)((count * 32 + 255) / 256), 256, 0, s>>>(
+      d_verts, count, m.d_sup_ptr.p, m.d_sup_idx.p, m.d_nbr_ptr.p, m.d_nbr_idx.p, m.d_Xrest.p, m.n, m.d_pinned.p,
+      m.d_vt_ptr.p, m.d_vt_tet.p, m.d_mat64.p, sig.p);
+  CCG_CUDA(cudaGetLastError());
+  std::vector<unsigned long long> hs(count);
+  std::vector<int32_t> hv(count);
+  CCG_CUDA(cudaMemcpyAsync(hs.data(), sig.p, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaMemcpyAsync(hv.data(), d_verts, count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaStreamSynchronize(s));
+  // the first listed vertex of every signature solves; the others copy it
+  std::vector<int64_t> order(count);
+  for (int64_t k = 0; k < count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return hs[a] < hs[b]; });
+  std::vector<int32_t> reps, mem_v, mem_r, mem_ri;
+  for (int64_t q = 0; q < count;) {
+    int64_t e = q;
+    while (e < count && hs[order[e]] == hs[order[q]]) ++e;
+    const int32_t r = hv[order[q]];
+    for (int64_t t = q + 1; t < e; ++t) {
+      mem_v.push_back(hv[order[t]]);
+      mem_r.push_back(r);
+      mem_ri.push_back((int32_t)reps.size());
+    }
+    reps.push_back(r);
+    q = e;
+  }
+  if ((int64_t)mem_v.size() * 4 < count) return patch_solves(m, d_verts, count, throw_on_fail);  // little to share
+  DBuf<int32_t> d_reps, d_mv, d_mr, d_bad;
+  d_reps.upload(reps, s);
+  int64_t fails = patch_solves(m, d_reps.p, (int64_t)reps.size(), throw_on_fail);
+  const int64_t nm = (int64_t)mem_v.size();
+  d_mv.upload(mem_v, s);
+  d_mr.upload(mem_r, s);
+  d_bad.alloc(nm);
+  CCG_CUDA(cudaMemsetAsync(d_bad.p, 0, nm * sizeof(int32_t), s));
+  k_copy_bases<<<(unsigned)((nm * 32 + 255) / 256), 256, 0, s>>>(d_mv.p, d_mr.p, nm, m.d_sup_ptr.p, m.f64.U.p,
+                                                                 d_bad.p);
+  CCG_CUDA(cudaGetLastError());
+  // every copied basis must solve its own patch's Eq. 5 as well as it solves
+  // the patch it was computed on: a translated copy (bitwise equal H_PP,
+  // H_Pi) reproduces its source's residual, while a patch that differs even
+  // in the last digits of its geometry leaves a residual of that size
+  const int64_t nr = (int64_t)reps.size();
+  DBuf<double> rho, rho_r;
+  rho.alloc(nm);
+  rho_r.alloc(nr);
+  basis_residuals(m, d_mv.p, nm, rho.p, s);
+  basis_residuals(m, d_reps.p, nr, rho_r.p, s);
+  std::vector<double> hr(nm), hrr(nr);
+  std::vector<int32_t> hb(nm);
+  CCG_CUDA(cudaMemcpyAsync(hr.data(), rho.p, nm * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaMemcpyAsync(hrr.data(), rho_r.p, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaMemcpyAsync(hb.data(), d_bad.p, nm * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CCG_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> own;
+  for (int64_t k = 0; k < nm; ++k)
+    if (hb[k] || !(hr[k] <= std::max(1e-10, 4.0 * hrr[mem_ri[k]]))) own.push_back(mem_v[k]);
+  if (!own.empty()) {
+    DBuf<int32_t> d_own;
+    d_own.upload(own, s);
+    fails += patch_solves(m, d_own.p, (int64_t)own.size(), throw_on_fail);
+  }
+  m.last_patch_shared = nm - (int64_t)own.size();
+  m.last_patch_solved = (int64_t)reps.size() + (int64_t)own.size();
+  return fails;
+}
+
 void run_subspace_build(Mesh& m, int32_t k) {
   build_supports(m, k);
   rest_hessian_f64(m);
-  patch_solves(m, m.d_free_rows.p, m.n_free, true);
+  patch_solves_shared(m, m.d_free_rows.p, m.n_free, true);
   bases_to_f32(m);
   CCG_CUDA(cudaStreamSynchronize(m.stream));
 }

@@ -607,6 +607,16 @@ struct MlpNet {
   }
 };
 
+// Eq. 5 residual rho_i = ||H_PP U_i + H_Pi|| / ||H_Pi|| (float64 bases and
+// block rows) of a device list of free vertices, into rho[count].
+void basis_residuals(Mesh& m, const int32_t* d_rows, int64_t count, double* rho, cudaStream_t s) {
+  if (count <= 0) return;
+  k_basis_residual<<<blocks_for(count * 32, 256), 256, 0, s>>>((int)count, d_rows, m.d_sup_ptr.p, m.d_sup_idx.p,
+                                                              m.d_up_ptr.p, m.d_up_col.p, m.d_nbr_ptr.p,
+                                                              m.d_nbr_idx.p, m.f64.bsr.p, m.f64.U.p, rho);
+  CCG_CUDA(cudaGetLastError());
+}
+
 }  // namespace ccg
 
 using namespace ccg;
