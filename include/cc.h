@@ -500,6 +500,13 @@ int64_t cc_mlp_param_count(const cc_mlp* net);
 cc_status cc_mlp_set_params(cc_mlp* net, const float* params, int64_t count);
 cc_status cc_mlp_get_params(const cc_mlp* net, float* params, int64_t count);
 
+/* Parameters to and from a file (path: host string): the layer widths, then
+ * the float32 parameters in the cc_mlp_set_params order.  Loading checks that
+ * the widths match this network (CC_ERR_INVALID_ARG otherwise) and, like
+ * cc_mlp_set_params, resets Adam's moments; the optimizer state is not saved. */
+cc_status cc_mlp_save(const cc_mlp* net, const char* path);
+cc_status cc_mlp_load(cc_mlp* net, const char* path);
+
 /* Y [rows x d_out] float32 (device, leading dimension ldy) of the inputs
  * X [rows x d_in] BF16 (device, leading dimension ldx, multiple of 8).
  * Any number of rows; the inference workspace grows as needed. */

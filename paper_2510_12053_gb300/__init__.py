@@ -151,6 +151,8 @@ _SIGS = {
     "cc_mlp_param_count": (ctypes.c_int64, [_P]),
     "cc_mlp_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "cc_mlp_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "cc_mlp_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "cc_mlp_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cc_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64]),
     "cc_mlp_loss_grad": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_double), _P]),
@@ -509,6 +511,12 @@ class MLP:
     def set_params(self, p: np.ndarray):
         p = np.ascontiguousarray(p, dtype=np.float32)
         _check(lib().cc_mlp_set_params(self._h, p.ctypes.data, p.size))
+
+    def save(self, path: str):
+        _check(lib().cc_mlp_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str):
+        _check(lib().cc_mlp_load(self._h, os.fsencode(path)))
 
     def get_params(self) -> np.ndarray:
         p = np.empty(self.param_count, dtype=np.float32)

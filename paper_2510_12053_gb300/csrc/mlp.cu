@@ -17,6 +17,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -829,6 +830,56 @@ cc_status cc_mlp_get_params(const cc_mlp* net, float* params, int64_t count) {
     CCG_CHECK(net && params && count == net->nparams, CC_ERR_INVALID_ARG, "parameter count mismatch");
     CCG_CUDA(cudaStreamSynchronize(net->stream));
     CCG_CUDA(cudaMemcpy(params, net->params.p, count * sizeof(float), cudaMemcpyDeviceToHost));
+  })
+}
+
+// File layout: 8-byte tag "CCMLP01\0", int32 count of widths, the widths
+// (d_in, hidden..., d_out), int64 parameter count, the float32 parameters in
+// the cc_mlp_set_params order; all little-endian as written by this host.
+static const char kMlpTag[8] = {'C', 'C', 'M', 'L', 'P', '0', '1', '\0'};
+
+cc_status cc_mlp_save(const cc_mlp* net, const char* path) {
+  CC_API_BODY("cc_mlp_save", {
+    CCG_CHECK(net && path, CC_ERR_INVALID_ARG, "NULL argument");
+    std::vector<float> p(net->nparams);
+    CCG_CUDA(cudaStreamSynchronize(net->stream));
+    CCG_CUDA(cudaMemcpy(p.data(), net->params.p, p.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    CCG_CHECK(f, CC_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+    const int32_t nd = (int32_t)net->dims.size();
+    const int64_t np = net->nparams;
+    bool ok = std::fwrite(kMlpTag, 1, 8, f) == 8 && std::fwrite(&nd, sizeof(nd), 1, f) == 1;
+    for (int d : net->dims) {
+      const int32_t v = d;
+      ok = ok && std::fwrite(&v, sizeof(v), 1, f) == 1;
+    }
+    ok = ok && std::fwrite(&np, sizeof(np), 1, f) == 1 && std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+    ok = (std::fclose(f) == 0) && ok;
+    CCG_CHECK(ok, CC_ERR_STATE, std::string("write to ") + path + " failed");
+  })
+}
+
+cc_status cc_mlp_load(cc_mlp* net, const char* path) {
+  CC_API_BODY("cc_mlp_load", {
+    CCG_CHECK(net && path, CC_ERR_INVALID_ARG, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    CCG_CHECK(f, CC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    char tag[8] = {0};
+    int32_t nd = 0;
+    int64_t np = 0;
+    bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, kMlpTag, 8) == 0 &&
+              std::fread(&nd, sizeof(nd), 1, f) == 1 && nd == (int32_t)net->dims.size();
+    for (int k = 0; ok && k < nd; ++k) {
+      int32_t v = 0;
+      ok = std::fread(&v, sizeof(v), 1, f) == 1 && v == net->dims[k];
+    }
+    ok = ok && std::fread(&np, sizeof(np), 1, f) == 1 && np == net->nparams;
+    std::vector<float> p(ok ? np : 0);
+    ok = ok && std::fread(p.data(), sizeof(float), p.size(), f) == p.size();
+    std::fclose(f);
+    CCG_CHECK(ok, CC_ERR_INVALID_ARG, std::string(path) + " is not a parameter file of this network's shape");
+    const cc_status st = cc_mlp_set_params(net, p.data(), np);
+    CCG_CHECK(st == CC_OK, st, "cc_mlp_load: setting the parameters failed");
   })
 }
 

@@ -335,3 +335,20 @@ def test_trained_network_gains_over_the_method_without_it():
     assert sU["n_fallback"] >= 2 * max(sL["n_fallback"], 1)  # training is what avoids them
     assert rL.iterations <= 1.5 * hist.iterations + 2        # near the oracle's computed-basis curve
     assert (not rD.converged) or rD.iterations >= 2 * rL.iterations
+
+
+def test_parameters_round_trip_through_a_file(tmp_path):
+    dims = meshgen.mlp_dims()
+    a = cc.MLP(max_batch=256)
+    p = meshgen.mlp_init(dims, 3)
+    a.set_params(p)
+    path = str(tmp_path / "net.bin")
+    a.save(path)
+    b = cc.MLP(max_batch=256)
+    b.load(path)
+    np.testing.assert_array_equal(b.get_params(), a.get_params())
+    other = cc.MLP(hidden=128, max_batch=256)
+    with pytest.raises(cc.CCError):
+        other.load(path)
+    for net in (a, b, other):
+        net.close()
