@@ -532,7 +532,7 @@ def run_batch(args, stream, dev):
     x.copy_(x0)
     torch.cuda.synchronize()
     ev0.record(stream)
-    res_ls = batch.solve_batch(x, precision="mixed", tol=1e-6, max_iters=args.max_iters // 4, check_every=8,
+    res_ls = batch.solve_batch(x, precision="mixed", tol=1e-6, max_iters=args.max_iters // 2, check_every=8,
                                line_search=True)
     ev1.record(stream)
     ev1.synchronize()
@@ -586,7 +586,7 @@ def run_batch(args, stream, dev):
                            "converged": int((res_ls["status"] == 1).sum()),
                            "diverged": int((res_ls["status"] == -1).sum()),
                            "not_reached": int((res_ls["status"] == 0).sum()), "by_nu": buckets(res_ls),
-                           "max_sweeps": args.max_iters // 4},
+                           "max_sweeps": args.max_iters // 2},
            "graph_replay_16_sweeps": {"wall_ms": wall16, "sum_of_kernel_ms": kern16,
                                       "note": "kernel time summed over classes from event-timed replays; "
                                               "wall minus that sum bounds what a persistent kernel could save"},
