@@ -127,3 +127,29 @@ def test_cube16_mixed_trajectory_matches_stored_oracle_trajectory(run):
     xs = cc.from_soa(xd)[gold["sample"]].ravel()
     assert np.abs(xs - gold["x"]).max() <= 1e-5 * diag
     m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_three_ring_dynamic_cantilever_sweeps_follow_the_oracle(precision):
+    """The cantilever workload's method at a size the oracle finishes: 3-ring
+    rest bases (M + h^2 K), backward Euler target with gravity, two coloured
+    CC sweeps of the first step, against the oracle's own sweeps."""
+    scene = meshgen.cantilever(4, 4, 12, cell=1.0 / 64.0, E=1e7, nu=0.45)
+    pb = fem.problem_from_scene(scene)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    sup, U = subspace.build_local_bases(pb, topo, 3)
+    xt = pb.inertial_target(scene.X, scene.v0)
+    x_o = scene.X.copy()
+    for _ in range(2):
+        x_o = solvers.sweep(pb, topo, sup, U, x_o, xt, "cc", "colored")
+    m = cc.Mesh.from_scene(scene)
+    m.color()
+    m.build_subspace(3)
+    assert m.info().support_max > 64
+    xd, vd = cc.to_soa(scene.X), cc.to_soa(scene.v0)
+    r = m.solve_step(xd, vd, precision=precision, tol=0.0, max_iters=2, min_iters=2)
+    assert r.iterations == 2
+    step = np.abs(x_o - scene.X).max()
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert np.abs(cc.from_soa(xd) - x_o).max() <= tol * step
+    m.close()
