@@ -203,6 +203,16 @@ void cc_destroy_mesh(cc_mesh* mesh);
  * tet.  colors_out: host [n] int32 or NULL; num_colors: host or NULL. */
 cc_status cc_color(cc_mesh* mesh, int32_t* colors_out, int32_t* num_colors);
 
+/* A colouring chosen by the caller instead (the coloured schedule of
+ * Alg. 1's local updates needs only that no two vertices of a tet share a
+ * colour; which valid colouring is used changes the order of the updates,
+ * not the method).  colors: host [n] int32 in [0, num_colors).  Checked:
+ * CC_ERR_INVALID_ARG if a colour is out of range or two vertices of one tet
+ * share a colour.  Example: every Kuhn grid (every edge offset's coordinates
+ * sum to 1, 2 or 3) is coloured by (i + j + k) mod 4 of the lattice
+ * coordinates, 4 colours where the greedy colouring of cc_color uses 8. */
+cc_status cc_set_colors(cc_mesh* mesh, const int32_t* colors, int32_t num_colors);
+
 /* Perturbation bases U_i = -H_PP^{-1} H_Pi at the rest configuration
  * (Eq. 5, Sec. 3.1), one per free vertex i, on the patch P = S_i: the free
  * vertices within k_ring 1-ring hops of i, i excluded, every DOF outside P

@@ -136,6 +136,18 @@ def kuhn_tets(nx: int, ny: int, nz: int) -> np.ndarray:
     return out.reshape(-1, 4).astype(np.int32)
 
 
+def lattice_colors(nx: int, ny: int, nz: int) -> np.ndarray:
+    """``(i + j + k) mod 4`` of every vertex's lattice coordinates ``[n]``.
+
+    A vertex colouring of the Kuhn grid in which no two vertices of a tet
+    share a colour: every tet edge joins ``v`` and ``v + d`` with ``d`` one of
+    the seven non-zero 0/1 vectors (or its negative), whose coordinates sum to
+    1, 2 or 3, never to a multiple of 4.  Jitter moves vertices, not edges, so
+    it holds for jittered grids too."""
+    i, j, k = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    return ((i + j + k).ravel(order="F") % 4).astype(np.int32)
+
+
 def boundary_mask(nx: int, ny: int, nz: int) -> np.ndarray:
     """1 for vertices on the box surface."""
     i, j, k = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")

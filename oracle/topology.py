@@ -112,12 +112,20 @@ def supports(n: int, k: int, nbr_ptr, nbr_idx, free) -> List[np.ndarray]:
 class Topology:
     """All adjacency of one mesh, computed once."""
 
-    def __init__(self, n: int, tets, free):
+    def __init__(self, n: int, tets, free, colors=None):
+        """``colors``: a given vertex colouring (no two vertices of a tet alike)
+        in place of the greedy one; the coloured schedule only needs validity."""
         self.n = n
         self.vt_ptr, self.vt_tet, self.vt_corner = vertex_tets(n, tets)
         self.nbr_ptr, self.nbr_idx = vertex_neighbors(n, tets)
         self.bsr_ptr, self.bsr_col = block_pattern(n, self.nbr_ptr, self.nbr_idx)
-        self.color = greedy_coloring(n, self.nbr_ptr, self.nbr_idx)
+        if colors is None:
+            self.color = greedy_coloring(n, self.nbr_ptr, self.nbr_idx)
+        else:
+            self.color = np.asarray(colors, dtype=np.int64).copy()
+            for v in range(n):
+                if np.any(self.color[self.nbr_idx[self.nbr_ptr[v]:self.nbr_ptr[v + 1]]] == self.color[v]):
+                    raise ValueError(f"vertex {v} shares its colour with a neighbour")
         self.num_colors = int(self.color.max()) + 1 if n else 0
         self.free = np.asarray(free).astype(bool)
 

@@ -129,6 +129,7 @@ _SIGS = {
                                      ctypes.c_double, _P, _P, ctypes.POINTER(_P)]),
     "cc_destroy_mesh": (None, [_P]),
     "cc_color": (ctypes.c_int, [_P, _P, _P]),
+    "cc_set_colors": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "cc_build_subspace": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_set_subspace": (ctypes.c_int, [_P, _P, _P, _P]),
     "cc_build_subspace_at": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
@@ -326,6 +327,12 @@ class Mesh:
         nc = ctypes.c_int32()
         _check(lib().cc_color(self._h, cols.ctypes.data, ctypes.byref(nc)))
         return cols
+
+    def set_colors(self, colors, num_colors: Optional[int] = None):
+        """A caller's colouring (no two vertices of a tet alike), e.g. a Kuhn
+        grid's lattice colouring (i + j + k) mod 4."""
+        c = np.ascontiguousarray(colors, dtype=np.int32)
+        _check(lib().cc_set_colors(self._h, c.ctypes.data, int(c.max()) + 1 if num_colors is None else int(num_colors)))
 
     def build_subspace(self, k: int):
         _check(lib().cc_build_subspace(self._h, int(k)))

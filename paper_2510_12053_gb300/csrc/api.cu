@@ -425,6 +425,14 @@ cc_status cc_color(cc_mesh* m, int32_t* colors_out, int32_t* num_colors) {
   })
 }
 
+cc_status cc_set_colors(cc_mesh* m, const int32_t* colors, int32_t num_colors) {
+  CC_API_BODY("cc_set_colors", {
+    CCG_CHECK(m && colors, CC_ERR_INVALID_ARG, "NULL argument");
+    drop_graph(*m);
+    ccg::set_coloring(*m, colors, num_colors);
+  })
+}
+
 cc_status cc_build_subspace(cc_mesh* m, int32_t k) {
   CC_API_BODY("cc_build_subspace", {
     CCG_CHECK(m, CC_ERR_INVALID_ARG, "mesh is NULL");

@@ -358,6 +358,10 @@ void launch_velocity(const double* x, const double* xold, int64_t n, double h, d
 void launch_line_point(const double* x0, const double* x1, int64_t n, double alpha, double* x, cudaStream_t s);
 // colouring and subspace build
 void run_coloring(Mesh& m);
+// a caller's colouring (validated: colours in [0, C), no two vertices of a
+// tet alike), then the per-colour vertex and tet lists
+void set_coloring(Mesh& m, const int32_t* colors, int32_t C);
+void build_color_lists(Mesh& m);
 void run_subspace_build(Mesh& m, int32_t k);
 void build_supports(Mesh& m, int32_t k);
 void rest_hessian_f64(Mesh& m);

@@ -198,6 +198,26 @@ void run_coloring(Mesh& m) {
     C = std::max(C, m.color[v] + 1);
   }
   m.num_colors = C;
+  build_color_lists(m);
+}
+
+void set_coloring(Mesh& m, const int32_t* colors, int32_t C) {
+  CCG_CHECK(C >= 1 && C <= 1024, CC_ERR_INVALID_ARG, "number of colours must be in [1, 1024]");
+  for (int64_t v = 0; v < m.n; ++v) {
+    CCG_CHECK(colors[v] >= 0 && colors[v] < C, CC_ERR_INVALID_ARG, "colour out of range");
+    for (int64_t p = m.nbr_ptr[v]; p < m.nbr_ptr[v + 1]; ++p)
+      CCG_CHECK(colors[m.nbr_idx[p]] != colors[v], CC_ERR_INVALID_ARG,
+                "two vertices of one tet share a colour (vertex " + std::to_string(v) + ")");
+  }
+  m.color.assign(colors, colors + m.n);
+  m.num_colors = C;
+  m.d_color.upload(m.color, m.stream);
+  build_color_lists(m);
+}
+
+void build_color_lists(Mesh& m) {
+  cudaStream_t s = m.stream;
+  const int32_t C = m.num_colors;
   // free vertices per colour (ascending) and tets whose free vertex of colour c moves
   m.cv_ptr.assign(C + 1, 0);
   std::vector<std::vector<int32_t>> cv(C), tl(C);

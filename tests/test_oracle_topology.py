@@ -1,6 +1,7 @@
 """Pins of the oracle's adjacency, colouring and k-rings against brute force
 and independent constructions."""
 import numpy as np
+import pytest
 import scipy.sparse as sp
 
 import meshgen
@@ -89,3 +90,21 @@ def test_supports_exclude_self_and_pinned():
             assert len(S) == 0
         else:
             assert v not in S and np.all(free[S]) and np.all(np.diff(S) > 0)
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (8, 8, 8), (6, 2, 9)])
+def test_lattice_colouring_is_valid_with_four_colours(dims):
+    """(i + j + k) mod 4 colours every Kuhn grid: no two vertices of a tet
+    alike (checked on the tets themselves, jittered or not), four colours."""
+    tets = meshgen.kuhn_tets(*dims)
+    col = meshgen.lattice_colors(*dims)
+    c = col[tets]
+    for a in range(4):
+        for b in range(a + 1, 4):
+            assert np.all(c[:, a] != c[:, b])
+    assert set(np.unique(col)) == {0, 1, 2, 3}
+    n = (dims[0] + 1) * (dims[1] + 1) * (dims[2] + 1)
+    topo = topology.Topology(n, tets, np.ones(n, bool), colors=col)
+    assert topo.num_colors == 4
+    with pytest.raises(ValueError):
+        topology.Topology(n, tets, np.ones(n, bool), colors=np.zeros(n, np.int32))
