@@ -105,6 +105,8 @@ def parse():
                    help="add the oracle's CD / CC / JGS2 / Newton timings on the 8^3 cube (100 iterations each)")
     p.add_argument("--cpu-full-sweep", action="store_true",
                    help="add one whole coloured CC sweep of the oracle on the 32^3 cube, single-threaded")
+    p.add_argument("--colors", choices=["lattice", "greedy"], default="lattice",
+                   help="colouring of the coloured schedule: the Kuhn grid's (i+j+k) mod 4 (4 colours) or greedy (8)")
     p.add_argument("--no-cfg3", action="store_true",
                    help="skip the dynamic cantilever: 64x64x256 cells, 3-ring bases, backward Euler, 20 steps")
     p.add_argument("--cfg3-cells", type=str, default="64,64,256", help="beam cells nx,ny,nz")
@@ -119,11 +121,29 @@ def scenes(nu):
                                 name=f"cube32_E{E:g}") for E in E_SWEEP]
 
 
+COLORING = {"mode": "lattice"}
+
+
+def colorize(mesh, scenes):
+    """Colours a mesh (or a batch of meshes, in order) for the coloured
+    schedule: the Kuhn grid's lattice colouring (i + j + k) mod 4 (four colour
+    phases per sweep), or with --colors greedy the library's greedy colouring
+    (eight on these grids)."""
+    if COLORING["mode"] == "greedy":
+        mesh.color()
+        return
+    import meshgen
+    scs = scenes if isinstance(scenes, (list, tuple)) else [scenes]
+    mesh.set_colors(np.concatenate([meshgen.lattice_colors(*sc.dims) for sc in scs]), num_colors=4)
+
+
 def workload_config(nu, n, T, n_free):
     return {"workload": f"cube32_stretch: {DIMS[0]}x{DIMS[1]}x{DIMS[2]} cells x 6 tets ({n} vertices, {T} tets), "
                         f"jitter 5% seed 0, x=0 clamped, x=1 pulled to 1.5, SNH nu={nu}, E in {E_SWEEP}, "
                         f"{K_RING}-ring bases, coloured CC, tol 1e-6 rel grad-norm",
             "n_free": n_free, "k_ring": K_RING, "schedule": "colored", "update": "cc",
+            "coloring": ("lattice (i+j+k) mod 4, 4 colours" if COLORING["mode"] == "lattice"
+                         else "greedy in ascending id, 8 colours"),
             "nu": nu, "E_values": E_SWEEP, "cells": list(DIMS), "tol": 1e-6,
             "nu_note": "the named configuration's nu=0.45 diverges with 2-ring rest bases (oracle and GPU agree); "
                        "its outcome is reported under cfg_nu045",
@@ -246,7 +266,9 @@ class OracleColour:
         _ow_init(nu, bases=self.cores == 1)
         self.pb = _OW["pb"]
         self.x0 = _ow_scene(nu).x0
-        topo = topology.Topology(self.pb.n, self.pb.tets, self.pb.free)
+        import meshgen
+        cols = meshgen.lattice_colors(*DIMS) if COLORING["mode"] == "lattice" else None
+        topo = topology.Topology(self.pb.n, self.pb.tets, self.pb.free, colors=cols)
         self.verts = np.asarray(topo.color_classes(free_only=True)[colour], dtype=np.int64)
         self.pool = None
         self.shm = []
@@ -497,7 +519,7 @@ def run_batch(args, stream, dev):
     scenes = meshgen.random_boxes(args.batch_count, seed=0)
     t0 = time.perf_counter()
     batch = cc.Mesh.from_scenes(scenes, stream=stream)
-    batch.color()
+    colorize(batch, scenes)
     batch.build_subspace(K_RING)
     torch.cuda.synchronize()
     setup_ms = 1e3 * (time.perf_counter() - t0)
@@ -561,7 +583,7 @@ def run_batch(args, stream, dev):
     loop_ms, loop_upd = 0.0, 0
     for sc in scenes[:16]:
         m = cc.Mesh.from_scene(sc, stream=stream)
-        m.color()
+        colorize(m, sc)
         m.build_subspace(K_RING)
         xs = cc.to_soa(sc.x0, device=dev)
         a, bq = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -625,7 +647,7 @@ def run_resolution(args, stream, dev):
         x0 = cc.to_soa(sc.x0, device=dev)
         for model, corot in (("snh", False), ("fcr", False), ("fcr", True)):
             m = cc.Mesh.from_scene(sc, stream=stream, model=model)
-            m.color()
+            colorize(m, sc)
             m.build_subspace(K_RING)
             x = x0.clone()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -661,7 +683,7 @@ def run_large(args, stream, dev):
     n_free = int((sc.pinned == 0).sum())
     t0 = time.perf_counter()
     m = cc.Mesh.from_scene(sc, stream=stream)
-    m.color()
+    colorize(m, sc)
     m.build_subspace(K_RING)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -733,7 +755,7 @@ def run_cfg3(args, stream, dev):
     t0 = time.perf_counter()
     m = cc.Mesh.from_scene(sc, stream=stream)
     t_mesh = time.perf_counter() - t0
-    m.color()
+    colorize(m, sc)
     t_col = time.perf_counter() - t0 - t_mesh
     m.build_subspace(3)
     torch.cuda.synchronize()
@@ -860,7 +882,7 @@ def run_learned(args, stream, dev):
 
     def fresh():
         m = cc.Mesh.from_scene(sc, stream=stream)
-        m.color()
+        colorize(m, sc)
         return m
 
     free = sc.pinned == 0
@@ -1001,7 +1023,7 @@ def run_nu045(args, stream, dev):
     out = []
     for sc in scenes(0.45):
         m = cc.Mesh.from_scene(sc, stream=stream)
-        m.color()
+        colorize(m, sc)
         m.build_subspace(K_RING)
         x = cc.to_soa(sc.x0, device=dev)
         rec = {"E": sc.material.E, "nu": 0.45}
@@ -1062,7 +1084,7 @@ def run_ours(args, rank, world):
     meshes = []
     for sc in scs:
         m = cc.Mesh.from_scene(sc, stream=stream)
-        m.color()
+        colorize(m, sc)
         m.build_subspace(K_RING)
         meshes.append(m)
     torch.cuda.synchronize()
@@ -1207,7 +1229,7 @@ def run_ours(args, rank, world):
     batched4 = None
     if not args.no_batch:
         b4 = cc.Mesh.from_scenes(scs, stream=stream)
-        b4.color()
+        colorize(b4, scs)
         b4.build_subspace(K_RING)
         xb0 = cc.to_soa(np.concatenate([sc.x0 for sc in scs]), device=dev)
         xb = xb0.clone()
@@ -1229,6 +1251,31 @@ def run_ours(args, rank, world):
                     "ms_per_mesh_sweep": msb / float(rb["iterations"].sum()),
                     "note": "the headline's four E values solved together as one 4-mesh batch"}
         b4.close()
+
+    # the same four solves with the greedy colouring (8 colours), for comparison
+    greedy_cmp = None
+    if COLORING["mode"] == "lattice" and not args.no_fp64:
+        gms, gsw = 0.0, []
+        for sc in scs:
+            mg = cc.Mesh.from_scene(sc, stream=stream)
+            mg.color()
+            mg.build_subspace(K_RING)
+            xg = x0.clone()
+            mg.solve_step(xg, precision="mixed", tol=1e-6, max_iters=args.max_iters, check_every=args.check_every,
+                          use_graph=not args.no_graph)   # warm-up (graph capture)
+            xg.copy_(x0)
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rg = mg.solve_step(xg, precision="mixed", tol=1e-6, max_iters=args.max_iters,
+                               check_every=args.check_every, use_graph=not args.no_graph)
+            ev1.record(stream)
+            ev1.synchronize()
+            gms += ev0.elapsed_time(ev1)
+            gsw.append(rg.iterations)
+            mg.close()
+        greedy_cmp = {"colors": 8, "ms_to_tol_per_solve": gms / len(scs), "sweeps_per_solve": float(np.mean(gsw)),
+                      "ms_per_sweep": gms / sum(gsw), "vertex_updates_per_s": n_free * sum(gsw) / (gms / 1e3)}
 
     nu045 = None if args.no_nu045 else run_nu045(args, stream, dev)
     batch_res = None
@@ -1278,6 +1325,7 @@ def run_ours(args, rank, world):
             "cpu_baseline": cpu,
             "cfg_nu045": nu045,
             "batched_four_solves": batched4,
+            "greedy_coloring_solves": greedy_cmp,
             "batch": batch_res,
             "learned": learned_res,
         }
@@ -1296,6 +1344,7 @@ def run_ours(args, rank, world):
 
 def main():
     args = parse()
+    COLORING["mode"] = args.colors
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
