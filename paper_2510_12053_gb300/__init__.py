@@ -155,6 +155,7 @@ _SIGS = {
     "cc_mlp_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cc_mlp_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "cc_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64]),
+    "cc_mlp_set_fused": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cc_mlp_loss_grad": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_double), _P]),
     "cc_mlp_adam_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(Adam)]),
@@ -529,6 +530,10 @@ class MLP:
         p = np.empty(self.param_count, dtype=np.float32)
         _check(lib().cc_mlp_get_params(self._h, p.ctypes.data, p.size))
         return p
+
+    def set_fused(self, on: bool = True):
+        """Inference in one kernel for every layer (True, the default) or one GEMM per layer."""
+        _check(lib().cc_mlp_set_fused(self._h, 1 if on else 0))
 
     def forward(self, X, out=None):
         """Y [rows, d_out] float32 for BF16 inputs X [rows, >= d_in] (row stride a multiple of 8)."""

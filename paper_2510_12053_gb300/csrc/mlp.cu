@@ -468,6 +468,7 @@ struct MlpNet {
   int64_t adam_t = 0;
   DBuf<bf16> inf_h[2];
   int64_t inf_rows = 0;
+  bool fused_inference = true;  // one kernel for every layer where the shape allows
 
   int d_in() const { return dims.front(); }
   int d_out() const { return dims.back(); }
@@ -580,6 +581,16 @@ struct MlpNet {
 
   // Inference over any number of rows: Y = net(X).
   void forward_rows(const bf16* X, int64_t ldx, int64_t rows, float* Y, int64_t ldy) {
+    if (fused_inference && mlp_fused_supported(dims)) {
+      std::vector<const bf16*> w(L);
+      std::vector<const float*> b(L);
+      for (int l = 0; l < L; ++l) {
+        w[l] = w16[l].p;
+        b[l] = params.p + off_b[l];
+      }
+      mlp_forward_fused(X, ldx, (int)rows, dims, w, ldk, b, Y, ldy, err.p, stream);
+      return;
+    }
     int hmax = 8;
     for (int l = 1; l < L; ++l) hmax = std::max(hmax, dims[l]);
     if (rows > inf_rows) {
@@ -892,6 +903,13 @@ cc_status cc_mlp_forward(cc_mlp* net, const void* X, int64_t ldx, int64_t rows, 
     CCG_CUDA(cudaMemsetAsync(net->err.p, 0, sizeof(int), net->stream));
     net->forward_rows(static_cast<const bf16*>(X), ldx, rows, Y, ldy);
     net->check_err();
+  })
+}
+
+cc_status cc_mlp_set_fused(cc_mlp* net, int32_t on) {
+  CC_API_BODY("cc_mlp_set_fused", {
+    CCG_CHECK(net, CC_ERR_INVALID_ARG, "NULL argument");
+    net->fused_inference = on != 0;
   })
 }
 

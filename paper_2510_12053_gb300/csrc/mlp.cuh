@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace ccg {
 
@@ -44,6 +45,27 @@ void gemm_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int 
 // at least one tile per SM, and (when allow_split) enough K splits to fill the
 // GPU with at least four K tiles per split.
 GemmShape gemm_pick_shape(int M, int N, int K, bool allow_split);
+// The whole network's inference in one kernel (activations kept on chip).
+constexpr int kFusedMaxLayers = 6;
+struct FusedNet {
+  int L = 0, M = 0;
+  int dims[kFusedMaxLayers + 1] = {};       // d_in, hidden..., d_out
+  int chunk[kFusedMaxLayers] = {};          // N columns per accumulator pass
+  const float* bias[kFusedMaxLayers] = {};
+  float* y = nullptr;
+  int64_t ldy = 0;
+};
+// True when the fused kernel covers the shape: at most kFusedMaxLayers layers,
+// hidden widths multiples of 64 up to 256, an output width that is a multiple
+// of 64 (any input width).
+bool mlp_fused_supported(const std::vector<int>& dims);
+// Y[M x d_out] (float32, leading dim ldy) = the network applied to the rows of
+// X (BF16, leading dim ldx, a multiple of 8): per hidden layer GELU(W h + b)
+// rounded to BF16, the output layer W h + b; w[l] is the BF16 [d_{l+1} x ldk[l]]
+// weight, bias[l] the float32 bias.  Bitwise the same as the per-layer GEMMs.
+void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>& dims,
+                       const std::vector<const __nv_bfloat16*>& w, const std::vector<int>& ldk,
+                       const std::vector<const float*>& bias, float* Y, int64_t ldy, int* err, cudaStream_t s);
 // out[3k .. 3k+2] = (erf, GELU, GELU') of x[k] with the epilogues' arithmetic
 void gelu_check(const float* x, int n, float* out, cudaStream_t s);
 

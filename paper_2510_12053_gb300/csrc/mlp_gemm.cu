@@ -112,33 +112,75 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// Accumulator fragment for stores along rows: 16 tensor-memory lanes x 16
+// columns.  Thread t holds lanes t/4 (v[0..1], v[4..5]) and t/4 + 8 (v[2..3],
+// v[6..7]) at columns 2 (t % 4) + {0, 1} (v[0..3]) and 8 + 2 (t % 4) + {0, 1}
+// (v[4..7]), so four consecutive threads hold 32 contiguous bytes of a row.
+__device__ __forceinline__ void tmem_ld_rows16(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 }  // namespace
 
-// erf(x) from Abramowitz and Stegun, Handbook of Mathematical Functions
-// (1964), formula 7.1.26 (Hastings' rational approximation):
+// Hardware approximations (flush to zero): reciprocal and 2^x.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float exp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// erfc(u) / 2 for u >= 0 by Abramowitz and Stegun, Handbook of Mathematical
+// Functions (1964), formula 7.1.26 (Hastings' rational approximation):
 //   erf(u) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-u^2),
-//   t = 1 / (1 + p u), u = |x|, odd in x, with |error| <= 1.5e-7.
+//   t = 1 / (1 + p u), |error| <= 1.5e-7,
+// with the a_k halved (exact in binary), and exp(-u^2) = 2^(-u^2 log2 e).
 // Branch-free: one reciprocal, one exponential, five FMAs.  Its error is ~1e-4
 // of a BF16 rounding step, where the activations it feeds are stored.
+struct HalfErfc {
+  float h;  // erfc(u) / 2
+  float e;  // exp(-u^2)
+};
+
+__device__ __forceinline__ HalfErfc half_erfc_as7126(float u) {
+  const float t = rcp_approx(fmaf(0.3275911f, u, 1.0f));
+  float q = fmaf(t, 0.5307027145f, -0.7265760135f);
+  q = fmaf(t, q, 0.7107068705f);
+  q = fmaf(t, q, -0.142248368f);
+  q = fmaf(t, q, 0.127414796f);
+  const float e = exp2_approx(u * (u * -1.4426950408889634f));
+  return {q * t * e, e};
+}
+
+// erf(x) = sign(x) (1 - erfc(|x|))
 __device__ __forceinline__ float erf_as7126(float x) {
-  const float u = fabsf(x);
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
-  float q = fmaf(t, 1.061405429f, -1.453152027f);
-  q = fmaf(t, q, 1.421413741f);
-  q = fmaf(t, q, -0.284496736f);
-  q = fmaf(t, q, 0.254829592f);
-  const float y = fmaf(-q * t, __expf(-u * u), 1.0f);
-  return copysignf(y, x);
+  return copysignf(fmaf(-2.0f, half_erfc_as7126(fabsf(x)).h, 1.0f), x);
 }
 
 namespace {
 
-// GELU, erf form: z Phi(z) = z (1 + erf(z / sqrt 2)) / 2, and its derivative
-// Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as7126(z * 0.70710678118654752f)); }
+// GELU, erf form: z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, i.e.
+// 1 - erfc(|z| / sqrt 2) / 2 for z >= 0 and erfc(|z| / sqrt 2) / 2 below; its
+// derivative Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
+__device__ __forceinline__ float gelu(float z) {
+  const float h = half_erfc_as7126(fabsf(z) * 0.70710678118654752f).h;
+  return z * (z >= 0.0f ? 1.0f - h : h);
+}
 
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erf_as7126(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+  const HalfErfc r = half_erfc_as7126(fabsf(z) * 0.70710678118654752f);
+  return (z >= 0.0f ? 1.0f - r.h : r.h) + z * 0.39894228040143268f * r.e;
 }
 
 __global__ void k_erf_check(const float* __restrict__ x, int n, float* __restrict__ out) {
@@ -540,6 +582,253 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_ws(const __grid_constant
   }
 }
 
+// ---- fused network inference ----------------------------------------------------
+// Every layer of the network for 128-row tiles in one persistent kernel: the
+// activations of a tile never leave shared memory.  A tile's hidden
+// activations (128 rows x up to 256 BF16) sit in its 64 KB buffer in the same
+// 128-byte-swizzled K-major layout TMA would give them, so the next layer's
+// tcgen05.mma reads them directly as its A operand; the input rows and every
+// weight tile stream through a ring of 32 KB stages by TMA.  Two tiles are in
+// flight per CTA (slots 0 and 1, each with its own activation buffer and
+// 256-column accumulator in tensor memory): while the epilogue warps drain one
+// slot's accumulator (bias, GELU, BF16 into the slot's buffer; bias and
+// float32 to global memory for the output layer), the MMAs of the other
+// slot's next layer run.  A job is one (tile, layer, N chunk); hidden layers
+// are one chunk (N <= 256), the output layer is split into chunks of at most
+// 256 columns.  Per slot, jobs run in order: MMA(j) -> epilogue(j) ->
+// MMA(j + 1), so a hidden layer's epilogue overwrites the activations the
+// layer's MMAs have finished reading.  The arithmetic of every output element
+// (K order of the MMAs, bias, GELU, BF16 rounding) is that of the per-layer
+// kernels, so both paths give the same bits.
+//   full[s] / empty[s]        producer <-> MMA, ring stage s
+//   acc_full[a] / acc_empty[a]  MMA <-> epilogue, slot a
+// Every wait is bounded as in the kernels above.
+constexpr int kFusedRing = 3;
+constexpr int kFusedStage = 32768;
+constexpr int kFusedHBytes = 65536;
+constexpr size_t kFusedSmem = 2 * (size_t)kFusedHBytes + (size_t)kFusedRing * kFusedStage + 1024;
+
+struct FusedMaps {
+  CUtensorMap x;
+  CUtensorMap w[kFusedMaxLayers];
+};
+
+// Walks one CTA's jobs in the order all three roles share: tile pairs
+// (t0, t0 + grid), then layers, N chunks and slots.  kWarp: the caller is a
+// whole warp whose job runs warp-collective instructions, so the failure flag
+// is read once for the warp.
+template <bool kWarp, typename F>
+__device__ __forceinline__ void fused_jobs(const FusedNet& net, volatile int* failed, F&& job) {
+  const int tiles = (net.M + kBM - 1) / kBM;
+  for (int t0 = blockIdx.x; t0 < tiles; t0 += 2 * gridDim.x) {
+    const int t1 = t0 + gridDim.x;
+    const int slots = t1 < tiles ? 2 : 1;
+    for (int l = 0; l < net.L; ++l) {
+      const int nch = net.dims[l + 1] / net.chunk[l];
+      for (int c = 0; c < nch; ++c)
+        for (int sl = 0; sl < slots; ++sl) {
+          const int stop = kWarp ? __shfl_sync(0xffffffffu, *failed, 0) : *failed;
+          if (stop) return;
+          if (!job(sl ? t1 : t0, sl, l, c)) {
+            *failed = 1;
+            return;
+          }
+        }
+    }
+  }
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps,
+                                                             const __grid_constant__ FusedNet net,
+                                                             int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* hbuf = smem;                      // [2][64 KB]
+  uint8_t* ring = smem + 2 * kFusedHBytes;   // [kFusedRing][32 KB]
+  __shared__ __align__(8) uint64_t full[kFusedRing], empty[kFusedRing], acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int failed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int s = 0; s < kFusedRing; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kWsEpiWarps);
+    }
+    mbar_init(&mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(2 * kWsAccCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: per job, (input tile, weight tile) per K tile of layer 0,
+    // a weight tile per K tile of the later layers ----
+    int it = 0;
+    auto stage = [&](const CUtensorMap* map, int c0, int c1, uint32_t bytes) -> bool {
+      const int s = it % kFusedRing;
+      const uint32_t ph = (uint32_t)(it / kFusedRing) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) return false;
+      mbar_expect_tx(&full[s], bytes);
+      tma_load_2d(ring + s * kFusedStage, map, &full[s], c0, c1);
+      ++it;
+      return true;
+    };
+    fused_jobs<false>(net, &failed, [&](int tile, int, int l, int c) -> bool {
+      const int kt = (net.dims[l] + kBK - 1) / kBK, N = net.chunk[l];
+      for (int k = 0; k < kt; ++k) {
+        if (l == 0 && !stage(&maps.x, k * kBK, tile * kBM, kBM * kBK * 2)) return false;
+        if (!stage(&maps.w[l], k * kBK, c * N, (uint32_t)N * kBK * 2)) return false;
+      }
+      return true;
+    });
+    if (failed) {
+      for (int q = max(0, it - kFusedRing); q < it; ++q)
+        mbar_wait(&full[q % kFusedRing], (uint32_t)(q / kFusedRing) & 1u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int it = 0;
+    int jc[2] = {0, 0};
+    auto take = [&](int& s) -> bool {
+      s = it % kFusedRing;
+      const bool ok = mbar_wait(&full[s], (uint32_t)(it / kFusedRing) & 1u);
+      ++it;
+      return ok;
+    };
+    fused_jobs<false>(net, &failed, [&](int, int sl, int l, int) -> bool {
+      if (!mbar_wait(&acc_empty[sl], ((uint32_t)jc[sl] & 1u) ^ 1u)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + (uint32_t)(sl * kWsAccCols);
+      const uint32_t idesc = instr_desc_bf16(net.chunk[l]);
+      const int kt = (net.dims[l] + kBK - 1) / kBK;
+      for (int k = 0; k < kt; ++k) {
+        int sx = -1, sw = -1;
+        if (l == 0 && !take(sx)) return false;
+        if (!take(sw)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ad = smem_desc_sw128(l == 0 ? ring + sx * kFusedStage : hbuf + sl * kFusedHBytes + k * kBM * kBK * 2);
+        const uint64_t bd = smem_desc_sw128(ring + sw * kFusedStage);
+#pragma unroll
+        for (int k4 = 0; k4 < kBK / 16; ++k4) mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc, (k > 0 || k4 > 0) ? 1u : 0u);
+        if (sx >= 0) mma_commit(&empty[sx]);
+        mma_commit(&empty[sw]);
+      }
+      mma_commit(&acc_full[sl]);
+      ++jc[sl];
+      return true;
+    });
+    mma_commit(&mma_done);
+    mbar_wait(&mma_done, 0u);
+  } else if (warp >= 2) {
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. and a
+    // quarter of the job's columns ----
+    const int ew = warp - 2, quarter = warp & 3, cg = ew >> 2;
+    const int rt = 32 * quarter + lane;  // row within the tile
+    int jc[2] = {0, 0};
+    fused_jobs<true>(net, &failed, [&](int tile, int sl, int l, int c) -> bool {
+      const bool ok = mbar_wait(&acc_full[sl], (uint32_t)jc[sl] & 1u);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int N = net.chunk[l], n0 = c * N, cpw = N / 4;
+      const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(sl * kWsAccCols);
+      const float* bias = net.bias[l] + n0;
+      const bool hidden = l + 1 < net.L;
+      const uint32_t hrow = smem_u32(hbuf + sl * kFusedHBytes) + (uint32_t)rt * 128u;
+      if (!hidden) {
+        // output layer: sector-complete float32 stores (8 rows x 32 bytes per
+        // warp store), from the 16-lane accumulator fragment
+#pragma unroll 1
+        for (int cc = cg * cpw; cc < (cg + 1) * cpw; cc += 16) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[8];
+            tmem_ld_rows16(base + ((uint32_t)(16 * h) << 16) + (uint32_t)cc, v);
+#pragma unroll
+            for (int rep = 0; rep < 2; ++rep) {
+              const int col = cc + 8 * rep + 2 * (lane & 3);
+              const float b0 = bias[col], b1 = bias[col + 1];
+#pragma unroll
+              for (int half = 0; half < 2; ++half) {
+                const int r = tile * kBM + 32 * quarter + 16 * h + 8 * half + (lane >> 2);
+                if (r < net.M) {
+                  float* dst = net.y + (int64_t)r * net.ldy + n0 + col;
+                  const float y0 = v[4 * rep + 2 * half] + b0, y1 = v[4 * rep + 2 * half + 1] + b1;
+                  if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+                    *reinterpret_cast<float2*>(dst) = make_float2(y0, y1);
+                  } else {
+                    dst[0] = y0;
+                    dst[1] = y1;
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+#pragma unroll 1
+      for (int cc = cg * cpw; hidden && cc < (cg + 1) * cpw; cc += 16) {
+        float v[16];
+        tmem_ld16(base + (uint32_t)cc, v);
+        if (aligned16(bias + cc)) {
+          float b[16];
+          load16(bias + cc, b);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] += b[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] += bias[cc + k];
+        }
+        {
+          uint32_t w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(gelu(v[2 * k]), gelu(v[2 * k + 1]));
+            w[k] = *reinterpret_cast<const uint32_t*>(&p2);
+          }
+          // columns cc .. cc + 15 = 16-byte chunks j, j + 1 of swizzle atom cc / 64
+          const int col = n0 + cc;
+          const uint32_t atom = hrow + (uint32_t)(col >> 6) * (uint32_t)(kBM * kBK * 2);
+          const uint32_t j = (uint32_t)(col & 63) >> 3, sw = (uint32_t)rt & 7u;
+          st_shared_v4(atom + ((j ^ sw) << 4), w[0], w[1], w[2], w[3]);
+          st_shared_v4(atom + (((j + 1) ^ sw) << 4), w[4], w[5], w[6], w[7]);
+        }
+      }
+      // activations written by these threads become the async proxy's MMA operand
+      if (hidden) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[sl]);
+      ++jc[sl];
+      return true;
+    });
+  }
+  __syncthreads();
+  if (failed && threadIdx.x == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWsAccCols)
+                 : "memory");
+  }
+}
+
 // ---- host side ----------------------------------------------------------------
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -624,6 +913,45 @@ void launch_epi(const void* A, int64_t lda, const void* B, int64_t ldb, int M, i
 
 void gelu_check(const float* x, int n, float* out, cudaStream_t s) {
   k_erf_check<<<(n + 255) / 256, 256, 0, s>>>(x, n, out);
+  CCG_CUDA(cudaGetLastError());
+}
+
+bool mlp_fused_supported(const std::vector<int>& dims) {
+  const int L = (int)dims.size() - 1;
+  if (L < 1 || L > kFusedMaxLayers || dims[0] < 1) return false;
+  for (int l = 1; l < L; ++l)
+    if (dims[l] % 64 != 0 || dims[l] > 256) return false;
+  return dims[L] % 64 == 0;
+}
+
+void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>& dims,
+                       const std::vector<const __nv_bfloat16*>& w, const std::vector<int>& ldk,
+                       const std::vector<const float*>& bias, float* Y, int64_t ldy, int* err, cudaStream_t s) {
+  CCG_CHECK(mlp_fused_supported(dims), CC_ERR_INVALID_ARG, "network shape not covered by the fused kernel");
+  const int L = (int)dims.size() - 1;
+  CCG_CHECK(M > 0 && (int)w.size() == L && (int)ldk.size() == L && (int)bias.size() == L && Y && ldy >= dims[L],
+            CC_ERR_INVALID_ARG, "fused network forward: bad arguments");
+  FusedMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  FusedNet net;
+  net.L = L;
+  net.M = M;
+  net.y = Y;
+  net.ldy = ldy;
+  maps.x = make_map(X, M, dims[0], ldx, kBM);
+  for (int l = 0; l <= L; ++l) net.dims[l] = dims[l];
+  for (int l = 0; l < L; ++l) {
+    int chunk = dims[l + 1];
+    if (l + 1 == L)  // the widest multiple of 64 up to 256 that divides the output width
+      for (chunk = 256; dims[L] % chunk != 0; chunk -= 64) {}
+    net.chunk[l] = chunk;
+    net.bias[l] = bias[l];
+    maps.w[l] = make_map(w[l], dims[l + 1], dims[l], ldk[l], chunk);
+  }
+  set_smem_limit(reinterpret_cast<const void*>(k_mlp_fused), kFusedSmem);
+  const int tiles = (M + kBM - 1) / kBM;
+  const unsigned grid = (unsigned)std::min(tiles, num_sms());
+  k_mlp_fused<<<grid, kWsThreads, kFusedSmem, s>>>(maps, net, err);
   CCG_CUDA(cudaGetLastError());
 }
 

@@ -99,9 +99,13 @@ def _rel(a, b):
 
 
 DIMS = [meshgen.mlp_dims(), [30, 40, 40, 24], [258, 64, 16]]
+# shapes the one-kernel inference covers besides the full network (hidden
+# widths multiples of 64 up to 256, output a multiple of 64)
+FUSED_DIMS = [[100, 128, 128, 192], [8, 256, 64], [300, 192, 192, 192, 192, 320]]
 
 
-@pytest.mark.parametrize("dims", DIMS, ids=["full", "small", "one-hidden"])
+@pytest.mark.parametrize("dims", DIMS + FUSED_DIMS[:1],
+                         ids=["full", "small", "one-hidden", "fused-small"])
 def test_forward_matches_oracle(dims):
     rows = 1000
     net, p = _net(dims, 64, 3)
@@ -126,6 +130,43 @@ def test_forward_at_full_size_on_sampled_rows():
     Ys = Y[torch.from_numpy(pick).cuda()].cpu().double().numpy()
     assert _rel(Ys, Yo) <= 1e-3
     assert np.abs(Ys - Yo).max() <= 1e-2 * np.abs(Yo).max()
+
+
+@pytest.mark.parametrize("dims", [DIMS[0]] + FUSED_DIMS, ids=["full", "three-layer", "in8", "five-layer"])
+@pytest.mark.parametrize("rows", [1, 127, 129, 1000, 2 * 152 * 128 + 5, 112847])
+def test_fused_inference_equals_per_layer_bit_for_bit(dims, rows):
+    """The one-kernel inference (activations in shared memory, two tiles in
+    flight per SM) against one GEMM launch per layer: the same MMAs, bias,
+    GELU and BF16 rounding, so the same bits, for ragged row counts and odd
+    numbers of tiles per SM (2 * 152 * 128 + 5 rows leaves some SMs a tile
+    without a partner)."""
+    if rows == 112847 and dims != DIMS[0]:
+        pytest.skip("full row count on the full network only")
+    net, _ = _net(dims, 64, 21)
+    ld = (dims[0] + 7) // 8 * 8 + 8  # a row stride wider than the inputs
+    X, _ = _bf16(rows, dims[0], 22, ld)
+    Yf = net.forward(X[:, :dims[0]]).clone()
+    net.set_fused(False)
+    Yl = net.forward(X[:, :dims[0]])
+    net.set_fused(True)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Yf).all()
+    assert torch.equal(Yf, Yl)
+
+
+def test_fused_inference_writes_a_strided_output_and_nothing_else():
+    """Y with a leading dimension wider than the output: the padding columns
+    stay untouched, the rows match the dense result bit for bit."""
+    dims = DIMS[0]
+    rows = 777
+    net, _ = _net(dims, 64, 23)
+    X, _ = _bf16(rows, dims[0], 24, 264)
+    dense = net.forward(X).clone()
+    Y = torch.full((rows, dims[-1] + 4), 7.0, dtype=torch.float32, device="cuda")
+    net.forward(X, out=Y[:, :dims[-1]])
+    torch.cuda.synchronize()
+    assert torch.equal(Y[:, :dims[-1]], dense)
+    assert bool((Y[:, dims[-1]:] == 7.0).all())
 
 
 @pytest.mark.parametrize("dims,B", [(DIMS[0], 1000), (DIMS[0], 4096), (DIMS[1], 77), (DIMS[2], 333)],
