@@ -47,17 +47,21 @@ void gemm_tn(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int 
 GemmShape gemm_pick_shape(int M, int N, int K, bool allow_split);
 // The whole network's inference in one kernel (activations kept on chip).
 constexpr int kFusedMaxLayers = 6;
+constexpr int kFusedMaxJobs = 32;           // (layer, N chunk) passes per tile
 struct FusedNet {
   int L = 0, M = 0;
   int dims[kFusedMaxLayers + 1] = {};       // d_in, hidden..., d_out
   int chunk[kFusedMaxLayers] = {};          // N columns per accumulator pass
+  int njobs = 0, shift = 0;                 // passes per tile; slot 1 runs `shift` passes behind slot 0
+  int job_layer[kFusedMaxJobs] = {};
+  int job_chunk[kFusedMaxJobs] = {};
   const float* bias[kFusedMaxLayers] = {};
   float* y = nullptr;
   int64_t ldy = 0;
 };
 // True when the fused kernel covers the shape: at most kFusedMaxLayers layers,
 // hidden widths multiples of 64 up to 256, an output width that is a multiple
-// of 64 (any input width).
+// of 64 (any input width), at most kFusedMaxJobs passes per tile.
 bool mlp_fused_supported(const std::vector<int>& dims);
 // Y[M x d_out] (float32, leading dim ldy) = the network applied to the rows of
 // X (BF16, leading dim ldx, a multiple of 8): per hidden layer GELU(W h + b)

@@ -584,7 +584,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_ws(const __grid_constant
 
 // ---- fused network inference ----------------------------------------------------
 // Every layer of the network for 128-row tiles in one persistent kernel: the
-// activations of a tile never leave shared memory.  A tile's hidden
+// activations of a tile never leave shared memory.  CTAs run in clusters of
+// two on a pair of SMs, each taking 128 rows of a 256-row super-tile through
+// the same sequence of jobs: each CTA fetches half the rows of every weight
+// tile and multicasts it into the same ring stage of both CTAs, so the pair
+// reads each weight tile from L2 once; a stage is released when both CTAs'
+// MMAs have read it (each MMA thread's commit arrives on both CTAs' empty
+// barrier).  A tile's hidden
 // activations (128 rows x up to 256 BF16) sit in its 64 KB buffer in the same
 // 128-byte-swizzled K-major layout TMA would give them, so the next layer's
 // tcgen05.mma reads them directly as its A operand; the input rows and every
@@ -600,7 +606,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_gemm_ws(const __grid_constant
 // layer's MMAs have finished reading.  The arithmetic of every output element
 // (K order of the MMAs, bias, GELU, BF16 rounding) is that of the per-layer
 // kernels, so both paths give the same bits.
-//   full[s] / empty[s]        producer <-> MMA, ring stage s
+//   full[s] / empty[s]        producers <-> MMA, ring stage s (empty counts
+//                             both CTAs' MMA commits)
 //   acc_full[a] / acc_empty[a]  MMA <-> epilogue, slot a
 // Every wait is bounded as in the kernels above.
 constexpr int kFusedRing = 3;
@@ -613,28 +620,40 @@ struct FusedMaps {
   CUtensorMap w[kFusedMaxLayers];
 };
 
-// Walks one CTA's jobs in the order all three roles share: tile pairs
-// (t0, t0 + grid), then layers, N chunks and slots.  kWarp: the caller is a
-// whole warp whose job runs warp-collective instructions, so the failure flag
-// is read once for the warp.
+// Walks one CTA's jobs in the order all three roles (and both CTAs of the
+// cluster) share.  The cluster's 256-row super-tiles t = cluster + k clusters
+// alternate between the slots (k even: slot 0), each slot's jobs are its
+// tiles' (layer, chunk) lists in turn, and the slots run half a tile's jobs
+// apart: net.shift jobs of slot 0 first, then one job of each slot in turn.
+// So consecutive epilogue jobs alternate between the output layer's stores
+// and a hidden layer's arithmetic, and one slot's MMAs run while the other
+// slot's epilogue does.  kWarp: the caller is a whole warp whose job runs
+// warp-collective instructions, so the failure flag is read once for the
+// warp.
 template <bool kWarp, typename F>
 __device__ __forceinline__ void fused_jobs(const FusedNet& net, volatile int* failed, F&& job) {
-  const int tiles = (net.M + kBM - 1) / kBM;
-  for (int t0 = blockIdx.x; t0 < tiles; t0 += 2 * gridDim.x) {
-    const int t1 = t0 + gridDim.x;
-    const int slots = t1 < tiles ? 2 : 1;
-    for (int l = 0; l < net.L; ++l) {
-      const int nch = net.dims[l + 1] / net.chunk[l];
-      for (int c = 0; c < nch; ++c)
-        for (int sl = 0; sl < slots; ++sl) {
-          const int stop = kWarp ? __shfl_sync(0xffffffffu, *failed, 0) : *failed;
-          if (stop) return;
-          if (!job(sl ? t1 : t0, sl, l, c)) {
-            *failed = 1;
-            return;
-          }
-        }
+  const int tiles = (net.M + 2 * kBM - 1) / (2 * kBM);
+  const int clusters = (int)gridDim.x >> 1, cid = (int)blockIdx.x >> 1;
+  const int mine = cid < tiles ? (tiles - cid + clusters - 1) / clusters : 0;
+  const int J = net.njobs;
+  const int n[2] = {(mine + 1) / 2 * J, mine / 2 * J};
+  int next[2] = {0, 0};
+  auto run = [&](int sl) -> bool {
+    const int stop = kWarp ? __shfl_sync(0xffffffffu, *failed, 0) : *failed;
+    if (stop) return false;
+    const int i = next[sl]++;
+    const int q = i % J;
+    if (!job(cid + (2 * (i / J) + sl) * clusters, sl, net.job_layer[q], net.job_chunk[q])) {
+      *failed = 1;
+      return false;
     }
+    return true;
+  };
+  while (next[0] < n[0] && next[0] < net.shift)
+    if (!run(0)) return;
+  while (next[0] < n[0] || next[1] < n[1]) {
+    if (next[1] < n[1] && !run(1)) return;
+    if (next[0] < n[0] && !run(0)) return;
   }
 }
 
@@ -642,7 +661,36 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-__global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps,
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA tile load delivered to the same shared-memory offset of every CTA in
+// mask, each CTA's mbarrier at the same offset receiving the bytes it got.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// Arrives (once) on the mbarrier at this offset in every CTA of mask when this
+// thread's earlier tcgen05 operations have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(smem_u32(bar)), "h"(mask)
+               : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps,
                                                              const __grid_constant__ FusedNet net,
                                                              int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -658,7 +706,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_consta
     failed = 0;
     for (int s = 0; s < kFusedRing; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], 2);  // both CTAs' MMAs
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -675,27 +723,39 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_consta
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // the peer's barriers are initialised before anything multicasts to them
+  cluster_sync_all();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
+  const int rank = (int)cluster_rank();
+  const int row0 = rank * kBM;  // this CTA's rows within a 256-row super-tile
 
   if (warp == 0 && lane == 0) {
     // ---- producer: per job, (input tile, weight tile) per K tile of layer 0,
-    // a weight tile per K tile of the later layers ----
+    // a weight tile per K tile of the later layers.  Input rows are this
+    // CTA's own; of each N x 64 weight tile this CTA fetches rows
+    // [rank N / 2, (rank + 1) N / 2) for both CTAs, the peer the other half ----
     int it = 0;
-    auto stage = [&](const CUtensorMap* map, int c0, int c1, uint32_t bytes) -> bool {
+    auto stage = [&](bool weight, const CUtensorMap* map, int c0, int c1, int N) -> bool {
       const int s = it % kFusedRing;
       const uint32_t ph = (uint32_t)(it / kFusedRing) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u)) return false;
-      mbar_expect_tx(&full[s], bytes);
-      tma_load_2d(ring + s * kFusedStage, map, &full[s], c0, c1);
+      uint8_t* dst = ring + s * kFusedStage;
+      if (weight) {
+        mbar_expect_tx(&full[s], (uint32_t)N * kBK * 2);  // both halves land here
+        tma_load_2d_mc(dst + rank * (N / 2) * kBK * 2, map, &full[s], c0, c1 + rank * (N / 2), (uint16_t)3);
+      } else {
+        mbar_expect_tx(&full[s], kBM * kBK * 2);
+        tma_load_2d(dst, map, &full[s], c0, c1);
+      }
       ++it;
       return true;
     };
     fused_jobs<false>(net, &failed, [&](int tile, int, int l, int c) -> bool {
       const int kt = (net.dims[l] + kBK - 1) / kBK, N = net.chunk[l];
       for (int k = 0; k < kt; ++k) {
-        if (l == 0 && !stage(&maps.x, k * kBK, tile * kBM, kBM * kBK * 2)) return false;
-        if (!stage(&maps.w[l], k * kBK, c * N, (uint32_t)N * kBK * 2)) return false;
+        if (l == 0 && !stage(false, &maps.x, k * kBK, tile * 2 * kBM + row0, kBM)) return false;
+        if (!stage(true, &maps.w[l], k * kBK, c * N, N)) return false;
       }
       return true;
     });
@@ -728,8 +788,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_consta
         const uint64_t bd = smem_desc_sw128(ring + sw * kFusedStage);
 #pragma unroll
         for (int k4 = 0; k4 < kBK / 16; ++k4) mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc, (k > 0 || k4 > 0) ? 1u : 0u);
-        if (sx >= 0) mma_commit(&empty[sx]);
-        mma_commit(&empty[sw]);
+        if (sx >= 0) mma_commit_mc(&empty[sx], (uint16_t)3);
+        mma_commit_mc(&empty[sw], (uint16_t)3);
       }
       mma_commit(&acc_full[sl]);
       ++jc[sl];
@@ -744,13 +804,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_consta
     const int rt = 32 * quarter + lane;  // row within the tile
     int jc[2] = {0, 0};
     fused_jobs<true>(net, &failed, [&](int tile, int sl, int l, int c) -> bool {
+      const bool hidden = l + 1 < net.L;
       const bool ok = mbar_wait(&acc_full[sl], (uint32_t)jc[sl] & 1u);
       if (!__all_sync(0xffffffffu, ok)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int N = net.chunk[l], n0 = c * N, cpw = N / 4;
       const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(sl * kWsAccCols);
       const float* bias = net.bias[l] + n0;
-      const bool hidden = l + 1 < net.L;
       const uint32_t hrow = smem_u32(hbuf + sl * kFusedHBytes) + (uint32_t)rt * 128u;
       if (!hidden) {
         // output layer: sector-complete float32 stores (8 rows x 32 bytes per
@@ -767,7 +827,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_consta
               const float b0 = bias[col], b1 = bias[col + 1];
 #pragma unroll
               for (int half = 0; half < 2; ++half) {
-                const int r = tile * kBM + 32 * quarter + 16 * h + 8 * half + (lane >> 2);
+                const int r = tile * 2 * kBM + row0 + 32 * quarter + 16 * h + 8 * half + (lane >> 2);
                 if (r < net.M) {
                   float* dst = net.y + (int64_t)r * net.ldy + n0 + col;
                   const float y0 = v[4 * rep + 2 * half] + b0, y1 = v[4 * rep + 2 * half + 1] + b1;
@@ -822,6 +882,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_consta
   }
   __syncthreads();
   if (failed && threadIdx.x == 0) atomicExch(err, 1);
+  // neither CTA leaves while the peer may still multicast into its ring or
+  // commit to its barriers
+  cluster_sync_all();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWsAccCols)
@@ -921,7 +984,8 @@ bool mlp_fused_supported(const std::vector<int>& dims) {
   if (L < 1 || L > kFusedMaxLayers || dims[0] < 1) return false;
   for (int l = 1; l < L; ++l)
     if (dims[l] % 64 != 0 || dims[l] > 256) return false;
-  return dims[L] % 64 == 0;
+  // one job per hidden layer, output chunks of at least 64 columns
+  return dims[L] % 64 == 0 && (L - 1) + dims[L] / 64 <= kFusedMaxJobs;
 }
 
 void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>& dims,
@@ -945,12 +1009,20 @@ void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>
     if (l + 1 == L)  // the widest multiple of 64 up to 256 that divides the output width
       for (chunk = 256; dims[L] % chunk != 0; chunk -= 64) {}
     net.chunk[l] = chunk;
+    for (int c = 0; c < dims[l + 1] / chunk; ++c) {
+      CCG_CHECK(net.njobs < kFusedMaxJobs, CC_ERR_INVALID_ARG, "network shape not covered by the fused kernel");
+      net.job_layer[net.njobs] = l;
+      net.job_chunk[net.njobs] = c;
+      ++net.njobs;
+    }
     net.bias[l] = bias[l];
-    maps.w[l] = make_map(w[l], dims[l + 1], dims[l], ldk[l], chunk);
+    maps.w[l] = make_map(w[l], dims[l + 1], dims[l], ldk[l], chunk / 2);  // each CTA of a pair fetches half
   }
+  net.shift = net.njobs / 2;
   set_smem_limit(reinterpret_cast<const void*>(k_mlp_fused), kFusedSmem);
-  const int tiles = (M + kBM - 1) / kBM;
-  const unsigned grid = (unsigned)std::min(tiles, num_sms());
+  // clusters of two CTAs (one per SM), one 256-row super-tile pair at a time
+  const int tiles = (M + 2 * kBM - 1) / (2 * kBM);
+  const unsigned grid = 2u * (unsigned)std::max(1, std::min(tiles, num_sms() / 2));
   k_mlp_fused<<<grid, kWsThreads, kFusedSmem, s>>>(maps, net, err);
   CCG_CUDA(cudaGetLastError());
 }
