@@ -147,20 +147,26 @@ __device__ __forceinline__ float exp2_approx(float x) {
 //   t = 1 / (1 + p u), |error| <= 1.5e-7,
 // with the a_k halved (exact in binary), and exp(-u^2) = 2^(-u^2 log2 e).
 // Branch-free: one reciprocal, one exponential, five FMAs.  Its error is ~1e-4
-// of a BF16 rounding step, where the activations it feeds are stored.
+// of a BF16 rounding step, where the activations it feeds are stored.  The
+// operations are the non-contracting _rn forms, one per step, so the
+// two-wide version below (fp32x2 instructions) gives the same bits.
+constexpr float kAsP = 0.3275911f, kAsA5 = 0.5307027145f, kAsA4 = -0.7265760135f, kAsA3 = 0.7107068705f,
+                kAsA2 = -0.142248368f, kAsA1 = 0.127414796f, kNegLog2e = -1.4426950408889634f,
+                kRsqrt2 = 0.70710678118654752f;
+
 struct HalfErfc {
   float h;  // erfc(u) / 2
   float e;  // exp(-u^2)
 };
 
 __device__ __forceinline__ HalfErfc half_erfc_as7126(float u) {
-  const float t = rcp_approx(fmaf(0.3275911f, u, 1.0f));
-  float q = fmaf(t, 0.5307027145f, -0.7265760135f);
-  q = fmaf(t, q, 0.7107068705f);
-  q = fmaf(t, q, -0.142248368f);
-  q = fmaf(t, q, 0.127414796f);
-  const float e = exp2_approx(u * (u * -1.4426950408889634f));
-  return {q * t * e, e};
+  const float t = rcp_approx(__fmaf_rn(kAsP, u, 1.0f));
+  float q = __fmaf_rn(t, kAsA5, kAsA4);
+  q = __fmaf_rn(t, q, kAsA3);
+  q = __fmaf_rn(t, q, kAsA2);
+  q = __fmaf_rn(t, q, kAsA1);
+  const float e = exp2_approx(__fmul_rn(u, __fmul_rn(u, kNegLog2e)));
+  return {__fmul_rn(__fmul_rn(q, t), e), e};
 }
 
 // erf(x) = sign(x) (1 - erfc(|x|))
@@ -171,15 +177,35 @@ __device__ __forceinline__ float erf_as7126(float x) {
 namespace {
 
 // GELU, erf form: z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, i.e.
-// 1 - erfc(|z| / sqrt 2) / 2 for z >= 0 and erfc(|z| / sqrt 2) / 2 below; its
-// derivative Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
+// 1 - h for z >= 0 and h below, h = erfc(|z| / sqrt 2) / 2; written
+// branch-free as z / 2 + |z| (1/2 - h).  Its derivative Phi(z) + z phi(z),
+// phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
 __device__ __forceinline__ float gelu(float z) {
-  const float h = half_erfc_as7126(fabsf(z) * 0.70710678118654752f).h;
-  return z * (z >= 0.0f ? 1.0f - h : h);
+  const float az = fabsf(z);
+  const float h = half_erfc_as7126(__fmul_rn(az, kRsqrt2)).h;
+  return __fmaf_rn(az, __fadd_rn(0.5f, -h), __fmul_rn(0.5f, z));
+}
+
+// gelu of two values with fp32x2 instructions (the MUFU steps stay scalar):
+// the same operations as gelu(), so the same bits
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  const float2 az = make_float2(fabsf(z.x), fabsf(z.y));
+  const float2 u = __fmul2_rn(az, make_float2(kRsqrt2, kRsqrt2));
+  const float2 d = __ffma2_rn(make_float2(kAsP, kAsP), u, make_float2(1.0f, 1.0f));
+  const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  float2 q = __ffma2_rn(t, make_float2(kAsA5, kAsA5), make_float2(kAsA4, kAsA4));
+  q = __ffma2_rn(t, q, make_float2(kAsA3, kAsA3));
+  q = __ffma2_rn(t, q, make_float2(kAsA2, kAsA2));
+  q = __ffma2_rn(t, q, make_float2(kAsA1, kAsA1));
+  const float2 w = __fmul2_rn(u, __fmul2_rn(u, make_float2(kNegLog2e, kNegLog2e)));
+  const float2 e = make_float2(exp2_approx(w.x), exp2_approx(w.y));
+  const float2 h = __fmul2_rn(__fmul2_rn(q, t), e);
+  return __ffma2_rn(az, __fadd2_rn(make_float2(0.5f, 0.5f), make_float2(-h.x, -h.y)),
+                    __fmul2_rn(make_float2(0.5f, 0.5f), z));
 }
 
 __device__ __forceinline__ float gelu_grad(float z) {
-  const HalfErfc r = half_erfc_as7126(fabsf(z) * 0.70710678118654752f);
+  const HalfErfc r = half_erfc_as7126(fabsf(z) * kRsqrt2);
   return (z >= 0.0f ? 1.0f - r.h : r.h) + z * 0.39894228040143268f * r.e;
 }
 
@@ -847,20 +873,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
       for (int cc = cg * cpw; hidden && cc < (cg + 1) * cpw; cc += 16) {
         float v[16];
         tmem_ld16(base + (uint32_t)cc, v);
+        float b[16];
         if (aligned16(bias + cc)) {
-          float b[16];
           load16(bias + cc, b);
-#pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] += b[k];
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] += bias[cc + k];
+          for (int k = 0; k < 16; ++k) b[k] = bias[cc + k];
         }
         {
           uint32_t w[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const __nv_bfloat162 p2 = __floats2bfloat162_rn(gelu(v[2 * k]), gelu(v[2 * k + 1]));
+            const float2 g = gelu2(__fadd2_rn(make_float2(v[2 * k], v[2 * k + 1]), make_float2(b[2 * k], b[2 * k + 1])));
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(g.x, g.y);
             w[k] = *reinterpret_cast<const uint32_t*>(&p2);
           }
           // columns cc .. cc + 15 = 16-byte chunks j, j + 1 of swizzle atom cc / 64
