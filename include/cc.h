@@ -522,13 +522,16 @@ cc_status cc_mlp_load(cc_mlp* net, const char* path);
  * Any number of rows; the inference workspace grows as needed. */
 cc_status cc_mlp_forward(cc_mlp* net, const void* X, int64_t ldx, int64_t rows, float* Y, int64_t ldy);
 
-/* Inference kernel of cc_mlp_forward and of the learned-basis build.  on != 0
+/* Inference kernel of cc_mlp_forward and of the learned-basis build.  on = 1
  * (the default): one persistent kernel runs every layer of 128-row tiles with
- * the hidden activations kept in shared memory (networks of at most 6 layers
- * whose hidden widths are multiples of 64 up to 256 and whose output width is
- * a multiple of 64; other shapes take the per-layer kernels).  on == 0: one
- * GEMM launch per layer, activations through device memory.  Both give the
- * same bits. */
+ * the hidden activations kept in shared memory, SMs in pairs that share each
+ * weight tile by TMA multicast (networks of at most 6 layers whose hidden
+ * widths are multiples of 64 up to 256 and whose output width is a multiple
+ * of 64; other shapes take the per-layer kernels).  on = 2: the same with
+ * M = 256 MMAs over each SM pair (tcgen05 cta_group::2), each SM holding half
+ * of every weight tile.  on = 0: one GEMM launch per layer, activations
+ * through device memory.  All three give the same bits; any other value is
+ * CC_ERR_INVALID_ARG. */
 cc_status cc_mlp_set_fused(cc_mlp* net, int32_t on);
 
 /* Mean squared error over rows x d_out against T (device float32 [rows x

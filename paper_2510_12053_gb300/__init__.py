@@ -531,9 +531,10 @@ class MLP:
         _check(lib().cc_mlp_get_params(self._h, p.ctypes.data, p.size))
         return p
 
-    def set_fused(self, on: bool = True):
-        """Inference in one kernel for every layer (True, the default) or one GEMM per layer."""
-        _check(lib().cc_mlp_set_fused(self._h, 1 if on else 0))
+    def set_fused(self, on=True):
+        """Inference kernel: one kernel for every layer (True or 1: SM pairs share weight tiles by
+        multicast; 2: SM-pair MMAs) or one GEMM per layer (False or 0)."""
+        _check(lib().cc_mlp_set_fused(self._h, int(on)))
 
     def forward(self, X, out=None):
         """Y [rows, d_out] float32 for BF16 inputs X [rows, >= d_in] (row stride a multiple of 8)."""

@@ -468,7 +468,7 @@ struct MlpNet {
   int64_t adam_t = 0;
   DBuf<bf16> inf_h[2];
   int64_t inf_rows = 0;
-  bool fused_inference = true;  // one kernel for every layer where the shape allows
+  int fused_inference = 1;  // 0: one GEMM per layer; 1, 2: one kernel for every layer (2: SM-pair MMAs)
 
   int d_in() const { return dims.front(); }
   int d_out() const { return dims.back(); }
@@ -588,7 +588,7 @@ struct MlpNet {
         w[l] = w16[l].p;
         b[l] = params.p + off_b[l];
       }
-      mlp_forward_fused(X, ldx, (int)rows, dims, w, ldk, b, Y, ldy, err.p, stream);
+      mlp_forward_fused(X, ldx, (int)rows, dims, w, ldk, b, Y, ldy, err.p, stream, fused_inference == 2);
       return;
     }
     int hmax = 8;
@@ -909,7 +909,8 @@ cc_status cc_mlp_forward(cc_mlp* net, const void* X, int64_t ldx, int64_t rows, 
 cc_status cc_mlp_set_fused(cc_mlp* net, int32_t on) {
   CC_API_BODY("cc_mlp_set_fused", {
     CCG_CHECK(net, CC_ERR_INVALID_ARG, "NULL argument");
-    net->fused_inference = on != 0;
+    CCG_CHECK(on >= 0 && on <= 2, CC_ERR_INVALID_ARG, "inference kernel must be 0, 1 or 2");
+    net->fused_inference = on;
   })
 }
 

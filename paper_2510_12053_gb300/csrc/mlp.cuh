@@ -67,9 +67,13 @@ bool mlp_fused_supported(const std::vector<int>& dims);
 // X (BF16, leading dim ldx, a multiple of 8): per hidden layer GELU(W h + b)
 // rounded to BF16, the output layer W h + b; w[l] is the BF16 [d_{l+1} x ldk[l]]
 // weight, bias[l] the float32 bias.  Bitwise the same as the per-layer GEMMs.
+// pair: M = 256 MMAs over SM pairs (cta_group::2), each SM holding half of
+// every weight tile; otherwise M = 128 per SM with the weight tiles
+// multicast to both SMs of a pair.
 void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>& dims,
                        const std::vector<const __nv_bfloat16*>& w, const std::vector<int>& ldk,
-                       const std::vector<const float*>& bias, float* Y, int64_t ldy, int* err, cudaStream_t s);
+                       const std::vector<const float*>& bias, float* Y, int64_t ldy, int* err, cudaStream_t s,
+                       bool pair);
 // out[3k .. 3k+2] = (erf, GELU, GELU') of x[k] with the epilogues' arithmetic
 void gelu_check(const float* x, int n, float* out, cudaStream_t s);
 

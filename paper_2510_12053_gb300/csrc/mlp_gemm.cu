@@ -126,6 +126,28 @@ __device__ __forceinline__ void tmem_ld_rows16(uint32_t taddr, float (&v)[8]) {
   for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// Both 16-lane halves of a warp's 32 lanes, 16 columns: v[0..7] lanes 0..15,
+// v[8..15] lanes 16..31 (tmem_ld_rows16 layout each), one wait for both.
+__device__ __forceinline__ void tmem_ld_rows32(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                 "=r"(r[15])
+               : "r"(taddr + (16u << 16)));
+  // the wait names the registers (in-out), so nothing reads them before it
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 }  // namespace
 
 // Hardware approximations (flush to zero): reciprocal and 2^x.
@@ -708,6 +730,53 @@ __device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map
       : "memory");
 }
 
+// Shared-memory address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// mbar_wait for barriers that other CTAs of the cluster arrive on.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// Pair MMA (cta_group::2): D [256 x N] over the two CTAs' tensor memories;
+// A's rows 0..127 come from this CTA's shared memory and rows 128..255 from
+// the peer's at the same offset, B's rows 0..N/2-1 from this CTA and the rest
+// from the peer.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(smem_u32(bar)), "h"(mask)
+               : "memory");
+}
+
 // Arrives (once) on the mbarrier at this offset in every CTA of mask when this
 // thread's earlier tcgen05 operations have completed.
 __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
@@ -716,41 +785,63 @@ __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
                : "memory");
 }
 
+// kPair = false: each CTA runs M = 128 MMAs on its own rows, the weight tiles
+// shared by multicast (3 stages of 32 KB).  kPair = true: the pair runs
+// M = 256 MMAs (cta_group::2, issued by CTA 0) over both CTAs' rows, each
+// CTA holding only its half of every weight tile (6 stages of 16 KB); CTA
+// 1's idle MMA thread forwards its stage arrivals to CTA 0 (pfull), and CTA
+// 1's epilogue warps arrive on CTA 0's acc_empty.
+template <bool kPair>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps,
                                                              const __grid_constant__ FusedNet net,
                                                              int* __restrict__ err) {
+  constexpr int kRing = kPair ? 6 : kFusedRing;
+  constexpr int kStage = kPair ? kFusedStage / 2 : kFusedStage;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* hbuf = smem;                      // [2][64 KB]
-  uint8_t* ring = smem + 2 * kFusedHBytes;   // [kFusedRing][32 KB]
-  __shared__ __align__(8) uint64_t full[kFusedRing], empty[kFusedRing], acc_full[2], acc_empty[2], mma_done;
+  // the ring first: every operand read from it stays inside the allocation
+  uint8_t* ring = smem;                              // [kRing][kStage] (96 KB)
+  uint8_t* hbuf = smem + kFusedRing * kFusedStage;   // [2][64 KB]
+  __shared__ __align__(8) uint64_t full[kRing], pfull[kRing], empty[kRing], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     failed = 0;
-    for (int s = 0; s < kFusedRing; ++s) {
+    for (int s = 0; s < kRing; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);  // both CTAs' MMAs
+      mbar_init(&pfull[s], 1);
+      mbar_init(&empty[s], kPair ? 1 : 2);  // the MMAs that read the stage
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], kWsEpiWarps);
+      mbar_init(&acc_empty[a], kPair ? 2 * kWsEpiWarps : kWsEpiWarps);
     }
     mbar_init(&mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
+  // the peer's barriers are initialised before anything multicasts or
+  // arrives on them, and both CTAs are resident for the pair allocation
+  cluster_sync_all();
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(2 * kWsAccCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    // with cta_group::2, warp 0 of both CTAs allocates collectively (the
+    // same columns in both tensor memories)
+    if constexpr (kPair) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                   ::"r"(smem_u32(&tmem_base_sh)), "r"(2 * kWsAccCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                   ::"r"(smem_u32(&tmem_base_sh)), "r"(2 * kWsAccCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  // the peer's barriers are initialised before anything multicasts to them
-  cluster_sync_all();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
   const int rank = (int)cluster_rank();
@@ -760,14 +851,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
     // ---- producer: per job, (input tile, weight tile) per K tile of layer 0,
     // a weight tile per K tile of the later layers.  Input rows are this
     // CTA's own; of each N x 64 weight tile this CTA fetches rows
-    // [rank N / 2, (rank + 1) N / 2) for both CTAs, the peer the other half ----
+    // [rank N / 2, (rank + 1) N / 2): multicast to both CTAs (kPair false) or
+    // into its own stage only, as its half of B (kPair true) ----
     int it = 0;
     auto stage = [&](bool weight, const CUtensorMap* map, int c0, int c1, int N) -> bool {
-      const int s = it % kFusedRing;
-      const uint32_t ph = (uint32_t)(it / kFusedRing) & 1u;
+      const int s = it % kRing;
+      const uint32_t ph = (uint32_t)(it / kRing) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u)) return false;
-      uint8_t* dst = ring + s * kFusedStage;
-      if (weight) {
+      uint8_t* dst = ring + s * kStage;
+      if (weight && kPair) {
+        mbar_expect_tx(&full[s], (uint32_t)(N / 2) * kBK * 2);
+        tma_load_2d(dst, map, &full[s], c0, c1 + rank * (N / 2));
+      } else if (weight) {
         mbar_expect_tx(&full[s], (uint32_t)N * kBK * 2);  // both halves land here
         tma_load_2d_mc(dst + rank * (N / 2) * kBK * 2, map, &full[s], c0, c1 + rank * (N / 2), (uint16_t)3);
       } else {
@@ -786,42 +881,69 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
       return true;
     });
     if (failed) {
-      for (int q = max(0, it - kFusedRing); q < it; ++q)
-        mbar_wait(&full[q % kFusedRing], (uint32_t)(q / kFusedRing) & 1u);
+      for (int q = max(0, it - kRing); q < it; ++q) mbar_wait(&full[q % kRing], (uint32_t)(q / kRing) & 1u);
     }
+  } else if (warp == 1 && lane == 0 && kPair && rank != 0) {
+    // ---- CTA 1 of a pair: tells CTA 0's MMA thread when each of its stages
+    // has landed ----
+    int it = 0;
+    const uint32_t lead_pfull = cluster_addr(&pfull[0], 0);
+    fused_jobs<false>(net, &failed, [&](int, int, int l, int) -> bool {
+      const int n = ((net.dims[l] + kBK - 1) / kBK) * (l == 0 ? 2 : 1);
+      for (int q = 0; q < n; ++q, ++it) {
+        const int s = it % kRing;
+        if (!mbar_wait(&full[s], (uint32_t)(it / kRing) & 1u)) return false;
+        mbar_arrive_remote(lead_pfull + (uint32_t)(s * sizeof(uint64_t)));
+      }
+      return true;
+    });
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
+    // ---- MMA issuer (CTA 0 of a pair, or every CTA without pairs) ----
     int it = 0;
     int jc[2] = {0, 0};
     auto take = [&](int& s) -> bool {
-      s = it % kFusedRing;
-      const bool ok = mbar_wait(&full[s], (uint32_t)(it / kFusedRing) & 1u);
+      s = it % kRing;
+      const uint32_t ph = (uint32_t)(it / kRing) & 1u;
+      bool ok = mbar_wait(&full[s], ph);
+      if (kPair && ok) ok = mbar_wait_cluster(&pfull[s], ph);
       ++it;
       return ok;
     };
     fused_jobs<false>(net, &failed, [&](int, int sl, int l, int) -> bool {
-      if (!mbar_wait(&acc_empty[sl], ((uint32_t)jc[sl] & 1u) ^ 1u)) return false;
+      const uint32_t eph = ((uint32_t)jc[sl] & 1u) ^ 1u;
+      if (!(kPair ? mbar_wait_cluster(&acc_empty[sl], eph) : mbar_wait(&acc_empty[sl], eph))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + (uint32_t)(sl * kWsAccCols);
-      const uint32_t idesc = instr_desc_bf16(net.chunk[l]);
+      // M = 256 over the pair (kPair) or 128
+      const uint32_t idesc = (instr_desc_bf16(net.chunk[l]) & ~(31u << 24)) | ((uint32_t)((kPair ? 256 : 128) >> 4) << 24);
       const int kt = (net.dims[l] + kBK - 1) / kBK;
       for (int k = 0; k < kt; ++k) {
         int sx = -1, sw = -1;
         if (l == 0 && !take(sx)) return false;
         if (!take(sw)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ad = smem_desc_sw128(l == 0 ? ring + sx * kFusedStage : hbuf + sl * kFusedHBytes + k * kBM * kBK * 2);
-        const uint64_t bd = smem_desc_sw128(ring + sw * kFusedStage);
+        const uint64_t ad = smem_desc_sw128(l == 0 ? ring + sx * kStage : hbuf + sl * kFusedHBytes + k * kBM * kBK * 2);
+        const uint64_t bd = smem_desc_sw128(ring + sw * kStage);
 #pragma unroll
-        for (int k4 = 0; k4 < kBK / 16; ++k4) mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc, (k > 0 || k4 > 0) ? 1u : 0u);
-        if (sx >= 0) mma_commit_mc(&empty[sx], (uint16_t)3);
-        mma_commit_mc(&empty[sw], (uint16_t)3);
+        for (int k4 = 0; k4 < kBK / 16; ++k4) {
+          if constexpr (kPair) mma_bf16_pair(acc, ad + 2 * k4, bd + 2 * k4, idesc, (k > 0 || k4 > 0) ? 1u : 0u);
+          else mma_bf16(acc, ad + 2 * k4, bd + 2 * k4, idesc, (k > 0 || k4 > 0) ? 1u : 0u);
+        }
+        if constexpr (kPair) {
+          if (sx >= 0) mma_commit_pair(&empty[sx], (uint16_t)3);
+          mma_commit_pair(&empty[sw], (uint16_t)3);
+        } else {
+          if (sx >= 0) mma_commit_mc(&empty[sx], (uint16_t)3);
+          mma_commit_mc(&empty[sw], (uint16_t)3);
+        }
       }
-      mma_commit(&acc_full[sl]);
+      if constexpr (kPair) mma_commit_pair(&acc_full[sl], (uint16_t)3);
+      else mma_commit(&acc_full[sl]);
       ++jc[sl];
       return true;
     });
-    mma_commit(&mma_done);
+    if constexpr (kPair) mma_commit_pair(&mma_done, (uint16_t)1);
+    else mma_commit(&mma_done);
     mbar_wait(&mma_done, 0u);
   } else if (warp >= 2) {
     // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. and a
@@ -840,39 +962,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
       const uint32_t hrow = smem_u32(hbuf + sl * kFusedHBytes) + (uint32_t)rt * 128u;
       if (!hidden) {
         // output layer: sector-complete float32 stores (8 rows x 32 bytes per
-        // warp store), from the 16-lane accumulator fragment
+        // warp store), from the 16-lane accumulator fragment; each piece's
+        // bias values (columns cc + 8 rp + 2 (lane % 4) + {0, 1}) are loaded
+        // before its accumulator read
 #pragma unroll 1
         for (int cc = cg * cpw; cc < (cg + 1) * cpw; cc += 16) {
+          float ob[4];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[8];
-            tmem_ld_rows16(base + ((uint32_t)(16 * h) << 16) + (uint32_t)cc, v);
+          for (int k = 0; k < 4; ++k) ob[k] = bias[cc + 8 * (k >> 1) + 2 * (lane & 3) + (k & 1)];
+          float v[16];
+          tmem_ld_rows32(base + (uint32_t)cc, v);
 #pragma unroll
-            for (int rep = 0; rep < 2; ++rep) {
-              const int col = cc + 8 * rep + 2 * (lane & 3);
-              const float b0 = bias[col], b1 = bias[col + 1];
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-              for (int half = 0; half < 2; ++half) {
-                const int r = tile * 2 * kBM + row0 + 32 * quarter + 16 * h + 8 * half + (lane >> 2);
-                if (r < net.M) {
-                  float* dst = net.y + (int64_t)r * net.ldy + n0 + col;
-                  const float y0 = v[4 * rep + 2 * half] + b0, y1 = v[4 * rep + 2 * half + 1] + b1;
-                  if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
-                    *reinterpret_cast<float2*>(dst) = make_float2(y0, y1);
-                  } else {
-                    dst[0] = y0;
-                    dst[1] = y1;
-                  }
+            for (int half = 0; half < 2; ++half) {
+              const int r = tile * 2 * kBM + row0 + 32 * quarter + 16 * h + 8 * half + (lane >> 2);
+              if (r >= net.M) continue;
+#pragma unroll
+              for (int rp = 0; rp < 2; ++rp) {
+                float* dst = net.y + (int64_t)r * net.ldy + n0 + cc + 8 * rp + 2 * (lane & 3);
+                const float y0 = v[8 * h + 4 * rp + 2 * half] + ob[2 * rp];
+                const float y1 = v[8 * h + 4 * rp + 2 * half + 1] + ob[2 * rp + 1];
+                if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+                  *reinterpret_cast<float2*>(dst) = make_float2(y0, y1);
+                } else {
+                  dst[0] = y0;
+                  dst[1] = y1;
                 }
               }
             }
-          }
         }
       }
 #pragma unroll 1
       for (int cc = cg * cpw; hidden && cc < (cg + 1) * cpw; cc += 16) {
-        float v[16];
-        tmem_ld16(base + (uint32_t)cc, v);
+        // bias first, so its load overlaps the accumulator read
         float b[16];
         if (aligned16(bias + cc)) {
           load16(bias + cc, b);
@@ -880,6 +1003,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
 #pragma unroll
           for (int k = 0; k < 16; ++k) b[k] = bias[cc + k];
         }
+        float v[16];
+        tmem_ld16(base + (uint32_t)cc, v);
         {
           uint32_t w[8];
 #pragma unroll
@@ -897,10 +1022,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
         }
       }
       // activations written by these threads become the async proxy's MMA operand
-      if (hidden) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // (all state spaces: with pairs the reader is the other CTA's MMA)
+      if (hidden) asm volatile("fence.proxy.async;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[sl]);
+      if (lane == 0) {
+        if (kPair && rank != 0) mbar_arrive_remote(cluster_addr(&acc_empty[sl], 0));
+        else mbar_arrive(&acc_empty[sl]);
+      }
       ++jc[sl];
       return true;
     });
@@ -912,8 +1041,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kWsThreads, 1) k_mlp
   cluster_sync_all();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWsAccCols)
-                 : "memory");
+    if constexpr (kPair)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWsAccCols)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWsAccCols)
+                   : "memory");
   }
 }
 
@@ -1015,7 +1148,8 @@ bool mlp_fused_supported(const std::vector<int>& dims) {
 
 void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>& dims,
                        const std::vector<const __nv_bfloat16*>& w, const std::vector<int>& ldk,
-                       const std::vector<const float*>& bias, float* Y, int64_t ldy, int* err, cudaStream_t s) {
+                       const std::vector<const float*>& bias, float* Y, int64_t ldy, int* err, cudaStream_t s,
+                       bool pair) {
   CCG_CHECK(mlp_fused_supported(dims), CC_ERR_INVALID_ARG, "network shape not covered by the fused kernel");
   const int L = (int)dims.size() - 1;
   CCG_CHECK(M > 0 && (int)w.size() == L && (int)ldk.size() == L && (int)bias.size() == L && Y && ldy >= dims[L],
@@ -1044,11 +1178,13 @@ void mlp_forward_fused(const void* X, int64_t ldx, int M, const std::vector<int>
     maps.w[l] = make_map(w[l], dims[l + 1], dims[l], ldk[l], chunk / 2);  // each CTA of a pair fetches half
   }
   net.shift = net.njobs / 2;
-  set_smem_limit(reinterpret_cast<const void*>(k_mlp_fused), kFusedSmem);
+  const void* kern = pair ? reinterpret_cast<const void*>(k_mlp_fused<true>) : reinterpret_cast<const void*>(k_mlp_fused<false>);
+  set_smem_limit(kern, kFusedSmem);
   // clusters of two CTAs (one per SM), one 256-row super-tile pair at a time
   const int tiles = (M + 2 * kBM - 1) / (2 * kBM);
   const unsigned grid = 2u * (unsigned)std::max(1, std::min(tiles, num_sms() / 2));
-  k_mlp_fused<<<grid, kWsThreads, kFusedSmem, s>>>(maps, net, err);
+  if (pair) k_mlp_fused<true><<<grid, kWsThreads, kFusedSmem, s>>>(maps, net, err);
+  else k_mlp_fused<false><<<grid, kWsThreads, kFusedSmem, s>>>(maps, net, err);
   CCG_CUDA(cudaGetLastError());
 }
 

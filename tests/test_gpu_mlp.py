@@ -132,23 +132,26 @@ def test_forward_at_full_size_on_sampled_rows():
     assert np.abs(Ys - Yo).max() <= 1e-2 * np.abs(Yo).max()
 
 
+@pytest.mark.parametrize("kind", [1, 2], ids=["multicast", "pair"])
 @pytest.mark.parametrize("dims", [DIMS[0]] + FUSED_DIMS, ids=["full", "three-layer", "in8", "five-layer"])
 @pytest.mark.parametrize("rows", [1, 127, 129, 1000, 2 * 152 * 128 + 5, 112847])
-def test_fused_inference_equals_per_layer_bit_for_bit(dims, rows):
+def test_fused_inference_equals_per_layer_bit_for_bit(dims, rows, kind):
     """The one-kernel inference (activations in shared memory, two tiles in
-    flight per SM) against one GEMM launch per layer: the same MMAs, bias,
-    GELU and BF16 rounding, so the same bits, for ragged row counts and odd
-    numbers of tiles per SM (2 * 152 * 128 + 5 rows leaves some SMs a tile
-    without a partner)."""
+    flight per SM, SM pairs sharing weight tiles by multicast, or SM-pair
+    M = 256 MMAs) against one GEMM launch per layer: the same MMAs, bias, GELU
+    and BF16 rounding, so the same bits, for ragged row counts and odd numbers
+    of 256-row super-tiles per SM pair (2 * 152 * 128 + 5 rows leaves some
+    pairs a super-tile without a partner)."""
     if rows == 112847 and dims != DIMS[0]:
         pytest.skip("full row count on the full network only")
     net, _ = _net(dims, 64, 21)
     ld = (dims[0] + 7) // 8 * 8 + 8  # a row stride wider than the inputs
     X, _ = _bf16(rows, dims[0], 22, ld)
+    net.set_fused(kind)
     Yf = net.forward(X[:, :dims[0]]).clone()
-    net.set_fused(False)
+    net.set_fused(0)
     Yl = net.forward(X[:, :dims[0]])
-    net.set_fused(True)
+    net.set_fused(1)
     torch.cuda.synchronize()
     assert torch.isfinite(Yf).all()
     assert torch.equal(Yf, Yl)
