@@ -53,12 +53,13 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(kernel_class):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary,
-    or None when the kernel source changed since the capture (hash mismatch)."""
+def ncu_traffic(kernel_class, summary=None):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary
+    (the sweep kernels' by default), or None when the kernel source changed
+    since the capture (hash mismatch)."""
     import hashlib
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(summary or PROFILE_SUMMARY).read()
     except OSError:
         return None
     for line in text.splitlines():
@@ -931,23 +932,44 @@ def run_learned(args, stream, dev):
                                 rho_mean=st["rho_mean"], rho_max_kept=st["rho_max"],
                                 rho_quantiles={"p50": rq[0], "p90": rq[1], "p99": rq[2], "max": rq[3]},
                                 acquisition_split_ms={k[3:]: st[k] for k in st if k.startswith("ms_")})
-    # the network's forward pass alone on the cube's inputs (tensor pipe)
+    # the network's forward pass alone on the cube's inputs (tensor pipe), L2
+    # flushed before every timed pass; the one-kernel inference (default), the
+    # SM-pair MMA variant and one GEMM launch per layer
     Xc, _ = m.learned_inputs()
     Yc = net.forward(Xc)
-    times = []
-    for _ in range(10):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        net.forward(Xc, out=Yc)
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-    inf_ms = statistics.median(times)
-    inf_tf = mlp_flops(dims, Xc.shape[0]) / (inf_ms / 1e3) / 1e12
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def time_forward(kind):
+        net.set_fused(kind)
+        for _ in range(3):
+            net.forward(Xc, out=Yc)
+        times = []
+        for _ in range(10):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.forward(Xc, out=Yc)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return statistics.median(times)
+
+    per_layer_ms, pair_ms, inf_ms = time_forward(0), time_forward(2), time_forward(1)
+    del flush
+    inf_flop = mlp_flops(dims, Xc.shape[0])
+    inf_tf = inf_flop / (inf_ms / 1e3) / 1e12
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-    out["inference_roofline"] = {"kernel": "k_gemm_tn (4 tcgen05 GEMMs, fused bias/GELU epilogues)", "bound": "tensor",
-                                 "achieved": inf_tf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": inf_tf / bf16_peak,
-                                 "rows": int(Xc.shape[0]), "ms": inf_ms, "peak_source": peak_src + " (bf16, burst)"}
+    out["inference_roofline"] = {"kernel": "k_mlp_fused (every layer in one persistent tcgen05 kernel, activations in "
+                                           "shared memory, SM pairs sharing weight tiles by TMA multicast)",
+                                 "bound": "tensor", "achieved": inf_tf, "peak": bf16_peak, "unit": "TFLOP/s",
+                                 "frac": inf_tf / bf16_peak, "rows": int(Xc.shape[0]), "ms": inf_ms,
+                                 "l2": "flushed before every timed pass",
+                                 "pair_mma_ms": pair_ms, "pair_mma_tflops": inf_flop / (pair_ms / 1e3) / 1e12,
+                                 "per_layer_ms": per_layer_ms,
+                                 "per_layer_tflops": inf_flop / (per_layer_ms / 1e3) / 1e12,
+                                 "traffic": ncu_traffic("k_mlp_fused",
+                                                        os.path.join(ROOT, "profiles", "mlp_gemm_cube48_rows.md")),
+                                 "peak_source": peak_src + " (bf16, burst)"}
     m.close()
     # coordinate descent: the method without any subspace
     m = fresh()
