@@ -62,7 +62,7 @@ void ensure_state(Mesh& m, cc_precision p) {
   if (p == CC_PREC_FP64) {
     if (!m.f64.gcon.p) {
       m.f64.gcon.alloc(3 * ne);
-      m.f64.hten.alloc(96 * (size_t)m.T);
+      m.f64.hten.alloc(kTetStore * (size_t)m.T);
       m.f64.g.alloc(3 * m.n);
       m.f64.bsr.alloc(12 * m.nnz_up);
       m.f64.cpl.alloc(32 * m.n_free);
@@ -85,7 +85,7 @@ void ensure_state(Mesh& m, cc_precision p) {
       CCG_CUDA(cudaMemsetAsync(m.mx.xt_lo.p, 0, m.n * sizeof(float4), s));
     }
     // the per-tet Hessian store exists only for the gather path
-    if (!rows_from_positions(m) && !m.mx.hten.p) m.mx.hten.alloc(96 * (size_t)m.T);
+    if (!rows_from_positions(m) && !m.mx.hten.p) m.mx.hten.alloc(kTetStore * (size_t)m.T);
   }
 }
 

@@ -86,11 +86,26 @@ struct DBuf {
   }
 };
 
+// Per-tet Hessian store: a tet's ten upper 3x3 blocks, corner pairs (a, b)
+// with a <= b in the order (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2)
+// (2,3) (3,3).  The four diagonal blocks are symmetric and keep their upper
+// triangles (6 values: (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)), the six others
+// all 9 values row-major: 78 values, kTetStore per tet.
+constexpr int kTetStore = 80;
+constexpr bool tet_pair_is_diag(int pair) { return pair == 0 || pair == 4 || pair == 7 || pair == 9; }
+// first value of a pair's block in the tet's record
+constexpr int tet_pair_offset(int pair) {
+  int o = 0;
+  for (int p = 0; p < pair; ++p) o += tet_pair_is_diag(p) ? 6 : 9;
+  return o;
+}
+static_assert(tet_pair_offset(5) == 39 && tet_pair_offset(10) == 78, "per-tet store layout");
+
 // Per-precision solver state: per-(vertex, incident-tet) contributions, the
 // assembled gradient and 3x3-block Hessian, and the basis blocks.
 struct StateF64 {
   DBuf<double> gcon;  // [4T][3]   gradient of tet at each (vertex, slot)
-  DBuf<double> hten;  // [T][96]  the tet's 10 upper 3x3 Hessian blocks (corner pairs a <= b)
+  DBuf<double> hten;  // [T][kTetStore]  the tet's 10 upper 3x3 Hessian blocks (corner pairs a <= b)
   DBuf<double> g;     // [n][3]
   DBuf<double> bsr;   // [nnz_up][12] upper Hessian blocks, rows padded to 4
   DBuf<double> U;     // [sup_total][9]
@@ -100,7 +115,7 @@ struct StateF64 {
 
 struct StateMixed {
   DBuf<float2> gcon;  // [4T][3]   float-float (hi, lo)
-  DBuf<float> hten;   // [T][96]
+  DBuf<float> hten;   // [T][kTetStore]
   DBuf<float> g_hi;   // [n][3]
   DBuf<float> g_lo;   // [n][3]
   DBuf<float> bsr;    // [nnz_up][12]

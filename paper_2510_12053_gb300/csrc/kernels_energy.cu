@@ -86,8 +86,9 @@ __device__ __forceinline__ void hess_block(const T* F, const T (&a_v)[3], const 
 }
 
 // The tet's upper Hessian blocks V K_ab (corner pairs a <= b, order (0,0),
-// (0,1), (0,2), (0,3), (1,1), (1,2), (1,3), (2,2), (2,3), (3,3)), each 3x3
-// row-major: pairs P0 <= pair < P1 into dst[9 (pair - P0) + q].
+// (0,1), (0,2), (0,3), (1,1), (1,2), (1,3), (2,2), (2,3), (3,3)) in the
+// per-tet store's layout (a diagonal block's upper triangle, the others 3x3
+// row-major): pairs P0 <= pair < P1 from dst[0] on.
 template <typename T, int P0 = 0, int P1 = 10>
 __device__ __forceinline__ void tet_hess_blocks(const T* F, const T* C, T s, T mu, T lh, T V, const T (&G)[4][3],
                                                 T* __restrict__ dst) {
@@ -104,8 +105,18 @@ __device__ __forceinline__ void tet_hess_blocks(const T* F, const T* C, T s, T m
       if (pair >= P0 && pair < P1) {
         T K[9];
         hess_block<T>(F, a[va], a[vb], G[va], G[vb], mu, lh, s, K);
+        T* d = dst + (tet_pair_offset(pair) - tet_pair_offset(P0));
+        if (va == vb) {
+          d[0] = V * K[0];
+          d[1] = V * K[1];
+          d[2] = V * K[2];
+          d[3] = V * K[4];
+          d[4] = V * K[5];
+          d[5] = V * K[8];
+        } else {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) dst[9 * (pair - P0) + q] = V * K[q];
+          for (int q = 0; q < 9; ++q) d[q] = V * K[q];
+        }
       }
       ++pair;
     }
@@ -114,29 +125,43 @@ __device__ __forceinline__ void tet_hess_blocks(const T* F, const T* C, T s, T m
 // Hessian staging.  Each thread stages its tet's blocks in shared memory at a
 // per-thread pitch, then the warp copies every live tet's staged values to
 // the per-tet store with coalesced stores (flush).  The SNH blocks are formed
-// and flushed in two halves of five pairs (45 values, half the shared memory
-// per thread, so more warps stay resident); FCR forms all ten at once (its
-// blocks accumulate over the nine directions of dF).  The pitches are odd so
-// that the 32 lanes' k-th values fall in distinct banks.
+// in the store's layout and flushed in two halves of five pairs (39 values,
+// half the shared memory per thread, so more warps stay resident); FCR forms
+// all ten 3x3 blocks at once (they accumulate over the nine directions of dF)
+// and the flush keeps the diagonal blocks' upper triangles.  The pitches are
+// odd so that the 32 lanes' k-th values fall in distinct banks.
 template <bool kFCR>
 struct TetStage {
-  static constexpr int kVals = kFCR ? 90 : 45;
-  static constexpr int kPitch = kFCR ? 91 : 45;
+  static constexpr int kVals = kFCR ? 90 : 39;  // staged values per tet (part)
+  static constexpr int kPitch = kFCR ? 91 : 39;
 };
 
-// Copies the warp's staged values (part `part` of each tet's 90) to the
-// per-tet store; t is this lane's tet (-1: none).  Every lane of the warp
+// Staged index (full 3x3 blocks, 9 per pair) of value e of the store layout.
+__device__ __forceinline__ int full_block_index(int e) {
+  int pair = 0;
+#pragma unroll
+  for (int p = 1; p < 10; ++p) pair += e >= tet_pair_offset(p) ? 1 : 0;
+  const int i = e - tet_pair_offset(pair);
+  const int q = !tet_pair_is_diag(pair) ? i : (i < 3 ? i : (i < 5 ? i + 1 : 8));  // upper triangle 0 1 2 4 5 8
+  return 9 * pair + q;
+}
+
+// Copies the warp's staged values (part `part` of each tet's record; with
+// kFromFull the ten staged 3x3 blocks, compacted to the store's layout) to
+// the per-tet store; t is this lane's tet (-1: none).  Every lane of the warp
 // calls it.
-template <typename T, int kVals, int kPitch>
+template <typename T, int kVals, int kPitch, bool kFromFull = false>
 __device__ __forceinline__ void flush_stage(const T* hstage, int t, int part, T* __restrict__ hten) {
   __syncwarp();
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  constexpr int kOut = kFromFull ? tet_pair_offset(10) : kVals;
   for (int u = 0; u < 32; ++u) {
     const int tu = __shfl_sync(0xffffffffu, t, u);
     if (tu < 0) continue;
     const T* src = hstage + (wbase + u) * kPitch;
 #pragma unroll
-    for (int e = lane; e < kVals; e += 32) hten[(int64_t)tu * 96 + part * kVals + e] = src[e];
+    for (int e = lane; e < kOut; e += 32)
+      hten[(int64_t)tu * kTetStore + part * kVals + e] = src[kFromFull ? full_block_index(e) : e];
   }
   __syncwarp();
 }
@@ -187,7 +212,7 @@ __device__ __forceinline__ void tet_grad_f64_body(const int4* __restrict__ tets,
   double* hdst = hstage + threadIdx.x * (fcr ? TetStage<true>::kPitch : TetStage<false>::kPitch);
   if (fcr) {
     fcr_hess_blocks<double>(kin.F, R, kin.C, kin.J, mu, lh, V, kin.G, hdst);
-    flush_stage<double, TetStage<true>::kVals, TetStage<true>::kPitch>(hstage, t_store, 0, hten);
+    flush_stage<double, TetStage<true>::kVals, TetStage<true>::kPitch, true>(hstage, t_store, 0, hten);
   } else {
     tet_hess_blocks<double, 0, 5>(kin.F, kin.C, s, mu, lh, V, kin.G, hdst);
     flush_stage<double, TetStage<false>::kVals, TetStage<false>::kPitch>(hstage, t_store, 0, hten);
@@ -322,7 +347,7 @@ __device__ __forceinline__ void tet_grad_mixed_body(const int4* __restrict__ tet
   const float V32 = volw32[t];
   if (fcr) {
     fcr_hess_blocks<float>(Ff, R32, Cf, J.hi, mu_f, lh_f, V32, G, hdst);
-    flush_stage<float, TetStage<true>::kVals, TetStage<true>::kPitch>(hstage, t_store, 0, hten);
+    flush_stage<float, TetStage<true>::kVals, TetStage<true>::kPitch, true>(hstage, t_store, 0, hten);
   } else {
     tet_hess_blocks<float, 0, 5>(Ff, Cf, s.hi, mu_f, lh_f, V32, G, hdst);
     flush_stage<float, TetStage<false>::kVals, TetStage<false>::kPitch>(hstage, t_store, 0, hten);
@@ -408,8 +433,9 @@ __device__ __forceinline__ void row_gradient(int j, int e0, int val, int lane, c
 // Every upper block (j, l) of the row sums its sources -- the stored blocks of
 // the incident tets, transposed where the tet lists l before j -- in a fixed
 // order, one lane per (block, component): the diagonal block's 24-odd
-// sources are split over three groups of nine lanes, the other blocks take
-// nine lanes each, three per round.  Blocks are written padded to 3 x 4.  The
+// sources (the tets' diagonal blocks, stored as upper triangles) are split
+// over three groups of nine lanes, the other blocks take nine lanes each,
+// three per round.  Blocks are written padded to 3 x 4.  The
 // row's gradient is the fixed-butterfly sum of its per-(vertex, slot) entries.
 // A row starts from its 32-byte record (row id, block and source ranges,
 // entry range), so the index chain before the stored blocks are read is two
@@ -436,6 +462,9 @@ __global__ void k_row_gather(const int4* __restrict__ row_hdr, int64_t nrows, co
                        dynamic, g64, g_hi, g_lo);
   const int c = lane % 9, grp = lane / 9, r = c / 3, col = c % 3;
   const int tidx = 3 * col + r;
+  // element (r, col) of a stored diagonal block (its upper triangle)
+  const int lo = min(r, col), hi = max(r, col);
+  const int sym = lo == 0 ? hi : (lo == 1 ? hi + 2 : 5);
   // the row's source offsets and per-block ranges, one coalesced pass
   int* roff = rsh + warp * (max_rs + max_up + 1);
   int* rsrc = roff + max_up + 1;
@@ -449,10 +478,7 @@ __global__ void k_row_gather(const int4* __restrict__ row_hdr, int64_t nrows, co
     if (grp < 3) {
       const int s1 = roff[1];
 #pragma unroll 4
-      for (int s = grp; s < s1; s += 3) {
-        const int v = rsrc[s];
-        acc += hten[(v & 0x7fffffff) + (v < 0 ? tidx : c)];
-      }
+      for (int s = grp; s < s1; s += 3) acc += hten[rsrc[s] + sym];  // diagonal pairs: never transposed
     }
     const HT a1 = __shfl_down_sync(0xffffffffu, acc, 9);
     const HT a2 = __shfl_down_sync(0xffffffffu, acc, 18);

@@ -148,7 +148,8 @@ void build_topology(Mesh& m) {
   // ---- per upper block (j, l) of a free row, its sources: the blocks
   //      K_{cj,w} of the incident tets t with tets[t][w] == l, as offsets of
   //      the tet's stored upper block pair (min(cj,w), max(cj,w)) in the
-  //      per-tet Hessian store (96 values per tet), bit 31 set when the
+  //      per-tet Hessian store (kTetStore values per tet; a diagonal pair,
+  //      cj == w, is stored as its upper triangle), bit 31 set when the
   //      stored block must be transposed (cj > w).  Ascending slot order.
   //      The same sources also get a row-local code k * 4 + w (k = the
   //      tet's position in the row's vertex-tet list, w = the corner of l in
@@ -171,7 +172,7 @@ void build_topology(Mesh& m) {
         const int32_t* tv = &m.tets[4 * t];
         for (int w = 0; w < 4; ++w)
           if (tv[w] == col) {
-            const uint32_t off = (uint32_t)(t * 96 + 9 * kPair[cj][w]);
+            const uint32_t off = (uint32_t)(t * kTetStore + tet_pair_offset(kPair[cj][w]));
             rs_src.push_back((int32_t)(off | (cj > w ? 0x80000000u : 0u)));
             rs_loc.push_back((uint16_t)(((e - m.vt_ptr[v]) << 2) | w));
           }
@@ -179,7 +180,8 @@ void build_topology(Mesh& m) {
       rs_ptr[p + 1] = (int32_t)rs_src.size();
     }
   }
-  CCG_CHECK(96 * T < (int64_t(1) << 31), CC_ERR_INVALID_ARG, "mesh too large for 31-bit Hessian offsets");
+  CCG_CHECK((int64_t)kTetStore * T < (int64_t(1) << 31), CC_ERR_INVALID_ARG,
+            "mesh too large for 31-bit Hessian offsets");
 
   m.max_up = 0;
   m.max_rs = 0;
