@@ -311,20 +311,39 @@ __global__ void k_basis_residual(int nrows, const int32_t* __restrict__ rows, co
 // Network kernels
 // ---------------------------------------------------------------------------
 // dst row b = src row idx[b] (BF16 rows of `cols` elements, 16-byte chunks).
-__global__ void k_gather_rows_bf16(const bf16* __restrict__ src, int64_t lds, const int32_t* __restrict__ idx, int B,
-                                   int chunks, bf16* __restrict__ dst, int64_t ldd) {
+// Training minibatch rows: row b of step *step is idx[*step * B + b] (the
+// step counter lives on the device, so one captured step replays for all).
+__global__ void k_gather_rows_bf16(const bf16* __restrict__ src, int64_t lds, const int32_t* __restrict__ idx,
+                                   const int* __restrict__ step, int B, int chunks, bf16* __restrict__ dst,
+                                   int64_t ldd) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= (int64_t)B * chunks) return;
   const int b = (int)(k / chunks), c = (int)(k % chunks);
-  reinterpret_cast<uint4*>(dst + (int64_t)b * ldd)[c] = reinterpret_cast<const uint4*>(src + (int64_t)idx[b] * lds)[c];
+  const int32_t row = idx[(int64_t)*step * B + b];
+  reinterpret_cast<uint4*>(dst + (int64_t)b * ldd)[c] = reinterpret_cast<const uint4*>(src + (int64_t)row * lds)[c];
 }
 
-__global__ void k_gather_rows_f32(const float* __restrict__ src, int64_t lds, const int32_t* __restrict__ idx, int B,
-                                  int cols, float* __restrict__ dst, int64_t ldd) {
+// vec = 4: cols, lds and ldd multiples of 4 and both bases 16-byte aligned
+// (float4 copies); else vec = 1.
+template <int vec>
+__global__ void k_gather_rows_f32(const float* __restrict__ src, int64_t lds, const int32_t* __restrict__ idx,
+                                  const int* __restrict__ step, int B, int cols, float* __restrict__ dst,
+                                  int64_t ldd) {
+  const int per = cols / vec;
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= (int64_t)B * cols) return;
-  const int b = (int)(k / cols), c = (int)(k % cols);
-  dst[(int64_t)b * ldd + c] = src[(int64_t)idx[b] * lds + c];
+  if (k >= (int64_t)B * per) return;
+  const int b = (int)(k / per), c = (int)(k % per) * vec;
+  const float* s = src + (int64_t)idx[(int64_t)*step * B + b] * lds + c;
+  float* d = dst + (int64_t)b * ldd + c;
+  if constexpr (vec == 4) *reinterpret_cast<float4*>(d) = *reinterpret_cast<const float4*>(s);
+  else *d = *s;
+}
+
+// end of a training step: the next step's number and beta^t
+__global__ void k_step_advance(int* __restrict__ step, double* __restrict__ pw, double b1, double b2) {
+  ++*step;
+  pw[0] *= b1;
+  pw[1] *= b2;
 }
 
 // dst [cols x ldd] = src [rows x cols]^T (BF16), 32 x 32 tiles through shared memory.
@@ -350,35 +369,38 @@ __global__ void k_loss_dy(const float* __restrict__ Y, int64_t ldy, const float*
                           int D, float scale, bf16* __restrict__ dy, int64_t lddy, bf16* __restrict__ dyt,
                           int64_t lddt, double* __restrict__ part) {
   __shared__ bf16 tile[32][33];
-  __shared__ double red[256];
+  __shared__ double red[8];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  double acc = 0.0;
+  float acc = 0.0f;  // a thread's four squares in float32; the block's warps' sums in float64
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int r = r0 + k, c = c0 + threadIdx.x;
     if (r < B && c < D) {
       const float d = Y[(int64_t)r * ldy + c] - T[(int64_t)r * ldt + c];
-      acc += (double)d * (double)d;
+      acc = fmaf(d, d, acc);
       const bf16 g = __float2bfloat16_rn(d * scale);
       dy[(int64_t)r * lddy + c] = g;
       tile[k][threadIdx.x] = g;
     }
   }
-  red[tid] = acc;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (threadIdx.x == 0) red[threadIdx.y] = (double)acc;
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int c = c0 + k, r = r0 + threadIdx.x;
     if (r < B && c < D) dyt[(int64_t)c * lddt + r] = tile[threadIdx.x][k];
   }
-  for (int s = 128; s > 0; s >>= 1) {
-    if (tid < s) red[tid] += red[tid + s];
-    __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)blockDim.y; ++w) sum += red[w];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = sum;
   }
-  if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
 // out[0] = scale * sum of part[0..count) in a fixed order (one block).
-__global__ void k_sum_partials(const double* __restrict__ part, int count, double scale, double* __restrict__ out) {
+// out[step ? *step : 0] = scale * sum of part[0 .. count)
+__global__ void k_sum_partials(const double* __restrict__ part, int count, double scale, double* __restrict__ out,
+                               const int* __restrict__ step) {
   __shared__ double red[256];
   double a = 0.0;
   for (int k = threadIdx.x; k < count; k += 256) a += part[k];
@@ -388,19 +410,37 @@ __global__ void k_sum_partials(const double* __restrict__ part, int count, doubl
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = red[0] * scale;
+  if (threadIdx.x == 0) out[step ? *step : 0] = red[0] * scale;
 }
 
 // out[row] = sum over the first `cols` entries of a BF16 row (one warp per row).
+// One block of 256 threads per row (blockIdx.x): thread t sums columns
+// t, t + 256, ... (pairs of columns when the row start and length allow),
+// then warps and the block reduce in a fixed order.
 __global__ void k_rowsum_bf16(const bf16* __restrict__ src, int64_t lds, int rows, int cols, float* __restrict__ out) {
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  __shared__ float wsum[8];
+  const int r = blockIdx.x;
   if (r >= rows) return;
+  const bf16* row = src + (int64_t)r * lds;
   float a = 0.0f;
-  for (int c = lane; c < cols; c += 32) a += __bfloat162float(src[(int64_t)r * lds + c]);
+  if ((lds & 1) == 0 && (cols & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 3) == 0) {
+    const __nv_bfloat162* row2 = reinterpret_cast<const __nv_bfloat162*>(row);
+    for (int c = threadIdx.x; c < cols / 2; c += 256) {
+      const float2 f = __bfloat1622float2(row2[c]);
+      a += f.x + f.y;
+    }
+  } else {
+    for (int c = threadIdx.x; c < cols; c += 256) a += __bfloat162float(row[c]);
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-  if (lane == 0) out[r] = a;
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    out[r] = t;
+  }
 }
 
 // out[k] = sum_s P[s * stride + k], s ascending.
@@ -415,10 +455,17 @@ __global__ void k_sum_slices(const float* __restrict__ P, int S, int64_t stride,
 }
 
 // Adam (Kingma and Ba 2015, Algorithm 1) on the float32 master parameters.
+// Adam with the bias corrections bc1, bc2, or 1 - pw[0], 1 - pw[1] when pw
+// (this step's beta1^t, beta2^t, kept on the device) is given.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       int64_t count, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+                       int64_t count, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                       const double* __restrict__ pw) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= count) return;
+  if (pw) {
+    bc1 = (float)(1.0 - pw[0]);
+    bc2 = (float)(1.0 - pw[1]);
+  }
   const float gk = g[k];
   const float mk = b1 * m[k] + (1.0f - b1) * gk;
   const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
@@ -464,6 +511,9 @@ struct MlpNet {
   DBuf<bf16> xb, xbt;
   DBuf<float> tb;
   DBuf<double> loss_part, loss_hist;
+  DBuf<int> step_dev;  // training step within a cc_mlp_train call
+  DBuf<double> adam_pw;     // that step's beta1^t, beta2^t
+  double adam_pw_host[2] = {0.0, 0.0};
   DBuf<int> err;
   int64_t adam_t = 0;
   DBuf<bf16> inf_h[2];
@@ -515,15 +565,17 @@ struct MlpNet {
     }
   }
 
-  // Loss into *loss_dev, gradient into `grad` (all parameters).  xbt holds X^T.
-  void backward(const float* T, int64_t ldt, int B, double* loss_dev) {
+  // Loss into loss_dev[step ? *step : 0], gradient into `grad` (all
+  // parameters).  xbt holds X^T.
+  void backward(const float* T, int64_t ldt, int B, double* loss_dev, const int* step = nullptr) {
     const int D = d_out();
     {
       const dim3 grid((unsigned)((D + 31) / 32), (unsigned)((B + 31) / 32));
       k_loss_dy<<<grid, dim3(32, 8), 0, stream>>>(y32.p, D, T, ldt, B, D, 2.0f / ((float)B * (float)D), dy16.p, D,
                                                   dyt16.p, ldB, loss_part.p);
       CCG_CUDA(cudaGetLastError());
-      k_sum_partials<<<1, 256, 0, stream>>>(loss_part.p, (int)(grid.x * grid.y), 1.0 / ((double)B * D), loss_dev);
+      k_sum_partials<<<1, 256, 0, stream>>>(loss_part.p, (int)(grid.x * grid.y), 1.0 / ((double)B * D), loss_dev,
+                                            step);
       CCG_CUDA(cudaGetLastError());
     }
     const bf16* dz = dy16.p;
@@ -545,7 +597,7 @@ struct MlpNet {
                                                                         grad.p + off_w[l], K, K, K);
       CCG_CUDA(cudaGetLastError());
       // bias gradient: row sums of dZ^T
-      k_rowsum_bf16<<<blocks_for((int64_t)N * 32, 256), 256, 0, stream>>>(dzt, ldB, N, B, grad.p + off_b[l]);
+      k_rowsum_bf16<<<(unsigned)N, 256, 0, stream>>>(dzt, ldB, N, B, grad.p + off_b[l]);
       CCG_CUDA(cudaGetLastError());
       if (l == 0) break;
       // input gradient dH_{l-1} = dZ W_l, times gelu'(Z_{l-1}) in the epilogue
@@ -568,7 +620,15 @@ struct MlpNet {
     const double bc1 = 1.0 - std::pow((double)o.beta1, (double)adam_t);
     const double bc2 = 1.0 - std::pow((double)o.beta2, (double)adam_t);
     k_adam<<<blocks_for(nparams, 256), 256, 0, stream>>>(params.p, g, adam_m.p, adam_v.p, nparams, o.lr, o.beta1,
-                                                         o.beta2, o.eps, (float)bc1, (float)bc2);
+                                                         o.beta2, o.eps, (float)bc1, (float)bc2, nullptr);
+    CCG_CUDA(cudaGetLastError());
+    refresh_bf16();
+  }
+
+  // Adam with this step's beta^t from the device (the training loop)
+  void adam_dev(const float* g, const cc_adam& o) {
+    k_adam<<<blocks_for(nparams, 256), 256, 0, stream>>>(params.p, g, adam_m.p, adam_v.p, nparams, o.lr, o.beta1,
+                                                         o.beta2, o.eps, 1.0f, 1.0f, adam_pw.p);
     CCG_CUDA(cudaGetLastError());
     refresh_bf16();
   }
@@ -799,6 +859,8 @@ cc_status cc_mlp_create(const cc_mlp_config* cfg, void* stream, cc_mlp** out) {
     net->tb.alloc((size_t)B * cfg->d_out);
     net->loss_part.alloc((size_t)((cfg->d_out + 31) / 32) * ((B + 31) / 32));
     net->loss_hist.alloc(1);
+    net->step_dev.alloc(1);
+    net->adam_pw.alloc(2);
     net->err.alloc(1);
     CCG_CUDA(cudaMemsetAsync(net->err.p, 0, sizeof(int), s));
     CCG_CUDA(cudaStreamSynchronize(s));
@@ -957,19 +1019,74 @@ cc_status cc_mlp_train(cc_mlp* net, const void* X, int64_t ldx, const float* T, 
     net->loss_hist.alloc(steps);
     const int ldxb = round8(net->d_in());
     const int chunks = ldxb / 8;
-    for (int st = 0; st < steps; ++st) {
-      const int32_t* bi = idx + (int64_t)st * batch;
-      k_gather_rows_bf16<<<blocks_for((int64_t)batch * chunks, 256), 256, 0, s>>>(
-          static_cast<const bf16*>(X), ldx, bi, batch, chunks, net->xb.p, ldxb);
+    const int64_t t0 = net->adam_t;
+    int* step = net->step_dev.p;
+    CCG_CUDA(cudaMemsetAsync(step, 0, sizeof(int), s));
+    const bool vec4 = net->d_out() % 4 == 0 && ldt % 4 == 0 && (reinterpret_cast<uintptr_t>(T) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(net->tb.p) & 15) == 0;
+    // beta^t of the first step; each step's advance multiplies them by beta
+    net->adam_pw_host[0] = std::pow((double)opt->beta1, (double)(t0 + 1));
+    net->adam_pw_host[1] = std::pow((double)opt->beta2, (double)(t0 + 1));
+    CCG_CUDA(cudaMemcpyAsync(net->adam_pw.p, net->adam_pw_host, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    // one training step; its minibatch, loss slot and Adam step number come
+    // from the device step counter, which the step advances last
+    auto one_step = [&]() {
+      cudaStream_t q = net->stream;
+      k_gather_rows_bf16<<<blocks_for((int64_t)batch * chunks, 256), 256, 0, q>>>(
+          static_cast<const bf16*>(X), ldx, idx, step, batch, chunks, net->xb.p, ldxb);
       CCG_CUDA(cudaGetLastError());
-      k_gather_rows_f32<<<blocks_for((int64_t)batch * net->d_out(), 256), 256, 0, s>>>(T, ldt, bi, batch, net->d_out(),
-                                                                                      net->tb.p, net->d_out());
+      if (vec4)
+        k_gather_rows_f32<4><<<blocks_for((int64_t)batch * net->d_out() / 4, 256), 256, 0, q>>>(
+            T, ldt, idx, step, batch, net->d_out(), net->tb.p, net->d_out());
+      else
+        k_gather_rows_f32<1><<<blocks_for((int64_t)batch * net->d_out(), 256), 256, 0, q>>>(
+            T, ldt, idx, step, batch, net->d_out(), net->tb.p, net->d_out());
       CCG_CUDA(cudaGetLastError());
       net->transpose_input(net->xb.p, ldxb, batch);
       net->forward_train(net->xb.p, ldxb, batch);
-      net->backward(net->tb.p, net->d_out(), batch, net->loss_hist.p + st);
-      net->adam(net->grad.p, *opt);
+      net->backward(net->tb.p, net->d_out(), batch, net->loss_hist.p, step);
+      net->adam_dev(net->grad.p, *opt);
+      k_step_advance<<<1, 1, 0, q>>>(step, net->adam_pw.p, (double)opt->beta1, (double)opt->beta2);
+      CCG_CUDA(cudaGetLastError());
+    };
+    // the first step runs directly (it also fills every host-side cache the
+    // launches use); the others replay one captured step (about 30 launches).
+    // The legacy default stream cannot be captured: the step is then recorded
+    // on a private stream, and the graph still runs on the network's stream.
+    one_step();
+    if (steps > 1) {
+      cudaStream_t cap = s, own = nullptr;
+      if (s == nullptr || s == cudaStreamLegacy) {
+        CCG_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        cap = own;
+      }
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        net->stream = cap;
+        try {
+          one_step();
+        } catch (...) {
+          net->stream = s;
+          cudaStreamEndCapture(cap, &g);
+          if (g) cudaGraphDestroy(g);
+          if (own) cudaStreamDestroy(own);
+          throw;
+        }
+        net->stream = s;
+        ce = cudaStreamEndCapture(cap, &g);
+      }
+      if (ce == cudaSuccess) {
+        ce = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+      }
+      for (int st = 1; st < steps && ce == cudaSuccess; ++st) ce = cudaGraphLaunch(exec, s);
+      if (exec) cudaGraphExecDestroy(exec);
+      if (own) cudaStreamDestroy(own);
+      CCG_CUDA(ce);
     }
+    net->adam_t += steps;
     if (losses) CCG_CUDA(cudaMemcpyAsync(losses, net->loss_hist.p, steps * sizeof(double), cudaMemcpyDeviceToHost, s));
     net->check_err();
   })

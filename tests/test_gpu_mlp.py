@@ -213,6 +213,26 @@ def test_training_losses_follow_the_oracle():
         p, m, v = mlp.adam_step(p, go, m, v, t + 1, lr)
 
 
+@pytest.mark.parametrize("dims", [DIMS[0], DIMS[1]], ids=["full", "small"])
+def test_training_steps_replayed_from_one_graph_equal_single_steps(dims):
+    """cc_mlp_train runs its first step directly and replays the others from
+    one captured step (minibatch, loss slot and Adam step number read from a
+    device step counter): a 7-step call gives the same bits, parameters and
+    losses, as seven one-step calls."""
+    n, B, steps = 3000, 512, 7
+    X, _ = _bf16(n, dims[0], 41, (dims[0] + 7) // 8 * 8)
+    Tn = (0.3 * meshgen.normal(43, np.arange(n * dims[-1]))).reshape(n, dims[-1]).astype(np.float32)
+    T = torch.from_numpy(Tn).cuda()
+    idx = torch.from_numpy(meshgen.batch_indices(47, 0, steps, B, n)).cuda()
+    a, _ = _net(dims, B, 45)
+    b, _ = _net(dims, B, 45)
+    la = a.train(X, T, idx, B, lr=1e-3)
+    lb = np.concatenate([b.train(X, T, idx[t:t + 1].contiguous(), B, lr=1e-3) for t in range(steps)])
+    assert np.array_equal(la, lb)
+    assert np.array_equal(a.get_params(), b.get_params())
+    assert la[-1] < la[0]
+
+
 def test_training_reduces_the_loss():
     dims = [30, 64, 64, 24]
     n, B = 4096, 512
