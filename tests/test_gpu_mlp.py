@@ -333,6 +333,37 @@ def test_learned_bases_residuals_and_fallback_match_oracle():
                                        atol=1e-10 * max(1.0, np.abs(out[i]).max()))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_learned_bases_solve_follows_the_oracle_sweep_by_sweep(precision):
+    """Coloured CC with learned bases (the network's output assembled per
+    vertex, Eq. 5 fallback to patch solves) against the oracle's solve with
+    its own assembly of the same network output: the residual after every
+    sweep and the final energy.  float64: 1e-8; mixed: 1e-4 of the start."""
+    sc = meshgen.stretch_box(5, 4, 4, E=1e5, nu=0.3, factor=1.2, jitter_amount=0.05, seed=8)
+    net, b = _constant_net()
+    m = cc.Mesh.from_scene(sc)
+    m.color()
+    m.build_learned_subspace(net, tau=1.0)
+    pb = fem.problem_from_scene(sc)
+    topo = topology.Topology(pb.n, pb.tets, pb.free)
+    rows = np.flatnonzero(pb.free)
+    sup, lb = learned.assemble(pb, topo, np.tile(b, (len(rows), 1)))
+    bases, _, _ = learned.with_fallback(pb, sup, lb, tau=1.0)
+    iters = 25
+    _, h_o = solvers.solve(pb, topo, sup, bases, sc.x0, kind="cc", tol=0.0, max_iters=iters)
+    r = m.solve_step(cc.to_soa(sc.x0), precision=precision, tol=0.0, max_iters=iters, check_every=1,
+                     history=True)
+    hist = np.asarray(r.residuals[:iters + 1])
+    go = np.asarray(h_o.grad_norm)
+    assert len(hist) == len(go) and h_o.rel[-1] < 1e-2
+    if precision == "fp64":
+        np.testing.assert_allclose(hist, go, rtol=1e-8)
+        assert r.energy == pytest.approx(h_o.energy[-1], rel=1e-10)
+    else:
+        assert np.abs(hist - go).max() <= 1e-4 * go[0]
+        assert r.energy == pytest.approx(h_o.energy[-1], rel=1e-6)
+
+
 def test_learned_subspace_rejects_dynamic_meshes_and_wrong_networks():
     sc = meshgen.cantilever(2, 2, 4, cell=0.25, E=1e5, nu=0.3, h=0.01)
     m = cc.Mesh.from_scene(sc)
