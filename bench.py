@@ -482,9 +482,10 @@ def local_solve_flops(mesh):
 
 def gather_bytes_per_refresh(scene):
     """Algorithmic bytes of one row-gather launch (all free rows): per row the
-    stored blocks it sums (one 36-byte block per incident tet and corner with
-    a vertex id >= the row's), its 24-byte float-float gradient entries, its
-    upper blocks written and its gradient written."""
+    stored blocks it sums (per incident tet its 24-byte diagonal block and a
+    36-byte block per other corner with a vertex id above the row's), its
+    24-byte float-float gradient entries, its upper blocks written and its
+    gradient written."""
     tets = np.asarray(scene.tets, dtype=np.int64)
     free = scene.pinned == 0
     n = scene.n
@@ -502,11 +503,12 @@ def gather_bytes_per_refresh(scene):
         if l > j:
             nup[j] += 1
     nup += 1
-    per = src * 36 + val * 24 + nup * 36 + 24
+    per = (src - val) * 36 + val * 24 + val * 24 + nup * 36 + 24
     return float(per[free].sum())
 
 
-TET_BYTES = 16 + 16 + 72 + 12 + 4 * 32 + 4 * 24 + 360   # ids, slots, D_m^-1, V w, positions; gradient + 10 blocks
+# ids, slots, D_m^-1, V w, positions; gradient + 10 blocks (4 diagonal ones as 6 values, 6 others as 9)
+TET_BYTES = 16 + 16 + 72 + 12 + 4 * 32 + 4 * 24 + 4 * (4 * 6 + 6 * 9)
 
 
 def run_batch(args, stream, dev):
@@ -714,7 +716,7 @@ def run_large(args, stream, dev):
     owner = np.repeat(np.arange(sc.n), np.diff(nbp))
     nup = np.bincount(owner[nbi > owner], minlength=sc.n) + 1
     free = sc.pinned == 0
-    gather_bytes = float((src * 36 + val * 24 + nup * 36 + 24)[free].sum())
+    gather_bytes = float(((src - val) * 36 + val * 24 + val * 24 + nup * 36 + 24)[free].sum())
     free_corners = int((sc.pinned[sc.tets] == 0).sum())
     active_tets = int((sc.pinned[sc.tets] == 0).any(axis=1).sum())
     tet_refreshes = r.iterations * free_corners + active_tets
