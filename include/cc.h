@@ -550,7 +550,11 @@ cc_status cc_mlp_adam_step(cc_mlp* net, const float* grad, const cc_adam* opt);
  * batch) (device int32, each < n_samples) of X (device BF16 [n_samples x
  * ldx]) and T (device float32 [n_samples x ldt]), runs forward, backward
  * and one Adam step.  losses (host [steps], or NULL) receives every step's
- * loss.  batch <= max_batch. */
+ * loss.  batch <= max_batch.  The first step runs directly; the others
+ * replay one CUDA graph of a step on the network's stream (recorded on a
+ * private stream when that is the legacy default stream), the step number,
+ * minibatch offset and Adam's beta^t kept on the device: the results equal
+ * those of `steps` calls of one step each, bit for bit. */
 cc_status cc_mlp_train(cc_mlp* net, const void* X, int64_t ldx, const float* T, int64_t ldt,
                        int64_t n_samples, const int32_t* idx, int32_t steps, int32_t batch,
                        const cc_adam* opt, double* losses);
