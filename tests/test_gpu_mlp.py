@@ -157,6 +157,16 @@ def test_fused_inference_equals_per_layer_bit_for_bit(dims, rows, kind):
     assert torch.equal(Yf, Yl)
 
 
+def test_inference_kernel_choice_is_checked():
+    net, _ = _net(DIMS[0], 64, 1)
+    for bad in (-1, 3):
+        with pytest.raises(cc.CCError) as e:
+            net.set_fused(bad)
+        assert e.value.status == cc.ERR_INVALID_ARG
+    net.set_fused(2)
+    net.set_fused(0)
+
+
 def test_fused_inference_writes_a_strided_output_and_nothing_else():
     """Y with a leading dimension wider than the output: the padding columns
     stay untouched, the rows match the dense result bit for bit."""
