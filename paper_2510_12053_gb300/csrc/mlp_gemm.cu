@@ -112,22 +112,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Accumulator fragment for stores along rows: 16 tensor-memory lanes x 16
-// columns.  Thread t holds lanes t/4 (v[0..1], v[4..5]) and t/4 + 8 (v[2..3],
-// v[6..7]) at columns 2 (t % 4) + {0, 1} (v[0..3]) and 8 + 2 (t % 4) + {0, 1}
-// (v[4..7]), so four consecutive threads hold 32 contiguous bytes of a row.
-__device__ __forceinline__ void tmem_ld_rows16(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-// Both 16-lane halves of a warp's 32 lanes, 16 columns: v[0..7] lanes 0..15,
-// v[8..15] lanes 16..31 (tmem_ld_rows16 layout each), one wait for both.
+// Accumulator fragment for stores along rows, 32 lanes x 16 columns by two
+// 16x256b.x2 loads: in each 16-lane half, thread t holds lanes t/4 (v[0..1],
+// v[4..5]) and t/4 + 8 (v[2..3], v[6..7]) at columns 2 (t % 4) + {0, 1}
+// (v[0..3]) and 8 + 2 (t % 4) + {0, 1} (v[4..7]), so four consecutive
+// threads hold 32 contiguous bytes of a row; v[0..7] lanes 0..15, v[8..15]
+// lanes 16..31; one wait for both loads.
 __device__ __forceinline__ void tmem_ld_rows32(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
