@@ -1421,6 +1421,8 @@ def run_ours(args, rank, world):
         ach_b = sweep_bytes / (ms_sweep_b / 1e3) / 1e9
         fl_b = flops_per_sweep / (ms_sweep_b / 1e3) / 1e12
         roofline = dict(roofline, achieved=ach_b, frac=ach_b / hbm, ms_per_sweep=ms_sweep_b,
+                        traffic_note="ncu DRAM bytes of the single-mesh launches per sweep; a batch launch "
+                                     "processes the four meshes' units, so per mesh-sweep the same bytes",
                         units="one coloured sweep of one mesh (every free vertex updated once); the batch's "
                               f"{nm} meshes sweep together, one launch per kernel per colour",
                         fp32_alu=dict(roofline["fp32_alu"], achieved_tflops=fl_b, frac=fl_b / FP32_PEAK_TFLOPS))
