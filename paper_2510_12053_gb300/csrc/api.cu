@@ -1038,10 +1038,19 @@ cc_status cc_autotune(cc_mesh* m, const double* x, const double* xt, cc_precisio
         ensure_state(*m, p);
       }
       const int ct[4] = {32, 64, 128, 256}, gw[3] = {2, 4, 8};
+      const int ct0 = m->tune_couple_threads;
       for (int k = 0; k < 4; ++k) {
         m->tune_couple_threads = ct[k];
-        out->couple_ms[k] = time_sweeps();
+        try {
+          out->couple_ms[k] = time_sweeps();
+        } catch (const Fail& f) {
+          // a shape whose shared memory this support does not fit is skipped
+          if (f.st != CC_ERR_INVALID_ARG) throw;
+          CCG_CUDA(cudaStreamSynchronize(s));
+          out->couple_ms[k] = 1e30;
+        }
       }
+      m->tune_couple_threads = ct0;
       int best = 0;
       for (int k = 1; k < 4; ++k)
         if (out->couple_ms[k] < out->couple_ms[best]) best = k;

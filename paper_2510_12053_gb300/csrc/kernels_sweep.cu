@@ -60,10 +60,13 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
 }
 
 
+// The coupling CTA's shared memory: U_i (padded rows), the support rows'
+// starts, lengths, ids and slot-map offsets, the slot map, and the 18
+// reduction partials of every thread (stride threads + 1).
 template <typename HT>
-__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nwarps) {
+__host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nthreads) {
   return align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
-         align16((size_t)smap_max * code_bytes) + (size_t)nwarps * 32 * sizeof(HT);
+         align16((size_t)smap_max * code_bytes) + (size_t)18 * (nthreads + 1) * sizeof(HT);
 }
 
 template <typename SlotT>
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   ptr += align16((size_t)(sup_max + 1) * 4);
   SlotT* codes = reinterpret_cast<SlotT*>(ptr);
   ptr += align16((size_t)smap_max * sizeof(SlotT));
-  HT* red = reinterpret_cast<HT*>(ptr);  // [warps][32]
+  HT* red = reinterpret_cast<HT*>(ptr);  // [18][kThreads + 1]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = verts[blockIdx.x];
@@ -464,21 +467,26 @@ __global__ void __launch_bounds__(kThreads) k_couple(
     }
   }
 
-  // CTA reduction of 18 values in a fixed order
-  HT vals[18] = {h00, h01, h02, h11, h12, h22, A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], A[8],
-                 b[0], b[1], b[2]};
+  // CTA reduction of 18 values in a fixed order: every thread stores its
+  // partials, thread v sums value v over the CTA's threads in four
+  // interleaved chains (the padded stride puts the 18 readers in distinct
+  // banks)
+  const HT vals[18] = {h00, h01, h02, h11, h12, h22, A[0], A[1], A[2], A[3], A[4], A[5], A[6], A[7], A[8],
+                       b[0], b[1], b[2]};
 #pragma unroll
-  for (int v = 0; v < 18; ++v) vals[v] = warp_sum(vals[v]);
-  if (lane == 0)
-#pragma unroll
-    for (int v = 0; v < 18; ++v) red[warp * 32 + v] = vals[v];
+  for (int v = 0; v < 18; ++v) red[v * (kThreads + 1) + tid] = vals[v];
   __syncthreads();
   if (tid < 18) {
-    // fixed-order sum of the warps' partials
-    HT tot = red[tid];
-#pragma unroll
-    for (int w = 1; w < kThreads / 32; ++w) tot += red[32 * w + tid];
-    cpl[(int64_t)blockIdx.x * 32 + tid] = tot;
+    const HT* src = red + tid * (kThreads + 1);
+    HT t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#pragma unroll 4
+    for (int t = 0; t < kThreads; t += 4) {
+      t0 += src[t];
+      t1 += src[t + 1];
+      t2 += src[t + 2];
+      t3 += src[t + 3];
+    }
+    cpl[(int64_t)blockIdx.x * 32 + tid] = (t0 + t1) + (t2 + t3);
   }
   if constexpr (kFuse) condense_group_tail<double, HT, kMixed, kUpd>(ca, 1e-12);
 }
@@ -626,7 +634,7 @@ void launch_couple(Mesh& m, const int32_t* verts, int64_t count, const HT* U, co
   const int lanes = m.tune_couple_row_lanes;
   CCG_CHECK(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8, CC_ERR_STATE, "bad coupling row lanes");
   const int lanes_log2 = lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : 3;
-  const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads / 32);
+  const size_t smem = cta_smem_bytes<HT>(supm, smx, m.smap_wide ? 2 : 1, kThreads);
   CCG_CHECK(smem <= 220 * 1024, CC_ERR_INVALID_ARG, "support too large for the coupling kernel");
   auto go = [&](auto kern, const auto* smap) {
     set_smem_limit(reinterpret_cast<const void*>(kern), smem);

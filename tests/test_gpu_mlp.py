@@ -367,7 +367,9 @@ def test_learned_bases_solve_follows_the_oracle_sweep_by_sweep(precision):
     go = np.asarray(h_o.grad_norm)
     assert len(hist) == len(go) and h_o.rel[-1] < 1e-2
     if precision == "fp64":
-        np.testing.assert_allclose(hist, go, rtol=1e-8)
+        # residuals fall seven orders of magnitude: compare to 1e-8 each, or to
+        # 1e-10 of the start (the scale of the termination test, Sec. 4.1)
+        np.testing.assert_allclose(hist, go, rtol=1e-8, atol=1e-10 * go[0])
         assert r.energy == pytest.approx(h_o.energy[-1], rel=1e-10)
     else:
         assert np.abs(hist - go).max() <= 1e-4 * go[0]
