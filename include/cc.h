@@ -386,6 +386,33 @@ typedef struct {
 cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_step_opts* opts,
                          cc_batch_stats* stats);
 
+/* Solves several independent meshes at once (no counterpart in the paper):
+ * mesh k runs cc_solve_step(meshes[k], x_dev[k], v_dev[k], &opts[k],
+ * &stats[k]) on its own stream (the one given to cc_build_mesh /
+ * cc_build_batch), one host thread per mesh (the calling thread takes mesh
+ * 0), so that the colours' short kernels of different meshes overlap on the
+ * GPU instead of queueing behind one another.  Results are those of the
+ * separate cc_solve_step calls, bit for bit.
+ *   count    number of meshes (0: nothing to do)
+ *   meshes   host [count], distinct meshes with distinct streams that are
+ *            neither NULL nor the legacy / per-thread default stream
+ *   x_dev    host [count] of device [3][n_k] float64, disjoint
+ *   v_dev    host [count] of device [3][n_k] (entries NULL for quasistatic
+ *            meshes); the array itself may be NULL when every mesh is
+ *            quasistatic
+ *   opts     host [count]; residual_history pointers, where given, distinct
+ *   stats    host [count] out (may be NULL)
+ *   status   host [count] out (may be NULL): each mesh's cc_solve_step status
+ * Every mesh runs to its own end even when another fails.  Returns CC_OK when
+ * every mesh converged, else the first error other than
+ * CC_ERR_NOT_CONVERGED in mesh order, else CC_ERR_NOT_CONVERGED;
+ * cc_last_error names the mesh.  CC_ERR_INVALID_ARG (nothing runs) for a
+ * NULL argument, a repeated mesh, stream or history, or a default stream.
+ * The worker threads use the calling thread's current CUDA device. */
+cc_status cc_solve_concurrent(int32_t count, cc_mesh* const* meshes, double* const* x_dev,
+                              double* const* v_dev, const cc_step_opts* opts, cc_step_stats* stats,
+                              cc_status* status);
+
 /* Launch-configuration autotuner (no counterpart in the paper).  Times
  * `sweeps` coloured CC sweeps from x_dev for each candidate configuration,
  * one parameter at a time in this order: the sweep variant

@@ -142,6 +142,8 @@ _SIGS = {
                                       ctypes.POINTER(_P)]),
     "cc_batch_offsets": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "cc_solve_batch": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(StepOpts), ctypes.POINTER(BatchStats)]),
+    "cc_solve_concurrent": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.POINTER(StepOpts),
+                                           ctypes.POINTER(StepStats), _P]),
     "cc_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
     "cc_gemm_bf16_tn": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -455,6 +457,39 @@ class Mesh:
         return SolveResult(st.iterations, bool(st.converged), st.g0, st.g_final, st.energy_final,
                            st.sweeps.updates, st.sweeps.fallback_empty, st.sweeps.fallback_reduced,
                            st.sweeps.fallback_schur, hist)
+
+
+def solve_concurrent(meshes, xs, vs=None, *, update: str = "cc", schedule: str = "colored",
+                     precision: str = "mixed", tol: float = 1e-6, max_iters: int = 200, min_iters: int = 0,
+                     check_every: int = 1, use_graph: bool = False, history: bool = False,
+                     corotated: bool = False, line_search: bool = False, restart_every: int = 0):
+    """Mesh.solve_step on several meshes at once (cc_solve_concurrent): each mesh on
+    its own stream and host thread, every mesh with the same options.  Returns one
+    SolveResult per mesh (``converged`` False where max_iters came first); raises
+    CCError for any other failure, with ``statuses`` (per mesh) attached."""
+    count = len(meshes)
+    if len(xs) != count or (vs is not None and len(vs) != count):
+        raise CCError(ERR_INVALID_ARG, "one x (and v) per mesh")
+    hists = [np.full(max_iters + 1, -1.0) if history else None for _ in range(count)]
+    opts = (StepOpts * count)()
+    for k in range(count):
+        opts[k] = StepOpts(UPDATE[update], SCHED[schedule], PREC[precision], tol, max_iters, min_iters,
+                           check_every, int(use_graph),
+                           hists[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None,
+                           int(corotated), int(restart_every), int(line_search))
+    hs = (_P * count)(*[m._h for m in meshes])
+    xp = (_P * count)(*[_dev3n(x, m.n, "x") for m, x in zip(meshes, xs)])
+    vp = None if vs is None else (_P * count)(*[_dev3n(v, m.n, "v") for m, v in zip(meshes, vs)])
+    st = (StepStats * count)()
+    rcs = (ctypes.c_int * count)()
+    rc = lib().cc_solve_concurrent(count, hs, xp, vp, opts, st, rcs)
+    if rc not in (OK, ERR_NOT_CONVERGED):
+        err = CCError(rc, lib().cc_last_error().decode())
+        err.statuses = list(rcs)
+        raise err
+    return [SolveResult(s_.iterations, bool(s_.converged), s_.g0, s_.g_final, s_.energy_final, s_.sweeps.updates,
+                        s_.sweeps.fallback_empty, s_.sweeps.fallback_reduced, s_.sweeps.fallback_schur, h)
+            for s_, h in zip(st, hists)]
 
 
 def gemm_bf16_tn(A, B, out=None, stream=None, n_tile: int = 0, k_splits: int = 0, one_tile_per_cta: bool = False):

@@ -58,7 +58,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
     lib64 = os.path.join(_cuda_home(nvcc), "lib64")
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-        "-Xlinker", "-rpath", "-Xlinker", lib64]
+        "-Xlinker", "-rpath", "-Xlinker", lib64, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -8,6 +8,9 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <system_error>
+#include <thread>
+#include <vector>
 
 #include "cc_internal.cuh"
 #include "mlp.cuh"
@@ -975,6 +978,81 @@ cc_status cc_solve_batch(cc_mesh* m, double* x, double* v, const cc_step_opts* o
     return f.st;
   } catch (...) {
     ccg::g_last_error = "cc_solve_batch: unexpected error";
+    return CC_ERR_STATE;
+  }
+}
+
+cc_status cc_solve_concurrent(int32_t count, cc_mesh* const* meshes, double* const* x, double* const* v,
+                              const cc_step_opts* o, cc_step_stats* st, cc_status* status) {
+  try {
+    ccg::g_last_error.clear();
+    CCG_CHECK(count >= 0, CC_ERR_INVALID_ARG, "negative count");
+    if (count == 0) return CC_OK;
+    CCG_CHECK(meshes && x && o, CC_ERR_INVALID_ARG, "NULL argument");
+    for (int32_t k = 0; k < count; ++k) {
+      CCG_CHECK(meshes[k] && x[k], CC_ERR_INVALID_ARG, "NULL mesh or x");
+      const cudaStream_t s = meshes[k]->stream;
+      CCG_CHECK(s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread, CC_ERR_INVALID_ARG,
+                "every mesh needs a stream of its own (not a default stream)");
+      for (int32_t j = 0; j < k; ++j) {
+        CCG_CHECK(meshes[j] != meshes[k], CC_ERR_INVALID_ARG, "a mesh appears twice");
+        CCG_CHECK(meshes[j]->stream != s, CC_ERR_INVALID_ARG, "two meshes share a stream");
+        CCG_CHECK(x[j] != x[k], CC_ERR_INVALID_ARG, "two meshes share x");
+        CCG_CHECK(!o[k].residual_history || o[j].residual_history != o[k].residual_history, CC_ERR_INVALID_ARG,
+                  "two meshes share a residual history");
+      }
+    }
+    int dev = 0;
+    CCG_CUDA(cudaGetDevice(&dev));
+    std::vector<cc_status> rc(count, CC_OK);
+    std::vector<std::string> msg(count);
+    auto work = [&](int32_t k) {
+      const cudaError_t e = cudaSetDevice(dev);
+      if (e != cudaSuccess) {
+        rc[k] = CC_ERR_CUDA;
+        msg[k] = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        return;
+      }
+      rc[k] = cc_solve_step(meshes[k], x[k], v ? v[k] : nullptr, &o[k], st ? &st[k] : nullptr);
+      msg[k] = ccg::g_last_error;
+    };
+    // One thread per further mesh; a mesh whose thread could not be started
+    // runs on the calling thread after mesh 0 (same result, less overlap).
+    std::vector<std::thread> pool;
+    std::vector<int32_t> here{0};
+    pool.reserve(count - 1);
+    for (int32_t k = 1; k < count; ++k) {
+      try {
+        pool.emplace_back(work, k);
+      } catch (const std::system_error&) {
+        here.push_back(k);
+      }
+    }
+    for (int32_t k : here) work(k);
+    for (auto& t : pool) t.join();
+    cc_status out = CC_OK;
+    int32_t who = -1;
+    for (int32_t k = 0; k < count; ++k) {
+      if (status) status[k] = rc[k];
+      if (rc[k] != CC_OK && rc[k] != CC_ERR_NOT_CONVERGED && (out == CC_OK || out == CC_ERR_NOT_CONVERGED)) {
+        out = rc[k];
+        who = k;
+      } else if (rc[k] == CC_ERR_NOT_CONVERGED && out == CC_OK) {
+        out = rc[k];
+        who = k;
+      }
+    }
+    ccg::g_last_error.clear();
+    if (who >= 0) ccg::g_last_error = "cc_solve_concurrent: mesh " + std::to_string(who) + ": " + msg[who];
+    return out;
+  } catch (const ccg::Fail& f) {
+    if (ccg::g_last_error.empty()) ccg::g_last_error = "cc_solve_concurrent";
+    return f.st;
+  } catch (const std::bad_alloc&) {
+    ccg::g_last_error = "cc_solve_concurrent: host out of memory";
+    return CC_ERR_OOM;
+  } catch (...) {
+    ccg::g_last_error = "cc_solve_concurrent: unexpected error";
     return CC_ERR_STATE;
   }
 }

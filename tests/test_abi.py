@@ -50,3 +50,16 @@ def test_binding_signatures_cover_the_header(libpath):
 def test_version_string(libpath):
     import paper_2510_12053_gb300 as cc
     assert "sm_103a" in cc.version()
+
+
+def test_concurrent_solve_checks_its_arguments_before_any_cuda_call(libpath):
+    import paper_2510_12053_gb300 as cc
+    lib = cc.lib()
+    opts = (cc.StepOpts * 2)()
+    assert lib.cc_solve_concurrent(0, None, None, None, None, None, None) == cc.OK
+    assert lib.cc_solve_concurrent(-1, None, None, None, opts, None, None) == cc.ERR_INVALID_ARG
+    assert "negative" in lib.cc_last_error().decode()
+    assert lib.cc_solve_concurrent(2, None, None, None, opts, None, None) == cc.ERR_INVALID_ARG
+    null2 = (ctypes.c_void_p * 2)()
+    assert lib.cc_solve_concurrent(2, null2, null2, None, opts, None, None) == cc.ERR_INVALID_ARG
+    assert "NULL mesh" in lib.cc_last_error().decode()
