@@ -92,6 +92,10 @@ struct DBuf {
 // triangles (6 values: (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)), the six others
 // all 9 values row-major: 78 values, kTetStore per tet.
 constexpr int kTetStore = 80;
+// Codes allocated past the end of a slot map (zeroed): the coupling kernel
+// copies a vertex's map in 4-byte words from the word holding its first code,
+// which reads up to 3 codes past the map's end.
+constexpr int kSlotMapSlack = 8;
 constexpr bool tet_pair_is_diag(int pair) { return pair == 0 || pair == 4 || pair == 7 || pair == 9; }
 // first value of a pair's block in the tet's record
 constexpr int tet_pair_offset(int pair) {

@@ -336,14 +336,16 @@ void build_slot_maps(Mesh& m) {
   const int64_t total = std::max<int64_t>(ptr[n], 1);
   const unsigned grid = (unsigned)((m.n_free * 32 + 255) / 256);
   if (m.smap_wide) {
-    m.d_smap16.alloc(total);
+    m.d_smap16.alloc(total + kSlotMapSlack);
     m.d_smap8.release();
+    CCG_CUDA(cudaMemsetAsync(m.d_smap16.p + total, 0, kSlotMapSlack * sizeof(uint16_t), s));
     if (m.n_free > 0)
       k_slot_maps<uint16_t><<<grid, 256, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_sup_ptr.p, m.d_sup_idx.p,
                                                  m.d_up_ptr.p, m.d_up_col.p, m.d_smap_ptr.p, m.d_smap16.p);
   } else {
-    m.d_smap8.alloc(total);
+    m.d_smap8.alloc(total + kSlotMapSlack);
     m.d_smap16.release();
+    CCG_CUDA(cudaMemsetAsync(m.d_smap8.p + total, 0, kSlotMapSlack, s));
     if (m.n_free > 0)
       k_slot_maps<uint8_t><<<grid, 256, 0, s>>>(m.d_free_rows.p, m.n_free, m.d_sup_ptr.p, m.d_sup_idx.p,
                                                 m.d_up_ptr.p, m.d_up_col.p, m.d_smap_ptr.p, m.d_smap8.p);

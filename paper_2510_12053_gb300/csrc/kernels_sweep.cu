@@ -66,7 +66,7 @@ __device__ __forceinline__ void load_block<double>(const double* __restrict__ bs
 template <typename HT>
 __host__ __device__ inline size_t cta_smem_bytes(int sup_max, int64_t smap_max, int code_bytes, int nthreads) {
   return align16((size_t)sup_max * 12 * sizeof(HT)) + 4 * align16((size_t)(sup_max + 1) * 4) +
-         align16((size_t)smap_max * code_bytes) + (size_t)18 * (nthreads + 1) * sizeof(HT);
+         align16((size_t)(smap_max + kSlotMapSlack) * code_bytes) + (size_t)18 * (nthreads + 1) * sizeof(HT);
 }
 
 template <typename SlotT>
@@ -89,12 +89,21 @@ template <typename HT, int kSlot = 9, int kRow = 3>
 __device__ __forceinline__ void stage_basis(HT* Us, const HT* __restrict__ U, const HT* __restrict__ rot,
                                             const int32_t* __restrict__ sup_idx, int s0, int m, int t, int nt) {
   if (!rot) {
-    if (kSlot == 9) {
+    if constexpr (kSlot == 9) {
       for (int k = t; k < 9 * m; k += nt) Us[k] = U[(int64_t)s0 * 9 + k];
     } else {
-      for (int k = t; k < kSlot * m; k += nt) {
-        const int a = k / kSlot, e = k - a * kSlot, r = e / kRow, d = e - r * kRow;
-        Us[k] = d < 3 ? U[(int64_t)(s0 + a) * 9 + 3 * r + d] : HT(0);
+      static_assert(kSlot == 12 && kRow == 4, "padded slots are three rows of four");
+      // row q of the copy (slot q / 3, row q % 3) is the three values at 3 q
+      // past the support's first block, stored as one padded row at 4 q
+      const HT* src = U + (int64_t)s0 * 9;
+      for (int q = t; q < 3 * m; q += nt) {
+        const HT u0 = __ldg(src + 3 * q), u1 = __ldg(src + 3 * q + 1), u2 = __ldg(src + 3 * q + 2);
+        if constexpr (sizeof(HT) == 4) {
+          reinterpret_cast<float4*>(Us)[q] = make_float4(u0, u1, u2, 0.f);
+        } else {
+          reinterpret_cast<double2*>(Us)[2 * q] = make_double2(u0, u1);
+          reinterpret_cast<double2*>(Us)[2 * q + 1] = make_double2(u2, 0.0);
+        }
       }
     }
     return;
@@ -365,8 +374,8 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   ptr += align16((size_t)(sup_max + 1) * 4);
   int* roff = reinterpret_cast<int*>(ptr);
   ptr += align16((size_t)(sup_max + 1) * 4);
-  SlotT* codes = reinterpret_cast<SlotT*>(ptr);
-  ptr += align16((size_t)smap_max * sizeof(SlotT));
+  SlotT* code_words = reinterpret_cast<SlotT*>(ptr);
+  ptr += align16((size_t)(smap_max + kSlotMapSlack) * sizeof(SlotT));
   HT* red = reinterpret_cast<HT*>(ptr);  // [18][kThreads + 1]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -377,7 +386,18 @@ __global__ void __launch_bounds__(kThreads) k_couple(
   const int ncodes = (int)(smap_ptr[i + 1] - c0);
 
   stage_basis<HT, 12, 4>(Us, U, rot, sup_idx, s0, m, tid, kThreads);
-  for (int k = tid; k < ncodes; k += kThreads) codes[k] = smap[c0 + k];
+  // the slot map in 4-byte words from the word holding its first code (the
+  // map is allocated with slack past its end); its codes start sh in
+  constexpr int kPerWord = 4 / (int)sizeof(SlotT);
+  const int64_t w0 = c0 / kPerWord;
+  const int sh = (int)(c0 - w0 * kPerWord);
+  const int nwords = (sh + ncodes + kPerWord - 1) / kPerWord;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(smap) + w0;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(code_words);
+    for (int k = tid; k < nwords; k += kThreads) dst[k] = __ldg(src + k);
+  }
+  const SlotT* codes = code_words + sh;
   for (int s = tid; s <= m; s += kThreads) {
     const int j = s < m ? sup_idx[s0 + s] : i;
     const int a = up_ptr[j];
