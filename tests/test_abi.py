@@ -63,3 +63,10 @@ def test_concurrent_solve_checks_its_arguments_before_any_cuda_call(libpath):
     null2 = (ctypes.c_void_p * 2)()
     assert lib.cc_solve_concurrent(2, null2, null2, None, opts, None, None) == cc.ERR_INVALID_ARG
     assert "NULL mesh" in lib.cc_last_error().decode()
+
+
+def test_concurrent_solve_binding_checks_one_x_per_mesh():
+    import paper_2510_12053_gb300 as cc
+    with pytest.raises(cc.CCError) as ei:
+        cc.solve_concurrent([object(), object()], [None])
+    assert ei.value.status == cc.ERR_INVALID_ARG
