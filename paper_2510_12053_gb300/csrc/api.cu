@@ -1010,22 +1010,37 @@ cc_status cc_solve_concurrent(int32_t count, cc_mesh* const* meshes, double* con
       const cudaError_t e = cudaSetDevice(dev);
       if (e != cudaSuccess) {
         rc[k] = CC_ERR_CUDA;
-        msg[k] = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        try {
+          msg[k] = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        } catch (...) {
+        }
         return;
       }
       rc[k] = cc_solve_step(meshes[k], x[k], v ? v[k] : nullptr, &o[k], st ? &st[k] : nullptr);
-      msg[k] = ccg::g_last_error;
+      try {
+        msg[k] = ccg::g_last_error;
+      } catch (...) {  // keep the status; lose only the message
+      }
     };
     // One thread per further mesh; a mesh whose thread could not be started
     // runs on the calling thread after mesh 0 (same result, less overlap).
     std::vector<std::thread> pool;
-    std::vector<int32_t> here{0};
+    std::vector<int32_t> here;
     pool.reserve(count - 1);
+    here.reserve(count);
+    here.push_back(0);
+    struct JoinAll {  // started threads are joined on every way out of this scope
+      std::vector<std::thread>& threads;
+      ~JoinAll() {
+        for (auto& t : threads)
+          if (t.joinable()) t.join();
+      }
+    } join_all{pool};
     for (int32_t k = 1; k < count; ++k) {
       try {
         pool.emplace_back(work, k);
       } catch (const std::system_error&) {
-        here.push_back(k);
+        here.push_back(k);  // capacity reserved: cannot throw
       }
     }
     for (int32_t k : here) work(k);
