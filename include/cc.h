@@ -408,7 +408,10 @@ cc_status cc_solve_batch(cc_mesh* mesh, double* x_dev, double* v_dev, const cc_s
  * CC_ERR_NOT_CONVERGED in mesh order, else CC_ERR_NOT_CONVERGED;
  * cc_last_error names the mesh.  CC_ERR_INVALID_ARG (nothing runs) for a
  * NULL argument, a repeated mesh, stream or history, or a default stream.
- * The worker threads use the calling thread's current CUDA device. */
+ * The worker threads use the calling thread's current CUDA device; a mesh
+ * whose thread cannot be started runs on the calling thread after mesh 0
+ * (same results, less overlap), and every started thread has been joined
+ * when the call returns. */
 cc_status cc_solve_concurrent(int32_t count, cc_mesh* const* meshes, double* const* x_dev,
                               double* const* v_dev, const cc_step_opts* opts, cc_step_stats* stats,
                               cc_status* status);
