@@ -135,7 +135,7 @@ typedef struct {
                           d = x_sweep - x becomes a direction, x <- x + a d with the largest
                           a in {1, 1/2, ..., 2^-29} for which E(x + a d) <= E(x) (float64
                           energy), a = 0 if none.  Host-synchronous, no graph replay;
-                          cc_solve_step only (cc_solve_batch rejects it). */
+                          cc_solve_batch takes one such step per mesh on its own energy. */
 } cc_step_opts;
 
 typedef struct {
